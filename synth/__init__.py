@@ -1,0 +1,18 @@
+"""Seeded synthetic inputs for 2-D multi-reference alignment in a steerable basis.
+
+This module only draws data from the observation model of Eq. (MRA_Model_FB):
+v_i = a o exp(-i k theta_i) + eps_i with complex Gaussian noise.  It holds none
+of the estimation arithmetic (synchronization, EM, prior learning); both the
+CUDA path and the CPU oracle consume what it produces.
+"""
+from .instances import (  # noqa: F401
+    CONFIGS,
+    Instance,
+    config,
+    make_instance,
+    make_signal,
+    random_init,
+    sigma2_for_snr,
+    to_c64,
+    c64_round,
+)

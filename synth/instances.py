@@ -1,0 +1,102 @@
+"""Synthetic MRA instances in coefficient space.
+
+Recipe (one instance):
+
+* signal ``x[k, q]`` for ``k = 0..K`` (angular index, only k >= 0 is stored
+  because a real image satisfies a_{-k,q} = conj(a_{k,q}), Sec. 1) and
+  ``q = 0..Q-1`` (radial index).  ``x[k, q] ~ CN(0, exp(-k^2 / decay))``,
+  ``x[0, q]`` real, then scaled so that ``||x||_2 = 1`` over the stored entries.
+* shifts ``s_i`` uniform on the grid ``{0, .., L-1}`` (rotation 2 pi s_i / L);
+  the paper draws its rotations from such a grid too (Sec. 2.2, E. coli test).
+* noise: i.i.d. circular complex Gaussian with E|eps|^2 = sigma^2 on every
+  stored entry (Eq. MRA_Model_FB), sigma^2 = 1 / (SNR * M) with M = (K+1) Q, the
+  coefficient-space form of the pixel SNR definition of Sec. 1 for ||x|| = 1.
+* observation ``y_i = x o exp(-2 pi i k s_i / L) + eps_i`` (Eq. MRA_Model_FB).
+
+The generator uses numpy's PCG64 stream seeded per instance.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+# Workload shapes.  Each entry is a coefficient-space stand-in for the paper's
+# sPCA-expanded projection images (the ribosome data set is not used).
+CONFIGS = {
+    # plain Synch-EM: |k| <= 10, Q = 8, N = 500, L = 72, SNR 1/10, window 24, 20 iterations
+    1: dict(K=10, Q=8, N=500, L=72, Lw=24, snr=1 / 10, decay=50.0, iters=20, P=100, gamma=100.0),
+    # Synch-EM at scale: |k| <= 32, Q = 24, N = 1e5, L = 360, SNR 1/50, window 36, 50 iterations
+    2: dict(K=32, Q=24, N=100_000, L=360, Lw=36, snr=1 / 50, decay=400.0, iters=50, P=100, gamma=100.0),
+    # differentiable log-likelihood: |k| <= 16, Q = 16, N = 2e4, L = 180, SNR 1/20
+    3: dict(K=16, Q=16, N=20_000, L=180, Lw=36, snr=1 / 20, decay=50.0, iters=30, P=100, gamma=100.0),
+    # mixed precision at the largest size: |k| <= 48, Q = 32, N = 1e6, L = 720, window 72, SNR 1/100
+    5: dict(K=48, Q=32, N=1_000_000, L=720, Lw=72, snr=1 / 100, decay=50.0, iters=50, P=100, gamma=100.0),
+}
+
+
+def config(n: int) -> dict:
+    return dict(CONFIGS[n])
+
+
+def sigma2_for_snr(snr: float, K: int, Q: int) -> float:
+    """Noise variance per stored complex entry for ||x|| = 1."""
+    return 1.0 / (snr * (K + 1) * Q)
+
+
+def make_signal(K: int, Q: int, decay: float, rng: np.random.Generator) -> np.ndarray:
+    k = np.arange(K + 1, dtype=np.float64)[:, None]
+    std = np.sqrt(np.exp(-(k ** 2) / decay)) * np.ones((1, Q))
+    x = (rng.standard_normal((K + 1, Q)) + 1j * rng.standard_normal((K + 1, Q))) * (std / np.sqrt(2.0))
+    x[0, :] = rng.standard_normal(Q) * std[0, :]
+    x /= np.linalg.norm(x)
+    return x
+
+
+def random_init(K: int, Q: int, decay: float, seed: int) -> np.ndarray:
+    """A random starting point for plain EM: a fresh draw of the signal prior."""
+    return make_signal(K, Q, decay, np.random.default_rng(seed))
+
+
+@dataclasses.dataclass
+class Instance:
+    K: int
+    Q: int
+    N: int
+    L: int
+    sigma2: float
+    x: np.ndarray  # complex128 [K+1, Q]
+    s: np.ndarray  # int64 [N]
+    y: np.ndarray  # complex128 [N, K+1, Q]
+
+
+def make_instance(K: int, Q: int, N: int, L: int, snr: float | None = None, decay: float = 50.0,
+                  seed: int = 0, sigma2: float | None = None, shifts: np.ndarray | None = None,
+                  x: np.ndarray | None = None) -> Instance:
+    """Draw one instance.  ``sigma2`` overrides ``snr``; ``sigma2 = 0`` is noise free."""
+    rng = np.random.default_rng(seed)
+    if x is None:
+        x = make_signal(K, Q, decay, rng)
+    if sigma2 is None:
+        sigma2 = sigma2_for_snr(snr, K, Q)
+    if shifts is None:
+        s = rng.integers(0, L, size=N).astype(np.int64)
+    else:
+        s = np.asarray(shifts, dtype=np.int64)
+    k = np.arange(K + 1, dtype=np.float64)
+    phase = np.exp(-2j * np.pi * np.outer(s, k) / L)  # [N, K+1]
+    y = x[None, :, :] * phase[:, :, None]
+    if sigma2 > 0:
+        noise = rng.standard_normal((N, K + 1, Q)) + 1j * rng.standard_normal((N, K + 1, Q))
+        y = y + noise * np.sqrt(sigma2 / 2.0)
+    return Instance(K=K, Q=Q, N=N, L=L, sigma2=float(sigma2), x=x, s=s, y=y)
+
+
+def to_c64(a: np.ndarray) -> np.ndarray:
+    """Contiguous complex64 copy (the device storage type of observations)."""
+    return np.ascontiguousarray(a, dtype=np.complex64)
+
+
+def c64_round(a: np.ndarray) -> np.ndarray:
+    """The complex128 values that a complex64 copy of ``a`` holds exactly."""
+    return to_c64(a).astype(np.complex128)

@@ -1,0 +1,387 @@
+"""Pins for the FP64 oracle against things other than itself.
+
+Each test ties one oracle function to brute force, a library routine, a closed
+form or an invariant fixed by the paper, so that a dropped term, a wrong sign,
+a wrong index or a transposed operand in the oracle fails at least one of them.
+"""
+import cmath
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
+
+
+def tiny(seed=0, K=2, Q=2, N=3, L=5, snr=0.5):
+    return synth.make_instance(K=K, Q=Q, N=N, L=L, snr=snr, decay=4.0, seed=seed)
+
+
+# --------------------------------------------------------------------------- rotations
+def test_rotation_group_law_and_sign():
+    """R_a R_b = R_{a+b}; rotating by 2 pi is the identity; the model's sign (Eq. fb_rotation)."""
+    rng = np.random.default_rng(1)
+    a = rng.standard_normal((4, 3)) + 1j * rng.standard_normal((4, 3))
+    np.testing.assert_allclose(O.rotate(O.rotate(a, 0.3), 1.1), O.rotate(a, 1.4), atol=1e-14)
+    np.testing.assert_allclose(O.rotate(a, 2 * math.pi), a, atol=1e-13)
+    # entry (k, q) picks up exp(-i k phi), written out element by element
+    phi = 0.7
+    for k in range(4):
+        for q in range(3):
+            assert abs(O.rotate(a, phi)[k, q] - a[k, q] * cmath.exp(-1j * k * phi)) < 1e-14
+
+
+# --------------------------------------------------------------------------- E-step by brute force
+def _dist2_loops(x, v, theta):
+    s = 0.0
+    for k in range(x.shape[0]):
+        for q in range(x.shape[1]):
+            d = x[k, q] * cmath.exp(-1j * k * theta) - v[k, q]
+            s += d.real * d.real + d.imag * d.imag
+    return s
+
+
+@pytest.mark.parametrize("Lw,l0", [(5, -2), (3, -1), (4, 0)])
+def test_posterior_and_loglik_by_joint_enumeration(Lw, l0):
+    """Enumerate all Lw^N joint rotations: marginals equal w_jl, log-sum equals the log-likelihood."""
+    inst = tiny(seed=3)
+    L, N, sigma2 = inst.L, inst.N, inst.sigma2
+    x = synth.make_signal(inst.K, inst.Q, 4.0, np.random.default_rng(9))
+    rng = np.random.default_rng(5)
+    rho = rng.random(Lw) + 0.1
+    rho /= rho.sum()
+    offs = [l0 + i for i in range(Lw)]
+    M = (inst.K + 1) * inst.Q
+    logp = {}
+    for combo in itertools.product(range(Lw), repeat=N):
+        lp = 0.0
+        for j, li in enumerate(combo):
+            lp += math.log(rho[li]) - _dist2_loops(x, inst.y[j], 2 * math.pi * offs[li] / L) / sigma2
+            lp -= M * math.log(math.pi * sigma2)
+        logp[combo] = lp
+    mx = max(logp.values())
+    Z = sum(math.exp(v - mx) for v in logp.values())
+    marg = np.zeros((N, Lw))
+    for combo, v in logp.items():
+        p = math.exp(v - mx) / Z
+        for j, li in enumerate(combo):
+            marg[j, li] += p
+    st = O.em_step(inst.y, x, np.log(rho), L, sigma2, Lw=Lw, l0=l0)
+    np.testing.assert_allclose(st.w, marg, atol=1e-12)
+    assert abs(st.loglik - (mx + math.log(Z))) < 1e-9 * abs(st.loglik)
+
+
+# --------------------------------------------------------------------------- M-step optimality
+def _Q(a, w, y, log_rho, offs, L, sigma2, gamma_a_inv):
+    """Q(a, rho | a_t, rho_t) of Eq. (expectation_step) + log p(a), written with loops over j, l."""
+    val = 0.0
+    for j in range(y.shape[0]):
+        for i, l in enumerate(offs):
+            val += w[j, i] * (log_rho[i] - _dist2_loops(a, y[j], 2 * math.pi * l / L) / sigma2)
+    if gamma_a_inv is not None:
+        val -= float(np.sum(gamma_a_inv * np.abs(a) ** 2))
+    return val
+
+
+@pytest.mark.parametrize("with_prior", [False, True])
+def test_mstep_maximises_Q(with_prior):
+    inst = tiny(seed=11, N=4, L=6)
+    L, sigma2 = inst.L, inst.sigma2
+    Lw, l0 = 4, -2
+    x = synth.make_signal(inst.K, inst.Q, 4.0, np.random.default_rng(2))
+    lr = np.log(np.full(Lw, 1.0 / Lw))
+    gi = None
+    if with_prior:
+        k = np.arange(inst.K + 1)[:, None] * np.ones((1, inst.Q))
+        gi = 1.0 / (4.0 * np.exp(-k / 8.0)) ** 2
+    st = O.em_step(inst.y, x, lr, L, sigma2, Lw=Lw, l0=l0, gamma_a_inv=gi)
+    offs = O.window_offsets(L, Lw, l0)
+    q0 = _Q(st.x, st.w, inst.y, lr, offs, L, sigma2, gi)
+    rng = np.random.default_rng(4)
+    h = 1e-5
+    # stationarity by central differences along every real coordinate
+    for k in range(inst.K + 1):
+        for q in range(inst.Q):
+            for unit in (1.0, 1j):
+                e = np.zeros_like(st.x)
+                e[k, q] = unit * h
+                g = (_Q(st.x + e, st.w, inst.y, lr, offs, L, sigma2, gi)
+                     - _Q(st.x - e, st.w, inst.y, lr, offs, L, sigma2, gi)) / (2 * h)
+                assert abs(g) < 1e-5 * max(1.0, abs(q0))
+    for _ in range(5):
+        d = 1e-2 * (rng.standard_normal(st.x.shape) + 1j * rng.standard_normal(st.x.shape))
+        assert _Q(st.x + d, st.w, inst.y, lr, offs, L, sigma2, gi) < q0
+
+
+def test_rho_update_maximises_lagrangian():
+    """rho_{t+1} maximises sum W log rho + gamma sum rho_bar log rho on the simplex (App. C)."""
+    inst = tiny(seed=21, N=6, L=7)
+    Lw, l0 = 5, -2
+    x = synth.make_signal(inst.K, inst.Q, 4.0, np.random.default_rng(3))
+    lrb = np.log(np.array([0.05, 0.2, 0.5, 0.2, 0.05]))
+    gamma = 3.0
+    st = O.em_step(inst.y, x, np.log(np.full(Lw, 0.2)), inst.L, inst.sigma2, Lw=Lw, l0=l0, gamma=gamma, log_rho_bar=lrb)
+    rho = np.exp(st.log_rho)
+    assert abs(rho.sum() - 1) < 1e-14
+    ratio = (st.W + gamma * np.exp(lrb)) / rho  # the Lagrange multiplier, equal for every l
+    np.testing.assert_allclose(ratio, ratio[0], rtol=1e-12)
+
+    def obj(r):
+        return float(np.sum(st.W * np.log(r)) + gamma * np.sum(np.exp(lrb) * np.log(r)))
+
+    rng = np.random.default_rng(0)
+    for _ in range(50):
+        r = rng.dirichlet(np.ones(Lw))
+        assert obj(r) <= obj(rho) + 1e-12
+
+
+# --------------------------------------------------------------------------- EM monotonicity
+@pytest.mark.parametrize("gamma,with_prior,Lw", [(0.0, False, 24), (10.0, False, 24), (5.0, True, 12), (0.0, False, 72)])
+def test_map_objective_nondecreasing(gamma, with_prior, Lw):
+    c = synth.config(1)
+    inst = synth.make_instance(K=6, Q=4, N=120, L=c["L"], snr=0.2, decay=20.0, seed=7)
+    L = inst.L
+    gi = None
+    if with_prior:
+        k = np.arange(inst.K + 1)[:, None] * np.ones((1, inst.Q))
+        gi = 1.0 / (4.0 * np.exp(-k / 8.0)) ** 2
+    lrb = None
+    if gamma > 0:
+        t = 3.0 * np.cos(2 * np.pi * O.window_offsets(L, Lw) / L)
+        lrb = t - np.log(np.sum(np.exp(t)))
+    x = synth.random_init(inst.K, inst.Q, 20.0, seed=99)
+    lr = np.log(np.full(Lw, 1.0 / Lw)) if lrb is None else lrb.copy()
+    kw = dict(Lw=Lw, gamma=gamma, log_rho_bar=lrb, gamma_a_inv=gi)
+    prev = O.map_objective(inst.y, x, lr, L, inst.sigma2, **kw)
+    for _ in range(12):
+        st = O.em_step(inst.y, x, lr, L, inst.sigma2, **kw)
+        x, lr = st.x, st.log_rho
+        cur = O.map_objective(inst.y, x, lr, L, inst.sigma2, **kw)
+        assert cur >= prev - 1e-9 * abs(prev)
+        prev = cur
+
+
+# --------------------------------------------------------------------------- reduction to full-search EM (FFT form)
+def _standard_em_fft(y, x, rho_full, L, sigma2):
+    """Plain EM over all L rotations written with numpy.fft: S_jl = Re sum_k c_jk e^{-2 pi i k l/L}."""
+    N, Kp1, Q = y.shape
+    c = np.einsum("jkq,kq->jk", np.conj(y), x)  # c_jk = sum_q conj(y) x
+    cpad = np.zeros((N, L), dtype=np.complex128)
+    cpad[:, :Kp1] = c
+    S = np.fft.fft(cpad, axis=1).real  # sum_k c_k e^{-2 pi i k l / L}
+    nx = np.sum(np.abs(x) ** 2)
+    ny = np.sum(np.abs(y) ** 2, axis=(1, 2))
+    t = np.log(rho_full)[None, :] - (nx + ny[:, None] - 2 * S) / sigma2
+    m = t.max(axis=1, keepdims=True)
+    w = np.exp(t - m)
+    w /= w.sum(axis=1, keepdims=True)
+    Wk = np.fft.ifft(w, axis=1)[:, :Kp1] * L  # sum_l w_jl e^{+2 pi i k l / L}
+    xn = np.einsum("jk,jkq->kq", Wk, y) / N
+    W = w.sum(axis=0)
+    return xn, W / W.sum(), w
+
+
+def test_full_window_uniform_prior_is_standard_em():
+    inst = synth.make_instance(K=5, Q=3, N=40, L=16, snr=0.3, decay=10.0, seed=12)
+    L = inst.L
+    x = synth.random_init(inst.K, inst.Q, 10.0, seed=5)
+    rng = np.random.default_rng(8)
+    rho_full = rng.random(L) + 0.2
+    rho_full /= rho_full.sum()
+    l0 = -(L // 2)
+    offs = O.window_offsets(L, L, l0)
+    st = O.em_step(inst.y, x, np.log(rho_full[np.mod(offs, L)]), L, inst.sigma2, Lw=L, l0=l0, gamma=0.0)
+    xn, rn, w = _standard_em_fft(inst.y, x, rho_full, L, inst.sigma2)
+    np.testing.assert_allclose(st.x, xn, atol=1e-12)
+    np.testing.assert_allclose(np.exp(st.log_rho), rn[np.mod(offs, L)], atol=1e-12)
+    np.testing.assert_allclose(st.w, w[:, np.mod(offs, L)], atol=1e-12)
+
+
+# --------------------------------------------------------------------------- equivariance
+def test_em_equivariant_under_global_rotation():
+    inst = synth.make_instance(K=6, Q=4, N=60, L=24, snr=0.3, decay=20.0, seed=31)
+    L, g = inst.L, 5
+    x0 = O.align_mean(inst.y, inst.s, L)
+    lr = np.log(np.full(9, 1 / 9))
+    a = O.em_step(inst.y, x0, lr, L, inst.sigma2, Lw=9)
+    yr = O.rotate(inst.y, 2 * np.pi * g / L)
+    b = O.em_step(yr, O.rotate(x0, 2 * np.pi * g / L), lr, L, inst.sigma2, Lw=9)
+    np.testing.assert_allclose(b.w, a.w, atol=1e-12)
+    np.testing.assert_allclose(b.x, O.rotate(a.x, 2 * np.pi * g / L), atol=1e-12)
+    assert abs(a.loglik - b.loglik) < 1e-9 * abs(a.loglik)
+
+
+def test_sync_invariant_under_global_rotation():
+    inst = synth.make_instance(K=5, Q=4, N=50, L=24, snr=2.0, decay=20.0, seed=41)
+    s1, _, _ = O.synchronize_and_match(inst.y, 12, inst.L)
+    s2, _, _ = O.synchronize_and_match(O.rotate(inst.y, 2 * np.pi * 7 / inst.L), 12, inst.L)
+    np.testing.assert_array_equal(s1, s2)
+
+
+# --------------------------------------------------------------------------- noise-free recovery
+def _covering_shifts(L, P, N, rng):
+    base = np.concatenate([np.arange(L), np.arange(L)])  # every rotation twice inside S_P
+    sp = np.concatenate([base, rng.integers(0, L, P - base.size)])
+    return np.concatenate([rng.permutation(sp), rng.integers(0, L, N - P)])
+
+
+def test_noise_free_synchronize_and_match_exact():
+    L, P, N = 8, 24, 60
+    rng = np.random.default_rng(0)
+    s = _covering_shifts(L, P, N, rng)
+    inst = synth.make_instance(K=4, Q=3, N=N, L=L, sigma2=0.0, decay=8.0, seed=2, shifts=s)
+    shat, phi, rel = O.synchronize_and_match(inst.y, P, L)
+    np.testing.assert_array_equal(shat, (s - s[0]) % L)
+    x0 = O.align_mean(inst.y, shat, L)
+    np.testing.assert_allclose(x0, O.rotate(inst.x, 2 * np.pi * s[0] / L), atol=1e-12)
+    assert O.relerr(x0, inst.x) < 1e-9
+    counts, c, r = O.residual_histogram(inst.y, s, shat, inst.x, L)
+    assert counts[0] == N and np.all(r == 0)
+    lp, _ = O.fit_prior(counts, L, 5)
+    assert lp[2] == 0.0 and np.all(np.isneginf(np.delete(lp, 2)))
+
+
+def test_prior_residual_sign_matches_em_window():
+    """A biased shift estimate for some images shows up at the same offset in the residual
+    histogram and in the EM posterior (tiny noise): r_j indexes the EM window."""
+    L, N = 12, 30
+    rng = np.random.default_rng(3)
+    s = rng.integers(0, L, N)
+    inst = synth.make_instance(K=4, Q=3, N=N, L=L, sigma2=1e-6, decay=8.0, seed=4, shifts=s)
+    shat = s.copy()
+    shat[:6] = (shat[:6] + 2) % L  # six images estimated 2 grid steps too far
+    counts, c, r = O.residual_histogram(inst.y, s, shat, inst.x, L)
+    assert c == 0
+    Lw = 7
+    xbar = O.align_mean(inst.y, shat, L)
+    st = O.em_step(inst.y, inst.x, np.log(np.full(Lw, 1 / Lw)), L, inst.sigma2, Lw=Lw, shifts=shat)
+    offs = O.window_offsets(L, Lw)
+    peak = offs[np.argmax(st.w, axis=1)] % L
+    np.testing.assert_array_equal(peak, r)
+    assert np.all(r[:6] == L - 2) and np.all(r[6:] == 0)
+    del xbar
+
+
+# --------------------------------------------------------------------------- synchronization pieces
+def test_relative_rotation_matches_fft_cross_correlation():
+    rng = np.random.default_rng(6)
+    for trial in range(5):
+        K, Q, L = 5, 3, 30
+        vi = rng.standard_normal((K + 1, Q)) + 1j * rng.standard_normal((K + 1, Q))
+        vj = rng.standard_normal((K + 1, Q)) + 1j * rng.standard_normal((K + 1, Q))
+        C = np.sum(np.conj(vi) * vj, axis=1)  # C_k
+        cp = np.zeros(L, dtype=np.complex128)
+        cp[:K + 1] = C
+        score = L * np.fft.ifft(cp).real  # Re sum_k C_k e^{+2 pi i k l / L}
+        assert O.relative_rotation(vi, vj, L) == int(np.argmax(score))
+
+
+def test_power_iteration_matches_eigh():
+    rng = np.random.default_rng(8)
+    P, L = 30, 64
+    th = rng.integers(0, L, P)
+    rel = (th[None, :] - th[:, None]) % L  # exact theta_j - theta_i
+    noise = rng.random((P, P)) < 0.2
+    rnd = rng.integers(0, L, (P, P))
+    rel = np.where(noise, rnd, rel)
+    rel = np.triu(rel, 1)
+    rel = (rel - rel.T) % L
+    H = O.sync_matrix(rel, L)
+    z = O.power_iteration(H, 500)
+    evals, evecs = np.linalg.eigh(H)
+    u = evecs[:, -1]
+    assert abs(abs(np.vdot(u, z)) - 1.0) < 1e-10
+    # and the leading eigenvector carries the rotations: phases of e^{i theta}
+    phi = O.ppm(rel, L, 50, 100)
+    d = (phi - th) % L
+    dev = (d - d[0] + L // 2) % L - L // 2  # circular deviation from one image's offset
+    assert np.max(np.abs(dev)) <= 4
+    wrong = (phi + th) % L  # the opposite sign convention would scatter over the circle
+    devw = (wrong - wrong[0] + L // 2) % L - L // 2
+    assert np.max(np.abs(devw)) > 8
+
+
+def test_match_excludes_self_and_picks_nearest():
+    rng = np.random.default_rng(2)
+    y = rng.standard_normal((10, 3, 2)) + 1j * rng.standard_normal((10, 3, 2))
+    y[7] = y[2] + 1e-3
+    y[1] = y[4] + 1e-3
+    phi = np.arange(5) * 10
+    s = O.match(y, 5, phi)
+    assert s[7] == phi[2] and s[1] == phi[4] and s[4] == phi[1]
+    for i in range(10):
+        cands = [n for n in range(5) if n != i]
+        dd = [np.sum(np.abs(y[i] - y[n]) ** 2) for n in cands]
+        assert s[i] == phi[cands[int(np.argmin(dd))]]
+
+
+# --------------------------------------------------------------------------- von Mises prior fit
+def test_von_mises_fit_recovers_kappa():
+    rng = np.random.default_rng(12)
+    L, kappa = 360, 40.0
+    th = rng.vonmises(0.0, kappa, 400_000)
+    r = np.floor(np.mod(th, 2 * np.pi) * L / (2 * np.pi) + 0.5).astype(int) % L
+    counts = np.bincount(r, minlength=L)
+    lp, k_hat = O.fit_prior(counts, L, 72, kind=1)
+    assert abs(k_hat - kappa) / kappa < 0.02
+    assert abs(np.sum(np.exp(lp)) - 1.0) < 1e-12
+
+
+def test_vm_ratio_series():
+    """A(kappa) against the power series of I_1 and I_0."""
+    for k in (0.1, 1.0, 5.0, 20.0):
+        i0 = sum((k / 2) ** (2 * m) / math.factorial(m) ** 2 for m in range(80))
+        i1 = sum((k / 2) ** (2 * m + 1) / (math.factorial(m) * math.factorial(m + 1)) for m in range(80))
+        assert abs(O.vm_ratio(k) - i1 / i0) < 1e-13
+
+
+# --------------------------------------------------------------------------- gradient
+def test_loglik_gradient_central_differences():
+    inst = synth.make_instance(K=3, Q=2, N=25, L=20, snr=0.5, decay=6.0, seed=17)
+    L, Lw = inst.L, 7
+    rng = np.random.default_rng(1)
+    x = synth.random_init(inst.K, inst.Q, 6.0, seed=3)
+    eta = 0.3 * rng.standard_normal(Lw)
+    kappa = 2.5
+    ll, dx, de, dk = O.loglik_grad(inst.y, x, eta, kappa, L, inst.sigma2)
+    h = 1e-6
+    for k in range(inst.K + 1):
+        for q in range(inst.Q):
+            for part, unit in ((0, 1.0), (1, 1j)):
+                e = np.zeros_like(x)
+                e[k, q] = unit * h
+                g = (O.loglik(inst.y, x + e, eta, kappa, L, inst.sigma2)
+                     - O.loglik(inst.y, x - e, eta, kappa, L, inst.sigma2)) / (2 * h)
+                an = dx[k, q].real if part == 0 else dx[k, q].imag
+                assert abs(g - an) <= 1e-6 * max(1.0, abs(an))
+    for l in range(Lw):
+        e = np.zeros(Lw)
+        e[l] = h
+        g = (O.loglik(inst.y, x, eta + e, kappa, L, inst.sigma2) - O.loglik(inst.y, x, eta - e, kappa, L, inst.sigma2)) / (2 * h)
+        assert abs(g - de[l]) <= 1e-6 * max(1.0, abs(de[l]))
+    g = (O.loglik(inst.y, x, eta, kappa + h, L, inst.sigma2) - O.loglik(inst.y, x, eta, kappa - h, L, inst.sigma2)) / (2 * h)
+    assert abs(g - dk) <= 1e-6 * max(1.0, abs(dk))
+    assert abs(np.sum(de)) < 1e-9  # the logits are defined up to a constant
+
+
+# --------------------------------------------------------------------------- relative error and step
+def test_relerr_continuous_rotation_and_scale():
+    x = synth.make_signal(8, 5, 20.0, np.random.default_rng(4))
+    assert O.relerr(O.rotate(x, 1.2345), x) < 1e-9
+    assert abs(O.relerr(1.1 * O.rotate(x, -0.77), x) - 0.1) < 1e-9
+    # k>0 rows count twice: perturbing only row k=1 by d gives sqrt(2|d|^2)/||I||
+    y = x.copy()
+    y[0, 0] += 0.01  # a real k=0 perturbation cannot be rotated away
+    wnorm = math.sqrt(np.sum(np.abs(x[0]) ** 2) + 2 * np.sum(np.abs(x[1:]) ** 2))
+    assert O.relerr(y, x) <= 0.01 / wnorm + 1e-12
+
+
+def test_step_is_zero_for_grid_rotation():
+    x = synth.make_signal(5, 3, 20.0, np.random.default_rng(5))
+    L = 40
+    assert O.step_size(O.rotate(x, 2 * np.pi * 13 / L), x, L) < 1e-26
+    assert O.step_size(x + 0.1, x, L) > 0
