@@ -1,0 +1,367 @@
+#!/usr/bin/env python
+"""Benchmark: Synch-EM on one GB300 at |k| <= 32, Q = 24, N = 100,000, L = 360, window 36, 50 EM iterations.
+
+One step = the whole hot path over one resident instance:
+  Synchronize and Match (P = 100) -> one trial of Algorithm 1 on the instance
+  (residual histogram + window prior) -> align and average -> 50 EM iterations
+  (one graph-captured mra_em_run).
+Metric: image-rotation evaluations per second, N * Lw * iterations / step time.
+Also reported: the sweep kernel's HBM roofline fraction, an end-to-end number
+through the public API with host buffers, the FP64 CPU oracle on a bounded
+sample, clocks during the timed region, and time to converge against
+full-search EM at equal error on the same GPU.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--no-ttc]
+"""
+import os
+
+# The CPU oracle leg is timed single-threaded (its core count is reported as 1).
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse  # noqa: E402
+import ctypes  # noqa: E402
+import hashlib  # noqa: E402
+import json  # noqa: E402
+import math  # noqa: E402
+import subprocess  # noqa: E402
+import sys  # noqa: E402
+import time  # noqa: E402
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+CFG = 2
+METRIC = "EM image-rotation evals/s"
+UNIT = "evals/s"
+
+
+def workload_config(c):
+    return {"workload": f"Synch-EM |k|<={c['K']} Q={c['Q']} N={c['N']} L={c['L']} Lw={c['Lw']} "
+                        f"SNR=1/{round(1 / c['snr'])} T={c['iters']} P={c['P']} gamma={c['gamma']}",
+            "K": c["K"], "Q": c["Q"], "N": c["N"], "L": c["L"], "Lw": c["Lw"], "iters": c["iters"], "P": c["P"],
+            "snr": c["snr"], "l2": "inputs larger than L2 (y is 633.6 MB per sweep)"}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def traffic_for(kernel_src):
+    """DRAM bytes per sweep launch from the committed ncu summary, if the kernel is unchanged since."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f)
+        sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
+        if t.get("source_sha256") == sha:
+            return float(t["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class Clocks:
+    def __init__(self, out):
+        self.out = out
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.f = open(self.out, "w")
+            self.p = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200", "-i", str(self._gpu())],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.p = None
+        return self
+
+    @staticmethod
+    def _gpu():
+        v = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0]
+        return v if v.isdigit() else "0"
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            self.p.wait()
+            self.f.close()
+
+    def summary(self):
+        try:
+            rows = [r.split(",") for r in open(self.out).read().strip().splitlines()]
+            sm = [float(r[1]) for r in rows]
+            mx = float(rows[0][2])
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip().lower() == "active"})
+            return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": reasons, "samples": len(rows)}
+        except Exception as e:  # no nvidia-smi
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "error": str(e)[:80]}
+
+
+# ------------------------------------------------------------------ CPU oracle (baseline and reference arm)
+def oracle_sample(inst, c, n_img, iters):
+    import oracle as O
+
+    y64 = synth.c64_round(inst.y[:n_img])
+    s = inst.s[:n_img]
+    Lw = c["Lw"]
+    x = O.align_mean(y64, s, inst.L)
+    lr = np.log(np.full(Lw, 1.0 / Lw))
+    t0 = time.perf_counter()
+    for _ in range(iters):
+        st = O.em_step(y64, x, lr, inst.L, inst.sigma2, Lw=Lw, shifts=s)
+        x, lr = st.x, st.log_rho
+    dt = time.perf_counter() - t0
+    return n_img * Lw * iters / dt, dt
+
+
+def run_reference(args, c):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    inst = synth.make_instance(c["K"], c["Q"], 6000, c["L"], c["snr"], c["decay"], seed=1000 * CFG)
+    n_img = 1500
+    for _ in range(args.warmup):
+        oracle_sample(inst, c, 200, 1)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v, _ = oracle_sample(inst, c, n_img, 1)
+        vals.append(v)
+    wall = time.perf_counter() - t0
+    value = args.steps * n_img * c["Lw"] / wall
+    sample = f"oracle em_step (FP64 numpy) on {n_img} images of the workload, 1 iteration per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(c),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu")
+    ap.add_argument("--no-ttc", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    c = synth.config(CFG)
+    if args.impl == "reference":
+        return run_reference(args, c)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2105_07372_gb300 import mra, pipeline
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    mra.load()
+
+    # ---- inputs resident in HBM (each rank its own independent instance: replicas)
+    inst = synth.make_instance(c["K"], c["Q"], c["N"], c["L"], c["snr"], c["decay"], seed=1000 * CFG + rank)
+    y_host = torch.from_numpy(synth.to_c64(inst.y)).pin_memory()
+    y = y_host.to(dev)
+    s_true = torch.from_numpy(inst.s.astype(np.int32)).to(dev)
+    x_true = torch.from_numpy(inst.x).to(dev)
+    N, K, Q, L, Lw, T, P = c["N"], c["K"], c["Q"], c["L"], c["Lw"], c["iters"], c["P"]
+    d = mra.dims(N, K, Q, L, inst.sigma2)
+    ws = pipeline.workspaces(d, Lw, P, dev)
+    l0 = -(Lw // 2)
+    shift = torch.empty(N, dtype=torch.int32, device=dev)
+    hist = torch.zeros(L, dtype=torch.int32, device=dev)
+    log_prior = torch.empty(Lw, dtype=torch.float64, device=dev)
+    kappa = torch.empty(1, dtype=torch.float64, device=dev)
+    x = torch.empty((K + 1, Q), dtype=torch.complex128, device=dev)
+    log_rho = torch.empty(Lw, dtype=torch.float64, device=dev)
+    stats = torch.empty((T, 2), dtype=torch.float64, device=dev)
+    sweep_ms = (ctypes.c_float * T)()
+    sweep_times = []
+
+    def step(timed_sweeps):
+        mra.mra_sync(d, y, P, 50, 100, shift, ws.sync)
+        hist.zero_()
+        mra.mra_prior_hist(d, y, s_true, shift, x_true, hist, None, ws.em)
+        mra.mra_fit_prior(L, Lw, l0, hist, 0, log_prior, kappa)
+        mra.mra_align_mean(d, y, shift, x, ws.em)
+        log_rho.copy_(log_prior)
+        prm = mra.em_params(Lw, l0=l0, gamma=c["gamma"], log_rho_bar=log_prior, max_iters=T,
+                            sweep_ms=sweep_ms if timed_sweeps else None)
+        n = mra.mra_em_run(d, prm, y, shift, x, log_rho, stats, None, ws.em)
+        if timed_sweeps:
+            sweep_times.extend(list(sweep_ms)[:n])
+        return n
+
+    # kernels of ours per step: sync 4, prior hist 5, fit 1, align 4, em_run 2 + 3 T + 1
+    launches_per_step = 4 + 5 + 1 + 4 + 2 + 3 * T + 1
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clk = Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv") if os.path.isdir(
+        os.path.join(ROOT, "gpurun_out")) else f"/tmp/mra_clocks_{rank}.csv")
+    with clk:
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step(True)
+        e1.record(stream)
+        barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    evals_per_step = N * Lw * T
+    value = world * evals_per_step / (ms / 1e3)
+
+    # ---- roofline of the dominant kernel (the EM sweep): algorithmic bytes = one read of y
+    bytes_per_sweep = N * (K + 1) * Q * 8
+    avg_sweep_s = float(np.mean(sweep_times)) / 1e3
+    achieved = bytes_per_sweep / avg_sweep_s / 1e9
+    peak, peak_kind = peaks()
+    traffic = traffic_for(os.path.join(ROOT, "paper_2105_07372_gb300", "csrc", "em.cu"))
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs", "kernel": "k_em_sweep",
+                "algorithmic_bytes_per_launch": bytes_per_sweep, "avg_launch_ms": avg_sweep_s * 1e3,
+                "launches_timed": len(sweep_times)}
+    em_ms = float(np.sum(sweep_times)) / args.steps
+
+    # ---- end to end through the public API with host buffers (H2D of the step's inputs, D2H of its result)
+    x_host = torch.empty((K + 1, Q), dtype=torch.complex128).pin_memory()
+    lr_host = torch.empty(Lw, dtype=torch.float64).pin_memory()
+    s_true_h = s_true.cpu().pin_memory()
+    x_true_h = x_true.cpu().pin_memory()
+    h2d = y_host.numel() * 8 + s_true_h.numel() * 4 + x_true_h.numel() * 16
+    d2h = x_host.numel() * 16 + lr_host.numel() * 8
+
+    def e2e_step():
+        y.copy_(y_host, non_blocking=True)
+        s_true.copy_(s_true_h, non_blocking=True)
+        x_true.copy_(x_true_h, non_blocking=True)
+        step(False)
+        x_host.copy_(x, non_blocking=True)
+        lr_host.copy_(log_rho, non_blocking=True)
+
+    e2e_step()
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    e2e = {"value": world * evals_per_step / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms}
+
+    relerr_final = pipeline.relerr(x, x_true, d)
+
+    # ---- time to converge against full-search EM at equal error (same GPU, same instance)
+    ttc = None
+    if not args.no_ttc and rank == 0:
+        ttc = time_to_converge(mra, pipeline, c, inst, d, y, s_true, x_true, ws, dev)
+
+    # ---- CPU oracle baseline (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        n_img, iters = 4000, 3
+        v, dt = oracle_sample(inst, c, n_img, iters)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"oracle em_step (FP64 numpy) on {n_img} of the {N} images, {iters} iterations, "
+                         f"{dt:.1f} s"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": dict(workload_config(c), parallelism="replicas" if world > 1 else "single"),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches_per_step * args.steps, "clocks": clk.summary(),
+                "em_only": {"ms_per_step": em_ms, "evals_per_s": evals_per_step / (em_ms / 1e3)},
+                "relerr_final": relerr_final, "ttc": ttc}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def time_to_converge(mra, pipeline, c, inst, d, y, s_true, x_true, ws, dev):
+    import torch
+
+    N, K, Q, L, Lw, P = c["N"], c["K"], c["Q"], c["L"], c["Lw"], c["P"]
+    tol, tmax = 1e-5, 1000
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    x0 = torch.from_numpy(synth.random_init(K, Q, c["decay"], seed=77)).to(dev)
+    dl = mra.dims(N, K, Q, L, inst.sigma2)
+    ws_full = mra.workspace(mra.mra_em_workspace_bytes(dl, L), dev)
+    full_ws = pipeline.Workspaces(em=ws_full, sync=ws.sync)
+    torch.cuda.synchronize()
+    ev0.record()
+    full = pipeline.full_search_em(y, dl, x0, iters=tmax, ws=full_ws, tol=tol, check_every=25)
+    ev1.record()
+    torch.cuda.synchronize()
+    t_full = ev0.elapsed_time(ev1) / 1e3
+    e_full = pipeline.relerr(full.x, x_true, dl)
+
+    l0 = -(Lw // 2)
+
+    def synch_run(max_iters, traj=None):
+        shift = pipeline.synchronize(y, dl, P, ws)
+        lp, _, _ = pipeline.learn_prior(y, dl, s_true, shift, x_true, Lw, l0, 0, ws)
+        return pipeline.synch_em(y, dl, P=P, Lw=Lw, iters=max_iters, gamma=c["gamma"], log_rho_bar=lp, ws=ws,
+                                 shift=shift, tol=tol, check_every=25, stats=False, x_traj=traj)
+
+    traj = torch.empty((tmax, K + 1, Q), dtype=torch.complex128, device=dev)
+    r = synch_run(tmax, traj)
+    errs = [pipeline.relerr(traj[i].contiguous(), x_true, dl) for i in range(r.iters)]
+    target = e_full * 1.01
+    hit = next((i + 1 for i, e in enumerate(errs) if e <= target), None)
+    out = {"full_search_s": t_full, "full_search_iters": full.iters, "full_search_relerr": e_full, "tol": tol,
+           "synch_em_iters_to_tol": r.iters, "synch_em_relerr_at_tol": errs[-1] if errs else None,
+           "equal_error_target": target}
+    if hit is not None:
+        synch_run(hit)  # warm
+        torch.cuda.synchronize()
+        ev0.record()
+        synch_run(hit)
+        ev1.record()
+        torch.cuda.synchronize()
+        t_s = ev0.elapsed_time(ev1) / 1e3
+        out.update({"synch_em_s": t_s, "synch_em_iters": hit, "speedup": t_full / t_s})
+    else:
+        out.update({"synch_em_s": None, "speedup": None, "note": "Synch-EM did not reach the full-search error"})
+    return out
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,217 @@
+/*
+ * mra.h -- C ABI of the GB300 Synch-EM library (libmra.so).
+ *
+ * Synch-EM for 2-D multi-reference alignment (Janco & Bendory, "An accelerated
+ * expectation-maximization algorithm for multi-reference alignment").  The
+ * library runs the hot path of the method on one CUDA device: Synchronize and
+ * Match, the learned rotation prior, the windowed prior-weighted EM iteration
+ * and the marginal log-likelihood with its gradient.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Coefficients.  An image is stored by its steerable coefficients a_{k,q} for
+ *   the angular index k = 0..K and the radial index q = 0..Q-1 (the k < 0 half
+ *   is the complex conjugate for a real image, Sec. 1).  M = (K+1) Q.  A
+ *   coefficient array is row-major [K+1][Q] of complex numbers stored as
+ *   interleaved (re, im) pairs.  Observations y are [N][K+1][Q] complex float
+ *   (8 bytes per coefficient), image-major.  Norms run over the M stored
+ *   entries.
+ * Rotations.  Rotating an image by phi multiplies a_{k,q} by exp(-i k phi)
+ *   (Eq. fb_rotation); observations follow y_i = x o exp(-i k theta_i) + eps_i
+ *   (Eq. MRA_Model_FB).  Rotations live on the grid theta = 2 pi s / L, s an
+ *   integer "shift" in [0, L).
+ * Window.  The EM searches the Lw offsets l0, l0+1, ..., l0+Lw-1 (mod L)
+ *   around the synchronized estimate (Sec. 3.3); the paper's band [-BW/2,
+ *   BW/2] is Lw = BW + 1, l0 = -BW/2.  Arrays over the window are [Lw], index i
+ *   meaning offset l0 + i.
+ * Alignment.  Where an entry point takes shift (device int32 [N] or NULL),
+ *   image j is used as y_j o exp(+2 pi i k shift[j] / L) (the alignment step
+ *   before Eq. synch_initialization), folded into the kernels; y is never
+ *   rewritten.  NULL means the images are used as given.
+ * Memory.  Every array argument is a DEVICE pointer on the current CUDA device
+ *   unless marked "host".  The caller owns every buffer; nothing is allocated
+ *   inside a call.  Scratch memory is the caller's workspace (ws, ws_bytes),
+ *   256-byte aligned, sized by the matching *_workspace_bytes query; its
+ *   contents need no initialisation and are not preserved between calls.
+ *   Observations y must be 16-byte aligned.
+ * Streams.  stream is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  Calls are asynchronous on that stream except where noted;
+ *   outputs are valid once the stream has reached the call.
+ * Errors.  Every entry point returns an mra_status.  Arguments are checked on
+ *   the host before any launch; on error nothing is launched and outputs are
+ *   untouched.  A device-side failure (a bounded wait that ran out) is
+ *   recorded in the workspace status word and returned by the next call that
+ *   synchronizes (mra_em_run, mra_ws_status).
+ */
+#ifndef MRA_H
+#define MRA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MRA_API __attribute__((visibility("default")))
+
+typedef enum {
+  MRA_OK = 0,
+  MRA_EINVAL = -1,     /* bad dimensions, NULL or misaligned pointer, window > L, ... */
+  MRA_ENOMEM = -2,     /* a host-side allocation inside the library failed */
+  MRA_ECUDA = -3,      /* a CUDA runtime call failed (launch, copy, graph) */
+  MRA_ETIMEOUT = -4,   /* a bounded device-side wait ran out; the kernel returned early */
+  MRA_ENUMERIC = -5,   /* non-finite value where a finite one is required */
+  MRA_EWORKSPACE = -6  /* ws_bytes smaller than the workspace query */
+} mra_status;
+
+/* Problem size.  sigma2 is the noise variance per stored complex entry
+ * (E|eps|^2 = sigma2, Eq. MRA_Model_FB); beta = 1/sigma2.
+ * Limits: N >= 1, K >= 0, Q >= 1, (K+1)*Q even, L >= 1, sigma2 > 0. */
+typedef struct {
+  int32_t N, K, Q, L;
+  double sigma2;
+} mra_dims;
+
+/* Parameters of Algorithm Synch-EM (inputs L, rho_bar, BW, gamma, Gamma_a, tol, T). */
+typedef struct {
+  int32_t Lw;                /* window size, 1 <= Lw <= L */
+  int32_t l0;                /* first window offset (any integer; taken mod L) */
+  double gamma;              /* prior weight gamma >= 0 of p(rho) ~ exp(-gamma KL(rho_bar, rho)) */
+  const double* log_rho_bar; /* device [Lw] log rho_bar on the window (-inf allowed); may be NULL if gamma == 0 */
+  const double* gamma_a_inv; /* device [(K+1)*Q] diagonal of Gamma_a^{-1} (>= 0), or NULL for a flat image prior */
+  int32_t update_rho;        /* 1: rho_{t+1} = (W + gamma rho_bar)/sum; 0: rho kept fixed */
+  double tol;                /* mra_em_run stops after the iteration whose step is < tol; <= 0 never stops early */
+  int32_t max_iters;         /* mra_em_run: at most this many iterations (T) */
+  int32_t check_every;       /* mra_em_run: iterations per CUDA-graph launch between host checks (>= 1) */
+  float* sweep_ms;           /* mra_em_run: host [max_iters] device time (ms) of each iteration's sweep over y,
+                                from CUDA events recorded around the sweep kernel; NULL = not timed.  When set,
+                                the run synchronizes after every graph launch. */
+} mra_em_params;
+
+MRA_API const char* mra_status_string(int status);
+
+/* Number of streaming multiprocessors and the persistent-grid size the EM
+ * sweep uses on the current device (host outputs).  Useful for sizing. */
+MRA_API int mra_device_info(int32_t* num_sms, int32_t* sweep_grid);
+
+/* ------------------------------------------------------------------ EM */
+
+/* Workspace bytes for mra_em_step, mra_em_run and mra_loglik_grad. */
+MRA_API size_t mra_em_workspace_bytes(const mra_dims* dims, int32_t Lw);
+
+/* One iteration of Algorithm Synch-EM (E-step with Eq. weights_2d_em on the
+ * window, normalisation, W_t, the a-update of Eq. coefficients_update and the
+ * prior-weighted rho update), plus the stopping quantity.
+ *   y          [N][K+1][Q] complex float observations
+ *   shift      [N] int32 alignment shifts or NULL
+ *   x_in       [K+1][Q] complex double a_t
+ *   log_rho_in [Lw] double log rho_t on the window (-inf allowed, not all -inf)
+ *   x_out      [K+1][Q] complex double a_{t+1}  (may alias x_in)
+ *   log_rho_out[Lw] double log rho_{t+1}        (may alias log_rho_in)
+ *   loglik_out [1] double: sum_j log sum_l rho_t[l] (pi sigma2)^{-M} exp(-||a_t o e^{-i k theta_l} - y_j||^2/sigma2)
+ *   step_out   [1] double: min over all L grid rotations of ||a_{t+1} - e^{-2 pi i k l/L} a_t||^2
+ *   w_out      [N][Lw] float posterior weights w_t^{l,j}, or NULL
+ * Any of loglik_out, step_out may be NULL. */
+MRA_API int mra_em_step(const mra_dims* dims, const mra_em_params* prm, const float* y, const int32_t* shift,
+                        const double* x_in, const double* log_rho_in, double* x_out, double* log_rho_out,
+                        double* loglik_out, double* step_out, float* w_out, void* ws, size_t ws_bytes,
+                        void* stream);
+
+/* Algorithm Synch-EM's loop: up to prm->max_iters iterations from (x_inout,
+ * log_rho_inout), stopping after the first iteration whose step is < prm->tol.
+ * The iterations run as CUDA-graph launches of prm->check_every iterations;
+ * a device flag skips the remaining work of a launch once converged.  This
+ * call synchronizes the stream between launches when tol > 0 and at the end.
+ *   x_inout        [K+1][Q] complex double: a_0 in, final a out
+ *   log_rho_inout  [Lw] double: log rho_0 in, final log rho out
+ *   iters_out      host int32: iterations performed
+ *   stats_out      [max_iters][2] double (loglik at a_t, step), or NULL
+ *   x_traj_out     [max_iters][K+1][Q] complex double a_{t+1} per iteration, or NULL */
+MRA_API int mra_em_run(const mra_dims* dims, const mra_em_params* prm, const float* y, const int32_t* shift,
+                       double* x_inout, double* log_rho_inout, int32_t* iters_out, double* stats_out,
+                       double* x_traj_out, void* ws, size_t ws_bytes, void* stream);
+
+/* Marginal log-likelihood over the window and its gradient (Fisher identity),
+ *   l(x, kappa, eta) = sum_j log sum_l rho_l (pi sigma2)^{-M} exp(-||x o e^{-i k theta_l} - y_j||^2 / sigma2),
+ *   log rho_l = kappa cos(theta_l) + eta_l - log sum_win exp(kappa cos theta + eta),  theta_l = 2 pi (l0+l)/L.
+ * The posterior is recomputed in one pass over y (never stored).
+ *   x       [K+1][Q] complex double
+ *   logits  [Lw] double eta (window logits)
+ *   loglik_out [1] double
+ *   dx_out  [K+1][Q] complex double dl/dRe x + i dl/dIm x = (2/sigma2)(sum_j sum_l w_jl e^{+i k theta_l} y_j - N x), or NULL
+ *   dlogits_out [Lw] double dl/deta_l = W_l - N rho_l, or NULL
+ *   dkappa_out  [1] double sum_l (W_l - N rho_l) cos theta_l, or NULL */
+MRA_API int mra_loglik_grad(const mra_dims* dims, int32_t Lw, int32_t l0, const float* y, const int32_t* shift,
+                            const double* x, const double* logits, double kappa, double* loglik_out, double* dx_out,
+                            double* dlogits_out, double* dkappa_out, void* ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------ synchronization */
+
+/* Workspace bytes for mra_sync and its parts. */
+MRA_API size_t mra_sync_workspace_bytes(const mra_dims* dims, int32_t P);
+
+/* Relative rotations of the first P images, Eq. (relative_angle_2d_dist):
+ * rel[i][j] = argmin_s sum_{k,q} |y_i - e^{2 pi i k s/L} y_j|^2 for i < j
+ * (smallest s on ties), rel[j][i] = (L - rel[i][j]) mod L, rel[i][i] = 0.
+ *   rel_out [P][P] int32.  1 <= P <= N. */
+MRA_API int mra_sync_pairwise(const mra_dims* dims, const float* y, int32_t P, int32_t* rel_out, void* stream);
+
+/* Projected power method on H_ij = exp(-2 pi i rel[i][j] / L) (Eq. cost_synchronization):
+ * z = 1, n_power steps z <- Hz/||Hz||, n_ppm steps z <- phase(Hz) with
+ * phase(0) = 1, global phase fixed so that phi[0] = 0, then
+ * phi[i] = floor(arg z_i L / (2 pi) + 1/2) mod L.
+ *   rel [P][P] int32 in, phi_out [P] int32.  1 <= P <= 1024. */
+MRA_API int mra_sync_ppm(int32_t L, int32_t P, const int32_t* rel, int32_t n_power, int32_t n_ppm, int32_t* phi_out,
+                         void* stream);
+
+/* Matching step of Algorithm Synchronize and Match: image i takes phi[n*],
+ * n* = argmin_{n < P, n != i} ||y_i - y_n||^2 (smallest n on ties).
+ *   phi [P] int32 in, shift_out [N] int32. */
+MRA_API int mra_sync_match(const mra_dims* dims, const float* y, int32_t P, const int32_t* phi, int32_t* shift_out,
+                           void* ws, size_t ws_bytes, void* stream);
+
+/* Algorithm Synchronize and Match: pairwise + PPM on the first P images, then
+ * matching for all N.  shift_out [N] int32. */
+MRA_API int mra_sync(const mra_dims* dims, const float* y, int32_t P, int32_t n_power, int32_t n_ppm,
+                     int32_t* shift_out, void* ws, size_t ws_bytes, void* stream);
+
+/* Align and average, Eq. (synch_initialization): x_out = (1/N) sum_i y_i o e^{+2 pi i k shift_i/L}.
+ *   x_out [K+1][Q] complex double.  Uses the EM workspace (mra_em_workspace_bytes with Lw = 1). */
+MRA_API int mra_align_mean(const mra_dims* dims, const float* y, const int32_t* shift, double* x_out, void* ws,
+                           size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------ rotation prior */
+
+/* One trial of Algorithm 1 (learning the post-synchronization rotation distribution):
+ * c = argmin_s ||xbar o e^{-2 pi i k s/L} - x_true||^2 with xbar = align_mean(y, shift_est),
+ * r_j = (shift_true[j] - shift_est[j] + c) mod L, hist_inout[r_j] += 1.
+ * r_j is the EM window offset of image j after alignment.
+ *   x_true [K+1][Q] complex double, hist_inout [L] int32 (accumulated), center_out [1] int32 or NULL.
+ * Uses the EM workspace (mra_em_workspace_bytes with Lw = 1). */
+MRA_API int mra_prior_hist(const mra_dims* dims, const float* y, const int32_t* shift_true, const int32_t* shift_est,
+                           const double* x_true, int32_t* hist_inout, int32_t* center_out, void* ws, size_t ws_bytes,
+                           void* stream);
+
+/* rho_bar from pooled residual counts (Algorithm 1, averaged over trials), on the window.
+ *   kind 0: log_prior_out[i] = log(rho_bar[(l0+i) mod L] / sum over the window)   (the learned histogram)
+ *   kind 1: von Mises fit, kappa solving I1(kappa)/I0(kappa) = sum_s rho_bar[s] cos(2 pi s/L)
+ *           (0 if that mean is <= 0), log_prior_out[i] = kappa cos(2 pi (l0+i)/L) - log Z
+ *   counts [L] int32, log_prior_out [Lw] double, kappa_out [1] double or NULL. */
+MRA_API int mra_fit_prior(int32_t L, int32_t Lw, int32_t l0, const int32_t* counts, int32_t kind,
+                          double* log_prior_out, double* kappa_out, void* stream);
+
+/* Relative error up to rotation (Sec. 2.2): min over continuous theta of
+ * ||R_theta x_hat - x||/||x|| with the k > 0 rows counted twice (the k < 0 half).
+ *   x_hat, x [K+1][Q] complex double; err_out [1] double. */
+MRA_API int mra_relerr(int32_t K, int32_t Q, const double* x_hat, const double* x, double* err_out, void* stream);
+
+/* Synchronize the stream and return the workspace's device status word
+ * (MRA_OK or MRA_ETIMEOUT), then clear it. */
+MRA_API int mra_ws_status(void* ws, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MRA_H */

@@ -288,14 +288,19 @@ def phase(v: np.ndarray) -> np.ndarray:
     return out
 
 
-def ppm(rel: np.ndarray, L: int, n_power: int = 50, n_ppm: int = 100) -> np.ndarray:
-    """Projected power method for max_{z in C_1^P} z^* H z; returns grid rotations phi_hat [P]."""
+def ppm_angles(rel: np.ndarray, L: int, n_power: int = 50, n_ppm: int = 100) -> np.ndarray:
+    """Projected power method for max_{z in C_1^P} z^* H z; returns arg z_i - arg z_0 in (-pi, pi]."""
     H = sync_matrix(rel, L)
     z = power_iteration(H, n_power)
     for _ in range(n_ppm):
         z = phase(H @ z)
     z = z * np.conj(z[0]) / abs(z[0])
-    ang = np.angle(z)
+    return np.angle(z)
+
+
+def ppm(rel: np.ndarray, L: int, n_power: int = 50, n_ppm: int = 100) -> np.ndarray:
+    """Grid rotations phi_hat [P] from the projected power method, rounded to the nearest grid point."""
+    ang = ppm_angles(rel, L, n_power, n_ppm)
     return (np.floor(ang * L / TWO_PI + 0.5).astype(np.int64)) % L
 
 

@@ -1,0 +1,157 @@
+// Shared device helpers and the workspace layout of libmra (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mra.h"
+
+#define MRA_CUDA_TRY(expr)                        \
+  do {                                            \
+    cudaError_t e_ = (expr);                      \
+    if (e_ != cudaSuccess) return MRA_ECUDA;      \
+  } while (0)
+
+namespace mra {
+
+constexpr int kSweepThreads = 256;
+constexpr int kSweepWarps = kSweepThreads / 32;
+constexpr double kPi = 3.141592653589793238462643383279502884;
+// Bounded device waits give up after this many nanoseconds and report MRA_ETIMEOUT.
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;
+
+// ---------------------------------------------------------------- small math
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cmul_conj_b(float2 a, float2 b) {  // a * conj(b)
+  return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// ---------------------------------------------------------------- mbarrier + bulk copy (TMA)
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for the phase with the given parity; false if it did not complete within kWaitLimitNs.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer_ns();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (globaltimer_ns() - t0 > kWaitLimitNs) return false;
+  }
+}
+// One-dimensional bulk copy global -> shared, completion counted on bar (bytes, addresses: multiples of 16).
+__device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src_gmem, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst_smem)),
+      "l"(src_gmem), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// ---------------------------------------------------------------- workspace
+// Control words at the start of every workspace.
+struct Ctrl {
+  int status;  // MRA_OK or MRA_ETIMEOUT, set by kernels
+  int done;    // em_run: converged flag, makes the remaining kernels of a graph return at entry
+  int iter;    // em_run: iterations performed
+  int pad[61];
+};
+
+// Offsets (bytes) of every array in the EM workspace; identical on host and device.
+struct EmLayout {
+  int G;        // persistent grid of the sweep
+  int M, Kp1, Lw, L;
+  int twp;      // padded row pitch (in complex) of the window twiddle table
+  int kp4;      // K+1 rounded up to a multiple of 4 (rows of the table)
+  int cols;     // 2M + Lw + 2 reduced columns
+  size_t ctrl, tf32, tf64, tw, x32, x64, inv_den, logrho32, rho64, rhobar64, part, tot, total;
+};
+
+__host__ __device__ inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+inline EmLayout em_layout(int N, int K, int Q, int L, int Lw, int G) {
+  (void)N;
+  EmLayout l{};
+  l.G = G;
+  l.Kp1 = K + 1;
+  l.M = (K + 1) * Q;
+  l.Lw = Lw;
+  l.L = L;
+  l.twp = (Lw + 3) & ~3;
+  l.kp4 = (K + 1 + 3) & ~3;
+  l.cols = 2 * l.M + Lw + 2;
+  size_t o = 0;
+  l.ctrl = o;      o = align256(o + sizeof(Ctrl));
+  l.tf32 = o;      o = align256(o + sizeof(float2) * L);
+  l.tf64 = o;      o = align256(o + sizeof(double2) * L);
+  l.tw = o;        o = align256(o + sizeof(float2) * (size_t)l.kp4 * l.twp);
+  l.x32 = o;       o = align256(o + sizeof(float2) * l.M);
+  l.x64 = o;       o = align256(o + sizeof(double2) * l.M);
+  l.inv_den = o;   o = align256(o + sizeof(double) * l.M);
+  l.logrho32 = o;  o = align256(o + sizeof(float) * Lw);
+  l.rho64 = o;     o = align256(o + sizeof(double) * Lw);
+  l.rhobar64 = o;  o = align256(o + sizeof(double) * Lw);
+  l.part = o;      o = align256(o + sizeof(double) * (size_t)l.cols * G);
+  l.tot = o;       o = align256(o + sizeof(double) * (l.cols + 8));
+  l.total = o;
+  return l;
+}
+
+// Device properties cached per device.
+struct DevInfo {
+  int sms;
+  int max_smem_optin;
+};
+int dev_info(DevInfo* out);
+int sweep_grid();  // persistent grid used by the sweep on the current device
+
+}  // namespace mra

@@ -1,0 +1,1281 @@
+// Windowed, prior-weighted EM for 2-D MRA (Algorithm Synch-EM) on sm_103a.
+//
+// One EM iteration is one pass over the observations y (the fused sweep), an
+// FP64 cross-CTA reduction and a one-CTA update:
+//
+//   sweep   per image j (tile of B images staged in shared memory by bulk copies):
+//             c_jk  = sum_q conj(y_jkq) x_kq                     (E-step distance, cross term)
+//             S_jl  = Re sum_k c_jk e^{-i k theta_l}, l in window
+//             s_jl  = log rho_l + (2/sigma^2) S_jl                (Eq. weights_2d_em up to a j-constant)
+//             w_jl  = exp(s_jl - m_j) / Z_j                       (normalisation over the window)
+//             W_jk  = sum_l w_jl e^{+i k theta_l}
+//             num_kq += W_jk y_jkq,  W[l] += w_jl,  sum_j (m_j + log Z_j)   (M-step numerator, W_t)
+//   reduce  FP64 sum of the per-CTA partials (deterministic order)
+//   update  a_{t+1} = num / (N + sigma^2 Gamma^{-1})                   (Eq. coefficients_update)
+//           rho_{t+1} = (W + gamma rho_bar) / sum                       (prior-weighted rho update)
+//           step = min_l ||a_{t+1} - e^{-2 pi i k l / L} a_t||^2          (stopping rule)
+//
+// Alignment by estimated shifts is folded in as a per-(image, k) phase on
+// c_jk and W_jk; y itself is read once per iteration and never rewritten.
+#include <math.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+
+namespace mra {
+
+// ============================================================================ device info
+int dev_info(DevInfo* out) {
+  static DevInfo cache[64];
+  static bool have[64] = {};
+  static std::mutex mu;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return MRA_ECUDA;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!have[dev]) {
+    int sms = 0, smem = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return MRA_ECUDA;
+    if (cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+      return MRA_ECUDA;
+    cache[dev].sms = sms;
+    cache[dev].max_smem_optin = smem;
+    have[dev] = true;
+  }
+  *out = cache[dev];
+  return MRA_OK;
+}
+
+int sweep_grid() {
+  DevInfo d;
+  if (dev_info(&d) != MRA_OK) return -1;
+  return d.sms;  // one persistent CTA per SM (the tile ring fills shared memory)
+}
+
+// ============================================================================ kernels
+struct SetupArgs {
+  int N, Kp1, Q, M, L, Lw, l0, twp, kp4;
+  double sigma2;
+  const double2* x_in;
+  const double* log_rho_in;   // may be null (loglik mode)
+  const double* log_rho_bar;  // may be null
+  const double* gamma_a_inv;  // may be null
+  float2* tf32;
+  double2* tf64;
+  float2* tw;
+  float2* x32;
+  double2* x64;
+  double* inv_den;
+  float* logrho32;
+  double* rho64;
+  double* rhobar64;
+  Ctrl* ctrl;
+};
+
+// Twiddles T[m] = e^{-2 pi i m / L} (FP64 and FP32), the state in FP32/FP64, 1/(N + sigma^2 Gamma^-1).
+__global__ void k_setup(const SetupArgs a) {
+  const int n = max(max(a.L, a.M), a.Lw);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (i < a.L) {
+      double s, c;
+      sincospi(2.0 * (double)i / (double)a.L, &s, &c);
+      a.tf64[i] = make_double2(c, -s);
+      a.tf32[i] = make_float2((float)c, (float)-s);
+    }
+    if (i < a.M) {
+      double2 x = a.x_in[i];
+      a.x64[i] = x;
+      a.x32[i] = make_float2((float)x.x, (float)x.y);
+      double g = a.gamma_a_inv ? a.gamma_a_inv[i] : 0.0;
+      a.inv_den[i] = 1.0 / ((double)a.N + a.sigma2 * g);
+    }
+    if (i < a.Lw) {
+      if (a.log_rho_in) {
+        // same derivation as the update kernel, so that a run resumed from its exported state
+        // continues bit for bit
+        const double lr = a.log_rho_in[i];
+        const double r = exp(lr);
+        a.rho64[i] = r;
+        a.logrho32[i] = r > 1e-30 ? logf((float)r) : (float)lr;
+      }
+      a.rhobar64[i] = a.log_rho_bar ? exp(a.log_rho_bar[i]) : 0.0;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.ctrl->status = MRA_OK;
+    a.ctrl->done = 0;
+    a.ctrl->iter = 0;
+  }
+}
+
+// Window twiddles Tw[k][i] = e^{-i k theta_{l0+i}} = T[(k (l0+i)) mod L], zero padded to [kp4][twp].
+__global__ void k_setup_tw(const SetupArgs a) {
+  const int n = a.kp4 * a.twp;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+    const int k = idx / a.twp, i = idx - k * a.twp;
+    float2 v = make_float2(0.f, 0.f);
+    if (k < a.Kp1 && i < a.Lw) {
+      int off = (a.l0 + i) % a.L;
+      if (off < 0) off += a.L;
+      const int m = (int)(((long long)k * off) % a.L);
+      v = a.tf32[m];
+    }
+    a.tw[idx] = v;
+  }
+}
+
+// log rho_l = kappa cos theta_l + eta_l - log sum exp(...) over the window (one CTA, FP64).
+__global__ void k_setup_vm(int L, int Lw, int l0, double kappa, const double* eta, double* rho64, float* logrho32) {
+  __shared__ double red[32];
+  __shared__ double bc;
+  const int tid = threadIdx.x;
+  double mx = -INFINITY;
+  for (int i = tid; i < Lw; i += blockDim.x) {
+    const double t = kappa * cospi(2.0 * (double)(l0 + i) / (double)L) + eta[i];
+    mx = fmax(mx, t);
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((tid & 31) == 0) red[tid >> 5] = mx;
+  __syncthreads();
+  if (tid == 0) {
+    double m = -INFINITY;
+    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) m = fmax(m, red[w]);
+    bc = m;
+  }
+  __syncthreads();
+  const double m = bc;
+  double s = 0.0;
+  for (int i = tid; i < Lw; i += blockDim.x) s += exp(kappa * cospi(2.0 * (double)(l0 + i) / (double)L) + eta[i] - m);
+  s = warp_sum_d(s);
+  __syncthreads();
+  if ((tid & 31) == 0) red[tid >> 5] = s;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) t += red[w];
+    bc = m + log(t);
+  }
+  __syncthreads();
+  const double lz = bc;
+  for (int i = tid; i < Lw; i += blockDim.x) {
+    const double lr = kappa * cospi(2.0 * (double)(l0 + i) / (double)L) + eta[i] - lz;
+    rho64[i] = exp(lr);
+    logrho32[i] = (float)lr;
+  }
+}
+
+struct SweepArgs {
+  const float2* y;
+  const int* shift;
+  int N, Kp1, Q, M, L, Lw, B;
+  int twp;
+  int slot_bytes;  // bytes per image slot in shared memory
+  int cp;          // row pitch (complex) of the c and W tiles
+  int sp;          // row pitch (floats) of the s / w tile
+  int off_ybuf, off_x, off_tw, off_tf, off_c, off_s, off_w, off_wl, off_lr;
+  float two_beta;
+  const float2* x32;
+  const float2* tw;
+  const float2* tf32;
+  const float* logrho32;
+  double* part;  // [cols][G]
+  int G;
+  float* w_out;  // [N][Lw] or null
+  Ctrl* ctrl;
+};
+
+// One EM sweep.  QEVEN: rows hold an even number of complex values and are
+// read as float4 (two coefficients); NCOL: accumulator columns per thread.
+template <bool QEVEN, int NCOL>
+__global__ void __launch_bounds__(kSweepThreads, 1) k_em_sweep(const SweepArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  if (a.ctrl->done) return;
+  const bool want_ysq = (a.ctrl->iter == 0);
+  constexpr int NT = kSweepThreads;
+  constexpr int VEC = QEVEN ? 2 : 1;  // complex values per accumulator column
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+  unsigned char* ybuf = smem + a.off_ybuf;
+  float2* xs = reinterpret_cast<float2*>(smem + a.off_x);
+  float2* tws = reinterpret_cast<float2*>(smem + a.off_tw);
+  float2* tfs = reinterpret_cast<float2*>(smem + a.off_tf);
+  float2* cs = reinterpret_cast<float2*>(smem + a.off_c);
+  float* ss = reinterpret_cast<float*>(smem + a.off_s);
+  float2* wsm = reinterpret_cast<float2*>(smem + a.off_w);
+  float* wl = reinterpret_cast<float*>(smem + a.off_wl);
+  float* lrs = reinterpret_cast<float*>(smem + a.off_lr);
+
+  const int B = a.B, Kp1 = a.Kp1, Q = a.Q, L = a.L, Lw = a.Lw;
+  const int ntiles = (a.N + B - 1) / B;
+  const int stage_bytes = B * a.slot_bytes;
+  const uint32_t img_bytes = (uint32_t)a.M * 8u;
+
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_barrier_init();
+  }
+  for (int i = tid; i < a.M; i += NT) xs[i] = a.x32[i];
+  {
+    const int kp4 = (Kp1 + 3) & ~3;
+    for (int i = tid; i < kp4 * a.twp; i += NT) tws[i] = a.tw[i];
+  }
+  for (int i = tid; i < L; i += NT) tfs[i] = a.tf32[i];
+  for (int i = tid; i < Lw; i += NT) lrs[i] = a.logrho32[i];
+  for (int i = tid; i < kSweepWarps * Lw; i += NT) wl[i] = 0.f;
+  __syncthreads();
+
+  const int first = blockIdx.x;
+  auto issue = [&](int tile, int s) {
+    const int b0 = tile * B;
+    const int nb = min(B, a.N - b0);
+    mbar_arrive_expect_tx(&bar[s], (uint32_t)nb * img_bytes);
+    unsigned char* dst = ybuf + s * stage_bytes;
+    for (int b = 0; b < nb; ++b)
+      bulk_g2s(dst + b * a.slot_bytes, a.y + (size_t)(b0 + b) * a.M, img_bytes, &bar[s]);
+  };
+  if (tid == 0) {
+    if (first < ntiles) issue(first, 0);
+    if (first + a.G < ntiles) issue(first + a.G, 1);
+  }
+
+  // accumulator columns owned by this thread
+  const int ncols = a.M / VEC;
+  int colf[NCOL], colk[NCOL];
+#pragma unroll
+  for (int c = 0; c < NCOL; ++c) {
+    colf[c] = tid + c * NT;
+    colk[c] = colf[c] < ncols ? (colf[c] * VEC) / Q : 0;
+  }
+  float acc[NCOL][2 * VEC];
+  double acc64[NCOL][2 * VEC];
+#pragma unroll
+  for (int c = 0; c < NCOL; ++c)
+#pragma unroll
+    for (int e = 0; e < 2 * VEC; ++e) acc[c][e] = 0.f, acc64[c][e] = 0.0;
+  double ll_acc = 0.0, ysq_acc = 0.0;
+
+  // item walkers (b fastest so that lanes map to images)
+  const int dB = NT % B, dK = NT / B;
+  const int nlq = (Lw + 3) >> 2, nkq = (Kp1 + 3) >> 2;
+
+  int it = 0;
+  for (;; ++it) {
+    const int tile = first + it * a.G;
+    if (tile >= ntiles) break;
+    const int s = it & 1;
+    const uint32_t parity = (uint32_t)((it >> 1) & 1);
+    const bool ok = mbar_wait_bounded(&bar[s], parity);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        atomicExch(&a.ctrl->status, (int)MRA_ETIMEOUT);
+        mbar_wait_bounded(&bar[s], parity);
+        if (tile + a.G < ntiles) mbar_wait_bounded(&bar[s ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
+      }
+      return;
+    }
+    const int b0 = tile * B;
+    const int nb = min(B, a.N - b0);
+    const unsigned char* yb = ybuf + s * stage_bytes;
+
+    // ---- P1: c_jk = sum_q conj(y_jkq) x_kq, folded with e^{-i k theta_hat_j}
+    {
+      int b = tid % B, k = tid / B;
+      float ysq_f = 0.f;
+      for (int i = tid; i < B * Kp1; i += NT) {
+        if (b < nb) {
+          float cr = 0.f, ci = 0.f, sq = 0.f;
+          const float2* yr = reinterpret_cast<const float2*>(yb + b * a.slot_bytes) + k * Q;
+          const float2* xr = xs + k * Q;
+          if constexpr (QEVEN) {
+            const float4* y4 = reinterpret_cast<const float4*>(yr);
+            const float4* x4 = reinterpret_cast<const float4*>(xr);
+            if (want_ysq) {
+              for (int p = 0; p < Q / 2; ++p) {
+                const float4 yv = y4[p], xv = x4[p];
+                cr = fmaf(yv.x, xv.x, cr); cr = fmaf(yv.y, xv.y, cr);
+                ci = fmaf(yv.x, xv.y, ci); ci = fmaf(-yv.y, xv.x, ci);
+                cr = fmaf(yv.z, xv.z, cr); cr = fmaf(yv.w, xv.w, cr);
+                ci = fmaf(yv.z, xv.w, ci); ci = fmaf(-yv.w, xv.z, ci);
+                sq = fmaf(yv.x, yv.x, sq); sq = fmaf(yv.y, yv.y, sq);
+                sq = fmaf(yv.z, yv.z, sq); sq = fmaf(yv.w, yv.w, sq);
+              }
+            } else {
+              for (int p = 0; p < Q / 2; ++p) {
+                const float4 yv = y4[p], xv = x4[p];
+                cr = fmaf(yv.x, xv.x, cr); cr = fmaf(yv.y, xv.y, cr);
+                ci = fmaf(yv.x, xv.y, ci); ci = fmaf(-yv.y, xv.x, ci);
+                cr = fmaf(yv.z, xv.z, cr); cr = fmaf(yv.w, xv.w, cr);
+                ci = fmaf(yv.z, xv.w, ci); ci = fmaf(-yv.w, xv.z, ci);
+              }
+            }
+          } else {
+            for (int q = 0; q < Q; ++q) {
+              const float2 yv = yr[q], xv = xr[q];
+              cr = fmaf(yv.x, xv.x, cr); cr = fmaf(yv.y, xv.y, cr);
+              ci = fmaf(yv.x, xv.y, ci); ci = fmaf(-yv.y, xv.x, ci);
+              sq = fmaf(yv.x, yv.x, sq); sq = fmaf(yv.y, yv.y, sq);
+            }
+          }
+          float2 c = make_float2(cr, ci);
+          if (a.shift) {
+            int sj = a.shift[b0 + b] % L;
+            if (sj < 0) sj += L;
+            c = cmul(c, tfs[(k * sj) % L]);
+          }
+          cs[b * a.cp + k] = c;
+          ysq_f += sq;
+        }
+        b += dB;
+        k += dK;
+        if (b >= B) { b -= B; ++k; }
+      }
+      if (want_ysq) ysq_acc += (double)ysq_f;
+    }
+    __syncthreads();
+
+    // ---- P2: s_jl = log rho_l + 2 beta Re sum_k c_jk Tw[k][l], four window offsets per item
+    {
+      int b = tid % B, lq = tid / B;
+      for (int i = tid; i < B * nlq; i += NT) {
+        if (b < nb) {
+          float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+          const float2* cr = cs + b * a.cp;
+          const float2* tcol = tws + 4 * lq;
+          for (int k = 0; k < Kp1; ++k) {
+            const float2 c = cr[k];
+            const float4 t01 = *reinterpret_cast<const float4*>(tcol + k * a.twp);
+            const float4 t23 = *reinterpret_cast<const float4*>(tcol + k * a.twp + 2);
+            s0 = fmaf(c.x, t01.x, s0); s0 = fmaf(-c.y, t01.y, s0);
+            s1 = fmaf(c.x, t01.z, s1); s1 = fmaf(-c.y, t01.w, s1);
+            s2 = fmaf(c.x, t23.x, s2); s2 = fmaf(-c.y, t23.y, s2);
+            s3 = fmaf(c.x, t23.z, s3); s3 = fmaf(-c.y, t23.w, s3);
+          }
+          float* srow = ss + b * a.sp;
+          const int l = 4 * lq;
+          srow[l] = fmaf(a.two_beta, s0, lrs[l]);
+          if (l + 1 < Lw) srow[l + 1] = fmaf(a.two_beta, s1, lrs[l + 1]);
+          if (l + 2 < Lw) srow[l + 2] = fmaf(a.two_beta, s2, lrs[l + 2]);
+          if (l + 3 < Lw) srow[l + 3] = fmaf(a.two_beta, s3, lrs[l + 3]);
+        }
+        b += dB;
+        lq += dK;
+        if (b >= B) { b -= B; ++lq; }
+      }
+    }
+    __syncthreads();
+
+    // ---- P3: normalise over the window (one warp per image)
+    for (int b = warp; b < nb; b += kSweepWarps) {
+      float* srow = ss + b * a.sp;
+      float m = -INFINITY;
+      for (int l = lane; l < Lw; l += 32) m = fmaxf(m, srow[l]);
+      m = warp_max(m);
+      float z = 0.f;
+      for (int l = lane; l < Lw; l += 32) {
+        const float e = expf(srow[l] - m);
+        srow[l] = e;
+        z += e;
+      }
+      z = warp_sum(z);
+      const float inv = 1.f / z;
+      float* wlw = wl + warp * Lw;
+      float* wo = a.w_out ? a.w_out + (size_t)(b0 + b) * Lw : nullptr;
+      for (int l = lane; l < Lw; l += 32) {
+        const float w = srow[l] * inv;
+        srow[l] = w;
+        wlw[l] += w;
+        if (wo) wo[l] = w;
+      }
+      if (lane == 0) ll_acc += (double)m + (double)logf(z);
+    }
+    __syncthreads();
+
+    // ---- P4: W_jk = sum_l w_jl conj(Tw[k][l]), folded with e^{+i k theta_hat_j}, four k per item
+    {
+      int b = tid % B, kq = tid / B;
+      for (int i = tid; i < B * nkq; i += NT) {
+        if (b < nb) {
+          float2 w0 = make_float2(0.f, 0.f), w1 = w0, w2 = w0, w3 = w0;
+          const float* srow = ss + b * a.sp;
+          const int k0 = 4 * kq;
+          const float2* t0 = tws + k0 * a.twp;
+          const float2* t1 = t0 + a.twp;
+          const float2* t2 = t1 + a.twp;
+          const float2* t3 = t2 + a.twp;
+          for (int l = 0; l < Lw; ++l) {
+            const float w = srow[l];
+            const float2 ta = t0[l], tb = t1[l], tc = t2[l], td = t3[l];
+            w0.x = fmaf(w, ta.x, w0.x); w0.y = fmaf(-w, ta.y, w0.y);
+            w1.x = fmaf(w, tb.x, w1.x); w1.y = fmaf(-w, tb.y, w1.y);
+            w2.x = fmaf(w, tc.x, w2.x); w2.y = fmaf(-w, tc.y, w2.y);
+            w3.x = fmaf(w, td.x, w3.x); w3.y = fmaf(-w, td.y, w3.y);
+          }
+          if (a.shift) {
+            int sj = a.shift[b0 + b] % L;
+            if (sj < 0) sj += L;
+            w0 = cmul_conj_b(w0, tfs[(k0 * sj) % L]);
+            w1 = cmul_conj_b(w1, tfs[((k0 + 1) * sj) % L]);
+            w2 = cmul_conj_b(w2, tfs[((k0 + 2) * sj) % L]);
+            w3 = cmul_conj_b(w3, tfs[((k0 + 3) * sj) % L]);
+          }
+          float2* wrow = wsm + b * a.cp;
+          if (k0 < Kp1) wrow[k0] = w0;
+          if (k0 + 1 < Kp1) wrow[k0 + 1] = w1;
+          if (k0 + 2 < Kp1) wrow[k0 + 2] = w2;
+          if (k0 + 3 < Kp1) wrow[k0 + 3] = w3;
+        }
+        b += dB;
+        kq += dK;
+        if (b >= B) { b -= B; ++kq; }
+      }
+    }
+    __syncthreads();
+
+    // ---- P5: num_kq += W_jk y_jkq over the tile
+    for (int b = 0; b < nb; ++b) {
+      const unsigned char* yimg = yb + b * a.slot_bytes;
+      const float2* wrow = wsm + b * a.cp;
+#pragma unroll
+      for (int c = 0; c < NCOL; ++c) {
+        if (colf[c] < ncols) {
+          const float2 W = wrow[colk[c]];
+          if constexpr (QEVEN) {
+            const float4 yv = reinterpret_cast<const float4*>(yimg)[colf[c]];
+            acc[c][0] = fmaf(W.x, yv.x, acc[c][0]); acc[c][0] = fmaf(-W.y, yv.y, acc[c][0]);
+            acc[c][1] = fmaf(W.x, yv.y, acc[c][1]); acc[c][1] = fmaf(W.y, yv.x, acc[c][1]);
+            acc[c][2] = fmaf(W.x, yv.z, acc[c][2]); acc[c][2] = fmaf(-W.y, yv.w, acc[c][2]);
+            acc[c][3] = fmaf(W.x, yv.w, acc[c][3]); acc[c][3] = fmaf(W.y, yv.z, acc[c][3]);
+          } else {
+            const float2 yv = reinterpret_cast<const float2*>(yimg)[colf[c]];
+            acc[c][0] = fmaf(W.x, yv.x, acc[c][0]); acc[c][0] = fmaf(-W.y, yv.y, acc[c][0]);
+            acc[c][1] = fmaf(W.x, yv.y, acc[c][1]); acc[c][1] = fmaf(W.y, yv.x, acc[c][1]);
+          }
+        }
+      }
+    }
+    if ((it & 15) == 15) {  // fold the FP32 tile sums into FP64 every 16 tiles
+#pragma unroll
+      for (int c = 0; c < NCOL; ++c)
+#pragma unroll
+        for (int e = 0; e < 2 * VEC; ++e) acc64[c][e] += (double)acc[c][e], acc[c][e] = 0.f;
+    }
+    __syncthreads();  // every thread is done with stage s
+    if (tid == 0 && tile + 2 * a.G < ntiles) issue(tile + 2 * a.G, s);
+  }
+
+  // ---- per-CTA partials, column-major [col][G]
+#pragma unroll
+  for (int c = 0; c < NCOL; ++c)
+#pragma unroll
+    for (int e = 0; e < 2 * VEC; ++e) acc64[c][e] += (double)acc[c][e];
+  const int G = a.G, cta = blockIdx.x;
+#pragma unroll
+  for (int c = 0; c < NCOL; ++c) {
+    if (colf[c] < ncols) {
+      const int base = 2 * VEC * colf[c];  // first real column of this accumulator
+#pragma unroll
+      for (int e = 0; e < 2 * VEC; ++e) a.part[(size_t)(base + e) * G + cta] = acc64[c][e];
+    }
+  }
+  __syncthreads();
+  for (int l = tid; l < Lw; l += NT) {
+    double s = 0.0;
+    for (int w = 0; w < kSweepWarps; ++w) s += (double)wl[w * Lw + l];
+    a.part[(size_t)(2 * a.M + l) * G + cta] = s;
+  }
+  __shared__ double red[2][kSweepWarps];
+  ll_acc = warp_sum_d(ll_acc);
+  ysq_acc = warp_sum_d(ysq_acc);
+  if (lane == 0) red[0][warp] = ll_acc, red[1][warp] = ysq_acc;
+  __syncthreads();
+  if (tid == 0) {
+    double t0 = 0.0, t1 = 0.0;
+    for (int w = 0; w < kSweepWarps; ++w) t0 += red[0][w], t1 += red[1][w];
+    a.part[(size_t)(2 * a.M + Lw) * G + cta] = t0;
+    a.part[(size_t)(2 * a.M + Lw + 1) * G + cta] = t1;
+  }
+}
+
+// tot[col] = sum_g part[col][g] in FP64, one warp per column, fixed summation order.
+__global__ void k_reduce_cols(const double* part, int G, int cols, double* tot, const Ctrl* ctrl) {
+  if (ctrl && ctrl->done) return;
+  const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (col >= cols) return;
+  const double* p = part + (size_t)col * G;
+  double s = 0.0;
+  for (int g = lane; g < G; g += 32) s += p[g];
+  s = warp_sum_d(s);
+  if (lane == 0) tot[col] = s;
+}
+
+struct UpdateArgs {
+  int N, Kp1, Q, M, L, Lw;
+  double sigma2, beta, gamma, tol;
+  int update_rho, max_iters;
+  const double* tot;  // [cols + 8]; tot[cols] keeps sum_j ||y_j||^2 from the first iteration
+  int cols;
+  double2* x64;
+  float2* x32;
+  const double* inv_den;
+  double* rho64;
+  float* logrho32;
+  const double* rhobar64;
+  const double2* tf64;
+  const float2* tf32;
+  Ctrl* ctrl;
+  double* stats;    // [T][2] or null
+  double2* x_traj;  // [T][M] or null
+  double2* x_out;
+  double* log_rho_out;
+  double* loglik_out;
+  double* step_out;
+};
+
+__device__ __forceinline__ double block_sum_d(double v, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = warp_sum_d(v);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  const int nw = (blockDim.x + 31) >> 5;
+  for (int w = 0; w < nw; ++w) t += red[w];
+  return t;
+}
+
+// One CTA: a_{t+1}, rho_{t+1}, log-likelihood at a_t, step; state update.
+__global__ void k_update(const UpdateArgs a) {
+  extern __shared__ __align__(16) unsigned char usmem[];
+  if (a.ctrl->done) return;
+  double2* xn = reinterpret_cast<double2*>(usmem);                  // [M]
+  double2* dk = xn + a.M;                                            // [Kp1]
+  float* sc = reinterpret_cast<float*>(dk + a.Kp1);                  // [L]
+  __shared__ double red[32];
+  __shared__ float fred[32];
+  __shared__ double ysq_total;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int iter = a.ctrl->iter;
+
+  double nx_old = 0.0, nx_new = 0.0;
+  for (int e = tid; e < a.M; e += nt) {
+    const double2 xo = a.x64[e];
+    const double2 v = make_double2(a.tot[2 * e] * a.inv_den[e], a.tot[2 * e + 1] * a.inv_den[e]);
+    xn[e] = v;
+    nx_old += xo.x * xo.x + xo.y * xo.y;
+    nx_new += v.x * v.x + v.y * v.y;
+  }
+  nx_old = block_sum_d(nx_old, red);
+  nx_new = block_sum_d(nx_new, red);
+  if (tid == 0) {
+    double* keep = const_cast<double*>(a.tot) + a.cols;
+    if (iter == 0) keep[0] = a.tot[2 * a.M + a.Lw + 1];
+    ysq_total = keep[0];
+  }
+  // d_k = sum_q conj(a_{t+1,kq}) a_{t,kq}
+  for (int k = tid; k < a.Kp1; k += nt) {
+    double2 d = make_double2(0.0, 0.0);
+    for (int q = 0; q < a.Q; ++q) {
+      const double2 u = xn[k * a.Q + q], v = a.x64[k * a.Q + q];
+      d.x += u.x * v.x + u.y * v.y;
+      d.y += u.x * v.y - u.y * v.x;
+    }
+    dk[k] = d;
+  }
+  __syncthreads();
+  const double ll = a.tot[2 * a.M + a.Lw] - a.beta * ysq_total - (double)a.N * a.beta * nx_old -
+                    (double)a.N * (double)a.M * log(kPi * a.sigma2);
+
+  // rho update
+  if (a.update_rho) {
+    double v = 0.0;
+    for (int l = tid; l < a.Lw; l += nt) v += a.tot[2 * a.M + l] + a.gamma * a.rhobar64[l];
+    const double tsum = block_sum_d(v, red);
+    for (int l = tid; l < a.Lw; l += nt) {
+      const double r = (a.tot[2 * a.M + l] + a.gamma * a.rhobar64[l]) / tsum;
+      a.rho64[l] = r;
+      a.logrho32[l] = r > 1e-30 ? logf((float)r) : (float)log(r);
+      if (a.log_rho_out) a.log_rho_out[l] = log(r);
+    }
+  } else if (a.log_rho_out) {
+    for (int l = tid; l < a.Lw; l += nt) a.log_rho_out[l] = log(a.rho64[l]);
+  }
+
+  // step: FP32 scan of score(l) = Re sum_k d_k e^{-2 pi i k l/L}, FP64 at the near-maximal candidates
+  float dmag = 0.f;
+  for (int k = 0; k < a.Kp1; ++k) dmag += fabsf((float)dk[k].x) + fabsf((float)dk[k].y);
+  float best = -INFINITY;
+  for (int l = tid; l < a.L; l += nt) {
+    float s = 0.f;
+    int m = 0;
+    for (int k = 0; k < a.Kp1; ++k) {
+      const float2 t = a.tf32[m];
+      s = fmaf((float)dk[k].x, t.x, s);
+      s = fmaf(-(float)dk[k].y, t.y, s);
+      m += l;
+      if (m >= a.L) m -= a.L;
+    }
+    sc[l] = s;
+    best = fmaxf(best, s);
+  }
+  best = warp_max(best);
+  __syncthreads();
+  if ((tid & 31) == 0) fred[tid >> 5] = best;
+  __syncthreads();
+  float gbest = -INFINITY;
+  for (int w = 0; w < (nt + 31) / 32; ++w) gbest = fmaxf(gbest, fred[w]);
+  const float thr = gbest - (1e-5f * dmag + 1e-30f);
+  double dmin = INFINITY;
+  for (int l = tid; l < a.L; l += nt) {
+    if (sc[l] >= thr) {
+      double s = 0.0;
+      int m = 0;
+      for (int k = 0; k < a.Kp1; ++k) {
+        const double2 t = a.tf64[m];
+        s += dk[k].x * t.x - dk[k].y * t.y;
+        m += l;
+        if (m >= a.L) m -= a.L;
+      }
+      dmin = fmin(dmin, nx_new + nx_old - 2.0 * s);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) dmin = fmin(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
+  __syncthreads();
+  if ((tid & 31) == 0) red[tid >> 5] = dmin;
+  __syncthreads();
+  double step = INFINITY;
+  for (int w = 0; w < (nt + 31) / 32; ++w) step = fmin(step, red[w]);
+  step = fmax(step, 0.0);
+
+  // state
+  for (int e = tid; e < a.M; e += nt) {
+    const double2 v = xn[e];
+    a.x64[e] = v;
+    a.x32[e] = make_float2((float)v.x, (float)v.y);
+    if (a.x_traj) a.x_traj[(size_t)iter * a.M + e] = v;
+    if (a.x_out) a.x_out[e] = v;
+  }
+  if (tid == 0) {
+    if (a.stats) {
+      a.stats[2 * iter] = ll;
+      a.stats[2 * iter + 1] = step;
+    }
+    if (a.loglik_out) *a.loglik_out = ll;
+    if (a.step_out) *a.step_out = step;
+    const int nit = iter + 1;
+    a.ctrl->iter = nit;
+    if ((a.tol > 0.0 && step < a.tol) || nit >= a.max_iters) a.ctrl->done = 1;
+  }
+}
+
+// em_run epilogue: final state out.
+__global__ void k_export(int M, int Lw, const double2* x64, const double* rho64, double2* x_out, double* log_rho_out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < max(M, Lw); i += gridDim.x * blockDim.x) {
+    if (i < M) x_out[i] = x64[i];
+    if (i < Lw) log_rho_out[i] = log(rho64[i]);
+  }
+}
+
+struct GradArgs {
+  int N, M, L, Lw, l0;
+  double sigma2, beta, kappa;
+  const double* tot;
+  int cols;
+  const double2* x64;
+  const double* rho64;
+  double* loglik_out;
+  double2* dx_out;
+  double* dlogits_out;
+  double* dkappa_out;
+};
+
+__global__ void k_grad(const GradArgs a) {
+  __shared__ double red[32];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  double nx = 0.0;
+  for (int e = tid; e < a.M; e += nt) {
+    const double2 x = a.x64[e];
+    nx += x.x * x.x + x.y * x.y;
+    if (a.dx_out)
+      a.dx_out[e] = make_double2(2.0 * a.beta * (a.tot[2 * e] - a.N * x.x), 2.0 * a.beta * (a.tot[2 * e + 1] - a.N * x.y));
+  }
+  nx = block_sum_d(nx, red);
+  double dk = 0.0;
+  for (int l = tid; l < a.Lw; l += nt) {
+    const double g = a.tot[2 * a.M + l] - (double)a.N * a.rho64[l];
+    if (a.dlogits_out) a.dlogits_out[l] = g;
+    dk += g * cospi(2.0 * (double)(a.l0 + l) / (double)a.L);
+  }
+  dk = block_sum_d(dk, red);
+  if (tid == 0) {
+    if (a.dkappa_out) *a.dkappa_out = dk;
+    if (a.loglik_out)
+      *a.loglik_out = a.tot[2 * a.M + a.Lw] - a.beta * a.tot[2 * a.M + a.Lw + 1] - (double)a.N * a.beta * nx -
+                      (double)a.N * (double)a.M * log(kPi * a.sigma2);
+  }
+}
+
+// ---- align and average: partial sums of y_j e^{+i k theta_hat_j} per CTA
+template <bool QEVEN, int NCOL>
+__global__ void __launch_bounds__(kSweepThreads) k_align_partial(const float2* y, const int* shift, int N, int M, int Q,
+                                                                  int L, const float2* tf32, double* part, int G) {
+  constexpr int VEC = QEVEN ? 2 : 1;
+  const int tid = threadIdx.x, ncols = M / VEC;
+  float acc[NCOL][2 * VEC];
+  double acc64[NCOL][2 * VEC];
+#pragma unroll
+  for (int c = 0; c < NCOL; ++c)
+#pragma unroll
+    for (int e = 0; e < 2 * VEC; ++e) acc[c][e] = 0.f, acc64[c][e] = 0.0;
+  int cnt = 0;
+  for (int j = blockIdx.x; j < N; j += G) {
+    int sj = shift ? shift[j] % L : 0;
+    if (sj < 0) sj += L;
+#pragma unroll
+    for (int c = 0; c < NCOL; ++c) {
+      const int f = tid + c * kSweepThreads;
+      if (f < ncols) {
+        const int k = (f * VEC) / Q;
+        const float2 t = tf32[(k * sj) % L];  // conj(t) = e^{+i k theta_hat_j}
+        if constexpr (QEVEN) {
+          const float4 v = reinterpret_cast<const float4*>(y + (size_t)j * M)[f];
+          acc[c][0] += v.x * t.x + v.y * t.y;
+          acc[c][1] += v.y * t.x - v.x * t.y;
+          acc[c][2] += v.z * t.x + v.w * t.y;
+          acc[c][3] += v.w * t.x - v.z * t.y;
+        } else {
+          const float2 v = y[(size_t)j * M + f];
+          acc[c][0] += v.x * t.x + v.y * t.y;
+          acc[c][1] += v.y * t.x - v.x * t.y;
+        }
+      }
+    }
+    if (++cnt == 32) {
+      cnt = 0;
+#pragma unroll
+      for (int c = 0; c < NCOL; ++c)
+#pragma unroll
+        for (int e = 0; e < 2 * VEC; ++e) acc64[c][e] += (double)acc[c][e], acc[c][e] = 0.f;
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < NCOL; ++c) {
+    const int f = tid + c * kSweepThreads;
+    if (f < ncols) {
+#pragma unroll
+      for (int e = 0; e < 2 * VEC; ++e) part[(size_t)(2 * VEC * f + e) * G + blockIdx.x] = acc64[c][e] + (double)acc[c][e];
+    }
+  }
+}
+
+__global__ void k_scale_out(int M, const double* tot, double inv, double2* x_out) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < M; e += gridDim.x * blockDim.x)
+    x_out[e] = make_double2(tot[2 * e] * inv, tot[2 * e + 1] * inv);
+}
+
+// Algorithm 1 centring: c = argmax_s Re sum_k g_k e^{-2 pi i k s/L}, g_k = sum_q xbar_kq conj(x_kq)  (FP64, one CTA)
+__global__ void k_center(int Kp1, int Q, int L, const double* tot, double invN, const double2* x_true,
+                         const double2* tf64, int* center_ws, int* center_out) {
+  extern __shared__ __align__(16) unsigned char csm[];
+  double2* g = reinterpret_cast<double2*>(csm);
+  __shared__ double rv[32];
+  __shared__ int ri[32];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int k = tid; k < Kp1; k += nt) {
+    double2 s = make_double2(0.0, 0.0);
+    for (int q = 0; q < Q; ++q) {
+      const int e = k * Q + q;
+      const double2 xb = make_double2(tot[2 * e] * invN, tot[2 * e + 1] * invN);
+      const double2 x = x_true[e];
+      s.x += xb.x * x.x + xb.y * x.y;
+      s.y += xb.y * x.x - xb.x * x.y;
+    }
+    g[k] = s;
+  }
+  __syncthreads();
+  double best = -INFINITY;
+  int bi = 0x7fffffff;
+  for (int l = tid; l < L; l += nt) {
+    double s = 0.0;
+    int m = 0;
+    for (int k = 0; k < Kp1; ++k) {
+      const double2 t = tf64[m];
+      s += g[k].x * t.x - g[k].y * t.y;
+      m += l;
+      if (m >= L) m -= L;
+    }
+    if (s > best || (s == best && l < bi)) best = s, bi = l;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ov > best || (ov == best && oi < bi)) best = ov, bi = oi;
+  }
+  if ((tid & 31) == 0) rv[tid >> 5] = best, ri[tid >> 5] = bi;
+  __syncthreads();
+  if (tid == 0) {
+    double b = rv[0];
+    int i = ri[0];
+    for (int w = 1; w < (nt + 31) / 32; ++w)
+      if (rv[w] > b || (rv[w] == b && ri[w] < i)) b = rv[w], i = ri[w];
+    *center_ws = i;
+    if (center_out) *center_out = i;
+  }
+}
+
+__global__ void k_hist(int N, int L, const int* s_true, const int* s_est, const int* center, int* hist) {
+  const int c = *center;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x) {
+    long long r = ((long long)s_true[j] - (long long)s_est[j] + c) % L;
+    if (r < 0) r += L;
+    atomicAdd(hist + r, 1);
+  }
+}
+
+// ============================================================================ host side
+namespace {
+
+struct SweepPlan {
+  int B, slot_bytes, cp, sp, smem;
+  int off_ybuf, off_x, off_tw, off_tf, off_c, off_s, off_w, off_wl, off_lr;
+};
+
+inline int al16(int v) { return (v + 15) & ~15; }
+
+// Shared-memory plan of the sweep: the largest tile (<= 32 images) whose two stages fit.
+bool plan_sweep(int Kp1, int Q, int L, int Lw, int max_smem, SweepPlan* p) {
+  const int M = Kp1 * Q;
+  int slot = al16(M * 8);
+  if (((slot / 16) & 1) == 0) slot += 16;  // odd number of 16-byte units: conflict-free across images
+  const int cp = (Kp1 & 1) ? Kp1 : Kp1 + 1;
+  const int sp = (Lw & 1) ? Lw : Lw + 1;
+  const int kp4 = (Kp1 + 3) & ~3, twp = (Lw + 3) & ~3;
+  for (int B = 32; B >= 1; --B) {
+    int o = 128;  // two mbarriers
+    p->off_ybuf = o; o += 2 * B * slot;
+    p->off_x = o; o += al16(M * 8);
+    p->off_tw = o; o += al16(kp4 * twp * 8);
+    p->off_tf = o; o += al16(L * 8);
+    p->off_c = o; o += al16(B * cp * 8);
+    p->off_s = o; o += al16(B * sp * 4);
+    p->off_w = o; o += al16(B * cp * 8);
+    p->off_wl = o; o += al16(kSweepWarps * Lw * 4);
+    p->off_lr = o; o += al16(Lw * 4);
+    if (o + 1024 <= max_smem) {  // leave room for the static reduction scratch
+      p->B = B;
+      p->slot_bytes = slot;
+      p->cp = cp;
+      p->sp = sp;
+      p->smem = o;
+      return true;
+    }
+  }
+  return false;
+}
+
+typedef void (*SweepFn)(const SweepArgs);
+
+SweepFn pick_sweep(bool qeven, int ncolmax) {
+  if (qeven) {
+    if (ncolmax <= 1) return k_em_sweep<true, 1>;
+    if (ncolmax <= 2) return k_em_sweep<true, 2>;
+    if (ncolmax <= 4) return k_em_sweep<true, 4>;
+    if (ncolmax <= 8) return k_em_sweep<true, 8>;
+    return nullptr;
+  }
+  if (ncolmax <= 1) return k_em_sweep<false, 1>;
+  if (ncolmax <= 2) return k_em_sweep<false, 2>;
+  if (ncolmax <= 4) return k_em_sweep<false, 4>;
+  if (ncolmax <= 8) return k_em_sweep<false, 8>;
+  return nullptr;
+}
+
+bool ptr_ok(const void* p, size_t align) { return p != nullptr && (reinterpret_cast<uintptr_t>(p) % align) == 0; }
+
+int check_dims(const mra_dims* d) {
+  if (!d) return MRA_EINVAL;
+  if (d->N < 1 || d->K < 0 || d->Q < 1 || d->L < 1) return MRA_EINVAL;
+  if (!(d->sigma2 > 0.0) || !isfinite(d->sigma2)) return MRA_EINVAL;
+  const long long M = (long long)(d->K + 1) * d->Q;
+  if (M % 2 != 0 || M > 4096) return MRA_EINVAL;
+  if ((long long)d->N * M > (1ll << 40)) return MRA_EINVAL;
+  return MRA_OK;
+}
+
+// Everything one EM-type call needs on the host.
+struct EmCall {
+  EmLayout lay;
+  SweepPlan plan;
+  SweepFn sweep;
+  SweepArgs sa;
+  SetupArgs su;
+  UpdateArgs ua;
+  Ctrl* ctrl;
+  double* tot;
+  int reduce_blocks;
+  int update_smem;
+};
+
+int prepare(const mra_dims* d, int Lw, int l0, const float* y, const int32_t* shift, void* ws, size_t ws_bytes,
+            EmCall* c) {
+  int st = check_dims(d);
+  if (st != MRA_OK) return st;
+  if (Lw < 1 || Lw > d->L) return MRA_EINVAL;
+  if (!ptr_ok(y, 16) || !ptr_ok(ws, 256)) return MRA_EINVAL;
+  if (shift && !ptr_ok(shift, 4)) return MRA_EINVAL;
+  DevInfo di;
+  if ((st = dev_info(&di)) != MRA_OK) return st;
+  const int G = di.sms;
+  c->lay = em_layout(d->N, d->K, d->Q, d->L, Lw, G);
+  if (ws_bytes < c->lay.total) return MRA_EWORKSPACE;
+  const int Kp1 = d->K + 1, M = Kp1 * d->Q;
+  if (!plan_sweep(Kp1, d->Q, d->L, Lw, di.max_smem_optin, &c->plan)) return MRA_EINVAL;
+  const bool qeven = (d->Q % 2) == 0;
+  const int vec = qeven ? 2 : 1;
+  const int ncolmax = (M / vec + kSweepThreads - 1) / kSweepThreads;
+  c->sweep = pick_sweep(qeven, ncolmax);
+  if (!c->sweep) return MRA_EINVAL;
+  if (cudaFuncSetAttribute(reinterpret_cast<const void*>(c->sweep), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           c->plan.smem) != cudaSuccess)
+    return MRA_ECUDA;
+  unsigned char* base = static_cast<unsigned char*>(ws);
+  const EmLayout& L_ = c->lay;
+  c->ctrl = reinterpret_cast<Ctrl*>(base + L_.ctrl);
+  c->tot = reinterpret_cast<double*>(base + L_.tot);
+
+  SweepArgs& s = c->sa;
+  s.y = reinterpret_cast<const float2*>(y);
+  s.shift = shift;
+  s.N = d->N; s.Kp1 = Kp1; s.Q = d->Q; s.M = M; s.L = d->L; s.Lw = Lw; s.B = c->plan.B;
+  s.twp = L_.twp;
+  s.slot_bytes = c->plan.slot_bytes; s.cp = c->plan.cp; s.sp = c->plan.sp;
+  s.off_ybuf = c->plan.off_ybuf; s.off_x = c->plan.off_x; s.off_tw = c->plan.off_tw; s.off_tf = c->plan.off_tf;
+  s.off_c = c->plan.off_c; s.off_s = c->plan.off_s; s.off_w = c->plan.off_w; s.off_wl = c->plan.off_wl;
+  s.off_lr = c->plan.off_lr;
+  s.two_beta = (float)(2.0 / d->sigma2);
+  s.x32 = reinterpret_cast<const float2*>(base + L_.x32);
+  s.tw = reinterpret_cast<const float2*>(base + L_.tw);
+  s.tf32 = reinterpret_cast<const float2*>(base + L_.tf32);
+  s.logrho32 = reinterpret_cast<const float*>(base + L_.logrho32);
+  s.part = reinterpret_cast<double*>(base + L_.part);
+  s.G = G;
+  s.w_out = nullptr;
+  s.ctrl = c->ctrl;
+
+  SetupArgs& u = c->su;
+  u.N = d->N; u.Kp1 = Kp1; u.Q = d->Q; u.M = M; u.L = d->L; u.Lw = Lw;
+  u.l0 = l0; u.twp = L_.twp; u.kp4 = L_.kp4; u.sigma2 = d->sigma2;
+  u.x_in = nullptr; u.log_rho_in = nullptr; u.log_rho_bar = nullptr; u.gamma_a_inv = nullptr;
+  u.tf32 = reinterpret_cast<float2*>(base + L_.tf32);
+  u.tf64 = reinterpret_cast<double2*>(base + L_.tf64);
+  u.tw = reinterpret_cast<float2*>(base + L_.tw);
+  u.x32 = reinterpret_cast<float2*>(base + L_.x32);
+  u.x64 = reinterpret_cast<double2*>(base + L_.x64);
+  u.inv_den = reinterpret_cast<double*>(base + L_.inv_den);
+  u.logrho32 = reinterpret_cast<float*>(base + L_.logrho32);
+  u.rho64 = reinterpret_cast<double*>(base + L_.rho64);
+  u.rhobar64 = reinterpret_cast<double*>(base + L_.rhobar64);
+  u.ctrl = c->ctrl;
+
+  UpdateArgs& up = c->ua;
+  up.N = d->N; up.Kp1 = Kp1; up.Q = d->Q; up.M = M; up.L = d->L; up.Lw = Lw;
+  up.sigma2 = d->sigma2; up.beta = 1.0 / d->sigma2; up.gamma = 0.0; up.tol = 0.0;
+  up.update_rho = 0; up.max_iters = 1 << 30;
+  up.tot = c->tot; up.cols = L_.cols;
+  up.x64 = u.x64; up.x32 = u.x32; up.inv_den = u.inv_den; up.rho64 = u.rho64; up.logrho32 = u.logrho32;
+  up.rhobar64 = u.rhobar64; up.tf64 = u.tf64; up.tf32 = u.tf32; up.ctrl = c->ctrl;
+  up.stats = nullptr; up.x_traj = nullptr; up.x_out = nullptr; up.log_rho_out = nullptr;
+  up.loglik_out = nullptr; up.step_out = nullptr;
+  c->update_smem = M * 16 + Kp1 * 16 + d->L * 4 + 64;
+  if (c->update_smem > 48 * 1024 &&
+      cudaFuncSetAttribute(reinterpret_cast<const void*>(k_update), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           c->update_smem) != cudaSuccess)
+    return MRA_ECUDA;
+  c->reduce_blocks = (L_.cols + 7) / 8;
+  return MRA_OK;
+}
+
+int launch_setup(const EmCall& c, cudaStream_t st) {
+  const int n = std::max(std::max(c.su.L, c.su.M), c.su.Lw);
+  const int blocks = std::min(1024, (n + 127) / 128);
+  k_setup<<<blocks, 128, 0, st>>>(c.su);
+  const int ntw = c.su.kp4 * c.su.twp;
+  k_setup_tw<<<std::min(1024, (ntw + 255) / 256), 256, 0, st>>>(c.su);
+  return cudaGetLastError() == cudaSuccess ? MRA_OK : MRA_ECUDA;
+}
+
+int launch_iteration(const EmCall& c, cudaStream_t st, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr) {
+  if (ev0 && cudaEventRecord(ev0, st) != cudaSuccess) return MRA_ECUDA;
+  c.sweep<<<c.lay.G, kSweepThreads, c.plan.smem, st>>>(c.sa);
+  if (ev1 && cudaEventRecord(ev1, st) != cudaSuccess) return MRA_ECUDA;
+  k_reduce_cols<<<c.reduce_blocks, 256, 0, st>>>(c.sa.part, c.lay.G, c.lay.cols, c.tot, c.ctrl);
+  k_update<<<1, 256, c.update_smem, st>>>(c.ua);
+  return cudaGetLastError() == cudaSuccess ? MRA_OK : MRA_ECUDA;
+}
+
+int check_params(const mra_dims* d, const mra_em_params* p) {
+  if (!p) return MRA_EINVAL;
+  if (p->Lw < 1 || p->Lw > d->L) return MRA_EINVAL;
+  if (!(p->gamma >= 0.0) || !isfinite(p->gamma)) return MRA_EINVAL;
+  if (p->gamma > 0.0 && !ptr_ok(p->log_rho_bar, 8)) return MRA_EINVAL;
+  if (p->gamma_a_inv && !ptr_ok(p->gamma_a_inv, 8)) return MRA_EINVAL;
+  return MRA_OK;
+}
+
+}  // namespace
+}  // namespace mra
+
+using namespace mra;
+
+// ---------------------------------------------------------------- entry points (C ABI)
+extern "C" {
+
+MRA_API const char* mra_status_string(int s) {
+  switch (s) {
+    case MRA_OK: return "ok";
+    case MRA_EINVAL: return "invalid argument";
+    case MRA_ENOMEM: return "host allocation failed";
+    case MRA_ECUDA: return "CUDA runtime error";
+    case MRA_ETIMEOUT: return "device wait timed out";
+    case MRA_ENUMERIC: return "non-finite value";
+    case MRA_EWORKSPACE: return "workspace too small";
+    default: return "unknown status";
+  }
+}
+
+MRA_API int mra_device_info(int32_t* num_sms, int32_t* sweep_grid_out) {
+  DevInfo d;
+  const int st = dev_info(&d);
+  if (st != MRA_OK) return st;
+  if (num_sms) *num_sms = d.sms;
+  if (sweep_grid_out) *sweep_grid_out = d.sms;
+  return MRA_OK;
+}
+
+MRA_API size_t mra_em_workspace_bytes(const mra_dims* d, int32_t Lw) {
+  if (check_dims(d) != MRA_OK || Lw < 1) return 0;
+  DevInfo di;
+  if (dev_info(&di) != MRA_OK) return 0;
+  return em_layout(d->N, d->K, d->Q, d->L, Lw, di.sms).total;
+}
+
+MRA_API int mra_em_step(const mra_dims* d, const mra_em_params* p, const float* y, const int32_t* shift,
+                        const double* x_in, const double* log_rho_in, double* x_out, double* log_rho_out,
+                        double* loglik_out, double* step_out, float* w_out, void* ws, size_t ws_bytes,
+                        void* stream) {
+  int st = check_dims(d);
+  if (st != MRA_OK) return st;
+  if ((st = check_params(d, p)) != MRA_OK) return st;
+  if (!ptr_ok(x_in, 16) || !ptr_ok(log_rho_in, 8) || !ptr_ok(x_out, 16) || !ptr_ok(log_rho_out, 8))
+    return MRA_EINVAL;
+  if (w_out && !ptr_ok(w_out, 4)) return MRA_EINVAL;
+  EmCall c;
+  if ((st = prepare(d, p->Lw, p->l0, y, shift, ws, ws_bytes, &c)) != MRA_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  c.su.x_in = reinterpret_cast<const double2*>(x_in);
+  c.su.log_rho_in = log_rho_in;
+  c.su.log_rho_bar = p->gamma > 0.0 ? p->log_rho_bar : nullptr;
+  c.su.gamma_a_inv = p->gamma_a_inv;
+  c.sa.w_out = w_out;
+  c.ua.gamma = p->gamma;
+  c.ua.update_rho = p->update_rho ? 1 : 0;
+  c.ua.x_out = reinterpret_cast<double2*>(x_out);
+  c.ua.log_rho_out = log_rho_out;
+  c.ua.loglik_out = loglik_out;
+  c.ua.step_out = step_out;
+  if ((st = launch_setup(c, s)) != MRA_OK) return st;
+  return launch_iteration(c, s);
+}
+
+MRA_API int mra_em_run(const mra_dims* d, const mra_em_params* p, const float* y, const int32_t* shift,
+                       double* x_inout, double* log_rho_inout, int32_t* iters_out, double* stats_out,
+                       double* x_traj_out, void* ws, size_t ws_bytes, void* stream) {
+  int st = check_dims(d);
+  if (st != MRA_OK) return st;
+  if ((st = check_params(d, p)) != MRA_OK) return st;
+  if (p->max_iters < 1 || p->check_every < 1) return MRA_EINVAL;
+  if (!ptr_ok(x_inout, 16) || !ptr_ok(log_rho_inout, 8)) return MRA_EINVAL;
+  if (stats_out && !ptr_ok(stats_out, 8)) return MRA_EINVAL;
+  if (x_traj_out && !ptr_ok(x_traj_out, 16)) return MRA_EINVAL;
+  EmCall c;
+  if ((st = prepare(d, p->Lw, p->l0, y, shift, ws, ws_bytes, &c)) != MRA_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  c.su.x_in = reinterpret_cast<const double2*>(x_inout);
+  c.su.log_rho_in = log_rho_inout;
+  c.su.log_rho_bar = p->gamma > 0.0 ? p->log_rho_bar : nullptr;
+  c.su.gamma_a_inv = p->gamma_a_inv;
+  c.ua.gamma = p->gamma;
+  c.ua.tol = p->tol;
+  c.ua.update_rho = p->update_rho ? 1 : 0;
+  c.ua.max_iters = p->max_iters;
+  c.ua.stats = stats_out;
+  c.ua.x_traj = reinterpret_cast<double2*>(x_traj_out);
+  if ((st = launch_setup(c, s)) != MRA_OK) return st;
+
+  const int chunk = std::min(p->check_every, p->max_iters);
+  const bool timed = p->sweep_ms != nullptr;
+  std::vector<cudaEvent_t> ev;
+  int rc = MRA_OK;
+  if (timed) {
+    ev.assign(2 * chunk, nullptr);
+    for (auto& e : ev)
+      if (cudaEventCreate(&e) != cudaSuccess) rc = MRA_ECUDA;
+  }
+  cudaStream_t cap = nullptr;
+  if (rc == MRA_OK && cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) rc = MRA_ECUDA;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  if (rc == MRA_OK && cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = MRA_ECUDA;
+  if (rc == MRA_OK) {
+    for (int i = 0; i < chunk && rc == MRA_OK; ++i)
+      rc = launch_iteration(c, cap, timed ? ev[2 * i] : nullptr, timed ? ev[2 * i + 1] : nullptr);
+    if (cudaStreamEndCapture(cap, &graph) != cudaSuccess) rc = MRA_ECUDA;
+  }
+  if (rc == MRA_OK && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) rc = MRA_ECUDA;
+  Ctrl host_ctrl{};
+  const int launches = (p->max_iters + chunk - 1) / chunk;
+  for (int i = 0; i < launches && rc == MRA_OK; ++i) {
+    if (cudaGraphLaunch(exec, s) != cudaSuccess) { rc = MRA_ECUDA; break; }
+    if ((p->tol > 0.0 && i + 1 < launches) || timed) {
+      const int before = host_ctrl.iter;
+      if (cudaMemcpyAsync(&host_ctrl, c.ctrl, 16, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess) {
+        rc = MRA_ECUDA;
+        break;
+      }
+      if (timed) {
+        for (int j = 0; j < chunk && before + j < host_ctrl.iter; ++j) {
+          float ms = 0.f;
+          if (cudaEventElapsedTime(&ms, ev[2 * j], ev[2 * j + 1]) != cudaSuccess) { rc = MRA_ECUDA; break; }
+          p->sweep_ms[before + j] = ms;
+        }
+      }
+      if (host_ctrl.done || host_ctrl.status != MRA_OK) break;
+    }
+  }
+  if (rc == MRA_OK) {
+    k_export<<<std::max(1, (std::max(c.lay.M, p->Lw) + 255) / 256), 256, 0, s>>>(
+        c.lay.M, p->Lw, c.su.x64, c.su.rho64, reinterpret_cast<double2*>(x_inout), log_rho_inout);
+    if (cudaGetLastError() != cudaSuccess) rc = MRA_ECUDA;
+  }
+  if (rc == MRA_OK) {
+    if (cudaMemcpyAsync(&host_ctrl, c.ctrl, 16, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      rc = MRA_ECUDA;
+    else {
+      if (iters_out) *iters_out = host_ctrl.iter;
+      if (host_ctrl.status != MRA_OK) rc = host_ctrl.status;
+    }
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  if (cap) cudaStreamDestroy(cap);
+  for (auto e : ev)
+    if (e) cudaEventDestroy(e);
+  return rc;
+}
+
+MRA_API int mra_loglik_grad(const mra_dims* d, int32_t Lw, int32_t l0, const float* y, const int32_t* shift,
+                            const double* x, const double* logits, double kappa, double* loglik_out, double* dx_out,
+                            double* dlogits_out, double* dkappa_out, void* ws, size_t ws_bytes, void* stream) {
+  int st = check_dims(d);
+  if (st != MRA_OK) return st;
+  if (!ptr_ok(x, 16) || !ptr_ok(logits, 8) || !isfinite(kappa)) return MRA_EINVAL;
+  if (dx_out && !ptr_ok(dx_out, 16)) return MRA_EINVAL;
+  EmCall c;
+  if ((st = prepare(d, Lw, l0, y, shift, ws, ws_bytes, &c)) != MRA_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  c.su.x_in = reinterpret_cast<const double2*>(x);
+  if ((st = launch_setup(c, s)) != MRA_OK) return st;
+  k_setup_vm<<<1, 256, 0, s>>>(d->L, Lw, l0, kappa, logits, c.su.rho64, c.su.logrho32);
+  c.sweep<<<c.lay.G, kSweepThreads, c.plan.smem, s>>>(c.sa);
+  k_reduce_cols<<<c.reduce_blocks, 256, 0, s>>>(c.sa.part, c.lay.G, c.lay.cols, c.tot, c.ctrl);
+  GradArgs g;
+  g.N = d->N; g.M = c.lay.M; g.L = d->L; g.Lw = Lw; g.l0 = l0;
+  g.sigma2 = d->sigma2; g.beta = 1.0 / d->sigma2; g.kappa = kappa;
+  g.tot = c.tot; g.cols = c.lay.cols;
+  g.x64 = c.su.x64; g.rho64 = c.su.rho64;
+  g.loglik_out = loglik_out; g.dx_out = reinterpret_cast<double2*>(dx_out);
+  g.dlogits_out = dlogits_out; g.dkappa_out = dkappa_out;
+  k_grad<<<1, 256, 0, s>>>(g);
+  return cudaGetLastError() == cudaSuccess ? MRA_OK : MRA_ECUDA;
+}
+
+}  // extern "C"
+
+static int align_into_tot(const mra_dims* d, const float* y, const int32_t* shift, void* ws, size_t ws_bytes,
+                          cudaStream_t s, EmCall* c) {
+  int st = prepare(d, 1, 0, y, shift, ws, ws_bytes, c);
+  if (st != MRA_OK) return st;
+  const bool qeven = (d->Q % 2) == 0;
+  const int M = c->lay.M, vec = qeven ? 2 : 1;
+  const int ncolmax = (M / vec + kSweepThreads - 1) / kSweepThreads;
+  void (*fn)(const float2*, const int*, int, int, int, int, const float2*, double*, int) = nullptr;
+  if (qeven) {
+    fn = ncolmax <= 1 ? k_align_partial<true, 1> : ncolmax <= 2 ? k_align_partial<true, 2>
+       : ncolmax <= 4 ? k_align_partial<true, 4> : k_align_partial<true, 8>;
+  } else {
+    fn = ncolmax <= 1 ? k_align_partial<false, 1> : ncolmax <= 2 ? k_align_partial<false, 2>
+       : ncolmax <= 4 ? k_align_partial<false, 4> : k_align_partial<false, 8>;
+  }
+  // tables only (x_in unused: point the setup at a zero-length state)
+  const int n = d->L;
+  SetupArgs u = c->su;
+  u.M = 0; u.Lw = 0;
+  k_setup<<<std::min(1024, (n + 127) / 128), 128, 0, s>>>(u);
+  fn<<<c->lay.G, kSweepThreads, 0, s>>>(reinterpret_cast<const float2*>(y), shift, d->N, M, d->Q, d->L, c->su.tf32,
+                                        c->sa.part, c->lay.G);
+  k_reduce_cols<<<(2 * M + 7) / 8, 256, 0, s>>>(c->sa.part, c->lay.G, 2 * M, c->tot, nullptr);
+  return cudaGetLastError() == cudaSuccess ? MRA_OK : MRA_ECUDA;
+}
+
+extern "C" {
+
+MRA_API int mra_align_mean(const mra_dims* d, const float* y, const int32_t* shift, double* x_out, void* ws,
+                           size_t ws_bytes, void* stream) {
+  int st = check_dims(d);
+  if (st != MRA_OK) return st;
+  if (!ptr_ok(x_out, 16)) return MRA_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  EmCall c;
+  if ((st = align_into_tot(d, y, shift, ws, ws_bytes, s, &c)) != MRA_OK) return st;
+  k_scale_out<<<(c.lay.M + 255) / 256, 256, 0, s>>>(c.lay.M, c.tot, 1.0 / d->N, reinterpret_cast<double2*>(x_out));
+  return cudaGetLastError() == cudaSuccess ? MRA_OK : MRA_ECUDA;
+}
+
+MRA_API int mra_prior_hist(const mra_dims* d, const float* y, const int32_t* shift_true, const int32_t* shift_est,
+                           const double* x_true, int32_t* hist_inout, int32_t* center_out, void* ws, size_t ws_bytes,
+                           void* stream) {
+  int st = check_dims(d);
+  if (st != MRA_OK) return st;
+  if (!ptr_ok(shift_true, 4) || !ptr_ok(shift_est, 4) || !ptr_ok(x_true, 16) || !ptr_ok(hist_inout, 4))
+    return MRA_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  EmCall c;
+  if ((st = align_into_tot(d, y, shift_est, ws, ws_bytes, s, &c)) != MRA_OK) return st;
+  int* center_ws = reinterpret_cast<int*>(c.tot + c.lay.cols + 4);
+  const int csm = (d->K + 1) * 16;
+  k_center<<<1, 256, csm, s>>>(d->K + 1, d->Q, d->L, c.tot, 1.0 / d->N, reinterpret_cast<const double2*>(x_true),
+                               c.su.tf64, center_ws, center_out);
+  k_hist<<<std::min(4096, (d->N + 255) / 256), 256, 0, s>>>(d->N, d->L, shift_true, shift_est, center_ws, hist_inout);
+  return cudaGetLastError() == cudaSuccess ? MRA_OK : MRA_ECUDA;
+}
+
+MRA_API int mra_ws_status(void* ws, void* stream) {
+  if (!ptr_ok(ws, 256)) return MRA_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int v = 0;
+  MRA_CUDA_TRY(cudaMemcpyAsync(&v, ws, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MRA_CUDA_TRY(cudaStreamSynchronize(s));
+  const int zero = 0;
+  MRA_CUDA_TRY(cudaMemcpyAsync(ws, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
+  MRA_CUDA_TRY(cudaStreamSynchronize(s));
+  return v;
+}
+
+}  // extern "C"

@@ -1,0 +1,528 @@
+// Synchronize and Match, rotation-prior fit and relative error on sm_103a.
+//
+//   pairwise  rel[i][j] = argmax_s Re sum_k C^{ij}_k e^{+2 pi i k s/L},  C^{ij}_k = sum_q conj(y_ikq) y_jkq
+//             (= argmin_s sum |y_i - e^{i k theta_s} y_j|^2, Eq. relative_angle_2d_dist)
+//   ppm       z <- Hz/||Hz|| then z <- phase(Hz) on H_ij = e^{-2 pi i rel_ij / L}     (Eq. cost_synchronization)
+//   match     n*(i) = argmin_{n<P, n != i} ||y_n||^2 - 2 Re <y_i, y_n>, shift_i = phi[n*]
+//             (Algorithm Synchronize and Match) -- an (N x 2M) by (2M x P) product with a fused argmin
+//   fit_prior rho_bar on the window, optional von Mises fit (Algorithm 1 + concentration fit)
+//   relerr    min_theta ||R_theta x_hat - x|| / ||x|| (Sec. 2.2)
+#include <math.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace mra {
+namespace {
+
+constexpr int kPairThreads = 128;
+
+// One CTA per pair (i < j) of the first P images.
+__global__ void __launch_bounds__(kPairThreads) k_pairwise(const float2* y, int Kp1, int Q, int L, int P, int* rel) {
+  extern __shared__ __align__(16) unsigned char psm[];
+  float2* tf = reinterpret_cast<float2*>(psm);  // [L] e^{-2 pi i m / L}
+  float2* C = tf + L;                           // [Kp1]
+  __shared__ float rv[kPairThreads / 32];
+  __shared__ int ri[kPairThreads / 32];
+  const int i = blockIdx.y, j = blockIdx.x, tid = threadIdx.x;
+  if (j < i) return;
+  if (j == i) {
+    if (tid == 0) rel[(size_t)i * P + i] = 0;
+    return;
+  }
+  const int M = Kp1 * Q;
+  for (int m = tid; m < L; m += kPairThreads) {
+    float s, c;
+    sincospif(2.0f * (float)m / (float)L, &s, &c);
+    tf[m] = make_float2(c, -s);
+  }
+  const float2* yi = y + (size_t)i * M;
+  const float2* yj = y + (size_t)j * M;
+  for (int k = tid; k < Kp1; k += kPairThreads) {
+    float cr = 0.f, ci = 0.f;
+    for (int q = 0; q < Q; ++q) {
+      const float2 a = yi[k * Q + q], b = yj[k * Q + q];
+      cr = fmaf(a.x, b.x, cr); cr = fmaf(a.y, b.y, cr);
+      ci = fmaf(a.x, b.y, ci); ci = fmaf(-a.y, b.x, ci);
+    }
+    C[k] = make_float2(cr, ci);
+  }
+  __syncthreads();
+  float best = -INFINITY;
+  int bi = 0x7fffffff;
+  for (int l = tid; l < L; l += kPairThreads) {
+    float s = 0.f;
+    int m = 0;
+    for (int k = 0; k < Kp1; ++k) {
+      const float2 t = tf[m], c = C[k];  // Re(C e^{+i phi}) with t = e^{-i phi}
+      s = fmaf(c.x, t.x, s);
+      s = fmaf(c.y, t.y, s);
+      m += l;
+      if (m >= L) m -= L;
+    }
+    if (s > best) best = s, bi = l;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ov = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ov > best || (ov == best && oi < bi)) best = ov, bi = oi;
+  }
+  if ((tid & 31) == 0) rv[tid >> 5] = best, ri[tid >> 5] = bi;
+  __syncthreads();
+  if (tid == 0) {
+    float b = rv[0];
+    int idx = ri[0];
+    for (int w = 1; w < kPairThreads / 32; ++w)
+      if (rv[w] > b || (rv[w] == b && ri[w] < idx)) b = rv[w], idx = ri[w];
+    rel[(size_t)i * P + j] = idx;
+    rel[(size_t)j * P + i] = (L - idx) % L;
+  }
+}
+
+// Projected power method, one CTA with one thread per image of S_P (P <= 1024).
+__global__ void k_ppm(int L, int P, const int* rel, int n_power, int n_ppm, int* phi) {
+  extern __shared__ __align__(16) unsigned char zsm[];
+  float2* tf = reinterpret_cast<float2*>(zsm);  // [L]
+  float2* z = tf + L;                           // [P]
+  __shared__ float red[32];
+  const int tid = threadIdx.x, nt = blockDim.x, i = tid;
+  for (int m = tid; m < L; m += nt) {
+    float s, c;
+    sincospif(2.0f * (float)m / (float)L, &s, &c);
+    tf[m] = make_float2(c, -s);
+  }
+  if (i < P) z[i] = make_float2(1.f, 0.f);
+  __syncthreads();
+  auto matvec = [&](int row) {
+    float vr = 0.f, vi = 0.f;
+    const int* r = rel + (size_t)row * P;
+    for (int j = 0; j < P; ++j) {
+      int m = r[j] % L;
+      if (m < 0) m += L;
+      const float2 h = tf[m], zz = z[j];
+      vr = fmaf(h.x, zz.x, vr); vr = fmaf(-h.y, zz.y, vr);
+      vi = fmaf(h.x, zz.y, vi); vi = fmaf(h.y, zz.x, vi);
+    }
+    return make_float2(vr, vi);
+  };
+  for (int it = 0; it < n_power; ++it) {
+    float2 v = make_float2(0.f, 0.f);
+    if (i < P) v = matvec(i);
+    float n2 = warp_sum(v.x * v.x + v.y * v.y);
+    if ((tid & 31) == 0) red[tid >> 5] = n2;
+    __syncthreads();
+    float tot = 0.f;
+    for (int w = 0; w < (nt + 31) / 32; ++w) tot += red[w];
+    const float inv = tot > 0.f ? rsqrtf(tot) : 0.f;
+    __syncthreads();
+    if (i < P) z[i] = tot > 0.f ? make_float2(v.x * inv, v.y * inv) : z[i];
+    __syncthreads();
+  }
+  for (int it = 0; it < n_ppm; ++it) {
+    float2 v = make_float2(0.f, 0.f);
+    if (i < P) v = matvec(i);
+    __syncthreads();
+    if (i < P) {
+      const float a = sqrtf(v.x * v.x + v.y * v.y);
+      z[i] = a > 0.f ? make_float2(v.x / a, v.y / a) : make_float2(1.f, 0.f);
+    }
+    __syncthreads();
+  }
+  if (i < P) {
+    const float2 z0 = z[0], zi = z[i];
+    const float wr = zi.x * z0.x + zi.y * z0.y, wi = zi.y * z0.x - zi.x * z0.y;  // z_i conj(z_0)
+    const float ang = atan2f(wi, wr);
+    int s = (int)floorf(ang * (float)L / (2.0f * (float)kPi) + 0.5f);
+    s %= L;
+    if (s < 0) s += L;
+    phi[i] = (i == 0) ? 0 : s;
+  }
+}
+
+__global__ void k_refnorm(const float* y, int D, int P, float* nrm) {
+  const int n = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (n >= P) return;
+  const float* r = y + (size_t)n * D;
+  float s = 0.f;
+  for (int d = lane; d < D; d += 32) s = fmaf(r[d], r[d], s);
+  s = warp_sum(s);
+  if (lane == 0) nrm[n] = s;
+}
+
+// Matching: 128 queries x 128 references per tile, 16 real coordinates per step,
+// 8 x 8 outputs per thread; score = ||y_n||^2 - 2 <y_i, y_n>, running argmin per query.
+constexpr int kMT = 128, kKC = 16;
+__global__ void __launch_bounds__(256) k_match(const float* y, int N, int D, int P, const float* nrm, const int* phi,
+                                               int* shift_out) {
+  __shared__ __align__(16) float As[kKC][kMT + 4];
+  __shared__ __align__(16) float Bs[kKC][kMT + 4];
+  const int tid = threadIdx.x;
+  const int tr = tid & 15, tq = tid >> 4;
+  const int q0 = blockIdx.x * kMT;
+  float bestv[8];
+  int besti[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) bestv[u] = INFINITY, besti[u] = 0x7fffffff;
+
+  for (int r0 = 0; r0 < P; r0 += kMT) {
+    float acc[8][8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+      for (int v = 0; v < 8; ++v) acc[u][v] = 0.f;
+    for (int kc = 0; kc < D; kc += kKC) {
+      // load: thread -> (row = tid/2, 8 coordinates at kc + 8*(tid&1))
+      {
+        const int row = tid >> 1, h = (tid & 1) * 8;
+        const int qi = q0 + row, ri = r0 + row;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int d = kc + h + e;
+          As[h + e][row] = (qi < N && d < D) ? y[(size_t)qi * D + d] : 0.f;
+          Bs[h + e][row] = (ri < P && d < D) ? y[(size_t)ri * D + d] : 0.f;
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < kKC; ++kk) {
+        const float4 a0 = *reinterpret_cast<const float4*>(&As[kk][tq * 4]);
+        const float4 a1 = *reinterpret_cast<const float4*>(&As[kk][64 + tq * 4]);
+        const float4 b0 = *reinterpret_cast<const float4*>(&Bs[kk][tr * 4]);
+        const float4 b1 = *reinterpret_cast<const float4*>(&Bs[kk][64 + tr * 4]);
+        const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+          for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int qi = q0 + (u < 4 ? tq * 4 + u : 64 + tq * 4 + (u - 4));
+#pragma unroll
+      for (int v = 0; v < 8; ++v) {
+        const int n = r0 + (v < 4 ? tr * 4 + v : 64 + tr * 4 + (v - 4));
+        if (n < P && n != qi) {
+          const float sc = nrm[n] - 2.f * acc[u][v];
+          if (sc < bestv[u] || (sc == bestv[u] && n < besti[u])) bestv[u] = sc, besti[u] = n;
+        }
+      }
+    }
+  }
+  // reduce over the 16 threads (same tq) that share these queries: lanes differ in tr
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    float bv = bestv[u];
+    int bi = besti[u];
+    for (int o = 8; o > 0; o >>= 1) {
+      const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov < bv || (ov == bv && oi < bi)) bv = ov, bi = oi;
+    }
+    const int qi = q0 + (u < 4 ? tq * 4 + u : 64 + tq * 4 + (u - 4));
+    if (tr == 0 && qi < N) shift_out[qi] = (bi < P) ? phi[bi] : 0;
+  }
+}
+
+// --- von Mises: A(kappa) = I_1(kappa)/I_0(kappa)
+// kappa < 50: backward recurrence of r_n = I_{n+1}/I_n = 1/(2(n+1)/kappa + r_{n+1}) from a deep start;
+// kappa >= 50: large-argument expansion I_nu(x) ~ e^x/sqrt(2 pi x) sum_k (-1)^k a_k(nu)/x^k,
+//              a_k(nu) = prod_{j=1..k} (4 nu^2 - (2j-1)^2) / (k! 8^k).
+__device__ double vm_A(double kappa) {
+  if (kappa <= 0.0) return 0.0;
+  if (kappa < 50.0) {
+    const int n0 = (int)(2.0 * kappa) + 60;
+    double r = 0.0;
+    for (int n = n0; n >= 0; --n) r = 1.0 / (2.0 * (double)(n + 1) / kappa + r);
+    return r;
+  }
+  double s0 = 1.0, s1 = 1.0, t0 = 1.0, t1 = 1.0;
+  for (int k = 1; k <= 12; ++k) {
+    const double f = (double)(2 * k - 1) * (double)(2 * k - 1);
+    t0 *= -(0.0 - f) / ((double)k * 8.0 * kappa);
+    t1 *= -(4.0 - f) / ((double)k * 8.0 * kappa);
+    s0 += t0;
+    s1 += t1;
+  }
+  return s1 / s0;
+}
+
+__global__ void k_fit_prior(int L, int Lw, int l0, const int* counts, int kind, double* log_prior, double* kappa_out) {
+  __shared__ double red[32];
+  __shared__ double bc[2];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  auto bsum = [&](double v) {
+    v = warp_sum_d(v);
+    __syncthreads();
+    if ((tid & 31) == 0) red[tid >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < (nt + 31) / 32; ++w) t += red[w];
+    return t;
+  };
+  double tot = 0.0, mc = 0.0;
+  for (int s = tid; s < L; s += nt) {
+    tot += (double)counts[s];
+    mc += (double)counts[s] * cospi(2.0 * (double)s / (double)L);
+  }
+  tot = bsum(tot);
+  mc = bsum(mc);
+  if (kind == 0) {
+    double wsum = 0.0;
+    for (int i = tid; i < Lw; i += nt) {
+      int s = (l0 + i) % L;
+      if (s < 0) s += L;
+      wsum += (double)counts[s];
+    }
+    wsum = bsum(wsum);
+    for (int i = tid; i < Lw; i += nt) {
+      int s = (l0 + i) % L;
+      if (s < 0) s += L;
+      log_prior[i] = log((double)counts[s] / wsum);
+    }
+    if (tid == 0 && kappa_out) *kappa_out = 0.0;
+    return;
+  }
+  if (tid == 0) {
+    const double target = mc / tot;
+    double kap = 0.0;
+    if (target > 0.0) {
+      double lo = 0.0, hi = 1.0;
+      while (vm_A(hi) < target && hi < 1e12) hi *= 2.0;
+      for (int it = 0; it < 200 && hi - lo > 1e-14 * hi; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (vm_A(mid) < target) lo = mid; else hi = mid;
+      }
+      kap = 0.5 * (lo + hi);
+    }
+    bc[0] = kap;
+  }
+  __syncthreads();
+  const double kap = bc[0];
+  double mx = -INFINITY;
+  for (int i = tid; i < Lw; i += nt) mx = fmax(mx, kap * cospi(2.0 * (double)(l0 + i) / (double)L));
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  __syncthreads();
+  if ((tid & 31) == 0) red[tid >> 5] = mx;
+  __syncthreads();
+  if (tid == 0) {
+    double m = -INFINITY;
+    for (int w = 0; w < (nt + 31) / 32; ++w) m = fmax(m, red[w]);
+    bc[1] = m;
+  }
+  __syncthreads();
+  const double m = bc[1];
+  double z = 0.0;
+  for (int i = tid; i < Lw; i += nt) z += exp(kap * cospi(2.0 * (double)(l0 + i) / (double)L) - m);
+  z = bsum(z);
+  const double lz = m + log(z);
+  for (int i = tid; i < Lw; i += nt) log_prior[i] = kap * cospi(2.0 * (double)(l0 + i) / (double)L) - lz;
+  if (tid == 0 && kappa_out) *kappa_out = kap;
+}
+
+// Relative error: FP32 scan of 4096 angles, FP64 golden-section refinement (one CTA).
+__global__ void k_relerr(int Kp1, int Q, const double2* xh, const double2* x, double* err) {
+  extern __shared__ __align__(16) unsigned char rsm[];
+  double2* g = reinterpret_cast<double2*>(rsm);  // [Kp1]
+  __shared__ double red[32];
+  __shared__ float fv[32];
+  __shared__ int fi[32];
+  __shared__ double AB[2];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  double A = 0.0, Bn = 0.0;
+  for (int e = tid; e < Kp1 * Q; e += nt) {
+    const double wk = (e / Q) > 0 ? 2.0 : 1.0;
+    A += wk * (xh[e].x * xh[e].x + xh[e].y * xh[e].y);
+    Bn += wk * (x[e].x * x[e].x + x[e].y * x[e].y);
+  }
+  A = warp_sum_d(A);
+  Bn = warp_sum_d(Bn);
+  if ((tid & 31) == 0) red[tid >> 5] = A;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (nt + 31) / 32; ++w) t += red[w];
+    AB[0] = t;
+  }
+  __syncthreads();
+  if ((tid & 31) == 0) red[tid >> 5] = Bn;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (nt + 31) / 32; ++w) t += red[w];
+    AB[1] = t;
+  }
+  for (int k = tid; k < Kp1; k += nt) {  // g_k = w_k sum_q xh_kq conj(x_kq)
+    const double wk = k > 0 ? 2.0 : 1.0;
+    double2 s = make_double2(0.0, 0.0);
+    for (int q = 0; q < Q; ++q) {
+      const double2 a = xh[k * Q + q], b = x[k * Q + q];
+      s.x += a.x * b.x + a.y * b.y;
+      s.y += a.y * b.x - a.x * b.y;
+    }
+    g[k] = make_double2(wk * s.x, wk * s.y);
+  }
+  __syncthreads();
+  // f(theta) = A + B - 2 Re sum_k g_k e^{-i k theta}; maximise h(theta) = Re sum_k g_k e^{-i k theta}
+  const int NG = 4096;
+  float best = -INFINITY;
+  int bi = 0;
+  for (int t = tid; t < NG; t += nt) {
+    float s = 0.f;
+    for (int k = 0; k < Kp1; ++k) {
+      float sn, cs;
+      sincospif(2.0f * (float)(((long long)k * t) % NG) / (float)NG, &sn, &cs);
+      s += (float)g[k].x * cs + (float)g[k].y * sn;
+    }
+    if (s > best) best = s, bi = t;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ov = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ov > best || (ov == best && oi < bi)) best = ov, bi = oi;
+  }
+  if ((tid & 31) == 0) fv[tid >> 5] = best, fi[tid >> 5] = bi;
+  __syncthreads();
+  if (tid == 0) {
+    float b = fv[0];
+    int idx = fi[0];
+    for (int w = 1; w < (nt + 31) / 32; ++w)
+      if (fv[w] > b || (fv[w] == b && fi[w] < idx)) b = fv[w], idx = fi[w];
+    auto h = [&](double th) {
+      double sn, cs;
+      sincos(th, &sn, &cs);
+      double er = 1.0, ei = 0.0, s = 0.0;  // e^{-i k th} by recurrence
+      for (int k = 0; k < Kp1; ++k) {
+        s += g[k].x * er - g[k].y * ei;
+        const double nr = er * cs + ei * sn, ni = ei * cs - er * sn;
+        er = nr;
+        ei = ni;
+      }
+      return s;
+    };
+    const double step = 2.0 * kPi / NG;
+    double lo = idx * step - step, hi = idx * step + step;
+    const double gr = 0.6180339887498949;
+    double c1 = hi - gr * (hi - lo), c2 = lo + gr * (hi - lo);
+    double h1 = h(c1), h2 = h(c2);
+    for (int it = 0; it < 80; ++it) {
+      if (h1 > h2) { hi = c2; c2 = c1; h2 = h1; c1 = hi - gr * (hi - lo); h1 = h(c1); }
+      else { lo = c1; c1 = c2; h1 = h2; c2 = lo + gr * (hi - lo); h2 = h(c2); }
+    }
+    const double hbest = fmax(fmax(h1, h2), h(idx * step));
+    const double f = fmax(AB[0] + AB[1] - 2.0 * hbest, 0.0);
+    *err = sqrt(f) / sqrt(AB[1]);
+  }
+}
+
+bool ok_ptr(const void* p, size_t a) { return p && (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+int check_sync_dims(const mra_dims* d, int P) {
+  if (!d || d->N < 1 || d->K < 0 || d->Q < 1 || d->L < 1) return MRA_EINVAL;
+  if (P < 1 || P > d->N) return MRA_EINVAL;
+  if (((long long)(d->K + 1) * d->Q) % 2 != 0) return MRA_EINVAL;
+  return MRA_OK;
+}
+
+struct SyncLayout {
+  size_t rel, phi, nrm, total;
+};
+SyncLayout sync_layout(int P) {
+  SyncLayout s;
+  size_t o = 0;
+  s.rel = o; o = align256(o + sizeof(int) * (size_t)P * P);
+  s.phi = o; o = align256(o + sizeof(int) * (size_t)P);
+  s.nrm = o; o = align256(o + sizeof(float) * (size_t)P);
+  s.total = o;
+  return s;
+}
+
+}  // namespace
+}  // namespace mra
+
+using namespace mra;
+
+extern "C" {
+
+MRA_API size_t mra_sync_workspace_bytes(const mra_dims* d, int32_t P) {
+  if (check_sync_dims(d, P) != MRA_OK) return 0;
+  return sync_layout(P).total;
+}
+
+MRA_API int mra_sync_pairwise(const mra_dims* d, const float* y, int32_t P, int32_t* rel_out, void* stream) {
+  if (check_sync_dims(d, P) != MRA_OK || !ok_ptr(y, 16) || !ok_ptr(rel_out, 4)) return MRA_EINVAL;
+  if (d->L > 8192 || d->K + 1 > 4096) return MRA_EINVAL;
+  const int smem = (d->L + d->K + 1) * 8;
+  if (smem > 48 * 1024 &&
+      cudaFuncSetAttribute(reinterpret_cast<const void*>(k_pairwise), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           smem) != cudaSuccess)
+    return MRA_ECUDA;
+  k_pairwise<<<dim3(P, P), kPairThreads, smem, static_cast<cudaStream_t>(stream)>>>(
+      reinterpret_cast<const float2*>(y), d->K + 1, d->Q, d->L, P, rel_out);
+  return cudaGetLastError() == cudaSuccess ? MRA_OK : MRA_ECUDA;
+}
+
+MRA_API int mra_sync_ppm(int32_t L, int32_t P, const int32_t* rel, int32_t n_power, int32_t n_ppm, int32_t* phi_out,
+                         void* stream) {
+  if (L < 1 || L > 8192 || P < 1 || P > 1024 || n_power < 0 || n_ppm < 0 || !ok_ptr(rel, 4) || !ok_ptr(phi_out, 4))
+    return MRA_EINVAL;
+  const int nt = ((P + 31) / 32) * 32;
+  const int smem = (L + P) * 8;
+  if (smem > 48 * 1024 &&
+      cudaFuncSetAttribute(reinterpret_cast<const void*>(k_ppm), cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+          cudaSuccess)
+    return MRA_ECUDA;
+  k_ppm<<<1, nt, smem, static_cast<cudaStream_t>(stream)>>>(L, P, rel, n_power, n_ppm, phi_out);
+  return cudaGetLastError() == cudaSuccess ? MRA_OK : MRA_ECUDA;
+}
+
+MRA_API int mra_sync_match(const mra_dims* d, const float* y, int32_t P, const int32_t* phi, int32_t* shift_out,
+                           void* ws, size_t ws_bytes, void* stream) {
+  if (check_sync_dims(d, P) != MRA_OK || !ok_ptr(y, 16) || !ok_ptr(phi, 4) || !ok_ptr(shift_out, 4) ||
+      !ok_ptr(ws, 256))
+    return MRA_EINVAL;
+  const SyncLayout sl = sync_layout(P);
+  if (ws_bytes < sl.total) return MRA_EWORKSPACE;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  float* nrm = reinterpret_cast<float*>(static_cast<unsigned char*>(ws) + sl.nrm);
+  const int D = 2 * (d->K + 1) * d->Q;
+  k_refnorm<<<(P + 7) / 8, 256, 0, s>>>(y, D, P, nrm);
+  k_match<<<(d->N + kMT - 1) / kMT, 256, 0, s>>>(y, d->N, D, P, nrm, phi, shift_out);
+  return cudaGetLastError() == cudaSuccess ? MRA_OK : MRA_ECUDA;
+}
+
+MRA_API int mra_sync(const mra_dims* d, const float* y, int32_t P, int32_t n_power, int32_t n_ppm, int32_t* shift_out,
+                     void* ws, size_t ws_bytes, void* stream) {
+  if (check_sync_dims(d, P) != MRA_OK || !ok_ptr(ws, 256)) return MRA_EINVAL;
+  const SyncLayout sl = sync_layout(P);
+  if (ws_bytes < sl.total) return MRA_EWORKSPACE;
+  unsigned char* base = static_cast<unsigned char*>(ws);
+  int* rel = reinterpret_cast<int*>(base + sl.rel);
+  int* phi = reinterpret_cast<int*>(base + sl.phi);
+  int st = mra_sync_pairwise(d, y, P, rel, stream);
+  if (st != MRA_OK) return st;
+  if ((st = mra_sync_ppm(d->L, P, rel, n_power, n_ppm, phi, stream)) != MRA_OK) return st;
+  return mra_sync_match(d, y, P, phi, shift_out, ws, ws_bytes, stream);
+}
+
+MRA_API int mra_fit_prior(int32_t L, int32_t Lw, int32_t l0, const int32_t* counts, int32_t kind,
+                          double* log_prior_out, double* kappa_out, void* stream) {
+  if (L < 1 || Lw < 1 || Lw > L || (kind != 0 && kind != 1) || !ok_ptr(counts, 4) || !ok_ptr(log_prior_out, 8))
+    return MRA_EINVAL;
+  if (kappa_out && !ok_ptr(kappa_out, 8)) return MRA_EINVAL;
+  k_fit_prior<<<1, 256, 0, static_cast<cudaStream_t>(stream)>>>(L, Lw, l0, counts, kind, log_prior_out, kappa_out);
+  return cudaGetLastError() == cudaSuccess ? MRA_OK : MRA_ECUDA;
+}
+
+MRA_API int mra_relerr(int32_t K, int32_t Q, const double* x_hat, const double* x, double* err_out, void* stream) {
+  if (K < 0 || Q < 1 || !ok_ptr(x_hat, 16) || !ok_ptr(x, 16) || !ok_ptr(err_out, 8)) return MRA_EINVAL;
+  if ((K + 1) * 16 > 40 * 1024) return MRA_EINVAL;
+  k_relerr<<<1, 256, (K + 1) * 16, static_cast<cudaStream_t>(stream)>>>(
+      K + 1, Q, reinterpret_cast<const double2*>(x_hat), reinterpret_cast<const double2*>(x), err_out);
+  return cudaGetLastError() == cudaSuccess ? MRA_OK : MRA_ECUDA;
+}
+
+}  // extern "C"

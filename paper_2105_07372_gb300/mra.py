@@ -1,0 +1,218 @@
+"""Thin ctypes binding of libmra (include/mra.h).
+
+Each function here has the name of the C entry point it calls and only
+marshals arguments: torch CUDA tensors become device pointers, the current
+torch stream becomes the cudaStream_t.  All computation happens in the CUDA
+kernels of libmra; there is no CPU fallback.  If the library is missing the
+import of any entry point raises.
+
+Complex arrays are torch complex tensors (complex64 observations, complex128
+state), which store interleaved (re, im) pairs exactly as the C ABI expects.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_double, c_int, c_int32, c_size_t, c_void_p
+
+import torch
+
+from . import build as _build
+
+MRA_OK = 0
+STATUS = {0: "ok", -1: "invalid argument", -2: "host allocation failed", -3: "CUDA runtime error",
+          -4: "device wait timed out", -5: "non-finite value", -6: "workspace too small"}
+
+
+class MraError(RuntimeError):
+    def __init__(self, fn: str, status: int):
+        super().__init__(f"{fn} failed: {STATUS.get(status, status)} ({status})")
+        self.status = status
+
+
+class mra_dims(ctypes.Structure):
+    _fields_ = [("N", c_int32), ("K", c_int32), ("Q", c_int32), ("L", c_int32), ("sigma2", c_double)]
+
+
+class mra_em_params(ctypes.Structure):
+    _fields_ = [("Lw", c_int32), ("l0", c_int32), ("gamma", c_double), ("log_rho_bar", c_void_p),
+                ("gamma_a_inv", c_void_p), ("update_rho", c_int32), ("tol", c_double), ("max_iters", c_int32),
+                ("check_every", c_int32), ("sweep_ms", c_void_p)]
+
+
+_lib = None
+_SIGS = {
+    "mra_status_string": (ctypes.c_char_p, [c_int]),
+    "mra_device_info": (c_int, [POINTER(c_int32), POINTER(c_int32)]),
+    "mra_em_workspace_bytes": (c_size_t, [POINTER(mra_dims), c_int32]),
+    "mra_em_step": (c_int, [POINTER(mra_dims), POINTER(mra_em_params)] + [c_void_p] * 9 + [c_void_p, c_size_t, c_void_p]),
+    "mra_em_run": (c_int, [POINTER(mra_dims), POINTER(mra_em_params)] + [c_void_p] * 4 + [POINTER(c_int32), c_void_p,
+                                                                                          c_void_p, c_void_p, c_size_t,
+                                                                                          c_void_p]),
+    "mra_loglik_grad": (c_int, [POINTER(mra_dims), c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_double,
+                                c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "mra_sync_workspace_bytes": (c_size_t, [POINTER(mra_dims), c_int32]),
+    "mra_sync_pairwise": (c_int, [POINTER(mra_dims), c_void_p, c_int32, c_void_p, c_void_p]),
+    "mra_sync_ppm": (c_int, [c_int32, c_int32, c_void_p, c_int32, c_int32, c_void_p, c_void_p]),
+    "mra_sync_match": (c_int, [POINTER(mra_dims), c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "mra_sync": (c_int, [POINTER(mra_dims), c_void_p, c_int32, c_int32, c_int32, c_void_p, c_void_p, c_size_t,
+                         c_void_p]),
+    "mra_align_mean": (c_int, [POINTER(mra_dims), c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "mra_prior_hist": (c_int, [POINTER(mra_dims), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                               c_size_t, c_void_p]),
+    "mra_fit_prior": (c_int, [c_int32, c_int32, c_int32, c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
+    "mra_relerr": (c_int, [c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "mra_ws_status": (c_int, [c_void_p, c_void_p]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libmra.so (building it in-tree first if it is missing); raise if that fails."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"libmra.so not built at {path}")
+        _build.build_library()
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols() -> list[str]:
+    return list(_SIGS)
+
+
+# ---------------------------------------------------------------- marshalling helpers
+def _p(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return c_void_p(t)
+    if not t.is_cuda:
+        raise ValueError("libmra takes device tensors")
+    if not t.is_contiguous():
+        raise ValueError("libmra takes contiguous tensors")
+    return c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return c_void_p(s.cuda_stream)
+
+
+def _check(fn: str, st: int):
+    if st != MRA_OK:
+        raise MraError(fn, st)
+
+
+def dims(N: int, K: int, Q: int, L: int, sigma2: float) -> mra_dims:
+    return mra_dims(int(N), int(K), int(Q), int(L), float(sigma2))
+
+
+def em_params(Lw: int, l0: int | None = None, gamma: float = 0.0, log_rho_bar=None, gamma_a_inv=None,
+              update_rho: bool = True, tol: float = 0.0, max_iters: int = 1, check_every: int | None = None,
+              sweep_ms=None):
+    """sweep_ms: optional host ctypes float array [max_iters] that receives each sweep's device time."""
+    if l0 is None:
+        l0 = -(Lw // 2)
+    p = mra_em_params(int(Lw), int(l0), float(gamma), _p(log_rho_bar), _p(gamma_a_inv), 1 if update_rho else 0,
+                      float(tol), int(max_iters), int(check_every if check_every else max_iters),
+                      ctypes.cast(sweep_ms, c_void_p) if sweep_ms is not None else None)
+    p._keep = (log_rho_bar, gamma_a_inv, sweep_ms)  # keep buffers alive with the struct
+    return p
+
+
+def mra_em_workspace_bytes(d: mra_dims, Lw: int) -> int:
+    return int(load().mra_em_workspace_bytes(ctypes.byref(d), int(Lw)))
+
+
+def mra_sync_workspace_bytes(d: mra_dims, P: int) -> int:
+    return int(load().mra_sync_workspace_bytes(ctypes.byref(d), int(P)))
+
+
+def workspace(nbytes: int, device=None) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device or "cuda")
+
+
+def mra_device_info():
+    a, b = c_int32(), c_int32()
+    _check("mra_device_info", load().mra_device_info(ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+# ---------------------------------------------------------------- entry points
+def mra_em_step(d, prm, y, shift, x_in, log_rho_in, x_out, log_rho_out, loglik_out=None, step_out=None, w_out=None,
+                ws=None, stream=None):
+    _check("mra_em_step", load().mra_em_step(ctypes.byref(d), ctypes.byref(prm), _p(y), _p(shift), _p(x_in),
+                                             _p(log_rho_in), _p(x_out), _p(log_rho_out), _p(loglik_out), _p(step_out),
+                                             _p(w_out), _p(ws), ws.numel(), _stream(stream)))
+
+
+def mra_em_run(d, prm, y, shift, x_inout, log_rho_inout, stats_out=None, x_traj_out=None, ws=None, stream=None) -> int:
+    it = c_int32(0)
+    _check("mra_em_run", load().mra_em_run(ctypes.byref(d), ctypes.byref(prm), _p(y), _p(shift), _p(x_inout),
+                                           _p(log_rho_inout), ctypes.byref(it), _p(stats_out), _p(x_traj_out), _p(ws),
+                                           ws.numel(), _stream(stream)))
+    return it.value
+
+
+def mra_loglik_grad(d, Lw, l0, y, shift, x, logits, kappa, loglik_out, dx_out=None, dlogits_out=None, dkappa_out=None,
+                    ws=None, stream=None):
+    _check("mra_loglik_grad", load().mra_loglik_grad(ctypes.byref(d), int(Lw), int(l0), _p(y), _p(shift), _p(x),
+                                                     _p(logits), float(kappa), _p(loglik_out), _p(dx_out),
+                                                     _p(dlogits_out), _p(dkappa_out), _p(ws), ws.numel(),
+                                                     _stream(stream)))
+
+
+def mra_sync_pairwise(d, y, P, rel_out, stream=None):
+    _check("mra_sync_pairwise", load().mra_sync_pairwise(ctypes.byref(d), _p(y), int(P), _p(rel_out), _stream(stream)))
+
+
+def mra_sync_ppm(L, P, rel, n_power, n_ppm, phi_out, stream=None):
+    _check("mra_sync_ppm", load().mra_sync_ppm(int(L), int(P), _p(rel), int(n_power), int(n_ppm), _p(phi_out),
+                                               _stream(stream)))
+
+
+def mra_sync_match(d, y, P, phi, shift_out, ws, stream=None):
+    _check("mra_sync_match", load().mra_sync_match(ctypes.byref(d), _p(y), int(P), _p(phi), _p(shift_out), _p(ws),
+                                                   ws.numel(), _stream(stream)))
+
+
+def mra_sync(d, y, P, n_power, n_ppm, shift_out, ws, stream=None):
+    _check("mra_sync", load().mra_sync(ctypes.byref(d), _p(y), int(P), int(n_power), int(n_ppm), _p(shift_out),
+                                       _p(ws), ws.numel(), _stream(stream)))
+
+
+def mra_align_mean(d, y, shift, x_out, ws, stream=None):
+    _check("mra_align_mean", load().mra_align_mean(ctypes.byref(d), _p(y), _p(shift), _p(x_out), _p(ws), ws.numel(),
+                                                   _stream(stream)))
+
+
+def mra_prior_hist(d, y, shift_true, shift_est, x_true, hist_inout, center_out=None, ws=None, stream=None):
+    _check("mra_prior_hist", load().mra_prior_hist(ctypes.byref(d), _p(y), _p(shift_true), _p(shift_est), _p(x_true),
+                                                   _p(hist_inout), _p(center_out), _p(ws), ws.numel(),
+                                                   _stream(stream)))
+
+
+def mra_fit_prior(L, Lw, l0, counts, kind, log_prior_out, kappa_out=None, stream=None):
+    _check("mra_fit_prior", load().mra_fit_prior(int(L), int(Lw), int(l0), _p(counts), int(kind), _p(log_prior_out),
+                                                 _p(kappa_out), _stream(stream)))
+
+
+def mra_relerr(K, Q, x_hat, x, err_out, stream=None):
+    _check("mra_relerr", load().mra_relerr(int(K), int(Q), _p(x_hat), _p(x), _p(err_out), _stream(stream)))
+
+
+def mra_ws_status(ws, stream=None) -> int:
+    return int(load().mra_ws_status(_p(ws), _stream(stream)))

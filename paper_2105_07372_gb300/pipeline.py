@@ -1,0 +1,89 @@
+"""Synch-EM (Algorithm Synch-EM) as a sequence of libmra calls on one device.
+
+  1. Synchronize and Match      mra_sync          -> shift_hat [N]
+  2. a_0 = mean of aligned y     mra_align_mean    (Eq. synch_initialization)
+  3. rho_0 = rho_bar             given, or learned by mra_prior_hist + mra_fit_prior (Algorithm 1)
+  4. EM loop on the window       mra_em_run        (graph-captured iterations)
+
+Plain full-search EM (the baseline of Sec. 4) is the same loop with the whole
+grid as the window, gamma = 0, a uniform rho_0 and no alignment.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import torch
+
+from . import mra
+
+
+@dataclasses.dataclass
+class Workspaces:
+    em: torch.Tensor
+    sync: torch.Tensor
+
+
+def workspaces(d: mra.mra_dims, Lw: int, P: int, device="cuda") -> Workspaces:
+    return Workspaces(em=mra.workspace(mra.mra_em_workspace_bytes(d, max(Lw, 1)), device),
+                      sync=mra.workspace(mra.mra_sync_workspace_bytes(d, P), device))
+
+
+@dataclasses.dataclass
+class SynchEMResult:
+    x: torch.Tensor         # complex128 [K+1, Q]
+    log_rho: torch.Tensor   # float64 [Lw]
+    shift: torch.Tensor     # int32 [N]
+    iters: int
+    stats: torch.Tensor | None
+
+
+def synchronize(y, d, P, ws: Workspaces, n_power=50, n_ppm=100, stream=None) -> torch.Tensor:
+    shift = torch.empty(d.N, dtype=torch.int32, device=y.device)
+    mra.mra_sync(d, y, P, n_power, n_ppm, shift, ws.sync, stream)
+    return shift
+
+
+def learn_prior(y, d, shift_true, shift_est, x_true, Lw, l0=None, kind=0, ws: Workspaces | None = None, stream=None):
+    """One Monte-Carlo trial of Algorithm 1 on a synthetic instance whose truth is known, then the window prior."""
+    if l0 is None:
+        l0 = -(Lw // 2)
+    hist = torch.zeros(d.L, dtype=torch.int32, device=y.device)
+    mra.mra_prior_hist(d, y, shift_true, shift_est, x_true, hist, None, ws.em, stream)
+    log_prior = torch.empty(Lw, dtype=torch.float64, device=y.device)
+    kappa = torch.empty(1, dtype=torch.float64, device=y.device)
+    mra.mra_fit_prior(d.L, Lw, l0, hist, kind, log_prior, kappa, stream)
+    return log_prior, kappa, hist
+
+
+def synch_em(y, d, *, P, Lw, iters, gamma, log_rho_bar, ws: Workspaces, shift=None, tol=0.0, check_every=None,
+             stats=True, x_traj=None, stream=None) -> SynchEMResult:
+    """Steps 1-4 given the learned window prior log_rho_bar [Lw] (float64 device tensor)."""
+    if shift is None:
+        shift = synchronize(y, d, P, ws, stream=stream)
+    x = torch.empty((d.K + 1, d.Q), dtype=torch.complex128, device=y.device)
+    mra.mra_align_mean(d, y, shift, x, ws.em, stream)
+    log_rho = log_rho_bar.clone()
+    prm = mra.em_params(Lw, gamma=gamma, log_rho_bar=log_rho_bar, update_rho=True, tol=tol, max_iters=iters,
+                        check_every=check_every or iters)
+    st = torch.empty((iters, 2), dtype=torch.float64, device=y.device) if stats else None
+    n = mra.mra_em_run(d, prm, y, shift, x, log_rho, st, x_traj, ws.em, stream)
+    return SynchEMResult(x=x, log_rho=log_rho, shift=shift, iters=n, stats=st)
+
+
+def full_search_em(y, d, x0, *, iters, ws: Workspaces, tol=0.0, check_every=None, x_traj=None, stream=None):
+    """Standard EM over all L rotations (uniform rho_0, rho updated without a prior)."""
+    L = d.L
+    x = x0.clone()
+    log_rho = torch.full((L,), -math.log(L), dtype=torch.float64, device=y.device)
+    prm = mra.em_params(L, l0=0, gamma=0.0, update_rho=True, tol=tol, max_iters=iters,
+                        check_every=check_every or iters)
+    st = torch.empty((iters, 2), dtype=torch.float64, device=y.device)
+    n = mra.mra_em_run(d, prm, y, None, x, log_rho, st, x_traj, ws.em, stream)
+    return SynchEMResult(x=x, log_rho=log_rho, shift=None, iters=n, stats=st)
+
+
+def relerr(x_hat, x, d, stream=None) -> float:
+    out = torch.empty(1, dtype=torch.float64, device=x.device)
+    mra.mra_relerr(d.K, d.Q, x_hat, x, out, stream)
+    return float(out.item())

@@ -1,0 +1,55 @@
+"""Host-side checks that need no GPU: the library builds, loads and exports every
+entry point that include/mra.h declares; the binding covers the same names;
+the C structs have the layout the header describes."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_names():
+    hdr = open(os.path.join(ROOT, "include", "mra.h")).read()
+    return re.findall(r"MRA_API\s+[\w\s\*]+?\b(mra_\w+)\s*\(", hdr)
+
+
+def test_header_declares_the_entry_points():
+    names = set(header_names())
+    for n in ("mra_sync", "mra_fit_prior", "mra_em_step", "mra_em_run", "mra_loglik_grad"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    shutil_nvcc = any(os.path.exists(p) for p in ("/usr/local/cuda/bin/nvcc",))
+    from paper_2105_07372_gb300 import build, mra
+
+    if not os.path.exists(build.LIB):
+        if not shutil_nvcc:
+            pytest.skip("no nvcc to build libmra")
+        build.build_library()
+    lib = ctypes.CDLL(build.LIB)
+    for n in header_names():
+        assert hasattr(lib, n), n
+    assert set(header_names()) == set(mra.exported_symbols())
+    lib.mra_status_string.restype = ctypes.c_char_p
+    assert lib.mra_status_string(-6) == b"workspace too small"
+
+
+def test_struct_layout():
+    from paper_2105_07372_gb300 import mra
+
+    assert ctypes.sizeof(mra.mra_dims) == 24
+    assert mra.mra_em_params.tol.offset == 40 and mra.mra_em_params.sweep_ms.offset == 56
+    assert ctypes.sizeof(mra.mra_em_params) == 64
+
+
+def test_oracle_not_imported_by_product():
+    """The product package never imports the oracle."""
+    pkg = os.path.join(ROOT, "paper_2105_07372_gb300")
+    pat = re.compile(r"^\s*(import\s+oracle|from\s+oracle|from\s+\.\.\s*import\s+oracle)", re.M)
+    for dp, _, fs in os.walk(pkg):
+        for f in fs:
+            if f.endswith(".py"):
+                assert not pat.search(open(os.path.join(dp, f)).read()), f
