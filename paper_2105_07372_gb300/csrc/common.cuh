@@ -106,6 +106,9 @@ struct Ctrl {
   int pad[61];
 };
 
+__host__ __device__ inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
+constexpr int kUnitChunk = 20;  // mirror units per warp chunk: 4 lanes x 5 units
+
 // Offsets (bytes) of every array in the EM workspace; identical on host and device.
 struct EmLayout {
   int G;        // persistent grid of the sweep
@@ -113,7 +116,8 @@ struct EmLayout {
   int twp;      // padded row pitch (in complex) of the window twiddle table
   int kp4;      // K+1 rounded up to a multiple of 4 (rows of the table)
   int cols;     // 2M + Lw + 2 reduced columns
-  size_t ctrl, tf32, tf64, tw, x32, x64, inv_den, logrho32, rho64, rhobar64, part, tot, total;
+  int nup;      // mirror units padded to a multiple of kUnitChunk
+  size_t ctrl, tf32, tf64, tw, x32, x64, inv_den, logrho32, rho64, rhobar64, units, tu, part, tot, total;
 };
 
 __host__ __device__ inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
@@ -129,6 +133,7 @@ inline EmLayout em_layout(int N, int K, int Q, int L, int Lw, int G) {
   l.twp = (Lw + 3) & ~3;
   l.kp4 = (K + 1 + 3) & ~3;
   l.cols = 2 * l.M + Lw + 2;
+  l.nup = round_up(Lw, kUnitChunk);  // the unit count never exceeds Lw
   size_t o = 0;
   l.ctrl = o;      o = align256(o + sizeof(Ctrl));
   l.tf32 = o;      o = align256(o + sizeof(float2) * L);
@@ -140,12 +145,64 @@ inline EmLayout em_layout(int N, int K, int Q, int L, int Lw, int G) {
   l.logrho32 = o;  o = align256(o + sizeof(float) * Lw);
   l.rho64 = o;     o = align256(o + sizeof(double) * Lw);
   l.rhobar64 = o;  o = align256(o + sizeof(double) * Lw);
+  l.units = o;     o = align256(o + sizeof(int2) * l.nup);
+  l.tu = o;        o = align256(o + sizeof(float2) * (size_t)l.Kp1 * l.nup);
   l.part = o;      o = align256(o + sizeof(double) * (size_t)l.cols * G);
   l.tot = o;       o = align256(o + sizeof(double) * (l.cols + 8));
   l.total = o;
   return l;
 }
 
+// Arguments of the warp-per-image sweep (sweep_impl.cuh).
+struct SweepV2Args {
+  const float2* y;
+  const int* shift;
+  int N, Kp1, M, L, Lw, NU, NUP;
+  int nwarps;      // active warps per CTA
+  int slot_bytes;  // bytes per ring slot
+  int sp;          // per-warp row pitch (floats) of the s/w and W[l] buffers
+  int off_ring, off_x, off_tu, off_tf, off_lr, off_units, off_lmap, off_s, off_wl;
+  float two_beta;
+  int align_only;  // 1: weights are 1 at offset 0 (align and average)
+  const float2* x32;
+  const float2* tu;    // [Kp1][NUP] e^{-i k theta} of each mirror unit's first offset
+  const int2* units;   // [NUP] window indices (a, b), b = -1 for a unit without mirror
+  const float2* tf32;
+  const float* logrho32;
+  double* part;
+  int G;
+  float* w_out;
+  Ctrl* ctrl;
+};
+struct SweepV2Launch {
+  void (*fn)(const SweepV2Args);
+  int threads;
+};
+SweepV2Launch sweep_v2_q1(int MR);
+SweepV2Launch sweep_v2_q2(int MR);
+SweepV2Launch sweep_v2_q3(int MR);
+SweepV2Launch sweep_v2_q4(int MR);
+
+// Mirror units of a window: offsets o and -o (mod L) share cos/sin.  Writes the
+// (a, b) index pairs in window order of a; returns the number of units.
+__host__ __device__ inline int window_units(int L, int Lw, int l0, int2* out) {
+  int nu = 0;
+  for (int i = 0; i < Lw; ++i) {
+    int off = (l0 + i) % L;
+    if (off < 0) off += L;
+    const int moff = (L - off) % L;
+    int im = (moff - l0) % L;
+    if (im < 0) im += L;
+    if (im < Lw && im != i) {
+      if (im < i) continue;  // covered by the unit of its mirror
+      if (out) out[nu] = make_int2(i, im);
+    } else {
+      if (out) out[nu] = make_int2(i, -1);
+    }
+    ++nu;
+  }
+  return nu;
+}
 // Device properties cached per device.
 struct DevInfo {
   int sms;

@@ -72,6 +72,9 @@ struct SetupArgs {
   float* logrho32;
   double* rho64;
   double* rhobar64;
+  int2* units;  // [nup]
+  float2* tu;   // [Kp1][nup]
+  int nu, nup;
   Ctrl* ctrl;
 };
 
@@ -124,6 +127,29 @@ __global__ void k_setup_tw(const SetupArgs a) {
       v = a.tf32[m];
     }
     a.tw[idx] = v;
+  }
+}
+
+// Mirror units of the window (one thread: integer bookkeeping over Lw entries).
+__global__ void k_setup_units(const SetupArgs a) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const int nu = window_units(a.L, a.Lw, a.l0, a.units);
+    for (int u = nu; u < a.nup; ++u) a.units[u] = make_int2(0, -1);
+  }
+}
+
+// tu[k][u] = e^{-i k theta} at the first offset of unit u (zero for padding units).
+__global__ void k_setup_tu(const SetupArgs a) {
+  const int n = a.Kp1 * a.nup;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+    const int k = idx / a.nup, u = idx - k * a.nup;
+    float2 v = make_float2(0.f, 0.f);
+    if (u < a.nu) {
+      int off = (a.l0 + a.units[u].x) % a.L;
+      if (off < 0) off += a.L;
+      v = a.tf32[(int)(((long long)k * off) % a.L)];
+    }
+    a.tu[idx] = v;
   }
 }
 
@@ -550,25 +576,31 @@ __device__ __forceinline__ double block_sum_d(double v, double* red) {
 }
 
 // One CTA: a_{t+1}, rho_{t+1}, log-likelihood at a_t, step; state update.
+// FP64 where the result needs it (a_{t+1}, norms, rho, the step at the chosen rotations);
+// the search over the L grid rotations for the step runs in FP32 and every rotation
+// within FP32 resolution of the best is re-evaluated exactly in FP64.
 __global__ void k_update(const UpdateArgs a) {
   extern __shared__ __align__(16) unsigned char usmem[];
   if (a.ctrl->done) return;
-  double2* xn = reinterpret_cast<double2*>(usmem);                  // [M]
-  double2* dk = xn + a.M;                                            // [Kp1]
-  float* sc = reinterpret_cast<float*>(dk + a.Kp1);                  // [L]
+  double2* xn = reinterpret_cast<double2*>(usmem);            // [M]
+  float2* d32 = reinterpret_cast<float2*>(xn + a.M);           // [Kp1]
+  float* sc = reinterpret_cast<float*>(d32 + a.Kp1);           // [L]
   __shared__ double red[32];
   __shared__ float fred[32];
   __shared__ double ysq_total;
-  const int tid = threadIdx.x, nt = blockDim.x;
+  __shared__ int ncand;
+  __shared__ int cand[16];
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   const int iter = a.ctrl->iter;
+  if (tid == 0) ncand = 0;
 
   double nx_old = 0.0, nx_new = 0.0;
   for (int e = tid; e < a.M; e += nt) {
     const double2 xo = a.x64[e];
     const double2 v = make_double2(a.tot[2 * e] * a.inv_den[e], a.tot[2 * e + 1] * a.inv_den[e]);
     xn[e] = v;
-    nx_old += xo.x * xo.x + xo.y * xo.y;
-    nx_new += v.x * v.x + v.y * v.y;
+    nx_old = fma(xo.x, xo.x, fma(xo.y, xo.y, nx_old));
+    nx_new = fma(v.x, v.x, fma(v.y, v.y, nx_new));
   }
   nx_old = block_sum_d(nx_old, red);
   nx_new = block_sum_d(nx_new, red);
@@ -577,15 +609,19 @@ __global__ void k_update(const UpdateArgs a) {
     if (iter == 0) keep[0] = a.tot[2 * a.M + a.Lw + 1];
     ysq_total = keep[0];
   }
-  // d_k = sum_q conj(a_{t+1,kq}) a_{t,kq}
-  for (int k = tid; k < a.Kp1; k += nt) {
-    double2 d = make_double2(0.0, 0.0);
-    for (int q = 0; q < a.Q; ++q) {
-      const double2 u = xn[k * a.Q + q], v = a.x64[k * a.Q + q];
-      d.x += u.x * v.x + u.y * v.y;
-      d.y += u.x * v.y - u.y * v.x;
+  // d_k = sum_q conj(a_{t+1,kq}) a_{t,kq} in FP32 (only used to rank rotations), one warp per row
+  for (int k = warp; k < a.Kp1; k += nw) {
+    float dr = 0.f, di = 0.f;
+    for (int q = lane; q < a.Q; q += 32) {
+      const double2 u = xn[k * a.Q + q];
+      const float2 v = a.x32[k * a.Q + q];
+      const float ur = (float)u.x, ui = (float)u.y;
+      dr = fmaf(ur, v.x, fmaf(ui, v.y, dr));
+      di = fmaf(ur, v.y, fmaf(-ui, v.x, di));
     }
-    dk[k] = d;
+    dr = warp_sum(dr);
+    di = warp_sum(di);
+    if (lane == 0) d32[k] = make_float2(dr, di);
   }
   __syncthreads();
   const double ll = a.tot[2 * a.M + a.Lw] - a.beta * ysq_total - (double)a.N * a.beta * nx_old -
@@ -596,8 +632,9 @@ __global__ void k_update(const UpdateArgs a) {
     double v = 0.0;
     for (int l = tid; l < a.Lw; l += nt) v += a.tot[2 * a.M + l] + a.gamma * a.rhobar64[l];
     const double tsum = block_sum_d(v, red);
+    const double inv = 1.0 / tsum;
     for (int l = tid; l < a.Lw; l += nt) {
-      const double r = (a.tot[2 * a.M + l] + a.gamma * a.rhobar64[l]) / tsum;
+      const double r = (a.tot[2 * a.M + l] + a.gamma * a.rhobar64[l]) * inv;
       a.rho64[l] = r;
       a.logrho32[l] = r > 1e-30 ? logf((float)r) : (float)log(r);
       if (a.log_rho_out) a.log_rho_out[l] = log(r);
@@ -606,51 +643,52 @@ __global__ void k_update(const UpdateArgs a) {
     for (int l = tid; l < a.Lw; l += nt) a.log_rho_out[l] = log(a.rho64[l]);
   }
 
-  // step: FP32 scan of score(l) = Re sum_k d_k e^{-2 pi i k l/L}, FP64 at the near-maximal candidates
+  // step: rank the L rotations in FP32
   float dmag = 0.f;
-  for (int k = 0; k < a.Kp1; ++k) dmag += fabsf((float)dk[k].x) + fabsf((float)dk[k].y);
+  for (int k = 0; k < a.Kp1; ++k) dmag += fabsf(d32[k].x) + fabsf(d32[k].y);
   float best = -INFINITY;
   for (int l = tid; l < a.L; l += nt) {
-    float s = 0.f;
+    float sv = 0.f;
     int m = 0;
     for (int k = 0; k < a.Kp1; ++k) {
-      const float2 t = a.tf32[m];
-      s = fmaf((float)dk[k].x, t.x, s);
-      s = fmaf(-(float)dk[k].y, t.y, s);
+      const float2 t = a.tf32[m], dv = d32[k];
+      sv = fmaf(dv.x, t.x, fmaf(-dv.y, t.y, sv));
       m += l;
       if (m >= a.L) m -= a.L;
     }
-    sc[l] = s;
-    best = fmaxf(best, s);
+    sc[l] = sv;
+    best = fmaxf(best, sv);
   }
   best = warp_max(best);
-  __syncthreads();
-  if ((tid & 31) == 0) fred[tid >> 5] = best;
+  if (lane == 0) fred[warp] = best;
   __syncthreads();
   float gbest = -INFINITY;
-  for (int w = 0; w < (nt + 31) / 32; ++w) gbest = fmaxf(gbest, fred[w]);
+  for (int w = 0; w < nw; ++w) gbest = fmaxf(gbest, fred[w]);
   const float thr = gbest - (1e-5f * dmag + 1e-30f);
-  double dmin = INFINITY;
   for (int l = tid; l < a.L; l += nt) {
     if (sc[l] >= thr) {
-      double s = 0.0;
-      int m = 0;
-      for (int k = 0; k < a.Kp1; ++k) {
-        const double2 t = a.tf64[m];
-        s += dk[k].x * t.x - dk[k].y * t.y;
-        m += l;
-        if (m >= a.L) m -= a.L;
-      }
-      dmin = fmin(dmin, nx_new + nx_old - 2.0 * s);
+      const int slot = atomicAdd(&ncand, 1);
+      if (slot < 16) cand[slot] = l;
     }
   }
-  for (int o = 16; o > 0; o >>= 1) dmin = fmin(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
   __syncthreads();
-  if ((tid & 31) == 0) red[tid >> 5] = dmin;
-  __syncthreads();
+  const int nc = min(ncand, 16);
   double step = INFINITY;
-  for (int w = 0; w < (nt + 31) / 32; ++w) step = fmin(step, red[w]);
+  for (int ci = 0; ci < nc; ++ci) {  // exact ||a_{t+1} - e^{-2 pi i k l/L} a_t||^2, FP64, block-parallel
+    const int l = cand[ci];
+    double part = 0.0;
+    for (int e = tid; e < a.M; e += nt) {
+      const int k = e / a.Q;
+      const double2 t = a.tf64[(int)(((long long)k * l) % a.L)];
+      const double2 xo = a.x64[e], v = xn[e];
+      const double dr = v.x - (xo.x * t.x - xo.y * t.y);
+      const double di = v.y - (xo.x * t.y + xo.y * t.x);
+      part = fma(dr, dr, fma(di, di, part));
+    }
+    step = fmin(step, block_sum_d(part, red));
+  }
   step = fmax(step, 0.0);
+  __syncthreads();
 
   // state
   for (int e = tid; e < a.M; e += nt) {
@@ -878,6 +916,49 @@ bool plan_sweep(int Kp1, int Q, int L, int Lw, int max_smem, SweepPlan* p) {
   return false;
 }
 
+struct V2Plan {
+  SweepV2Launch launch;
+  int nwarps, slot_bytes, sp, smem;
+  int off_ring, off_x, off_tu, off_tf, off_lr, off_units, off_lmap, off_s, off_wl;
+};
+
+// Shared-memory plan of the warp-per-image sweep: as many warps (each with a
+// two-image ring) as fit, at least half of the launch so that the ring can
+// hold every warp's sums at the end.
+bool plan_v2(int Kp1, int Q, int L, int Lw, int nup, int max_smem, V2Plan* p) {
+  if (Q % 8 != 0 || Q / 8 > 4) return false;
+  const int QV = Q / 8, MR = (Kp1 + 7) / 8;
+  if (MR > 7) return false;
+  SweepV2Launch ln = QV == 1 ? sweep_v2_q1(MR) : QV == 2 ? sweep_v2_q2(MR) : QV == 3 ? sweep_v2_q3(MR)
+                                                                                      : sweep_v2_q4(MR);
+  if (!ln.fn) return false;
+  const int M = Kp1 * Q;
+  const int maxw = ln.threads / 32;
+  const int slot = al16(M * 8);
+  const int sp = (Lw + 3) & ~3;
+  for (int nw = maxw; nw * 2 >= maxw; --nw) {
+    int o = al16(2 * maxw * 8);
+    p->off_ring = o; o += 2 * nw * slot;
+    p->off_x = o; o += al16(M * 8);
+    p->off_tu = o; o += al16(Kp1 * nup * 8);
+    p->off_tf = o; o += al16(L * 8);
+    p->off_lr = o; o += al16(Lw * 4);
+    p->off_units = o; o += al16(nup * 8);
+    p->off_lmap = o; o += al16(Lw * 8);
+    p->off_s = o; o += al16(maxw * sp * 4);
+    p->off_wl = o; o += al16(maxw * sp * 4);
+    if (o + 1024 <= max_smem) {
+      p->launch = ln;
+      p->nwarps = nw;
+      p->slot_bytes = slot;
+      p->sp = sp;
+      p->smem = o;
+      return true;
+    }
+  }
+  return false;
+}
+
 typedef void (*SweepFn)(const SweepArgs);
 
 SweepFn pick_sweep(bool qeven, int ncolmax) {
@@ -919,6 +1000,13 @@ struct EmCall {
   double* tot;
   int reduce_blocks;
   int update_smem;
+  bool v2;  // warp-per-image sweep (rows of Q a multiple of 8) instead of the tile sweep
+  V2Plan v2p;
+  SweepV2Args sa2;
+  void set_w_out(float* w) {
+    sa.w_out = w;
+    sa2.w_out = w;
+  }
 };
 
 int prepare(const mra_dims* d, int Lw, int l0, const float* y, const int32_t* shift, void* ws, size_t ws_bytes,
@@ -934,15 +1022,25 @@ int prepare(const mra_dims* d, int Lw, int l0, const float* y, const int32_t* sh
   c->lay = em_layout(d->N, d->K, d->Q, d->L, Lw, G);
   if (ws_bytes < c->lay.total) return MRA_EWORKSPACE;
   const int Kp1 = d->K + 1, M = Kp1 * d->Q;
-  if (!plan_sweep(Kp1, d->Q, d->L, Lw, di.max_smem_optin, &c->plan)) return MRA_EINVAL;
-  const bool qeven = (d->Q % 2) == 0;
-  const int vec = qeven ? 2 : 1;
-  const int ncolmax = (M / vec + kSweepThreads - 1) / kSweepThreads;
-  c->sweep = pick_sweep(qeven, ncolmax);
-  if (!c->sweep) return MRA_EINVAL;
-  if (cudaFuncSetAttribute(reinterpret_cast<const void*>(c->sweep), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           c->plan.smem) != cudaSuccess)
-    return MRA_ECUDA;
+  const int nu = window_units(d->L, Lw, l0, nullptr);
+  const int nup = round_up(nu, kUnitChunk);
+  c->v2 = plan_v2(Kp1, d->Q, d->L, Lw, nup, di.max_smem_optin, &c->v2p);
+  if (c->v2) {
+    if (cudaFuncSetAttribute(reinterpret_cast<const void*>(c->v2p.launch.fn),
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, c->v2p.smem) != cudaSuccess)
+      return MRA_ECUDA;
+    c->sweep = nullptr;
+  } else {
+    if (!plan_sweep(Kp1, d->Q, d->L, Lw, di.max_smem_optin, &c->plan)) return MRA_EINVAL;
+    const bool qeven = (d->Q % 2) == 0;
+    const int vec = qeven ? 2 : 1;
+    const int ncolmax = (M / vec + kSweepThreads - 1) / kSweepThreads;
+    c->sweep = pick_sweep(qeven, ncolmax);
+    if (!c->sweep) return MRA_EINVAL;
+    if (cudaFuncSetAttribute(reinterpret_cast<const void*>(c->sweep), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             c->plan.smem) != cudaSuccess)
+      return MRA_ECUDA;
+  }
   unsigned char* base = static_cast<unsigned char*>(ws);
   const EmLayout& L_ = c->lay;
   c->ctrl = reinterpret_cast<Ctrl*>(base + L_.ctrl);
@@ -967,6 +1065,25 @@ int prepare(const mra_dims* d, int Lw, int l0, const float* y, const int32_t* sh
   s.w_out = nullptr;
   s.ctrl = c->ctrl;
 
+  SweepV2Args& v = c->sa2;
+  v.y = s.y;
+  v.shift = shift;
+  v.N = d->N; v.Kp1 = Kp1; v.M = M; v.L = d->L; v.Lw = Lw; v.NU = nu; v.NUP = nup;
+  v.nwarps = c->v2p.nwarps; v.slot_bytes = c->v2p.slot_bytes; v.sp = c->v2p.sp;
+  v.off_ring = c->v2p.off_ring; v.off_x = c->v2p.off_x; v.off_tu = c->v2p.off_tu; v.off_tf = c->v2p.off_tf;
+  v.off_lr = c->v2p.off_lr; v.off_units = c->v2p.off_units; v.off_lmap = c->v2p.off_lmap; v.off_s = c->v2p.off_s; v.off_wl = c->v2p.off_wl;
+  v.two_beta = s.two_beta;
+  v.align_only = 0;
+  v.x32 = s.x32;
+  v.tu = reinterpret_cast<const float2*>(base + L_.tu);
+  v.units = reinterpret_cast<const int2*>(base + L_.units);
+  v.tf32 = s.tf32;
+  v.logrho32 = s.logrho32;
+  v.part = s.part;
+  v.G = G;
+  v.w_out = nullptr;
+  v.ctrl = c->ctrl;
+
   SetupArgs& u = c->su;
   u.N = d->N; u.Kp1 = Kp1; u.Q = d->Q; u.M = M; u.L = d->L; u.Lw = Lw;
   u.l0 = l0; u.twp = L_.twp; u.kp4 = L_.kp4; u.sigma2 = d->sigma2;
@@ -980,6 +1097,10 @@ int prepare(const mra_dims* d, int Lw, int l0, const float* y, const int32_t* sh
   u.logrho32 = reinterpret_cast<float*>(base + L_.logrho32);
   u.rho64 = reinterpret_cast<double*>(base + L_.rho64);
   u.rhobar64 = reinterpret_cast<double*>(base + L_.rhobar64);
+  u.units = reinterpret_cast<int2*>(base + L_.units);
+  u.tu = reinterpret_cast<float2*>(base + L_.tu);
+  u.nu = nu;
+  u.nup = nup;
   u.ctrl = c->ctrl;
 
   UpdateArgs& up = c->ua;
@@ -991,7 +1112,7 @@ int prepare(const mra_dims* d, int Lw, int l0, const float* y, const int32_t* sh
   up.rhobar64 = u.rhobar64; up.tf64 = u.tf64; up.tf32 = u.tf32; up.ctrl = c->ctrl;
   up.stats = nullptr; up.x_traj = nullptr; up.x_out = nullptr; up.log_rho_out = nullptr;
   up.loglik_out = nullptr; up.step_out = nullptr;
-  c->update_smem = M * 16 + Kp1 * 16 + d->L * 4 + 64;
+  c->update_smem = M * 16 + Kp1 * 8 + d->L * 4 + 64;
   if (c->update_smem > 48 * 1024 &&
       cudaFuncSetAttribute(reinterpret_cast<const void*>(k_update), cudaFuncAttributeMaxDynamicSharedMemorySize,
                            c->update_smem) != cudaSuccess)
@@ -1004,15 +1125,29 @@ int launch_setup(const EmCall& c, cudaStream_t st) {
   const int n = std::max(std::max(c.su.L, c.su.M), c.su.Lw);
   const int blocks = std::min(1024, (n + 127) / 128);
   k_setup<<<blocks, 128, 0, st>>>(c.su);
-  const int ntw = c.su.kp4 * c.su.twp;
-  k_setup_tw<<<std::min(1024, (ntw + 255) / 256), 256, 0, st>>>(c.su);
+  if (c.v2) {
+    k_setup_units<<<1, 32, 0, st>>>(c.su);
+    const int ntu = c.su.Kp1 * c.su.nup;
+    k_setup_tu<<<std::min(1024, (ntu + 255) / 256), 256, 0, st>>>(c.su);
+  } else {
+    const int ntw = c.su.kp4 * c.su.twp;
+    k_setup_tw<<<std::min(1024, (ntw + 255) / 256), 256, 0, st>>>(c.su);
+  }
   return cudaGetLastError() == cudaSuccess ? MRA_OK : MRA_ECUDA;
 }
 
+void launch_sweep(const EmCall& c, cudaStream_t st) {
+  if (c.v2)
+    c.v2p.launch.fn<<<c.lay.G, c.v2p.launch.threads, c.v2p.smem, st>>>(c.sa2);
+  else
+    c.sweep<<<c.lay.G, kSweepThreads, c.plan.smem, st>>>(c.sa);
+}
+
 int launch_iteration(const EmCall& c, cudaStream_t st, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr) {
-  if (ev0 && cudaEventRecord(ev0, st) != cudaSuccess) return MRA_ECUDA;
-  c.sweep<<<c.lay.G, kSweepThreads, c.plan.smem, st>>>(c.sa);
-  if (ev1 && cudaEventRecord(ev1, st) != cudaSuccess) return MRA_ECUDA;
+  // external event nodes: inside stream capture a plain record would only add a dependency edge
+  if (ev0 && cudaEventRecordWithFlags(ev0, st, cudaEventRecordExternal) != cudaSuccess) return MRA_ECUDA;
+  launch_sweep(c, st);
+  if (ev1 && cudaEventRecordWithFlags(ev1, st, cudaEventRecordExternal) != cudaSuccess) return MRA_ECUDA;
   k_reduce_cols<<<c.reduce_blocks, 256, 0, st>>>(c.sa.part, c.lay.G, c.lay.cols, c.tot, c.ctrl);
   k_update<<<1, 256, c.update_smem, st>>>(c.ua);
   return cudaGetLastError() == cudaSuccess ? MRA_OK : MRA_ECUDA;
@@ -1081,7 +1216,7 @@ MRA_API int mra_em_step(const mra_dims* d, const mra_em_params* p, const float* 
   c.su.log_rho_in = log_rho_in;
   c.su.log_rho_bar = p->gamma > 0.0 ? p->log_rho_bar : nullptr;
   c.su.gamma_a_inv = p->gamma_a_inv;
-  c.sa.w_out = w_out;
+  c.set_w_out(w_out);
   c.ua.gamma = p->gamma;
   c.ua.update_rho = p->update_rho ? 1 : 0;
   c.ua.x_out = reinterpret_cast<double2*>(x_out);
@@ -1193,7 +1328,7 @@ MRA_API int mra_loglik_grad(const mra_dims* d, int32_t Lw, int32_t l0, const flo
   c.su.x_in = reinterpret_cast<const double2*>(x);
   if ((st = launch_setup(c, s)) != MRA_OK) return st;
   k_setup_vm<<<1, 256, 0, s>>>(d->L, Lw, l0, kappa, logits, c.su.rho64, c.su.logrho32);
-  c.sweep<<<c.lay.G, kSweepThreads, c.plan.smem, s>>>(c.sa);
+  launch_sweep(c, s);
   k_reduce_cols<<<c.reduce_blocks, 256, 0, s>>>(c.sa.part, c.lay.G, c.lay.cols, c.tot, c.ctrl);
   GradArgs g;
   g.N = d->N; g.M = c.lay.M; g.L = d->L; g.Lw = Lw; g.l0 = l0;
@@ -1228,8 +1363,14 @@ static int align_into_tot(const mra_dims* d, const float* y, const int32_t* shif
   SetupArgs u = c->su;
   u.M = 0; u.Lw = 0;
   k_setup<<<std::min(1024, (n + 127) / 128), 128, 0, s>>>(u);
-  fn<<<c->lay.G, kSweepThreads, 0, s>>>(reinterpret_cast<const float2*>(y), shift, d->N, M, d->Q, d->L, c->su.tf32,
-                                        c->sa.part, c->lay.G);
+  if (c->v2) {  // the sweep with weight 1 at offset 0 accumulates sum_j y_j e^{+i k theta_hat_j}
+    k_setup_units<<<1, 32, 0, s>>>(c->su);
+    c->sa2.align_only = 1;
+    launch_sweep(*c, s);
+  } else {
+    fn<<<c->lay.G, kSweepThreads, 0, s>>>(reinterpret_cast<const float2*>(y), shift, d->N, M, d->Q, d->L,
+                                          c->su.tf32, c->sa.part, c->lay.G);
+  }
   k_reduce_cols<<<(2 * M + 7) / 8, 256, 0, s>>>(c->sa.part, c->lay.G, 2 * M, c->tot, nullptr);
   return cudaGetLastError() == cudaSuccess ? MRA_OK : MRA_ECUDA;
 }

@@ -80,63 +80,85 @@ __global__ void __launch_bounds__(kPairThreads) k_pairwise(const float2* y, int 
   }
 }
 
-// Projected power method, one CTA with one thread per image of S_P (P <= 1024).
-__global__ void k_ppm(int L, int P, const int* rel, int n_power, int n_ppm, int* phi) {
+// Projected power method, one CTA of 32 warps: warp w forms (Hz)_i for rows i = w, w+32, ...
+// with lanes striding over j.  rel is staged in shared memory as int16 when it fits.
+constexpr int kPpmThreads = 1024;
+__global__ void __launch_bounds__(kPpmThreads) k_ppm(int L, int P, const int* rel, int n_power, int n_ppm, int* phi,
+                                                     int stage) {
   extern __shared__ __align__(16) unsigned char zsm[];
   float2* tf = reinterpret_cast<float2*>(zsm);  // [L]
   float2* z = tf + L;                           // [P]
+  float2* zn = z + P;                           // [P]
+  short* rs = reinterpret_cast<short*>(zn + P);  // [P][P] when staged
   __shared__ float red[32];
-  const int tid = threadIdx.x, nt = blockDim.x, i = tid;
-  for (int m = tid; m < L; m += nt) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int m = tid; m < L; m += kPpmThreads) {
     float s, c;
     sincospif(2.0f * (float)m / (float)L, &s, &c);
     tf[m] = make_float2(c, -s);
   }
-  if (i < P) z[i] = make_float2(1.f, 0.f);
-  __syncthreads();
-  auto matvec = [&](int row) {
-    float vr = 0.f, vi = 0.f;
-    const int* r = rel + (size_t)row * P;
-    for (int j = 0; j < P; ++j) {
-      int m = r[j] % L;
+  for (int i = tid; i < P; i += kPpmThreads) z[i] = make_float2(1.f, 0.f);
+  if (stage) {
+    for (int e = tid; e < P * P; e += kPpmThreads) {
+      int m = rel[e] % L;
       if (m < 0) m += L;
-      const float2 h = tf[m], zz = z[j];
-      vr = fmaf(h.x, zz.x, vr); vr = fmaf(-h.y, zz.y, vr);
-      vi = fmaf(h.x, zz.y, vi); vi = fmaf(h.y, zz.x, vi);
+      rs[e] = (short)m;
     }
-    return make_float2(vr, vi);
-  };
-  for (int it = 0; it < n_power; ++it) {
-    float2 v = make_float2(0.f, 0.f);
-    if (i < P) v = matvec(i);
-    float n2 = warp_sum(v.x * v.x + v.y * v.y);
-    if ((tid & 31) == 0) red[tid >> 5] = n2;
+  }
+  __syncthreads();
+  const int total = n_power + n_ppm;
+  for (int it = 0; it < total; ++it) {
+    const bool power = it < n_power;
+    float part = 0.f;
+    for (int i = warp; i < P; i += 32) {
+      float vr = 0.f, vi = 0.f;
+      for (int jj = lane; jj < P; jj += 32) {
+        int m;
+        if (stage) {
+          m = rs[i * P + jj];
+        } else {
+          m = rel[(size_t)i * P + jj] % L;
+          if (m < 0) m += L;
+        }
+        const float2 h = tf[m], zz = z[jj];
+        vr = fmaf(h.x, zz.x, fmaf(-h.y, zz.y, vr));
+        vi = fmaf(h.x, zz.y, fmaf(h.y, zz.x, vi));
+      }
+      vr = warp_sum(vr);
+      vi = warp_sum(vi);
+      if (lane == 0) {
+        if (power) {
+          zn[i] = make_float2(vr, vi);
+          part += vr * vr + vi * vi;
+        } else {
+          const float a = sqrtf(vr * vr + vi * vi);
+          zn[i] = a > 0.f ? make_float2(vr / a, vi / a) : make_float2(1.f, 0.f);
+        }
+      }
+    }
+    float inv = 1.f;
+    if (power) {
+      if (lane == 0) red[warp] = part;
+      __syncthreads();
+      float t = 0.f;
+      for (int w = 0; w < 32; ++w) t += red[w];
+      inv = t > 0.f ? rsqrtf(t) : 1.f;
+    }
     __syncthreads();
-    float tot = 0.f;
-    for (int w = 0; w < (nt + 31) / 32; ++w) tot += red[w];
-    const float inv = tot > 0.f ? rsqrtf(tot) : 0.f;
-    __syncthreads();
-    if (i < P) z[i] = tot > 0.f ? make_float2(v.x * inv, v.y * inv) : z[i];
+    for (int i = tid; i < P; i += kPpmThreads) {
+      const float2 v = zn[i];
+      z[i] = power ? make_float2(v.x * inv, v.y * inv) : v;
+    }
     __syncthreads();
   }
-  for (int it = 0; it < n_ppm; ++it) {
-    float2 v = make_float2(0.f, 0.f);
-    if (i < P) v = matvec(i);
-    __syncthreads();
-    if (i < P) {
-      const float a = sqrtf(v.x * v.x + v.y * v.y);
-      z[i] = a > 0.f ? make_float2(v.x / a, v.y / a) : make_float2(1.f, 0.f);
-    }
-    __syncthreads();
-  }
-  if (i < P) {
+  for (int i = tid; i < P; i += kPpmThreads) {
     const float2 z0 = z[0], zi = z[i];
     const float wr = zi.x * z0.x + zi.y * z0.y, wi = zi.y * z0.x - zi.x * z0.y;  // z_i conj(z_0)
     const float ang = atan2f(wi, wr);
-    int s = (int)floorf(ang * (float)L / (2.0f * (float)kPi) + 0.5f);
-    s %= L;
-    if (s < 0) s += L;
-    phi[i] = (i == 0) ? 0 : s;
+    int sv = (int)floorf(ang * (float)L / (2.0f * (float)kPi) + 0.5f);
+    sv %= L;
+    if (sv < 0) sv += L;
+    phi[i] = (i == 0) ? 0 : sv;
   }
 }
 
@@ -469,13 +491,14 @@ MRA_API int mra_sync_ppm(int32_t L, int32_t P, const int32_t* rel, int32_t n_pow
                          void* stream) {
   if (L < 1 || L > 8192 || P < 1 || P > 1024 || n_power < 0 || n_ppm < 0 || !ok_ptr(rel, 4) || !ok_ptr(phi_out, 4))
     return MRA_EINVAL;
-  const int nt = ((P + 31) / 32) * 32;
-  const int smem = (L + P) * 8;
+  const int base = (L + 2 * P) * 8;
+  const int stage = (base + P * P * 2 <= 200 * 1024) ? 1 : 0;
+  const int smem = base + (stage ? P * P * 2 : 0);
   if (smem > 48 * 1024 &&
       cudaFuncSetAttribute(reinterpret_cast<const void*>(k_ppm), cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
           cudaSuccess)
     return MRA_ECUDA;
-  k_ppm<<<1, nt, smem, static_cast<cudaStream_t>(stream)>>>(L, P, rel, n_power, n_ppm, phi_out);
+  k_ppm<<<1, kPpmThreads, smem, static_cast<cudaStream_t>(stream)>>>(L, P, rel, n_power, n_ppm, phi_out, stage);
   return cudaGetLastError() == cudaSuccess ? MRA_OK : MRA_ECUDA;
 }
 

@@ -13,6 +13,8 @@ from .instances import (  # noqa: F401
     make_signal,
     random_init,
     sigma2_for_snr,
+    image_energy,
+    NPIX,
     to_c64,
     c64_round,
 )

@@ -9,8 +9,12 @@ Recipe (one instance):
 * shifts ``s_i`` uniform on the grid ``{0, .., L-1}`` (rotation 2 pi s_i / L);
   the paper draws its rotations from such a grid too (Sec. 2.2, E. coli test).
 * noise: i.i.d. circular complex Gaussian with E|eps|^2 = sigma^2 on every
-  stored entry (Eq. MRA_Model_FB), sigma^2 = 1 / (SNR * M) with M = (K+1) Q, the
-  coefficient-space form of the pixel SNR definition of Sec. 1 for ||x|| = 1.
+  stored entry (Eq. MRA_Model_FB).  The SNR is the paper's pixel-space SNR,
+  ||I||_F^2 / (n_pix sigma^2) (Sec. 1), for the paper's 129 x 129 images
+  (n_pix = 16641, Sec. 2.2 and Sec. 4).  An orthonormal steerable basis keeps
+  the per-coefficient noise variance equal to the pixel variance (App. A) and
+  ||I||_F^2 equals the two-sided coefficient energy |a_0|^2 + 2 sum_{k>0} |a_k|^2,
+  so sigma^2 = (|x_0|^2 + 2 sum_{k>0} |x_k|^2) / (16641 SNR).
 * observation ``y_i = x o exp(-2 pi i k s_i / L) + eps_i`` (Eq. MRA_Model_FB).
 
 The generator uses numpy's PCG64 stream seeded per instance.
@@ -39,9 +43,17 @@ def config(n: int) -> dict:
     return dict(CONFIGS[n])
 
 
-def sigma2_for_snr(snr: float, K: int, Q: int) -> float:
-    """Noise variance per stored complex entry for ||x|| = 1."""
-    return 1.0 / (snr * (K + 1) * Q)
+NPIX = 129 * 129  # pixels of the paper's projection images
+
+
+def image_energy(x: np.ndarray) -> float:
+    """||I||_F^2 of the real image with stored coefficients x (k < 0 half = conjugate of k > 0)."""
+    return float(np.sum(np.abs(x[0]) ** 2) + 2.0 * np.sum(np.abs(x[1:]) ** 2))
+
+
+def sigma2_for_snr(snr: float, x: np.ndarray) -> float:
+    """Noise variance per coefficient for pixel-space SNR = ||I||_F^2 / (n_pix sigma^2)."""
+    return image_energy(x) / (NPIX * snr)
 
 
 def make_signal(K: int, Q: int, decay: float, rng: np.random.Generator) -> np.ndarray:
@@ -78,7 +90,7 @@ def make_instance(K: int, Q: int, N: int, L: int, snr: float | None = None, deca
     if x is None:
         x = make_signal(K, Q, decay, rng)
     if sigma2 is None:
-        sigma2 = sigma2_for_snr(snr, K, Q)
+        sigma2 = sigma2_for_snr(snr, x)
     if shifts is None:
         s = rng.integers(0, L, size=N).astype(np.int64)
     else:

@@ -11,7 +11,7 @@ import torch
 
 import oracle as O
 import synth
-from gpu_helpers import TOL_W, TOL_X, dev, dev_y, host, rel_err
+from gpu_helpers import TOL_LL, TOL_W, TOL_X, dev, dev_y, host, loglik_scale, rel_err
 
 pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore::RuntimeWarning")]
 
@@ -55,7 +55,7 @@ def test_em_step_full_size(gpu_lib, cfg2):
     st = O.em_step(y64, x0, lrb, inst.L, inst.sigma2, Lw=Lw, gamma=c["gamma"], log_rho_bar=lrb, shifts=sh)
     assert rel_err(host(xo), st.x) <= TOL_X
     np.testing.assert_allclose(np.exp(host(lro)), np.exp(st.log_rho), atol=1e-5, rtol=0)
-    assert abs(ll.item() - st.loglik) <= 1e-6 * abs(st.loglik)
+    assert abs(ll.item() - st.loglik) <= TOL_LL * loglik_scale(y64, x0, inst.sigma2)
     assert abs(stp.item() - st.step) <= 1e-5 * math.sqrt(st.step) + 1e-10
 
 

@@ -17,8 +17,13 @@ import synth
 pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
 
 
+def soft(snr, K, Q):
+    """A noise variance that keeps the posteriors of small test instances spread over several rotations."""
+    return 1.0 / (snr * (K + 1) * Q)
+
+
 def tiny(seed=0, K=2, Q=2, N=3, L=5, snr=0.5):
-    return synth.make_instance(K=K, Q=Q, N=N, L=L, snr=snr, decay=4.0, seed=seed)
+    return synth.make_instance(K=K, Q=Q, N=N, L=L, sigma2=soft(snr, K, Q), decay=4.0, seed=seed)
 
 
 # --------------------------------------------------------------------------- rotations
@@ -143,7 +148,7 @@ def test_rho_update_maximises_lagrangian():
 @pytest.mark.parametrize("gamma,with_prior,Lw", [(0.0, False, 24), (10.0, False, 24), (5.0, True, 12), (0.0, False, 72)])
 def test_map_objective_nondecreasing(gamma, with_prior, Lw):
     c = synth.config(1)
-    inst = synth.make_instance(K=6, Q=4, N=120, L=c["L"], snr=0.2, decay=20.0, seed=7)
+    inst = synth.make_instance(K=6, Q=4, N=120, L=c["L"], sigma2=soft(0.2, 6, 4), decay=20.0, seed=7)
     L = inst.L
     gi = None
     if with_prior:
@@ -186,7 +191,7 @@ def _standard_em_fft(y, x, rho_full, L, sigma2):
 
 
 def test_full_window_uniform_prior_is_standard_em():
-    inst = synth.make_instance(K=5, Q=3, N=40, L=16, snr=0.3, decay=10.0, seed=12)
+    inst = synth.make_instance(K=5, Q=3, N=40, L=16, sigma2=soft(0.3, 5, 3), decay=10.0, seed=12)
     L = inst.L
     x = synth.random_init(inst.K, inst.Q, 10.0, seed=5)
     rng = np.random.default_rng(8)
@@ -203,7 +208,7 @@ def test_full_window_uniform_prior_is_standard_em():
 
 # --------------------------------------------------------------------------- equivariance
 def test_em_equivariant_under_global_rotation():
-    inst = synth.make_instance(K=6, Q=4, N=60, L=24, snr=0.3, decay=20.0, seed=31)
+    inst = synth.make_instance(K=6, Q=4, N=60, L=24, sigma2=soft(0.3, 6, 4), decay=20.0, seed=31)
     L, g = inst.L, 5
     x0 = O.align_mean(inst.y, inst.s, L)
     lr = np.log(np.full(9, 1 / 9))
@@ -216,7 +221,7 @@ def test_em_equivariant_under_global_rotation():
 
 
 def test_sync_invariant_under_global_rotation():
-    inst = synth.make_instance(K=5, Q=4, N=50, L=24, snr=2.0, decay=20.0, seed=41)
+    inst = synth.make_instance(K=5, Q=4, N=50, L=24, sigma2=soft(2.0, 5, 4), decay=20.0, seed=41)
     s1, _, _ = O.synchronize_and_match(inst.y, 12, inst.L)
     s2, _, _ = O.synchronize_and_match(O.rotate(inst.y, 2 * np.pi * 7 / inst.L), 12, inst.L)
     np.testing.assert_array_equal(s1, s2)
@@ -341,7 +346,7 @@ def test_vm_ratio_series():
 
 # --------------------------------------------------------------------------- gradient
 def test_loglik_gradient_central_differences():
-    inst = synth.make_instance(K=3, Q=2, N=25, L=20, snr=0.5, decay=6.0, seed=17)
+    inst = synth.make_instance(K=3, Q=2, N=25, L=20, sigma2=soft(0.5, 3, 2), decay=6.0, seed=17)
     L, Lw = inst.L, 7
     rng = np.random.default_rng(1)
     x = synth.random_init(inst.K, inst.Q, 6.0, seed=3)
