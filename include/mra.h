@@ -206,6 +206,27 @@ MRA_API int mra_fit_prior(int32_t L, int32_t Lw, int32_t l0, const int32_t* coun
  *   x_hat, x [K+1][Q] complex double; err_out [1] double. */
 MRA_API int mra_relerr(int32_t K, int32_t Q, const double* x_hat, const double* x, double* err_out, void* stream);
 
+/* mra_em_step for callers that cannot allocate device memory (no counterpart
+ * in the paper).  Some callers cannot hand the library a workspace: code that
+ * runs where another component owns all device memory and offers no extra
+ * buffer, or code that must not call cudaMalloc/cudaFree because those calls
+ * can synchronize the device.  This entry point takes the same arguments as
+ * mra_em_step without ws/ws_bytes and computes the same results; its scratch
+ * is one fixed array of 8 MiB that the library places in device memory when it
+ * is loaded, on every device that loads it, until the process exits.  Nothing
+ * is allocated by the call.
+ *   - Problems whose EM workspace (mra_em_workspace_bytes) exceeds 8 MiB are
+ *     rejected with MRA_EWORKSPACE.
+ *   - The first call on a device looks up the array's device address (once per
+ *     device, with that device current); make that first call before any CUDA
+ *     stream capture.
+ *   - All calls share the one array and it keeps the previous call's contents;
+ *     the call initialises everything it reads.  Calls that overlap on the GPU
+ *     (for example on two streams) race on the array: serialise them. */
+MRA_API int mra_em_step_noalloc(const mra_dims* dims, const mra_em_params* prm, const float* y, const int32_t* shift,
+                                const double* x_in, const double* log_rho_in, double* x_out, double* log_rho_out,
+                                double* loglik_out, double* step_out, float* w_out, void* stream);
+
 /* Synchronize the stream and return the workspace's device status word
  * (MRA_OK or MRA_ETIMEOUT), then clear it. */
 MRA_API int mra_ws_status(void* ws, void* stream);

@@ -1407,6 +1407,47 @@ MRA_API int mra_prior_hist(const mra_dims* d, const float* y, const int32_t* shi
   return cudaGetLastError() == cudaSuccess ? MRA_OK : MRA_ECUDA;
 }
 
+}  // extern "C"
+
+// ---------------------------------------------------------------- fixed-scratch variant of mra_em_step
+// Scratch for mra_em_step_noalloc: one array per device, loaded with the library and kept
+// until the process exits.  Host code must not use the symbol itself as a device address;
+// the address comes from cudaGetSymbolAddress once per device.
+constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+static int noalloc_scratch(void** out) {
+  static void* addr[64] = {};
+  static std::mutex mu;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return MRA_ECUDA;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return MRA_ECUDA;
+    addr[dev] = p;
+  }
+  *out = addr[dev];
+  return MRA_OK;
+}
+
+extern "C" {
+
+MRA_API int mra_em_step_noalloc(const mra_dims* d, const mra_em_params* p, const float* y, const int32_t* shift,
+                                const double* x_in, const double* log_rho_in, double* x_out, double* log_rho_out,
+                                double* loglik_out, double* step_out, float* w_out, void* stream) {
+  int st = check_dims(d);
+  if (st != MRA_OK) return st;
+  if ((st = check_params(d, p)) != MRA_OK) return st;
+  DevInfo di;
+  if ((st = dev_info(&di)) != MRA_OK) return st;
+  if (em_layout(d->N, d->K, d->Q, d->L, p->Lw, di.sms).total > kNoAllocScratchBytes) return MRA_EWORKSPACE;
+  void* scratch = nullptr;
+  if ((st = noalloc_scratch(&scratch)) != MRA_OK) return st;
+  return mra_em_step(d, p, y, shift, x_in, log_rho_in, x_out, log_rho_out, loglik_out, step_out, w_out, scratch,
+                     kNoAllocScratchBytes, stream);
+}
+
 MRA_API int mra_ws_status(void* ws, void* stream) {
   if (!ptr_ok(ws, 256)) return MRA_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);

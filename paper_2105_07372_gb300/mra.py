@@ -46,6 +46,7 @@ _SIGS = {
     "mra_device_info": (c_int, [POINTER(c_int32), POINTER(c_int32)]),
     "mra_em_workspace_bytes": (c_size_t, [POINTER(mra_dims), c_int32]),
     "mra_em_step": (c_int, [POINTER(mra_dims), POINTER(mra_em_params)] + [c_void_p] * 9 + [c_void_p, c_size_t, c_void_p]),
+    "mra_em_step_noalloc": (c_int, [POINTER(mra_dims), POINTER(mra_em_params)] + [c_void_p] * 9 + [c_void_p]),
     "mra_em_run": (c_int, [POINTER(mra_dims), POINTER(mra_em_params)] + [c_void_p] * 4 + [POINTER(c_int32), c_void_p,
                                                                                           c_void_p, c_void_p, c_size_t,
                                                                                           c_void_p]),
@@ -157,6 +158,15 @@ def mra_em_step(d, prm, y, shift, x_in, log_rho_in, x_out, log_rho_out, loglik_o
     _check("mra_em_step", load().mra_em_step(ctypes.byref(d), ctypes.byref(prm), _p(y), _p(shift), _p(x_in),
                                              _p(log_rho_in), _p(x_out), _p(log_rho_out), _p(loglik_out), _p(step_out),
                                              _p(w_out), _p(ws), ws.numel(), _stream(stream)))
+
+
+def mra_em_step_noalloc(d, prm, y, shift, x_in, log_rho_in, x_out, log_rho_out, loglik_out=None, step_out=None,
+                        w_out=None, stream=None):
+    """mra_em_step without a workspace argument: the library's fixed 8 MiB device array serves as scratch."""
+    _check("mra_em_step_noalloc", load().mra_em_step_noalloc(ctypes.byref(d), ctypes.byref(prm), _p(y), _p(shift),
+                                                             _p(x_in), _p(log_rho_in), _p(x_out), _p(log_rho_out),
+                                                             _p(loglik_out), _p(step_out), _p(w_out),
+                                                             _stream(stream)))
 
 
 def mra_em_run(d, prm, y, shift, x_inout, log_rho_inout, stats_out=None, x_traj_out=None, ws=None, stream=None) -> int:
