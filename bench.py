@@ -56,12 +56,12 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def traffic_for(kernel_src):
-    """DRAM bytes per sweep launch from the committed ncu summary, if the kernel is unchanged since."""
+def traffic_for():
+    """DRAM bytes per sweep launch from the committed ncu summary, if the kernel source is unchanged since."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             t = json.load(f)
-        sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
+        sha = hashlib.sha256(b"".join(open(os.path.join(ROOT, s), "rb").read() for s in t["sources"])).hexdigest()
         if t.get("source_sha256") == sha:
             return float(t["dram_bytes_per_launch"])
     except Exception:
@@ -251,9 +251,9 @@ def main():
     avg_sweep_s = float(np.mean(sweep_times)) / 1e3
     achieved = bytes_per_sweep / avg_sweep_s / 1e9
     peak, peak_kind = peaks()
-    traffic = traffic_for(os.path.join(ROOT, "paper_2105_07372_gb300", "csrc", "em.cu"))
+    traffic = traffic_for()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs", "kernel": "k_em_sweep",
+                "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs", "kernel": "k_sweep_v2",
                 "algorithmic_bytes_per_launch": bytes_per_sweep, "avg_launch_ms": avg_sweep_s * 1e3,
                 "launches_timed": len(sweep_times)}
     em_ms = float(np.sum(sweep_times)) / args.steps

@@ -178,10 +178,11 @@ struct SweepV2Launch {
   void (*fn)(const SweepV2Args);
   int threads;
 };
-SweepV2Launch sweep_v2_q1(int MR);
-SweepV2Launch sweep_v2_q2(int MR);
-SweepV2Launch sweep_v2_q3(int MR);
-SweepV2Launch sweep_v2_q4(int MR);
+// ipw: images each warp carries at once (2 only for windows of at most one unit chunk).
+SweepV2Launch sweep_v2_q1(int MR, int ipw);
+SweepV2Launch sweep_v2_q2(int MR, int ipw);
+SweepV2Launch sweep_v2_q3(int MR, int ipw);
+SweepV2Launch sweep_v2_q4(int MR, int ipw);
 
 // Mirror units of a window: offsets o and -o (mod L) share cos/sin.  Writes the
 // (a, b) index pairs in window order of a; returns the number of units.

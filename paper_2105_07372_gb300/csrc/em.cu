@@ -563,16 +563,21 @@ struct UpdateArgs {
   double* step_out;
 };
 
+// Block-wide FP64 sum, fixed order; red needs 33 slots.
 __device__ __forceinline__ double block_sum_d(double v, double* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   v = warp_sum_d(v);
   __syncthreads();
   if (lane == 0) red[warp] = v;
   __syncthreads();
-  double t = 0.0;
-  const int nw = (blockDim.x + 31) >> 5;
-  for (int w = 0; w < nw; ++w) t += red[w];
-  return t;
+  if (warp == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    double t = lane < nw ? red[lane] : 0.0;
+    t = warp_sum_d(t);
+    if (lane == 0) red[32] = t;
+  }
+  __syncthreads();
+  return red[32];
 }
 
 // One CTA: a_{t+1}, rho_{t+1}, log-likelihood at a_t, step; state update.
@@ -583,9 +588,11 @@ __global__ void k_update(const UpdateArgs a) {
   extern __shared__ __align__(16) unsigned char usmem[];
   if (a.ctrl->done) return;
   double2* xn = reinterpret_cast<double2*>(usmem);            // [M]
-  float2* d32 = reinterpret_cast<float2*>(xn + a.M);           // [Kp1]
+  double2* t64 = xn + a.M;                                      // [L]
+  float2* t32 = reinterpret_cast<float2*>(t64 + a.L);          // [L]
+  float2* d32 = t32 + a.L;                                      // [Kp1]
   float* sc = reinterpret_cast<float*>(d32 + a.Kp1);           // [L]
-  __shared__ double red[32];
+  __shared__ double red[33];
   __shared__ float fred[32];
   __shared__ double ysq_total;
   __shared__ int ncand;
@@ -593,6 +600,7 @@ __global__ void k_update(const UpdateArgs a) {
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   const int iter = a.ctrl->iter;
   if (tid == 0) ncand = 0;
+  for (int l = tid; l < a.L; l += nt) t64[l] = a.tf64[l], t32[l] = a.tf32[l];
 
   double nx_old = 0.0, nx_new = 0.0;
   for (int e = tid; e < a.M; e += nt) {
@@ -651,7 +659,7 @@ __global__ void k_update(const UpdateArgs a) {
     float sv = 0.f;
     int m = 0;
     for (int k = 0; k < a.Kp1; ++k) {
-      const float2 t = a.tf32[m], dv = d32[k];
+      const float2 t = t32[m], dv = d32[k];
       sv = fmaf(dv.x, t.x, fmaf(-dv.y, t.y, sv));
       m += l;
       if (m >= a.L) m -= a.L;
@@ -679,7 +687,7 @@ __global__ void k_update(const UpdateArgs a) {
     double part = 0.0;
     for (int e = tid; e < a.M; e += nt) {
       const int k = e / a.Q;
-      const double2 t = a.tf64[(int)(((long long)k * l) % a.L)];
+      const double2 t = t64[(k * l) % a.L];
       const double2 xo = a.x64[e], v = xn[e];
       const double dr = v.x - (xo.x * t.x - xo.y * t.y);
       const double di = v.y - (xo.x * t.y + xo.y * t.x);
@@ -733,7 +741,7 @@ struct GradArgs {
 };
 
 __global__ void k_grad(const GradArgs a) {
-  __shared__ double red[32];
+  __shared__ double red[33];
   const int tid = threadIdx.x, nt = blockDim.x;
   double nx = 0.0;
   for (int e = tid; e < a.M; e += nt) {
@@ -922,38 +930,40 @@ struct V2Plan {
   int off_ring, off_x, off_tu, off_tf, off_lr, off_units, off_lmap, off_s, off_wl;
 };
 
-// Shared-memory plan of the warp-per-image sweep: as many warps (each with a
-// two-image ring) as fit, at least half of the launch so that the ring can
-// hold every warp's sums at the end.
+// Shared-memory plan of the warp-streaming sweep: each warp carries ipw images
+// (2 when the window fits one unit chunk) in a two-stage ring; as many warps as
+// fit, at least enough that the ring can hold every warp's sums at the end.
 bool plan_v2(int Kp1, int Q, int L, int Lw, int nup, int max_smem, V2Plan* p) {
   if (Q % 8 != 0 || Q / 8 > 4) return false;
   const int QV = Q / 8, MR = (Kp1 + 7) / 8;
   if (MR > 7) return false;
-  SweepV2Launch ln = QV == 1 ? sweep_v2_q1(MR) : QV == 2 ? sweep_v2_q2(MR) : QV == 3 ? sweep_v2_q3(MR)
-                                                                                      : sweep_v2_q4(MR);
-  if (!ln.fn) return false;
   const int M = Kp1 * Q;
-  const int maxw = ln.threads / 32;
   const int slot = al16(M * 8);
   const int sp = (Lw + 3) & ~3;
-  for (int nw = maxw; nw * 2 >= maxw; --nw) {
-    int o = al16(2 * maxw * 8);
-    p->off_ring = o; o += 2 * nw * slot;
-    p->off_x = o; o += al16(M * 8);
-    p->off_tu = o; o += al16(Kp1 * nup * 8);
-    p->off_tf = o; o += al16(L * 8);
-    p->off_lr = o; o += al16(Lw * 4);
-    p->off_units = o; o += al16(nup * 8);
-    p->off_lmap = o; o += al16(Lw * 8);
-    p->off_s = o; o += al16(maxw * sp * 4);
-    p->off_wl = o; o += al16(maxw * sp * 4);
-    if (o + 1024 <= max_smem) {
-      p->launch = ln;
-      p->nwarps = nw;
-      p->slot_bytes = slot;
-      p->sp = sp;
-      p->smem = o;
-      return true;
+  for (int ipw = 1; ipw >= 1; --ipw) {  // two images per warp measured slower (fewer resident warps)
+    SweepV2Launch ln = QV == 1 ? sweep_v2_q1(MR, ipw) : QV == 2 ? sweep_v2_q2(MR, ipw)
+                     : QV == 3 ? sweep_v2_q3(MR, ipw) : sweep_v2_q4(MR, ipw);
+    if (!ln.fn) continue;
+    const int maxw = ln.threads / 32;
+    for (int nw = maxw; nw * 2 * ipw >= maxw && nw >= 1; --nw) {
+      int o = al16(2 * maxw * 8);
+      p->off_ring = o; o += 2 * ipw * nw * slot;
+      p->off_x = o; o += al16(M * 8);
+      p->off_tu = o; o += al16(Kp1 * nup * 8);
+      p->off_tf = o; o += al16(L * 8);
+      p->off_lr = o; o += al16(Lw * 4);
+      p->off_units = o; o += al16(nup * 8);
+      p->off_lmap = o; o += al16(Lw * 8);
+      p->off_s = o; o += al16(maxw * ipw * sp * 4);
+      p->off_wl = o; o += al16(maxw * sp * 4);
+      if (o + 1024 <= max_smem) {
+        p->launch = ln;
+        p->nwarps = nw;
+        p->slot_bytes = slot;
+        p->sp = sp;
+        p->smem = o;
+        return true;
+      }
     }
   }
   return false;
@@ -1112,7 +1122,7 @@ int prepare(const mra_dims* d, int Lw, int l0, const float* y, const int32_t* sh
   up.rhobar64 = u.rhobar64; up.tf64 = u.tf64; up.tf32 = u.tf32; up.ctrl = c->ctrl;
   up.stats = nullptr; up.x_traj = nullptr; up.x_out = nullptr; up.log_rho_out = nullptr;
   up.loglik_out = nullptr; up.step_out = nullptr;
-  c->update_smem = M * 16 + Kp1 * 8 + d->L * 4 + 64;
+  c->update_smem = M * 16 + d->L * 24 + Kp1 * 8 + d->L * 4 + 64;
   if (c->update_smem > 48 * 1024 &&
       cudaFuncSetAttribute(reinterpret_cast<const void*>(k_update), cudaFuncAttributeMaxDynamicSharedMemorySize,
                            c->update_smem) != cudaSuccess)

@@ -1,8 +1,10 @@
-// Warp-per-image EM sweep (rows of Q a multiple of 8 coefficients).
+// Warp-streaming EM sweep (rows of Q a multiple of 8 coefficients).
 //
-// Each warp owns a private two-slot shared-memory ring filled by bulk copies
-// (one image per copy) and runs an image through every stage with warp-level
-// synchronisation only:
+// Each warp owns a private shared-memory ring filled by bulk copies (one image
+// per copy, IPW images per ring stage, two stages) and runs its images through
+// every stage with warp-level synchronisation only.  With IPW = 2 the warp
+// carries two images at once: the x and twiddle loads are shared by both and
+// the two images give independent instruction streams.
 //
 //   lanes form 8 quads; quad r owns the rows k = r, r+8, r+16, ...; lane j of a
 //   quad owns the float4 columns j, j+4, ... of those rows (QV of them per row).
@@ -11,46 +13,57 @@
 //   forward       S_l = Re sum_k c_k e^{-i k theta_l}, window offsets grouped in
 //                 mirror units {+o, -o}: A = sum c.x cos, B = sum c.y sin give
 //                 S_{+o} = A - B and S_{-o} = A + B (halves the work)
-//   normalise     w_l = exp(s_l - max) / Z over the per-warp s buffer
+//   normalise     w_l = exp(s_l - max) / Z over a per-warp buffer
 //   back          W_k = sum_l w_l e^{+i k theta_l} = sum_units (w_+ + w_-) cos + i (w_- - w_+) sin
 //   accumulate    num_kq += W_k y_kq into per-lane FP32 registers
 //
+// FP32 log-weights reach 2 beta S ~ hundreds; to keep their differences accurate a
+// first pass locates each image's peak rotation and the per-quad partial sums are
+// re-expressed relative to the peak's partial before the cross-quad sums.
 // The CTA combines its warps' sums once at the end and writes FP64 partials.
 #pragma once
 #include "common.cuh"
 
 namespace mra {
 
-template <int QV, int MR>
+template <int QV, int MR, int IPW>
 struct SweepV2Shape {
-  static constexpr int kThreads = (MR * QV * 4 > 64) ? 256 : 512;
-  static constexpr int kWarps = kThreads / 32;
+  static constexpr int kThreads = (IPW == 2 || MR * QV * 4 > 64) ? 256 : 512;
 };
 
 constexpr int kUC = 5;  // mirror units per lane per chunk
 
-template <int QV, int MR>
-__global__ void __launch_bounds__(SweepV2Shape<QV, MR>::kThreads, 1) k_sweep_v2(const SweepV2Args a) {
+// a mod L for 0 <= a < 2^24 using a float reciprocal of L, corrected to the exact residue.
+__device__ __forceinline__ int mod_small(int a, int L, float invL) {
+  int m = a - __float2int_rz((float)a * invL) * L;
+  if (m < 0) m += L;
+  if (m >= L) m -= L;
+  return m;
+}
+
+template <int QV, int MR, int IPW>
+__global__ void __launch_bounds__(SweepV2Shape<QV, MR, IPW>::kThreads, 1) k_sweep_v2(const SweepV2Args a) {
   extern __shared__ __align__(128) unsigned char smem[];
-  constexpr int NT = SweepV2Shape<QV, MR>::kThreads;
+  constexpr int NT = SweepV2Shape<QV, MR, IPW>::kThreads;
   if (a.ctrl->done) return;
   const bool want_ysq = (a.ctrl->iter == 0);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int nwarps = a.nwarps;  // <= NT/32 (warps beyond it only join the final reduction)
+  const int nwarps = a.nwarps;  // <= NT/32 (warps beyond it only join the final combination)
   const int r = lane >> 2, j = lane & 3;
   const int Kp1 = a.Kp1, L = a.L, Lw = a.Lw, NU = a.NU, NUP = a.NUP, M = a.M;
-  const int row4 = QV * 4;  // float4 per row
+  const float invL = 1.0f / (float)L;
+  constexpr int row4 = QV * 4;  // float4 per row
 
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem);  // [nwarps][2]
-  unsigned char* ring = smem + a.off_ring;            // [nwarps][2][slot]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem);  // [NT/32][2]
+  unsigned char* ring = smem + a.off_ring;            // [nwarps][2][IPW][slot]
   const float4* xs4 = reinterpret_cast<const float4*>(smem + a.off_x);
   const float2* tus = reinterpret_cast<const float2*>(smem + a.off_tu);  // [Kp1][NUP]
   const float2* tfs = reinterpret_cast<const float2*>(smem + a.off_tf);  // [L]
   const float* lrs = reinterpret_cast<const float*>(smem + a.off_lr);    // [Lw]
   const int2* uab = reinterpret_cast<const int2*>(smem + a.off_units);   // [NUP] (a, b) window indices, b < 0: single
   const int2* lmap = reinterpret_cast<const int2*>(smem + a.off_lmap);   // [Lw] (unit, -1 first offset / +1 mirror)
-  float* sbuf = reinterpret_cast<float*>(smem + a.off_s) + warp * a.sp;   // per-warp [Lw]
-  float* wlw = reinterpret_cast<float*>(smem + a.off_wl) + warp * a.sp;   // per-warp [Lw]
+  float* sbuf0 = reinterpret_cast<float*>(smem + a.off_s) + warp * IPW * a.sp;  // per warp [IPW][sp]
+  float* wlw = reinterpret_cast<float*>(smem + a.off_wl) + warp * a.sp;          // per warp [sp]
 
   // ---- shared tables
   {
@@ -82,8 +95,22 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR>::kThreads, 1) k_sweep_v2(
 
   const int gw = blockIdx.x * nwarps + warp, GW = gridDim.x * nwarps;
   const uint32_t img_bytes = (uint32_t)M * 8u;
-  unsigned char* const slot0 = ring + (size_t)(warp * 2) * a.slot_bytes;  // slot s at slot0 + s * slot_bytes
+  unsigned char* const wring = ring + (size_t)warp * 2 * IPW * a.slot_bytes;
   uint64_t* mybar = bar + 2 * warp;
+  // ring stage st (0/1) holds group p's images; image i of it sits in slot st * IPW + i
+  auto issue = [&](int p, int st) {
+    int nv = 0;
+#pragma unroll
+    for (int i = 0; i < IPW; ++i) nv += (gw + (p * IPW + i) * GW < a.N) ? 1 : 0;
+    if (nv == 0) return;
+    mbar_arrive_expect_tx(&mybar[st], (uint32_t)nv * img_bytes);
+#pragma unroll
+    for (int i = 0; i < IPW; ++i) {
+      const int im = gw + (p * IPW + i) * GW;
+      if (im < a.N)
+        bulk_g2s(wring + (size_t)(st * IPW + i) * a.slot_bytes, a.y + (size_t)im * M, img_bytes, &mybar[st]);
+    }
+  };
 
   float4 acc[MR][QV];
 #pragma unroll
@@ -94,193 +121,212 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR>::kThreads, 1) k_sweep_v2(
   const float two_beta = a.two_beta;
 
   if (warp < nwarps && lane == 0) {
-    if (gw < a.N) {
-      mbar_arrive_expect_tx(&mybar[0], img_bytes);
-      bulk_g2s(slot0, a.y + (size_t)gw * M, img_bytes, &mybar[0]);
-    }
-    if (gw + GW < a.N) {
-      mbar_arrive_expect_tx(&mybar[1], img_bytes);
-      bulk_g2s(slot0 + a.slot_bytes, a.y + (size_t)(gw + GW) * M, img_bytes, &mybar[1]);
-    }
+    issue(0, 0);
+    issue(1, 1);
   }
 
-  int n = 0;
-  for (int img = gw; warp < nwarps && img < a.N; img += GW, ++n) {
-    const int s = n & 1;
-    const uint32_t parity = (uint32_t)((n >> 1) & 1);
-    const bool ok = mbar_wait_bounded(&mybar[s], parity);
+  for (int p = 0; warp < nwarps && gw + p * IPW * GW < a.N; ++p) {
+    const int st = p & 1;
+    const uint32_t parity = (uint32_t)((p >> 1) & 1);
+    const bool ok = mbar_wait_bounded(&mybar[st], parity);
     if (!__all_sync(0xffffffffu, ok)) {
       if (lane == 0) {
         atomicExch(&a.ctrl->status, (int)MRA_ETIMEOUT);
-        mbar_wait_bounded(&mybar[s], parity);
-        if (img + GW < a.N) mbar_wait_bounded(&mybar[s ^ 1], (uint32_t)(((n + 1) >> 1) & 1));
+        mbar_wait_bounded(&mybar[st], parity);
+        if (gw + (p + 1) * IPW * GW < a.N) mbar_wait_bounded(&mybar[st ^ 1], (uint32_t)(((p + 1) >> 1) & 1));
       }
       break;
     }
-    unsigned char* const cur = slot0 + s * a.slot_bytes;
-    const float4* y4 = reinterpret_cast<const float4*>(cur);
-
-    int sj = 0;
-    if (a.shift) {
-      sj = a.shift[img] % L;
-      if (sj < 0) sj += L;
+    int img[IPW];
+    bool valid[IPW];
+    const float4* y4[IPW];
+    int ph0[IPW], phstep[IPW];
+#pragma unroll
+    for (int i = 0; i < IPW; ++i) {
+      img[i] = gw + (p * IPW + i) * GW;
+      valid[i] = img[i] < a.N;
+      y4[i] = reinterpret_cast<const float4*>(wring + (size_t)(st * IPW + i) * a.slot_bytes);
+      int sj = 0;
+      if (a.shift && valid[i]) {
+        sj = a.shift[img[i]] % L;
+        if (sj < 0) sj += L;
+      }
+      ph0[i] = mod_small(r * sj, L, invL);
+      phstep[i] = mod_small(8 * sj, L, invL);
     }
-    const int ph0 = (r * sj) % L, phstep = (8 * sj) % L;
 
-    float2 W[MR];
+    float2 W[IPW][MR];
     if (a.align_only) {
       // weights are exactly 1 at offset 0: W_k = e^{+i k theta_hat_j}
-      int ph = ph0;
 #pragma unroll
-      for (int m = 0; m < MR; ++m) {
-        const float2 t = tfs[ph];
-        W[m] = make_float2(t.x, -t.y);
-        ph += phstep;
-        if (ph >= L) ph -= L;
-      }
-    } else {
-      // ---- correlation
-      float2 c[MR];
-      float sq = 0.f;
-#pragma unroll
-      for (int m = 0; m < MR; ++m) {
-        const int k = r + 8 * m;
-        float cr = 0.f, ci = 0.f;
-        if (k < Kp1) {
-#pragma unroll
-          for (int u = 0; u < QV; ++u) {
-            const int p = k * row4 + j + 4 * u;
-            const float4 yv = y4[p], xv = xs4[p];
-            cr = fmaf(yv.x, xv.x, cr); cr = fmaf(yv.y, xv.y, cr);
-            ci = fmaf(yv.x, xv.y, ci); ci = fmaf(-yv.y, xv.x, ci);
-            cr = fmaf(yv.z, xv.z, cr); cr = fmaf(yv.w, xv.w, cr);
-            ci = fmaf(yv.z, xv.w, ci); ci = fmaf(-yv.w, xv.z, ci);
-            if (want_ysq) {
-              sq = fmaf(yv.x, yv.x, sq); sq = fmaf(yv.y, yv.y, sq);
-              sq = fmaf(yv.z, yv.z, sq); sq = fmaf(yv.w, yv.w, sq);
-            }
-          }
-        }
-        cr += __shfl_xor_sync(0xffffffffu, cr, 1);
-        ci += __shfl_xor_sync(0xffffffffu, ci, 1);
-        cr += __shfl_xor_sync(0xffffffffu, cr, 2);
-        ci += __shfl_xor_sync(0xffffffffu, ci, 2);
-        c[m] = make_float2(cr, ci);
-      }
-      if (want_ysq) {
-        sq = warp_sum(sq);
-        if (lane == 0) ysq_acc += (double)sq;
-      }
-      if (a.shift) {  // c_k e^{-i k theta_hat_j}
-        int ph = ph0;
+      for (int i = 0; i < IPW; ++i) {
+        int ph = ph0[i];
 #pragma unroll
         for (int m = 0; m < MR; ++m) {
-          c[m] = cmul(c[m], tfs[ph]);
-          ph += phstep;
+          const float2 t = tfs[ph];
+          W[i][m] = make_float2(t.x, -t.y);
+          ph += phstep[i];
           if (ph >= L) ph -= L;
         }
       }
-
-      // ---- forward transform over mirror units (chunks of 4 * kUC units).
-      // Pass 1 gives FP32 log-weights good enough to find each image's peak rotation l*.
-      // Pass 2 re-expresses every quad partial relative to the quad partial of l* before
-      // the cross-quad sums, so that near the peak (where the weights are not negligible)
-      // the sums add small numbers: s is stored relative to s(l*).
-      auto partials = [&](int u0, float (&A)[kUC], float (&Bv)[kUC]) {
+    } else {
+      // ---- correlation (x loads shared by the IPW images)
+      float2 c[IPW][MR];
+      float sq[IPW];
 #pragma unroll
-        for (int t = 0; t < kUC; ++t) A[t] = 0.f, Bv[t] = 0.f;
+      for (int i = 0; i < IPW; ++i) sq[i] = 0.f;
 #pragma unroll
-        for (int m = 0; m < MR; ++m) {
-          const int k = r + 8 * m;
-          if (k < Kp1) {
-            const float2 cc = c[m];
-            const float2* trow = tus + k * NUP + u0 + j;
+      for (int m = 0; m < MR; ++m) {
+        const int k = r + 8 * m;
+        float cr[IPW], ci[IPW];
 #pragma unroll
-            for (int t = 0; t < kUC; ++t) {
-              const float2 tv = trow[4 * t];
-              A[t] = fmaf(cc.x, tv.x, A[t]);
-              Bv[t] = fmaf(cc.y, tv.y, Bv[t]);
+        for (int i = 0; i < IPW; ++i) cr[i] = 0.f, ci[i] = 0.f;
+        if (k < Kp1) {
+#pragma unroll
+          for (int u = 0; u < QV; ++u) {
+            const int pidx = k * row4 + j + 4 * u;
+            const float4 xv = xs4[pidx];
+#pragma unroll
+            for (int i = 0; i < IPW; ++i) {
+              const float4 yv = y4[i][pidx];
+              cr[i] = fmaf(yv.x, xv.x, cr[i]); cr[i] = fmaf(yv.y, xv.y, cr[i]);
+              ci[i] = fmaf(yv.x, xv.y, ci[i]); ci[i] = fmaf(-yv.y, xv.x, ci[i]);
+              cr[i] = fmaf(yv.z, xv.z, cr[i]); cr[i] = fmaf(yv.w, xv.w, cr[i]);
+              ci[i] = fmaf(yv.z, xv.w, ci[i]); ci[i] = fmaf(-yv.w, xv.z, ci[i]);
+              if (want_ysq) {
+                sq[i] = fmaf(yv.x, yv.x, sq[i]); sq[i] = fmaf(yv.y, yv.y, sq[i]);
+                sq[i] = fmaf(yv.z, yv.z, sq[i]); sq[i] = fmaf(yv.w, yv.w, sq[i]);
+              }
             }
           }
         }
-      };
+#pragma unroll
+        for (int i = 0; i < IPW; ++i) {
+          cr[i] += __shfl_xor_sync(0xffffffffu, cr[i], 1);
+          ci[i] += __shfl_xor_sync(0xffffffffu, ci[i], 1);
+          cr[i] += __shfl_xor_sync(0xffffffffu, cr[i], 2);
+          ci[i] += __shfl_xor_sync(0xffffffffu, ci[i], 2);
+          c[i][m] = make_float2(cr[i], ci[i]);
+        }
+      }
+      if (want_ysq) {
+#pragma unroll
+        for (int i = 0; i < IPW; ++i) {
+          const float t = warp_sum(sq[i]);
+          if (lane == 0 && valid[i]) ysq_acc += (double)t;
+        }
+      }
+      if (a.shift) {  // c_k e^{-i k theta_hat_j}
+#pragma unroll
+        for (int i = 0; i < IPW; ++i) {
+          int ph = ph0[i];
+#pragma unroll
+          for (int m = 0; m < MR; ++m) {
+            c[i][m] = cmul(c[i][m], tfs[ph]);
+            ph += phstep[i];
+            if (ph >= L) ph -= L;
+          }
+        }
+      }
+
+      // ---- forward transform over mirror units (chunks of 4 * kUC units)
       auto quad_sum = [&](float v) {
         v += __shfl_xor_sync(0xffffffffu, v, 4);
         v += __shfl_xor_sync(0xffffffffu, v, 8);
         v += __shfl_xor_sync(0xffffffffu, v, 16);
         return v;
       };
-      auto store_rel = [&](int u0, const float (&Da)[kUC], const float (&Db)[kUC], float lr_ref) {
-        if (r == 0) {
+      // per-quad partials of this lane's units for all IPW images (twiddle loads shared)
+      auto partials = [&](int u0, float (&A)[IPW][kUC], float (&Bv)[IPW][kUC]) {
 #pragma unroll
-          for (int t = 0; t < kUC; ++t) {
-            const int u = u0 + j + 4 * t;
-            if (u < NU) {
-              const int2 ab = uab[u];
-              sbuf[ab.x] = fmaf(two_beta, Da[t], lrs[ab.x] - lr_ref);
-              if (ab.y >= 0) sbuf[ab.y] = fmaf(two_beta, Db[t], lrs[ab.y] - lr_ref);
+        for (int i = 0; i < IPW; ++i)
+#pragma unroll
+          for (int t = 0; t < kUC; ++t) A[i][t] = 0.f, Bv[i][t] = 0.f;
+#pragma unroll
+        for (int m = 0; m < MR; ++m) {
+          const int k = r + 8 * m;
+          if (k < Kp1) {
+            const float2* trow = tus + k * NUP + u0 + j;
+#pragma unroll
+            for (int t = 0; t < kUC; ++t) {
+              const float2 tv = trow[4 * t];
+#pragma unroll
+              for (int i = 0; i < IPW; ++i) {
+                A[i][t] = fmaf(c[i][m].x, tv.x, A[i][t]);
+                Bv[i][t] = fmaf(c[i][m].y, tv.y, Bv[i][t]);
+              }
             }
           }
         }
       };
-      float vref;  // FP32 log-weight at l* (absolute)
+      float vref[IPW];  // FP32 log-weight at the peak l* (absolute)
       if (NUP == 4 * kUC) {
-        float A[kUC], Bv[kUC];
+        float A[IPW][kUC], Bv[IPW][kUC];
         partials(0, A, Bv);
-        float bv = -INFINITY;
-        int bl = 0x7fffffff;
 #pragma unroll
-        for (int t = 0; t < kUC; ++t) {
-          const int u = j + 4 * t;
-          const float At = quad_sum(A[t]), Bt = quad_sum(Bv[t]);
-          if (u < NU) {
-            const int2 ab = uab[u];
-            const float sa = fmaf(two_beta, At - Bt, lrs[ab.x]);
-            if (sa > bv || (sa == bv && ab.x < bl)) bv = sa, bl = ab.x;
-            if (ab.y >= 0) {
-              const float sb = fmaf(two_beta, At + Bt, lrs[ab.y]);
-              if (sb > bv || (sb == bv && ab.y < bl)) bv = sb, bl = ab.y;
+        for (int i = 0; i < IPW; ++i) {
+          float bv = -INFINITY;
+          int bl = 0x7fffffff;
+#pragma unroll
+          for (int t = 0; t < kUC; ++t) {
+            const int u = j + 4 * t;
+            const float At = quad_sum(A[i][t]), Bt = quad_sum(Bv[i][t]);
+            if (u < NU) {
+              const int2 ab = uab[u];
+              const float sa = fmaf(two_beta, At - Bt, lrs[ab.x]);
+              if (sa > bv || (sa == bv && ab.x < bl)) bv = sa, bl = ab.x;
+              if (ab.y >= 0) {
+                const float sb = fmaf(two_beta, At + Bt, lrs[ab.y]);
+                if (sb > bv || (sb == bv && ab.y < bl)) bv = sb, bl = ab.y;
+              }
+            }
+          }
+#pragma unroll
+          for (int o = 1; o <= 2; o <<= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            const int ol = __shfl_xor_sync(0xffffffffu, bl, o);
+            if (ov > bv || (ov == bv && ol < bl)) bv = ov, bl = ol;
+          }
+          if (bl >= Lw) bl = 0;  // only if every log-weight is -inf
+          vref[i] = bv;
+          const int2 um = lmap[bl];  // (unit, -1 for its first offset / +1 for the mirror)
+          const int tstar = um.x >> 2, jstar = um.x & 3;
+          float pa = A[i][0], pb = Bv[i][0];
+#pragma unroll
+          for (int t = 1; t < kUC; ++t)
+            if (t == tstar) pa = A[i][t], pb = Bv[i][t];
+          float pr = um.y < 0 ? pa - pb : pa + pb;
+          pr = __shfl_sync(0xffffffffu, pr, (lane & ~3) | jstar);
+          const float lr_ref = lrs[bl];
+          float* sb = sbuf0 + i * a.sp;
+#pragma unroll
+          for (int t = 0; t < kUC; ++t) {
+            const float da = quad_sum((A[i][t] - Bv[i][t]) - pr);
+            const float db = quad_sum((A[i][t] + Bv[i][t]) - pr);
+            const int u = j + 4 * t;
+            if (r == 0 && u < NU) {
+              const int2 ab = uab[u];
+              sb[ab.x] = fmaf(two_beta, da, lrs[ab.x] - lr_ref);
+              if (ab.y >= 0) sb[ab.y] = fmaf(two_beta, db, lrs[ab.y] - lr_ref);
             }
           }
         }
-#pragma unroll
-        for (int o = 1; o <= 2; o <<= 1) {
-          const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
-          const int ol = __shfl_xor_sync(0xffffffffu, bl, o);
-          if (ov > bv || (ov == bv && ol < bl)) bv = ov, bl = ol;
-        }
-        if (bl >= Lw) bl = 0;  // only if every log-weight is -inf
-        vref = bv;
-        const int2 um = lmap[bl];  // (unit, -1 for its first offset / +1 for the mirror)
-        const int tstar = um.x >> 2, jstar = um.x & 3;
-        float pa = A[0], pb = Bv[0];
-#pragma unroll
-        for (int t = 1; t < kUC; ++t)
-          if (t == tstar) pa = A[t], pb = Bv[t];
-        float pr = um.y < 0 ? pa - pb : pa + pb;
-        pr = __shfl_sync(0xffffffffu, pr, (lane & ~3) | jstar);
-        float Da[kUC], Db[kUC];
-#pragma unroll
-        for (int t = 0; t < kUC; ++t) {
-          Da[t] = quad_sum((A[t] - Bv[t]) - pr);
-          Db[t] = quad_sum((A[t] + Bv[t]) - pr);
-        }
-        store_rel(0, Da, Db, lrs[bl]);
-      } else {
+      } else if constexpr (IPW == 1) {
+        float* sb = sbuf0;
         for (int u0 = 0; u0 < NUP; u0 += 4 * kUC) {  // pass 1 into the per-warp buffer
-          float A[kUC], Bv[kUC];
+          float A[1][kUC], Bv[1][kUC];
           partials(u0, A, Bv);
           float At[kUC], Bt[kUC];
 #pragma unroll
-          for (int t = 0; t < kUC; ++t) At[t] = quad_sum(A[t]), Bt[t] = quad_sum(Bv[t]);
+          for (int t = 0; t < kUC; ++t) At[t] = quad_sum(A[0][t]), Bt[t] = quad_sum(Bv[0][t]);
           if (r == 0) {
 #pragma unroll
             for (int t = 0; t < kUC; ++t) {
               const int u = u0 + j + 4 * t;
               if (u < NU) {
                 const int2 ab = uab[u];
-                sbuf[ab.x] = fmaf(two_beta, At[t] - Bt[t], lrs[ab.x]);
-                if (ab.y >= 0) sbuf[ab.y] = fmaf(two_beta, At[t] + Bt[t], lrs[ab.y]);
+                sb[ab.x] = fmaf(two_beta, At[t] - Bt[t], lrs[ab.x]);
+                if (ab.y >= 0) sb[ab.y] = fmaf(two_beta, At[t] + Bt[t], lrs[ab.y]);
               }
             }
           }
@@ -289,7 +335,7 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR>::kThreads, 1) k_sweep_v2(
         float bv = -INFINITY;
         int bl = 0x7fffffff;
         for (int l = lane; l < Lw; l += 32) {
-          const float v = sbuf[l];
+          const float v = sb[l];
           if (v > bv) bv = v, bl = l;
         }
 #pragma unroll
@@ -299,50 +345,55 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR>::kThreads, 1) k_sweep_v2(
           if (ov > bv || (ov == bv && ol < bl)) bv = ov, bl = ol;
         }
         if (bl >= Lw) bl = 0;
-        vref = bv;
+        vref[0] = bv;
         const int2 um = lmap[bl];
-        float pa = 0.f, pb = 0.f;  // the reference's quad partial, same arithmetic as partials()
+        float pa = 0.f, pb = 0.f;  // the peak's quad partial, same arithmetic as partials()
 #pragma unroll
         for (int m = 0; m < MR; ++m) {
           const int k = r + 8 * m;
           if (k < Kp1) {
             const float2 tv = tus[k * NUP + um.x];
-            pa = fmaf(c[m].x, tv.x, pa);
-            pb = fmaf(c[m].y, tv.y, pb);
+            pa = fmaf(c[0][m].x, tv.x, pa);
+            pb = fmaf(c[0][m].y, tv.y, pb);
           }
         }
         const float pr = um.y < 0 ? pa - pb : pa + pb;
         const float lr_ref = lrs[bl];
-        for (int u0 = 0; u0 < NUP; u0 += 4 * kUC) {  // pass 2 where the weights matter
+        for (int u0 = 0; u0 < NUP; u0 += 4 * kUC) {  // pass 2 where the weights are not negligible
           bool sig = false;
 #pragma unroll
           for (int t = 0; t < kUC; ++t) {
             const int u = u0 + j + 4 * t;
             if (u < NU) {
               const int2 ab = uab[u];
-              sig |= sbuf[ab.x] >= vref - 40.f;
-              if (ab.y >= 0) sig |= sbuf[ab.y] >= vref - 40.f;
+              sig |= sb[ab.x] >= bv - 40.f;
+              if (ab.y >= 0) sig |= sb[ab.y] >= bv - 40.f;
             }
           }
           sig = __any_sync(0xffffffffu, sig);
           __syncwarp();
           if (sig) {
-            float A[kUC], Bv[kUC], Da[kUC], Db[kUC];
+            float A[1][kUC], Bv[1][kUC];
             partials(u0, A, Bv);
 #pragma unroll
             for (int t = 0; t < kUC; ++t) {
-              Da[t] = quad_sum((A[t] - Bv[t]) - pr);
-              Db[t] = quad_sum((A[t] + Bv[t]) - pr);
+              const float da = quad_sum((A[0][t] - Bv[0][t]) - pr);
+              const float db = quad_sum((A[0][t] + Bv[0][t]) - pr);
+              const int u = u0 + j + 4 * t;
+              if (r == 0 && u < NU) {
+                const int2 ab = uab[u];
+                sb[ab.x] = fmaf(two_beta, da, lrs[ab.x] - lr_ref);
+                if (ab.y >= 0) sb[ab.y] = fmaf(two_beta, db, lrs[ab.y] - lr_ref);
+              }
             }
-            store_rel(u0, Da, Db, lr_ref);
           } else if (r == 0) {
 #pragma unroll
             for (int t = 0; t < kUC; ++t) {
               const int u = u0 + j + 4 * t;
               if (u < NU) {
                 const int2 ab = uab[u];
-                sbuf[ab.x] -= vref;
-                if (ab.y >= 0) sbuf[ab.y] -= vref;
+                sb[ab.x] -= bv;
+                if (ab.y >= 0) sb[ab.y] -= bv;
               }
             }
           }
@@ -350,44 +401,52 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR>::kThreads, 1) k_sweep_v2(
       }
       __syncwarp();
 
-      // ---- normalisation over the window
-      float mx = -INFINITY;
-      for (int l = lane; l < Lw; l += 32) mx = fmaxf(mx, sbuf[l]);
-      mx = warp_max(mx);
-      float z = 0.f;
-      for (int l = lane; l < Lw; l += 32) {
-        const float e = expf(sbuf[l] - mx);
-        sbuf[l] = e;
-        z += e;
+      // ---- normalisation over the window (values are relative to the peak)
+#pragma unroll
+      for (int i = 0; i < IPW; ++i) {
+        float* sb = sbuf0 + i * a.sp;
+        float mx = -INFINITY;
+        for (int l = lane; l < Lw; l += 32) mx = fmaxf(mx, sb[l]);
+        mx = warp_max(mx);
+        float z = 0.f;
+        for (int l = lane; l < Lw; l += 32) {
+          const float e = expf(sb[l] - mx);
+          sb[l] = e;
+          z += e;
+        }
+        z = warp_sum(z);
+        const float inv = 1.f / z;
+        float* wo = (a.w_out && valid[i]) ? a.w_out + (size_t)img[i] * Lw : nullptr;
+        for (int l = lane; l < Lw; l += 32) {
+          const float w = sb[l] * inv;
+          sb[l] = w;
+          if (valid[i]) wlw[l] += w;
+          if (wo) wo[l] = w;
+        }
+        if (lane == 0 && valid[i]) ll_acc += (double)vref[i] + (double)mx + (double)logf(z);
       }
-      z = warp_sum(z);
-      const float inv = 1.f / z;
-      float* wo = a.w_out ? a.w_out + (size_t)img * Lw : nullptr;
-      for (int l = lane; l < Lw; l += 32) {
-        const float w = sbuf[l] * inv;
-        sbuf[l] = w;
-        wlw[l] += w;
-        if (wo) wo[l] = w;
-      }
-      if (lane == 0) ll_acc += (double)vref + (double)mx + (double)logf(z);
       __syncwarp();
 
-      // ---- back transform
+      // ---- back transform (twiddle loads shared by the IPW images)
 #pragma unroll
-      for (int m = 0; m < MR; ++m) W[m] = make_float2(0.f, 0.f);
+      for (int i = 0; i < IPW; ++i)
+#pragma unroll
+        for (int m = 0; m < MR; ++m) W[i][m] = make_float2(0.f, 0.f);
       for (int u0 = 0; u0 < NUP; u0 += 4 * kUC) {
-        float sw[kUC], dw[kUC];
+        float sw[IPW][kUC], dw[IPW][kUC];
 #pragma unroll
         for (int t = 0; t < kUC; ++t) {
           const int u = u0 + j + 4 * t;
-          float wa = 0.f, wb = 0.f;
-          if (u < NU) {
-            const int2 ab = uab[u];
-            wa = sbuf[ab.x];
-            wb = ab.y >= 0 ? sbuf[ab.y] : 0.f;
+          int2 ab = make_int2(0, -1);
+          if (u < NU) ab = uab[u];
+#pragma unroll
+          for (int i = 0; i < IPW; ++i) {
+            const float* sb = sbuf0 + i * a.sp;
+            const float wa = u < NU ? sb[ab.x] : 0.f;
+            const float wb = (u < NU && ab.y >= 0) ? sb[ab.y] : 0.f;
+            sw[i][t] = wa + wb;
+            dw[i][t] = wb - wa;
           }
-          sw[t] = wa + wb;
-          dw[t] = wb - wa;
         }
 #pragma unroll
         for (int m = 0; m < MR; ++m) {
@@ -397,26 +456,32 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR>::kThreads, 1) k_sweep_v2(
 #pragma unroll
             for (int t = 0; t < kUC; ++t) {
               const float2 tv = trow[4 * t];
-              W[m].x = fmaf(sw[t], tv.x, W[m].x);
-              W[m].y = fmaf(dw[t], tv.y, W[m].y);
+#pragma unroll
+              for (int i = 0; i < IPW; ++i) {
+                W[i][m].x = fmaf(sw[i][t], tv.x, W[i][m].x);
+                W[i][m].y = fmaf(dw[i][t], tv.y, W[i][m].y);
+              }
             }
           }
         }
       }
 #pragma unroll
-      for (int m = 0; m < MR; ++m) {
-        W[m].x += __shfl_xor_sync(0xffffffffu, W[m].x, 1);
-        W[m].y += __shfl_xor_sync(0xffffffffu, W[m].y, 1);
-        W[m].x += __shfl_xor_sync(0xffffffffu, W[m].x, 2);
-        W[m].y += __shfl_xor_sync(0xffffffffu, W[m].y, 2);
-      }
-      if (a.shift) {  // W_k e^{+i k theta_hat_j}
-        int ph = ph0;
+      for (int i = 0; i < IPW; ++i) {
 #pragma unroll
         for (int m = 0; m < MR; ++m) {
-          W[m] = cmul_conj_b(W[m], tfs[ph]);
-          ph += phstep;
-          if (ph >= L) ph -= L;
+          W[i][m].x += __shfl_xor_sync(0xffffffffu, W[i][m].x, 1);
+          W[i][m].y += __shfl_xor_sync(0xffffffffu, W[i][m].y, 1);
+          W[i][m].x += __shfl_xor_sync(0xffffffffu, W[i][m].x, 2);
+          W[i][m].y += __shfl_xor_sync(0xffffffffu, W[i][m].y, 2);
+        }
+        if (a.shift) {  // W_k e^{+i k theta_hat_j}
+          int ph = ph0[i];
+#pragma unroll
+          for (int m = 0; m < MR; ++m) {
+            W[i][m] = cmul_conj_b(W[i][m], tfs[ph]);
+            ph += phstep[i];
+            if (ph >= L) ph -= L;
+          }
         }
       }
     }
@@ -426,24 +491,27 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR>::kThreads, 1) k_sweep_v2(
     for (int m = 0; m < MR; ++m) {
       const int k = r + 8 * m;
       if (k < Kp1) {
-        const float2 w = W[m];
 #pragma unroll
-        for (int u = 0; u < QV; ++u) {
-          const float4 yv = y4[k * row4 + j + 4 * u];
-          float4& q = acc[m][u];
-          q.x = fmaf(w.x, yv.x, q.x); q.x = fmaf(-w.y, yv.y, q.x);
-          q.y = fmaf(w.x, yv.y, q.y); q.y = fmaf(w.y, yv.x, q.y);
-          q.z = fmaf(w.x, yv.z, q.z); q.z = fmaf(-w.y, yv.w, q.z);
-          q.w = fmaf(w.x, yv.w, q.w); q.w = fmaf(w.y, yv.z, q.w);
+        for (int i = 0; i < IPW; ++i) {
+          if (!valid[i]) continue;
+          const float2 w = W[i][m];
+#pragma unroll
+          for (int u = 0; u < QV; ++u) {
+            const float4 yv = y4[i][k * row4 + j + 4 * u];
+            float4& q = acc[m][u];
+            q.x = fmaf(w.x, yv.x, q.x); q.x = fmaf(-w.y, yv.y, q.x);
+            q.y = fmaf(w.x, yv.y, q.y); q.y = fmaf(w.y, yv.x, q.y);
+            q.z = fmaf(w.x, yv.z, q.z); q.z = fmaf(-w.y, yv.w, q.z);
+            q.w = fmaf(w.x, yv.w, q.w); q.w = fmaf(w.y, yv.z, q.w);
+          }
         }
       }
     }
-    // slot s may be refilled once every lane has finished reading it
+    // ring stage st may be refilled once every lane has finished reading it
     __syncwarp();
-    if (lane == 0 && img + 2 * GW < a.N) {
+    if (lane == 0) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_arrive_expect_tx(&mybar[s], img_bytes);
-      bulk_g2s(cur, a.y + (size_t)(img + 2 * GW) * M, img_bytes, &mybar[s]);
+      issue(p + 2, st);
     }
   }
 
@@ -486,19 +554,23 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR>::kThreads, 1) k_sweep_v2(
 
 }  // namespace mra
 
-// Instantiation table for one row width QV: MR = 1..7 rows per quad.
-#define MRA_SWEEP_V2_TABLE(QV)                                                                   \
-  namespace mra {                                                                               \
-  SweepV2Launch sweep_v2_q##QV(int MR) {                                                        \
-    switch (MR) {                                                                                \
-      case 1: return {k_sweep_v2<QV, 1>, SweepV2Shape<QV, 1>::kThreads};                         \
-      case 2: return {k_sweep_v2<QV, 2>, SweepV2Shape<QV, 2>::kThreads};                         \
-      case 3: return {k_sweep_v2<QV, 3>, SweepV2Shape<QV, 3>::kThreads};                         \
-      case 4: return {k_sweep_v2<QV, 4>, SweepV2Shape<QV, 4>::kThreads};                         \
-      case 5: return {k_sweep_v2<QV, 5>, SweepV2Shape<QV, 5>::kThreads};                         \
-      case 6: return {k_sweep_v2<QV, 6>, SweepV2Shape<QV, 6>::kThreads};                         \
-      case 7: return {k_sweep_v2<QV, 7>, SweepV2Shape<QV, 7>::kThreads};                         \
-      default: return {nullptr, 0};                                                              \
-    }                                                                                            \
-  }                                                                                              \
+// Instantiation table for one row width QV: MR = 1..7 rows per quad, IPW = 1 or 2 images per warp.
+#define MRA_SWEEP_V2_CASE(QV, MR)                                                                        \
+  case MR:                                                                                               \
+    return ipw == 2 ? SweepV2Launch{k_sweep_v2<QV, MR, 2>, SweepV2Shape<QV, MR, 2>::kThreads}             \
+                    : SweepV2Launch{k_sweep_v2<QV, MR, 1>, SweepV2Shape<QV, MR, 1>::kThreads};
+#define MRA_SWEEP_V2_TABLE(QV)                     \
+  namespace mra {                                 \
+  SweepV2Launch sweep_v2_q##QV(int MR, int ipw) { \
+    switch (MR) {                                  \
+      MRA_SWEEP_V2_CASE(QV, 1)                     \
+      MRA_SWEEP_V2_CASE(QV, 2)                     \
+      MRA_SWEEP_V2_CASE(QV, 3)                     \
+      MRA_SWEEP_V2_CASE(QV, 4)                     \
+      MRA_SWEEP_V2_CASE(QV, 5)                     \
+      MRA_SWEEP_V2_CASE(QV, 6)                     \
+      MRA_SWEEP_V2_CASE(QV, 7)                     \
+      default: return {nullptr, 0};                \
+    }                                              \
+  }                                                \
   }

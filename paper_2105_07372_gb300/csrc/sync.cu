@@ -80,18 +80,21 @@ __global__ void __launch_bounds__(kPairThreads) k_pairwise(const float2* y, int 
   }
 }
 
-// Projected power method, one CTA of 32 warps: warp w forms (Hz)_i for rows i = w, w+32, ...
-// with lanes striding over j.  rel is staged in shared memory as int16 when it fits.
+// Projected power method, one CTA: a group of g lanes (a power of two, g <= 32)
+// forms (Hz)_i for each row i, lanes striding over j, then sums with log2(g)
+// shuffles.  rel is staged in shared memory as int16 when it fits.
 constexpr int kPpmThreads = 1024;
 __global__ void __launch_bounds__(kPpmThreads) k_ppm(int L, int P, const int* rel, int n_power, int n_ppm, int* phi,
-                                                     int stage) {
+                                                     int stage, int g) {
   extern __shared__ __align__(16) unsigned char zsm[];
   float2* tf = reinterpret_cast<float2*>(zsm);  // [L]
   float2* z = tf + L;                           // [P]
   float2* zn = z + P;                           // [P]
   short* rs = reinterpret_cast<short*>(zn + P);  // [P][P] when staged
-  __shared__ float red[32];
+  __shared__ float red[33];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int rows_per_pass = kPpmThreads / g;
+  const int sub = tid % g, row0 = tid / g;
   for (int m = tid; m < L; m += kPpmThreads) {
     float s, c;
     sincospif(2.0f * (float)m / (float)L, &s, &c);
@@ -110,23 +113,28 @@ __global__ void __launch_bounds__(kPpmThreads) k_ppm(int L, int P, const int* re
   for (int it = 0; it < total; ++it) {
     const bool power = it < n_power;
     float part = 0.f;
-    for (int i = warp; i < P; i += 32) {
+    for (int i0 = 0; i0 < P; i0 += rows_per_pass) {
+      const int i = i0 + row0;
       float vr = 0.f, vi = 0.f;
-      for (int jj = lane; jj < P; jj += 32) {
-        int m;
-        if (stage) {
-          m = rs[i * P + jj];
-        } else {
-          m = rel[(size_t)i * P + jj] % L;
-          if (m < 0) m += L;
+      if (i < P) {
+        for (int jj = sub; jj < P; jj += g) {
+          int m;
+          if (stage) {
+            m = rs[i * P + jj];
+          } else {
+            m = rel[(size_t)i * P + jj] % L;
+            if (m < 0) m += L;
+          }
+          const float2 h = tf[m], zz = z[jj];
+          vr = fmaf(h.x, zz.x, fmaf(-h.y, zz.y, vr));
+          vi = fmaf(h.x, zz.y, fmaf(h.y, zz.x, vi));
         }
-        const float2 h = tf[m], zz = z[jj];
-        vr = fmaf(h.x, zz.x, fmaf(-h.y, zz.y, vr));
-        vi = fmaf(h.x, zz.y, fmaf(h.y, zz.x, vi));
       }
-      vr = warp_sum(vr);
-      vi = warp_sum(vi);
-      if (lane == 0) {
+      for (int o = 1; o < g; o <<= 1) {
+        vr += __shfl_xor_sync(0xffffffffu, vr, o);
+        vi += __shfl_xor_sync(0xffffffffu, vi, o);
+      }
+      if (i < P && sub == 0) {
         if (power) {
           zn[i] = make_float2(vr, vi);
           part += vr * vr + vi * vi;
@@ -136,15 +144,18 @@ __global__ void __launch_bounds__(kPpmThreads) k_ppm(int L, int P, const int* re
         }
       }
     }
-    float inv = 1.f;
     if (power) {
+      part = warp_sum(part);
       if (lane == 0) red[warp] = part;
       __syncthreads();
-      float t = 0.f;
-      for (int w = 0; w < 32; ++w) t += red[w];
-      inv = t > 0.f ? rsqrtf(t) : 1.f;
+      if (warp == 0) {
+        float t = red[lane];
+        t = warp_sum(t);
+        if (lane == 0) red[32] = t > 0.f ? rsqrtf(t) : 1.f;
+      }
     }
     __syncthreads();
+    const float inv = power ? red[32] : 1.f;
     for (int i = tid; i < P; i += kPpmThreads) {
       const float2 v = zn[i];
       z[i] = power ? make_float2(v.x * inv, v.y * inv) : v;
@@ -498,7 +509,9 @@ MRA_API int mra_sync_ppm(int32_t L, int32_t P, const int32_t* rel, int32_t n_pow
       cudaFuncSetAttribute(reinterpret_cast<const void*>(k_ppm), cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
           cudaSuccess)
     return MRA_ECUDA;
-  k_ppm<<<1, kPpmThreads, smem, static_cast<cudaStream_t>(stream)>>>(L, P, rel, n_power, n_ppm, phi_out, stage);
+  int g = 32;  // lanes per row: the largest power of two with g * P <= 1024
+  while (g > 1 && g * P > kPpmThreads) g >>= 1;
+  k_ppm<<<1, kPpmThreads, smem, static_cast<cudaStream_t>(stream)>>>(L, P, rel, n_power, n_ppm, phi_out, stage, g);
   return cudaGetLastError() == cudaSuccess ? MRA_OK : MRA_ECUDA;
 }
 
