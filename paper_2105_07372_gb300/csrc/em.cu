@@ -632,17 +632,14 @@ __global__ void k_update(const UpdateArgs a) {
     if (lane == 0) d32[k] = make_float2(dr, di);
   }
   __syncthreads();
-  const double ll = a.tot[2 * a.M + a.Lw] - a.beta * ysq_total - (double)a.N * a.beta * nx_old -
-                    (double)a.N * (double)a.M * log(kPi * a.sigma2);
 
   // rho update
   if (a.update_rho) {
     double v = 0.0;
     for (int l = tid; l < a.Lw; l += nt) v += a.tot[2 * a.M + l] + a.gamma * a.rhobar64[l];
     const double tsum = block_sum_d(v, red);
-    const double inv = 1.0 / tsum;
     for (int l = tid; l < a.Lw; l += nt) {
-      const double r = (a.tot[2 * a.M + l] + a.gamma * a.rhobar64[l]) * inv;
+      const double r = (a.tot[2 * a.M + l] + a.gamma * a.rhobar64[l]) / tsum;
       a.rho64[l] = r;
       a.logrho32[l] = r > 1e-30 ? logf((float)r) : (float)log(r);
       if (a.log_rho_out) a.log_rho_out[l] = log(r);
@@ -707,6 +704,8 @@ __global__ void k_update(const UpdateArgs a) {
     if (a.x_out) a.x_out[e] = v;
   }
   if (tid == 0) {
+    const double ll = a.tot[2 * a.M + a.Lw] - a.beta * ysq_total - (double)a.N * a.beta * nx_old -
+                      (double)a.N * (double)a.M * log(kPi * a.sigma2);
     if (a.stats) {
       a.stats[2 * iter] = ll;
       a.stats[2 * iter + 1] = step;

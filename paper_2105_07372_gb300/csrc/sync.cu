@@ -90,7 +90,8 @@ __global__ void __launch_bounds__(kPpmThreads) k_ppm(int L, int P, const int* re
   float2* tf = reinterpret_cast<float2*>(zsm);  // [L]
   float2* z = tf + L;                           // [P]
   float2* zn = z + P;                           // [P]
-  short* rs = reinterpret_cast<short*>(zn + P);  // [P][P] when staged
+  float2* hs = zn + P;                           // [P][P] H when stage == 2
+  short* rs = reinterpret_cast<short*>(zn + P);  // [P][P] twiddle indices when stage == 1
   __shared__ float red[33];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int rows_per_pass = kPpmThreads / g;
@@ -101,11 +102,13 @@ __global__ void __launch_bounds__(kPpmThreads) k_ppm(int L, int P, const int* re
     tf[m] = make_float2(c, -s);
   }
   for (int i = tid; i < P; i += kPpmThreads) z[i] = make_float2(1.f, 0.f);
+  __syncthreads();
   if (stage) {
     for (int e = tid; e < P * P; e += kPpmThreads) {
       int m = rel[e] % L;
       if (m < 0) m += L;
-      rs[e] = (short)m;
+      if (stage == 2) hs[e] = tf[m];
+      else rs[e] = (short)m;
     }
   }
   __syncthreads();
@@ -117,15 +120,22 @@ __global__ void __launch_bounds__(kPpmThreads) k_ppm(int L, int P, const int* re
       const int i = i0 + row0;
       float vr = 0.f, vi = 0.f;
       if (i < P) {
+#pragma unroll 4
         for (int jj = sub; jj < P; jj += g) {
-          int m;
-          if (stage) {
-            m = rs[i * P + jj];
+          float2 h;
+          if (stage == 2) {
+            h = hs[i * P + jj];
           } else {
-            m = rel[(size_t)i * P + jj] % L;
-            if (m < 0) m += L;
+            int m;
+            if (stage == 1) {
+              m = rs[i * P + jj];
+            } else {
+              m = rel[(size_t)i * P + jj] % L;
+              if (m < 0) m += L;
+            }
+            h = tf[m];
           }
-          const float2 h = tf[m], zz = z[jj];
+          const float2 zz = z[jj];
           vr = fmaf(h.x, zz.x, fmaf(-h.y, zz.y, vr));
           vi = fmaf(h.x, zz.y, fmaf(h.y, zz.x, vi));
         }
@@ -185,44 +195,63 @@ __global__ void k_refnorm(const float* y, int D, int P, float* nrm) {
 
 // Matching: 128 queries x 128 references per tile, 16 real coordinates per step,
 // 8 x 8 outputs per thread; score = ||y_n||^2 - 2 <y_i, y_n>, running argmin per query.
+// The next step's coordinates are fetched into registers while the current step
+// computes from the other shared-memory buffer.
 constexpr int kMT = 128, kKC = 16;
 __global__ void __launch_bounds__(256) k_match(const float* y, int N, int D, int P, const float* nrm, const int* phi,
                                                int* shift_out) {
-  __shared__ __align__(16) float As[kKC][kMT + 4];
-  __shared__ __align__(16) float Bs[kKC][kMT + 4];
+  __shared__ __align__(16) float As[2][kKC][kMT + 4];
+  __shared__ __align__(16) float Bs[2][kKC][kMT + 4];
   const int tid = threadIdx.x;
   const int tr = tid & 15, tq = tid >> 4;
   const int q0 = blockIdx.x * kMT;
+  const int lrow = tid >> 1, lh = (tid & 1) * 8;  // loader: row and 8-coordinate half of a step
   float bestv[8];
   int besti[8];
 #pragma unroll
   for (int u = 0; u < 8; ++u) bestv[u] = INFINITY, besti[u] = 0x7fffffff;
 
   for (int r0 = 0; r0 < P; r0 += kMT) {
+    const int qi = q0 + lrow, ri = r0 + lrow;
+    const float* qa = y + (size_t)min(qi, N - 1) * D;
+    const float* ra = y + (size_t)min(ri, P - 1) * D;
+    float4 pa[2], pb[2];
+    auto fetch = [&](int kc) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int d = kc + lh + 4 * h;
+        const bool in = d < D;
+        pa[h] = (qi < N && in) ? *reinterpret_cast<const float4*>(qa + d) : make_float4(0.f, 0.f, 0.f, 0.f);
+        pb[h] = (ri < P && in) ? *reinterpret_cast<const float4*>(ra + d) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    };
+    auto stash = [&](int buf) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int e = lh + 4 * h;
+        As[buf][e][lrow] = pa[h].x; As[buf][e + 1][lrow] = pa[h].y;
+        As[buf][e + 2][lrow] = pa[h].z; As[buf][e + 3][lrow] = pa[h].w;
+        Bs[buf][e][lrow] = pb[h].x; Bs[buf][e + 1][lrow] = pb[h].y;
+        Bs[buf][e + 2][lrow] = pb[h].z; Bs[buf][e + 3][lrow] = pb[h].w;
+      }
+    };
     float acc[8][8];
 #pragma unroll
     for (int u = 0; u < 8; ++u)
 #pragma unroll
       for (int v = 0; v < 8; ++v) acc[u][v] = 0.f;
-    for (int kc = 0; kc < D; kc += kKC) {
-      // load: thread -> (row = tid/2, 8 coordinates at kc + 8*(tid&1))
-      {
-        const int row = tid >> 1, h = (tid & 1) * 8;
-        const int qi = q0 + row, ri = r0 + row;
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int d = kc + h + e;
-          As[h + e][row] = (qi < N && d < D) ? y[(size_t)qi * D + d] : 0.f;
-          Bs[h + e][row] = (ri < P && d < D) ? y[(size_t)ri * D + d] : 0.f;
-        }
-      }
+    fetch(0);
+    int buf = 0;
+    for (int kc = 0; kc < D; kc += kKC, buf ^= 1) {
+      stash(buf);
       __syncthreads();
+      if (kc + kKC < D) fetch(kc + kKC);
 #pragma unroll
       for (int kk = 0; kk < kKC; ++kk) {
-        const float4 a0 = *reinterpret_cast<const float4*>(&As[kk][tq * 4]);
-        const float4 a1 = *reinterpret_cast<const float4*>(&As[kk][64 + tq * 4]);
-        const float4 b0 = *reinterpret_cast<const float4*>(&Bs[kk][tr * 4]);
-        const float4 b1 = *reinterpret_cast<const float4*>(&Bs[kk][64 + tr * 4]);
+        const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][tq * 4]);
+        const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][64 + tq * 4]);
+        const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tr * 4]);
+        const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][64 + tr * 4]);
         const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
         const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
@@ -230,15 +259,15 @@ __global__ void __launch_bounds__(256) k_match(const float* y, int N, int D, int
 #pragma unroll
           for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
       }
-      __syncthreads();
     }
+    __syncthreads();  // the buffers are refilled by the next reference tile
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      const int qi = q0 + (u < 4 ? tq * 4 + u : 64 + tq * 4 + (u - 4));
+      const int q = q0 + (u < 4 ? tq * 4 + u : 64 + tq * 4 + (u - 4));
 #pragma unroll
       for (int v = 0; v < 8; ++v) {
         const int n = r0 + (v < 4 ? tr * 4 + v : 64 + tr * 4 + (v - 4));
-        if (n < P && n != qi) {
+        if (n < P && n != q) {
           const float sc = nrm[n] - 2.f * acc[u][v];
           if (sc < bestv[u] || (sc == bestv[u] && n < besti[u])) bestv[u] = sc, besti[u] = n;
         }
@@ -255,8 +284,8 @@ __global__ void __launch_bounds__(256) k_match(const float* y, int N, int D, int
       const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
       if (ov < bv || (ov == bv && oi < bi)) bv = ov, bi = oi;
     }
-    const int qi = q0 + (u < 4 ? tq * 4 + u : 64 + tq * 4 + (u - 4));
-    if (tr == 0 && qi < N) shift_out[qi] = (bi < P) ? phi[bi] : 0;
+    const int q = q0 + (u < 4 ? tq * 4 + u : 64 + tq * 4 + (u - 4));
+    if (tr == 0 && q < N) shift_out[q] = (bi < P) ? phi[bi] : 0;
   }
 }
 
@@ -503,8 +532,8 @@ MRA_API int mra_sync_ppm(int32_t L, int32_t P, const int32_t* rel, int32_t n_pow
   if (L < 1 || L > 8192 || P < 1 || P > 1024 || n_power < 0 || n_ppm < 0 || !ok_ptr(rel, 4) || !ok_ptr(phi_out, 4))
     return MRA_EINVAL;
   const int base = (L + 2 * P) * 8;
-  const int stage = (base + P * P * 2 <= 200 * 1024) ? 1 : 0;
-  const int smem = base + (stage ? P * P * 2 : 0);
+  const int stage = (base + P * P * 8 <= 200 * 1024) ? 2 : (base + P * P * 2 <= 200 * 1024) ? 1 : 0;
+  const int smem = base + (stage == 2 ? P * P * 8 : stage == 1 ? P * P * 2 : 0);
   if (smem > 48 * 1024 &&
       cudaFuncSetAttribute(reinterpret_cast<const void*>(k_ppm), cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
           cudaSuccess)

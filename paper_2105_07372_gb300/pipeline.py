@@ -56,6 +56,20 @@ def learn_prior(y, d, shift_true, shift_est, x_true, Lw, l0=None, kind=0, ws: Wo
     return log_prior, kappa, hist
 
 
+def window_for_mass(hist: torch.Tensor, L: int, mass: float) -> int:
+    """Smallest window Lw (offsets -Lw//2 .. Lw-1-Lw//2 around the synchronized estimate) holding
+    at least `mass` of the learned residual distribution (Sec. 3.3: BW chosen from the learned
+    distribution).  Host-side choice of a parameter from the L histogram counts."""
+    h = hist.detach().double().cpu()
+    tot = float(h.sum())
+    for Lw in range(1, L + 1):
+        l0 = -(Lw // 2)
+        idx = torch.arange(l0, l0 + Lw) % L
+        if float(h[idx].sum()) >= mass * tot:
+            return Lw
+    return L
+
+
 def synch_em(y, d, *, P, Lw, iters, gamma, log_rho_bar, ws: Workspaces, shift=None, tol=0.0, check_every=None,
              stats=True, x_traj=None, stream=None) -> SynchEMResult:
     """Steps 1-4 given the learned window prior log_rho_bar [Lw] (float64 device tensor)."""
