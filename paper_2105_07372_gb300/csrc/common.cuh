@@ -117,7 +117,7 @@ struct EmLayout {
   int kp4;      // K+1 rounded up to a multiple of 4 (rows of the table)
   int cols;     // 2M + Lw + 2 reduced columns
   int nup;      // mirror units padded to a multiple of kUnitChunk
-  size_t ctrl, tf32, tf64, tw, x32, x64, inv_den, logrho32, rho64, rhobar64, units, tu, part, tot, total;
+  size_t ctrl, tf32, tf64, tw, x32, x64, inv_den, logrho32, rho64, rhobar64, units, tu, td, part, tot, total;
 };
 
 __host__ __device__ inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
@@ -147,6 +147,7 @@ inline EmLayout em_layout(int N, int K, int Q, int L, int Lw, int G) {
   l.rhobar64 = o;  o = align256(o + sizeof(double) * Lw);
   l.units = o;     o = align256(o + sizeof(int2) * l.nup);
   l.tu = o;        o = align256(o + sizeof(float2) * (size_t)l.Kp1 * l.nup);
+  l.td = o;        o = align256(o + sizeof(float2) * (size_t)l.Kp1 * (size_t)(Lw > L / 2 + 1 ? Lw : L / 2 + 1));
   l.part = o;      o = align256(o + sizeof(double) * (size_t)l.cols * G);
   l.tot = o;       o = align256(o + sizeof(double) * (l.cols + 8));
   l.total = o;
@@ -183,6 +184,38 @@ SweepV2Launch sweep_v2_q1(int MR, int ipw);
 SweepV2Launch sweep_v2_q2(int MR, int ipw);
 SweepV2Launch sweep_v2_q3(int MR, int ipw);
 SweepV2Launch sweep_v2_q4(int MR, int ipw);
+
+// Arguments of the CTA-cooperative sweep (sweep3_impl.cuh), launched with kV3Threads threads.
+constexpr int kV3Threads = 512;
+struct SweepV3Args {
+  const float2* y;
+  const int* shift;
+  int N, Kp1, M, L, Lw;
+  int ns;          // ring stages
+  int slot_bytes;  // bytes per ring slot (an odd number of 16-byte words)
+  int cp, sp, dp;  // per-image pitches (odd) of the c/W, s/w and unit-weight buffers
+  int nd;          // distance units in the table: L/2 + 1 for the whole circle, else Lw
+  int wrap;        // 1: the window is the whole circle (Lw == L), indices wrap
+  int r0, d1;      // first reference (window index) and the distance pass 1 covers
+  int fsplit;      // threads per forward item (1 or 2)
+  int phase0;      // (l0 + r0) mod L
+  int off_ring, off_x, off_xr, off_td, off_tf, off_lr, off_c, off_s, off_w2, off_info, off_wl;
+  float two_beta;
+  double two_beta_d;
+  const float2* x32;
+  const float2* td;  // [Kp1][nd] (cos 2 pi k d / L - 1, -sin 2 pi k d / L)
+  const float2* tf32;
+  const float* logrho32;
+  double* part;
+  float* w_out;
+  Ctrl* ctrl;
+};
+typedef void (*SweepV3Fn)(const SweepV3Args);
+// QH = float4 per row (Q / 2); bi = images per batch (16, 12, 8 or 4).
+SweepV3Fn sweep_v3_qh4(int bi);
+SweepV3Fn sweep_v3_qh8(int bi);
+SweepV3Fn sweep_v3_qh12(int bi);
+SweepV3Fn sweep_v3_qh16(int bi);
 
 // Mirror units of a window: offsets o and -o (mod L) share cos/sin.  Writes the
 // (a, b) index pairs in window order of a; returns the number of units.

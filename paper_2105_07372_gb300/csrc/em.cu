@@ -19,6 +19,8 @@
 // c_jk and W_jk; y itself is read once per iteration and never rewritten.
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
 
 #include <algorithm>
 #include <mutex>
@@ -74,7 +76,8 @@ struct SetupArgs {
   double* rhobar64;
   int2* units;  // [nup]
   float2* tu;   // [Kp1][nup]
-  int nu, nup;
+  float2* td;   // [Kp1][nd]
+  int nu, nup, nd;
   Ctrl* ctrl;
 };
 
@@ -150,6 +153,20 @@ __global__ void k_setup_tu(const SetupArgs a) {
       v = a.tf32[(int)(((long long)k * off) % a.L)];
     }
     a.tu[idx] = v;
+  }
+}
+
+// Distance-unit table of the batch sweep: (cos t - 1, -sin t), t = 2 pi k d / L, with
+// cos t - 1 = -2 sin^2(t / 2) so that small angles keep their relative precision (FP64).
+__global__ void k_setup_td(const SetupArgs a) {
+  const int n = a.Kp1 * a.nd;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+    const int k = idx / a.nd, d = idx - k * a.nd;
+    const int m = (int)(((long long)k * d) % a.L);
+    double sh, ch, s, c;
+    sincospi((double)m / (double)a.L, &sh, &ch);
+    sincospi(2.0 * (double)m / (double)a.L, &s, &c);
+    a.td[idx] = make_float2((float)(-2.0 * sh * sh), (float)(-s));
   }
 }
 
@@ -968,6 +985,80 @@ bool plan_v2(int Kp1, int Q, int L, int Lw, int nup, int max_smem, V2Plan* p) {
   return false;
 }
 
+struct V3Plan {
+  SweepV3Fn fn;
+  int bi, ns, slot_bytes, cp, sp, dp, nd, wrap, r0, d1, phase0, fsplit, smem;
+  int off_ring, off_x, off_xr, off_td, off_tf, off_lr, off_c, off_s, off_w2, off_info, off_wl;
+};
+
+// Shared-memory plan of the CTA-cooperative sweep: the first (batch, stages) of
+// (16, 2), (12, 2), (8, 3), (8, 2), (4, 3), (4, 2) whose ring and tables fit.  Per-image pitches
+// are odd (in words of their element type) so that the images of one warp fall in
+// distinct banks.
+bool plan_v3(int Kp1, int Q, int L, int Lw, int l0, int max_smem, V3Plan* p) {
+  if (Q % 8 != 0) return false;
+  const int QH = Q / 2;
+  if (Kp1 * (QH / 2) > kV3Threads) return false;
+  const int M = Kp1 * Q;
+  int words = (M * 8 + 15) / 16;
+  if (words % 2 == 0) ++words;
+  const int slot = words * 16;
+  p->wrap = Lw == L ? 1 : 0;
+  p->nd = p->wrap ? L / 2 + 1 : Lw;
+  int r0 = (-l0) % L;
+  if (r0 < 0) r0 += L;
+  if (r0 >= Lw) r0 = Lw / 2;  // rotation 0 outside the window: start from its centre
+  p->r0 = r0;
+  p->d1 = p->wrap ? L / 2 : std::max(r0, Lw - 1 - r0);
+  p->phase0 = ((l0 + r0) % L + L) % L;
+  const int cp = Kp1 | 1, sp = Lw | 1, dp = p->nd | 1;
+  const int cfg[6][2] = {{16, 2}, {12, 2}, {8, 3}, {8, 2}, {4, 3}, {4, 2}};
+  const char* fb = getenv("MRA_SWEEP_BI");  // batch and stages for tuning runs
+  const char* fs = getenv("MRA_SWEEP_NS");
+  const int want_bi = fb ? atoi(fb) : 0, want_ns = fs ? atoi(fs) : 0;
+  for (const auto& bn : cfg) {
+    const int bi = bn[0], ns = bn[1];
+    if ((want_bi && bi != want_bi) || (want_ns && ns != want_ns)) continue;
+    const SweepV3Fn fn = QH == 4 ? sweep_v3_qh4(bi) : QH == 8 ? sweep_v3_qh8(bi)
+                       : QH == 12 ? sweep_v3_qh12(bi) : QH == 16 ? sweep_v3_qh16(bi) : nullptr;
+    if (!fn) return false;
+    int o = 128;  // ring mbarriers
+    p->off_ring = o; o += ns * bi * slot;
+    p->off_x = o; o += al16(M * 8);
+    p->off_xr = o; o += al16(M * 8);
+    p->off_td = o; o += al16(Kp1 * dp * 8);
+    p->off_tf = o; o += al16(L * 8);
+    p->off_lr = o; o += al16(Lw * 4);
+    p->off_c = o; o += al16(bi * cp * 8);
+    p->off_s = o; o += al16(bi * sp * 4);
+    p->off_w2 = o; o += al16(bi * dp * 8);
+    p->off_info = o; o += al16(bi * 16);
+    p->off_wl = o; o += al16((kV3Threads / 32) * sp * 4);
+    if (o + 1024 <= max_smem) {
+      p->fn = fn;
+      p->bi = bi;
+      p->ns = ns;
+      p->slot_bytes = slot;
+      p->cp = cp; p->sp = sp; p->dp = dp;
+      p->fsplit = (p->d1 + 1) * bi * 2 <= kV3Threads ? 2 : 1;  // two threads per forward item if all fit
+      p->smem = o;
+      return true;
+    }
+  }
+  return false;
+}
+
+// MRA_SWEEP=warp or MRA_SWEEP=cta selects one EM sweep where both apply (for comparisons);
+// MRA_SWEEP_BI=16|12|8|4 and MRA_SWEEP_NS=2|3 fix the batch and ring stages of the
+// CTA-cooperative sweep (for tuning).  0: automatic, 1: warp, 2: cta.
+int sweep_choice() {
+  const char* e = getenv("MRA_SWEEP");
+  if (!e) return 0;
+  if (strcmp(e, "warp") == 0) return 1;
+  if (strcmp(e, "cta") == 0) return 2;
+  return 0;
+}
+
 typedef void (*SweepFn)(const SweepArgs);
 
 SweepFn pick_sweep(bool qeven, int ncolmax) {
@@ -1012,14 +1103,18 @@ struct EmCall {
   bool v2;  // warp-per-image sweep (rows of Q a multiple of 8) instead of the tile sweep
   V2Plan v2p;
   SweepV2Args sa2;
+  bool v3;  // CTA-cooperative sweep over image batches
+  V3Plan v3p;
+  SweepV3Args sa3;
   void set_w_out(float* w) {
     sa.w_out = w;
     sa2.w_out = w;
+    sa3.w_out = w;
   }
 };
 
 int prepare(const mra_dims* d, int Lw, int l0, const float* y, const int32_t* shift, void* ws, size_t ws_bytes,
-            EmCall* c) {
+            EmCall* c, bool allow_v3 = true) {
   int st = check_dims(d);
   if (st != MRA_OK) return st;
   if (Lw < 1 || Lw > d->L) return MRA_EINVAL;
@@ -1033,8 +1128,18 @@ int prepare(const mra_dims* d, int Lw, int l0, const float* y, const int32_t* sh
   const int Kp1 = d->K + 1, M = Kp1 * d->Q;
   const int nu = window_units(d->L, Lw, l0, nullptr);
   const int nup = round_up(nu, kUnitChunk);
+  // The warp sweep keeps a window of one unit chunk in registers and is the faster one
+  // there; wider windows (up to the whole circle) go to the batch sweep.
   c->v2 = plan_v2(Kp1, d->Q, d->L, Lw, nup, di.max_smem_optin, &c->v2p);
-  if (c->v2) {
+  c->v3 = allow_v3 && sweep_choice() != 1 && (!c->v2 || nup > kUnitChunk || sweep_choice() == 2) &&
+          plan_v3(Kp1, d->Q, d->L, Lw, l0, di.max_smem_optin, &c->v3p);
+  if (c->v3) c->v2 = false;
+  if (c->v3) {
+    if (cudaFuncSetAttribute(reinterpret_cast<const void*>(c->v3p.fn), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             c->v3p.smem) != cudaSuccess)
+      return MRA_ECUDA;
+    c->sweep = nullptr;
+  } else if (c->v2) {
     if (cudaFuncSetAttribute(reinterpret_cast<const void*>(c->v2p.launch.fn),
                              cudaFuncAttributeMaxDynamicSharedMemorySize, c->v2p.smem) != cudaSuccess)
       return MRA_ECUDA;
@@ -1093,6 +1198,26 @@ int prepare(const mra_dims* d, int Lw, int l0, const float* y, const int32_t* sh
   v.w_out = nullptr;
   v.ctrl = c->ctrl;
 
+  SweepV3Args& w = c->sa3;
+  const V3Plan& q3 = c->v3p;
+  w.y = s.y;
+  w.shift = shift;
+  w.N = d->N; w.Kp1 = Kp1; w.M = M; w.L = d->L; w.Lw = Lw;
+  w.ns = q3.ns; w.slot_bytes = q3.slot_bytes; w.cp = q3.cp; w.sp = q3.sp; w.dp = q3.dp; w.nd = q3.nd;
+  w.wrap = q3.wrap; w.r0 = q3.r0; w.d1 = q3.d1; w.phase0 = q3.phase0; w.fsplit = q3.fsplit;
+  w.off_ring = q3.off_ring; w.off_x = q3.off_x; w.off_xr = q3.off_xr; w.off_td = q3.off_td; w.off_tf = q3.off_tf;
+  w.off_lr = q3.off_lr; w.off_c = q3.off_c; w.off_s = q3.off_s; w.off_w2 = q3.off_w2; w.off_info = q3.off_info;
+  w.off_wl = q3.off_wl;
+  w.two_beta = s.two_beta;
+  w.two_beta_d = 2.0 / d->sigma2;
+  w.x32 = s.x32;
+  w.td = reinterpret_cast<const float2*>(base + L_.td);
+  w.tf32 = s.tf32;
+  w.logrho32 = s.logrho32;
+  w.part = s.part;
+  w.w_out = nullptr;
+  w.ctrl = c->ctrl;
+
   SetupArgs& u = c->su;
   u.N = d->N; u.Kp1 = Kp1; u.Q = d->Q; u.M = M; u.L = d->L; u.Lw = Lw;
   u.l0 = l0; u.twp = L_.twp; u.kp4 = L_.kp4; u.sigma2 = d->sigma2;
@@ -1108,6 +1233,8 @@ int prepare(const mra_dims* d, int Lw, int l0, const float* y, const int32_t* sh
   u.rhobar64 = reinterpret_cast<double*>(base + L_.rhobar64);
   u.units = reinterpret_cast<int2*>(base + L_.units);
   u.tu = reinterpret_cast<float2*>(base + L_.tu);
+  u.td = reinterpret_cast<float2*>(base + L_.td);
+  u.nd = c->v3 ? c->v3p.nd : 0;
   u.nu = nu;
   u.nup = nup;
   u.ctrl = c->ctrl;
@@ -1134,7 +1261,10 @@ int launch_setup(const EmCall& c, cudaStream_t st) {
   const int n = std::max(std::max(c.su.L, c.su.M), c.su.Lw);
   const int blocks = std::min(1024, (n + 127) / 128);
   k_setup<<<blocks, 128, 0, st>>>(c.su);
-  if (c.v2) {
+  if (c.v3) {
+    const int ntd = c.su.Kp1 * c.su.nd;
+    k_setup_td<<<std::min(1024, (ntd + 255) / 256), 256, 0, st>>>(c.su);
+  } else if (c.v2) {
     k_setup_units<<<1, 32, 0, st>>>(c.su);
     const int ntu = c.su.Kp1 * c.su.nup;
     k_setup_tu<<<std::min(1024, (ntu + 255) / 256), 256, 0, st>>>(c.su);
@@ -1146,7 +1276,9 @@ int launch_setup(const EmCall& c, cudaStream_t st) {
 }
 
 void launch_sweep(const EmCall& c, cudaStream_t st) {
-  if (c.v2)
+  if (c.v3)
+    c.v3p.fn<<<c.lay.G, kV3Threads, c.v3p.smem, st>>>(c.sa3);
+  else if (c.v2)
     c.v2p.launch.fn<<<c.lay.G, c.v2p.launch.threads, c.v2p.smem, st>>>(c.sa2);
   else
     c.sweep<<<c.lay.G, kSweepThreads, c.plan.smem, st>>>(c.sa);
@@ -1354,7 +1486,7 @@ MRA_API int mra_loglik_grad(const mra_dims* d, int32_t Lw, int32_t l0, const flo
 
 static int align_into_tot(const mra_dims* d, const float* y, const int32_t* shift, void* ws, size_t ws_bytes,
                           cudaStream_t s, EmCall* c) {
-  int st = prepare(d, 1, 0, y, shift, ws, ws_bytes, c);
+  int st = prepare(d, 1, 0, y, shift, ws, ws_bytes, c, /*allow_v3=*/false);  // align mode lives in the warp sweep
   if (st != MRA_OK) return st;
   const bool qeven = (d->Q % 2) == 0;
   const int M = c->lay.M, vec = qeven ? 2 : 1;

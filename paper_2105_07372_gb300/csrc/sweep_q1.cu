@@ -1,4 +1,7 @@
-// Warp-per-image EM sweep for rows of 8 coefficients (1 float4 per lane per row).
+// EM sweeps for rows of 8 coefficients: warp per image (1 float4 per lane per row) and
+// CTA-cooperative batches (4 float4 per row).
 #include "sweep_impl.cuh"
+#include "sweep3_impl.cuh"
 
 MRA_SWEEP_V2_TABLE(1)
+MRA_SWEEP_V3_TABLE(4)

@@ -1,4 +1,7 @@
-// Warp-per-image EM sweep for rows of 16 coefficients (2 float4 per lane per row).
+// EM sweeps for rows of 16 coefficients: warp per image (2 float4 per lane per row) and
+// CTA-cooperative batches (8 float4 per row).
 #include "sweep_impl.cuh"
+#include "sweep3_impl.cuh"
 
 MRA_SWEEP_V2_TABLE(2)
+MRA_SWEEP_V3_TABLE(8)

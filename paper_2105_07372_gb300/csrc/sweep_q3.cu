@@ -1,4 +1,7 @@
-// Warp-per-image EM sweep for rows of 24 coefficients (3 float4 per lane per row).
+// EM sweeps for rows of 24 coefficients: warp per image (3 float4 per lane per row) and
+// CTA-cooperative batches (12 float4 per row).
 #include "sweep_impl.cuh"
+#include "sweep3_impl.cuh"
 
 MRA_SWEEP_V2_TABLE(3)
+MRA_SWEEP_V3_TABLE(12)

@@ -49,7 +49,14 @@ def compare(mra, inst, x, log_rho, Lw, l0=None, shifts=None, **kw):
     return xg, st
 
 
-def test_em_step_config1_window(gpu_lib):
+@pytest.fixture(params=["cta", "warp"])
+def sweep(request, monkeypatch):
+    """Both EM sweeps: the CTA-cooperative batch sweep and the warp-per-image one."""
+    monkeypatch.setenv("MRA_SWEEP", request.param)
+    return request.param
+
+
+def test_em_step_config1_window(gpu_lib, sweep):
     c = synth.config(1)
     inst = synth.make_instance(c["K"], c["Q"], c["N"], c["L"], c["snr"], c["decay"], seed=1001)
     x0 = O.align_mean(synth.c64_round(inst.y), inst.s, inst.L)
@@ -71,7 +78,7 @@ def test_em_step_config1_prior_gamma(gpu_lib):
     compare(gpu_lib, inst, x0, lr, Lw, shifts=sh, gamma=c["gamma"], log_rho_bar=lrb)
 
 
-def test_em_step_full_search_and_signal_prior(gpu_lib):
+def test_em_step_full_search_and_signal_prior(gpu_lib, sweep):
     c = synth.config(1)
     inst = synth.make_instance(c["K"], c["Q"], 300, c["L"], c["snr"], c["decay"], seed=1003)
     x0 = synth.random_init(inst.K, inst.Q, c["decay"], seed=5)
@@ -82,15 +89,17 @@ def test_em_step_full_search_and_signal_prior(gpu_lib):
 
 
 @pytest.mark.parametrize("K,Q,N,L,Lw", [(5, 3, 77, 30, 7), (0, 2, 40, 12, 5), (3, 4, 1, 16, 16), (7, 6, 33, 50, 1),
-                                        (12, 10, 500, 90, 13)])
-def test_em_step_shapes_and_edges(gpu_lib, K, Q, N, L, Lw):
-    """Odd Q (float2 path), K = 0, N = 1, Lw = L, Lw = 1, ragged tiles."""
+                                        (12, 10, 500, 90, 13), (4, 8, 1, 16, 16), (6, 16, 301, 40, 9),
+                                        (48, 32, 203, 72, 72), (63, 8, 150, 128, 20)])
+def test_em_step_shapes_and_edges(gpu_lib, sweep, K, Q, N, L, Lw):
+    """Odd Q (float2 path), K = 0, N = 1, Lw = L, Lw = 1, ragged tiles and batches, the
+    largest rows (M = 1568) and the most rows (64) of the batch sweep."""
     inst = synth.make_instance(K, Q, N, L, sigma2=1 / (0.3 * (K + 1) * Q), decay=20.0, seed=K * 100 + N)
     x0 = synth.random_init(K, Q, 20.0, seed=3)
     compare(gpu_lib, inst, x0, np.log(np.full(Lw, 1 / Lw)), Lw, shifts=inst.s, update_rho=(Lw % 2 == 1))
 
 
-def test_em_step_config2_subset_several_tiles(gpu_lib):
+def test_em_step_config2_subset_several_tiles(gpu_lib, sweep):
     c = synth.config(2)
     inst = synth.make_instance(c["K"], c["Q"], 4097, c["L"], c["snr"], c["decay"], seed=2001)
     y64 = synth.c64_round(inst.y)
@@ -99,6 +108,17 @@ def test_em_step_config2_subset_several_tiles(gpu_lib):
     x0 = O.align_mean(y64, sh, inst.L)
     Lw = c["Lw"]
     compare(gpu_lib, inst, x0, np.log(np.full(Lw, 1 / Lw)), Lw, shifts=sh)
+
+
+@pytest.mark.parametrize("bi", ["16", "12", "8", "4"])
+def test_em_step_batch_sizes(gpu_lib, bi, monkeypatch):
+    """Every batch size of the CTA-cooperative sweep, with a ragged last batch."""
+    monkeypatch.setenv("MRA_SWEEP", "cta")
+    monkeypatch.setenv("MRA_SWEEP_BI", bi)
+    inst = synth.make_instance(7, 8, 1000 + 13, 36, sigma2=1 / (0.3 * 64), decay=20.0, seed=77)
+    x0 = synth.random_init(7, 8, 20.0, seed=3)
+    Lw = 11
+    compare(gpu_lib, inst, x0, np.log(np.full(Lw, 1 / Lw)), Lw, shifts=inst.s)
 
 
 def test_em_run_trajectory_resume_and_tol(gpu_lib):
