@@ -132,6 +132,29 @@ MRA_API int mra_em_run(const mra_dims* dims, const mra_em_params* prm, const flo
                        double* x_inout, double* log_rho_inout, int32_t* iters_out, double* stats_out,
                        double* x_traj_out, void* ws, size_t ws_bytes, void* stream);
 
+/* y as a BF16 hi/lo split (a storage format for the streamed observations; the
+ * paper's method is unchanged).  Each pair of complex values (re0, im0, re1, im1)
+ * of y occupies one 16-byte group: bf16 hi of the four values, then bf16 lo of
+ * their residuals, hi = rn_bf16(v), lo = rn_bf16(v - hi); the kernels read
+ * v = hi + lo, which FP32 holds exactly (relative error of the split <= 2^-16).
+ * Same 8 bytes per complex value as complex64, same [N][K+1][Q] order.
+ *   y        device [count] complex64, 16-byte aligned
+ *   count    complex values, even (N (K+1) Q)
+ *   y_hl_out device [count / 2] 16-byte groups, 16-byte aligned */
+MRA_API int mra_y_split_bf16(const float* y, int64_t count, void* y_hl_out, void* stream);
+
+/* mra_em_step / mra_em_run with y in the BF16 hi/lo split (other arguments as
+ * there).  Products and sums stay FP32 as in the complex64 path; the cross-image
+ * reductions are FP64.  MRA_EINVAL where the batch sweep cannot take the shape
+ * (Q a multiple of 8 and (K+1) Q / 4 <= 512 are required). */
+MRA_API int mra_em_step_hl(const mra_dims* dims, const mra_em_params* prm, const void* y_hl, const int32_t* shift,
+                           const double* x_in, const double* log_rho_in, double* x_out, double* log_rho_out,
+                           double* loglik_out, double* step_out, float* w_out, void* ws, size_t ws_bytes,
+                           void* stream);
+MRA_API int mra_em_run_hl(const mra_dims* dims, const mra_em_params* prm, const void* y_hl, const int32_t* shift,
+                          double* x_inout, double* log_rho_inout, int32_t* iters_out, double* stats_out,
+                          double* x_traj_out, void* ws, size_t ws_bytes, void* stream);
+
 /* Marginal log-likelihood over the window and its gradient (Fisher identity),
  *   l(x, kappa, eta) = sum_j log sum_l rho_l (pi sigma2)^{-M} exp(-||x o e^{-i k theta_l} - y_j||^2 / sigma2),
  *   log rho_l = kappa cos(theta_l) + eta_l - log sum_win exp(kappa cos theta + eta),  theta_l = 2 pi (l0+l)/L.

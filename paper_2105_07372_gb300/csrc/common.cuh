@@ -211,11 +211,12 @@ struct SweepV3Args {
   Ctrl* ctrl;
 };
 typedef void (*SweepV3Fn)(const SweepV3Args);
-// QH = float4 per row (Q / 2); bi = images per batch (16, 12, 8 or 4).
-SweepV3Fn sweep_v3_qh4(int bi);
-SweepV3Fn sweep_v3_qh8(int bi);
-SweepV3Fn sweep_v3_qh12(int bi);
-SweepV3Fn sweep_v3_qh16(int bi);
+// QH = float4 per row (Q / 2); bi = images per batch (16, 12, 8 or 4); yf = 1 for y
+// stored as the BF16 hi/lo split.
+SweepV3Fn sweep_v3_qh4(int bi, int yf);
+SweepV3Fn sweep_v3_qh8(int bi, int yf);
+SweepV3Fn sweep_v3_qh12(int bi, int yf);
+SweepV3Fn sweep_v3_qh16(int bi, int yf);
 
 // Mirror units of a window: offsets o and -o (mod L) share cos/sin.  Writes the
 // (a, b) index pairs in window order of a; returns the number of units.

@@ -20,6 +20,7 @@
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
+#include <cuda_bf16.h>
 #include <string.h>
 
 #include <algorithm>
@@ -995,7 +996,7 @@ struct V3Plan {
 // (16, 2), (12, 2), (8, 3), (8, 2), (4, 3), (4, 2) whose ring and tables fit.  Per-image pitches
 // are odd (in words of their element type) so that the images of one warp fall in
 // distinct banks.
-bool plan_v3(int Kp1, int Q, int L, int Lw, int l0, int max_smem, V3Plan* p) {
+bool plan_v3(int Kp1, int Q, int L, int Lw, int l0, int yf, int max_smem, V3Plan* p) {
   if (Q % 8 != 0) return false;
   const int QH = Q / 2;
   if (Kp1 * (QH / 2) > kV3Threads) return false;
@@ -1019,8 +1020,8 @@ bool plan_v3(int Kp1, int Q, int L, int Lw, int l0, int max_smem, V3Plan* p) {
   for (const auto& bn : cfg) {
     const int bi = bn[0], ns = bn[1];
     if ((want_bi && bi != want_bi) || (want_ns && ns != want_ns)) continue;
-    const SweepV3Fn fn = QH == 4 ? sweep_v3_qh4(bi) : QH == 8 ? sweep_v3_qh8(bi)
-                       : QH == 12 ? sweep_v3_qh12(bi) : QH == 16 ? sweep_v3_qh16(bi) : nullptr;
+    const SweepV3Fn fn = QH == 4 ? sweep_v3_qh4(bi, yf) : QH == 8 ? sweep_v3_qh8(bi, yf)
+                       : QH == 12 ? sweep_v3_qh12(bi, yf) : QH == 16 ? sweep_v3_qh16(bi, yf) : nullptr;
     if (!fn) return false;
     int o = 128;  // ring mbarriers
     p->off_ring = o; o += ns * bi * slot;
@@ -1113,8 +1114,9 @@ struct EmCall {
   }
 };
 
+// yfmt: 0 = y in complex64, 1 = y as the BF16 hi/lo split (batch sweep only).
 int prepare(const mra_dims* d, int Lw, int l0, const float* y, const int32_t* shift, void* ws, size_t ws_bytes,
-            EmCall* c, bool allow_v3 = true) {
+            EmCall* c, bool allow_v3 = true, int yfmt = 0) {
   int st = check_dims(d);
   if (st != MRA_OK) return st;
   if (Lw < 1 || Lw > d->L) return MRA_EINVAL;
@@ -1130,10 +1132,16 @@ int prepare(const mra_dims* d, int Lw, int l0, const float* y, const int32_t* sh
   const int nup = round_up(nu, kUnitChunk);
   // The warp sweep keeps a window of one unit chunk in registers and is the faster one
   // there; wider windows (up to the whole circle) go to the batch sweep.
-  c->v2 = plan_v2(Kp1, d->Q, d->L, Lw, nup, di.max_smem_optin, &c->v2p);
-  c->v3 = allow_v3 && sweep_choice() != 1 && (!c->v2 || nup > kUnitChunk || sweep_choice() == 2) &&
-          plan_v3(Kp1, d->Q, d->L, Lw, l0, di.max_smem_optin, &c->v3p);
-  if (c->v3) c->v2 = false;
+  if (yfmt) {
+    c->v2 = false;
+    c->v3 = plan_v3(Kp1, d->Q, d->L, Lw, l0, 1, di.max_smem_optin, &c->v3p);
+    if (!c->v3) return MRA_EINVAL;  // no sweep for this shape reads the split format
+  } else {
+    c->v2 = plan_v2(Kp1, d->Q, d->L, Lw, nup, di.max_smem_optin, &c->v2p);
+    c->v3 = allow_v3 && sweep_choice() != 1 && (!c->v2 || nup > kUnitChunk || sweep_choice() == 2) &&
+            plan_v3(Kp1, d->Q, d->L, Lw, l0, 0, di.max_smem_optin, &c->v3p);
+    if (c->v3) c->v2 = false;
+  }
   if (c->v3) {
     if (cudaFuncSetAttribute(reinterpret_cast<const void*>(c->v3p.fn), cudaFuncAttributeMaxDynamicSharedMemorySize,
                              c->v3p.smem) != cudaSuccess)
@@ -1340,7 +1348,9 @@ MRA_API size_t mra_em_workspace_bytes(const mra_dims* d, int32_t Lw) {
   return em_layout(d->N, d->K, d->Q, d->L, Lw, di.sms).total;
 }
 
-MRA_API int mra_em_step(const mra_dims* d, const mra_em_params* p, const float* y, const int32_t* shift,
+}  // extern "C"
+
+static int em_step_impl(const mra_dims* d, const mra_em_params* p, const float* y, int yfmt, const int32_t* shift,
                         const double* x_in, const double* log_rho_in, double* x_out, double* log_rho_out,
                         double* loglik_out, double* step_out, float* w_out, void* ws, size_t ws_bytes,
                         void* stream) {
@@ -1351,7 +1361,7 @@ MRA_API int mra_em_step(const mra_dims* d, const mra_em_params* p, const float* 
     return MRA_EINVAL;
   if (w_out && !ptr_ok(w_out, 4)) return MRA_EINVAL;
   EmCall c;
-  if ((st = prepare(d, p->Lw, p->l0, y, shift, ws, ws_bytes, &c)) != MRA_OK) return st;
+  if ((st = prepare(d, p->Lw, p->l0, y, shift, ws, ws_bytes, &c, true, yfmt)) != MRA_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   c.su.x_in = reinterpret_cast<const double2*>(x_in);
   c.su.log_rho_in = log_rho_in;
@@ -1368,7 +1378,7 @@ MRA_API int mra_em_step(const mra_dims* d, const mra_em_params* p, const float* 
   return launch_iteration(c, s);
 }
 
-MRA_API int mra_em_run(const mra_dims* d, const mra_em_params* p, const float* y, const int32_t* shift,
+static int em_run_impl(const mra_dims* d, const mra_em_params* p, const float* y, int yfmt, const int32_t* shift,
                        double* x_inout, double* log_rho_inout, int32_t* iters_out, double* stats_out,
                        double* x_traj_out, void* ws, size_t ws_bytes, void* stream) {
   int st = check_dims(d);
@@ -1379,7 +1389,7 @@ MRA_API int mra_em_run(const mra_dims* d, const mra_em_params* p, const float* y
   if (stats_out && !ptr_ok(stats_out, 8)) return MRA_EINVAL;
   if (x_traj_out && !ptr_ok(x_traj_out, 16)) return MRA_EINVAL;
   EmCall c;
-  if ((st = prepare(d, p->Lw, p->l0, y, shift, ws, ws_bytes, &c)) != MRA_OK) return st;
+  if ((st = prepare(d, p->Lw, p->l0, y, shift, ws, ws_bytes, &c, true, yfmt)) != MRA_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   c.su.x_in = reinterpret_cast<const double2*>(x_inout);
   c.su.log_rho_in = log_rho_inout;
@@ -1454,6 +1464,69 @@ MRA_API int mra_em_run(const mra_dims* d, const mra_em_params* p, const float* y
   for (auto e : ev)
     if (e) cudaEventDestroy(e);
   return rc;
+}
+
+extern "C" {
+
+MRA_API int mra_em_step(const mra_dims* d, const mra_em_params* p, const float* y, const int32_t* shift,
+                        const double* x_in, const double* log_rho_in, double* x_out, double* log_rho_out,
+                        double* loglik_out, double* step_out, float* w_out, void* ws, size_t ws_bytes,
+                        void* stream) {
+  return em_step_impl(d, p, y, 0, shift, x_in, log_rho_in, x_out, log_rho_out, loglik_out, step_out, w_out, ws,
+                      ws_bytes, stream);
+}
+
+MRA_API int mra_em_step_hl(const mra_dims* d, const mra_em_params* p, const void* y_hl, const int32_t* shift,
+                           const double* x_in, const double* log_rho_in, double* x_out, double* log_rho_out,
+                           double* loglik_out, double* step_out, float* w_out, void* ws, size_t ws_bytes,
+                           void* stream) {
+  return em_step_impl(d, p, static_cast<const float*>(y_hl), 1, shift, x_in, log_rho_in, x_out, log_rho_out,
+                      loglik_out, step_out, w_out, ws, ws_bytes, stream);
+}
+
+MRA_API int mra_em_run(const mra_dims* d, const mra_em_params* p, const float* y, const int32_t* shift,
+                       double* x_inout, double* log_rho_inout, int32_t* iters_out, double* stats_out,
+                       double* x_traj_out, void* ws, size_t ws_bytes, void* stream) {
+  return em_run_impl(d, p, y, 0, shift, x_inout, log_rho_inout, iters_out, stats_out, x_traj_out, ws, ws_bytes,
+                     stream);
+}
+
+MRA_API int mra_em_run_hl(const mra_dims* d, const mra_em_params* p, const void* y_hl, const int32_t* shift,
+                          double* x_inout, double* log_rho_inout, int32_t* iters_out, double* stats_out,
+                          double* x_traj_out, void* ws, size_t ws_bytes, void* stream) {
+  return em_run_impl(d, p, static_cast<const float*>(y_hl), 1, shift, x_inout, log_rho_inout, iters_out, stats_out,
+                     x_traj_out, ws, ws_bytes, stream);
+}
+
+// y (complex64) -> BF16 hi/lo split: per pair of complex values, bf16 hi of (re, im, re, im)
+// then bf16 lo of the residuals, both rounded to nearest even.
+__global__ void k_split_bf16(const float4* y, long long groups, uint4* out) {
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < groups;
+       g += (long long)gridDim.x * blockDim.x) {
+    const float4 v = y[g];
+    const float f[4] = {v.x, v.y, v.z, v.w};
+    unsigned short h[4], l[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const __nv_bfloat16 bh = __float2bfloat16_rn(f[t]);
+      const __nv_bfloat16 bl = __float2bfloat16_rn(f[t] - __bfloat162float(bh));
+      h[t] = __bfloat16_as_ushort(bh);
+      l[t] = __bfloat16_as_ushort(bl);
+    }
+    out[g] = make_uint4(h[0] | ((unsigned)h[1] << 16), h[2] | ((unsigned)h[3] << 16), l[0] | ((unsigned)l[1] << 16),
+                        l[2] | ((unsigned)l[3] << 16));
+  }
+}
+
+MRA_API int mra_y_split_bf16(const float* y, int64_t count, void* y_hl_out, void* stream) {
+  if (count < 0 || count % 2 != 0) return MRA_EINVAL;
+  if (count == 0) return MRA_OK;
+  if (!ptr_ok(y, 16) || !ptr_ok(y_hl_out, 16)) return MRA_EINVAL;
+  const long long groups = count / 2;
+  const int blocks = (int)std::min<long long>((groups + 255) / 256, 152LL * 16);
+  k_split_bf16<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(reinterpret_cast<const float4*>(y), groups,
+                                                                        static_cast<uint4*>(y_hl_out));
+  return cudaGetLastError() == cudaSuccess ? MRA_OK : MRA_ECUDA;
 }
 
 MRA_API int mra_loglik_grad(const mra_dims* d, int32_t Lw, int32_t l0, const float* y, const int32_t* shift,

@@ -32,6 +32,24 @@
 
 namespace mra {
 
+// Two complex values of y at float4 index f of an image: FP32 (YF = 0), or the BF16
+// hi/lo split (YF = 1) whose 16-byte group f holds bf16 hi of (re, im, re, im) and then
+// bf16 lo of the same four values; hi + lo is exact in FP32.
+template <int YF>
+__device__ __forceinline__ float4 load_y4(const float4* img, int f) {
+  if constexpr (YF == 0) {
+    return img[f];
+  } else {
+    const uint4 v = reinterpret_cast<const uint4*>(img)[f];
+    const float2 h0 = make_float2(__uint_as_float(v.x << 16), __uint_as_float(v.x & 0xffff0000u));
+    const float2 h1 = make_float2(__uint_as_float(v.y << 16), __uint_as_float(v.y & 0xffff0000u));
+    const float2 l0 = make_float2(__uint_as_float(v.z << 16), __uint_as_float(v.z & 0xffff0000u));
+    const float2 l1 = make_float2(__uint_as_float(v.w << 16), __uint_as_float(v.w & 0xffff0000u));
+    const float2 a = __fadd2_rn(h0, l0), b = __fadd2_rn(h1, l1);
+    return make_float4(a.x, a.y, b.x, b.y);
+  }
+}
+
 // window indices of distance unit d around the reference p (-1 where absent)
 __device__ __forceinline__ int2 unit_pair(int p, int d, int Lw, int L, bool wrap) {
   if (wrap) {
@@ -44,7 +62,7 @@ __device__ __forceinline__ int2 unit_pair(int p, int d, int Lw, int L, bool wrap
   return make_int2(p + d < Lw ? p + d : -1, (d > 0 && p - d >= 0) ? p - d : -1);
 }
 
-template <int QH, int BI>
+template <int QH, int BI, int YF>
 __global__ void __launch_bounds__(kV3Threads, 1) k_sweep_v3(const SweepV3Args a) {
   extern __shared__ __align__(128) unsigned char smem[];
   constexpr int NT = kV3Threads;
@@ -227,7 +245,7 @@ __global__ void __launch_bounds__(kV3Threads, 1) k_sweep_v3(const SweepV3Args a)
         const float4* xq = xr4 + k * QH;
 #pragma unroll
         for (int p = 0; p < QH; ++p) {
-          const float4 yv = yr[p], xv = xr[p], xw = xq[p];
+          const float4 yv = load_y4<YF>(yr, p), xv = xr[p], xw = xq[p];
           const float2 ya = make_float2(yv.x, yv.y), yb = make_float2(yv.z, yv.w);
           p0 = __ffma2_rn(ya, make_float2(xv.x, xv.y), p0);
           p1 = __ffma2_rn(yb, make_float2(xv.z, xv.w), p1);
@@ -360,7 +378,7 @@ __global__ void __launch_bounds__(kV3Threads, 1) k_sweep_v3(const SweepV3Args a)
 #pragma unroll 4
       for (int i = 0; i < nv; ++i) {
         const float4* y4 = reinterpret_cast<const float4*>(stage + (size_t)i * slot);
-        const float4 ya = y4[af0], yb = y4[af0 + PH];
+        const float4 ya = load_y4<YF>(y4, af0), yb = load_y4<YF>(y4, af0 + PH);
         const float2 w = cbuf[i * cp + ak];
         const float2 wre = make_float2(w.x, w.x), wim = make_float2(w.y, w.y);
         const float2 yv[4] = {make_float2(ya.x, ya.y), make_float2(ya.z, ya.w), make_float2(yb.x, yb.y),
@@ -407,16 +425,21 @@ __global__ void __launch_bounds__(kV3Threads, 1) k_sweep_v3(const SweepV3Args a)
 
 }  // namespace mra
 
-// Instantiation table for one row width QH (float4 per row): batches of 16, 12, 8 or 4 images.
-#define MRA_SWEEP_V3_TABLE(QH)            \
-  namespace mra {                         \
-  SweepV3Fn sweep_v3_qh##QH(int bi) {     \
-    switch (bi) {                         \
-      case 16: return k_sweep_v3<QH, 16>; \
-      case 12: return k_sweep_v3<QH, 12>; \
-      case 8: return k_sweep_v3<QH, 8>;   \
-      case 4: return k_sweep_v3<QH, 4>;   \
-      default: return nullptr;            \
-    }                                     \
-  }                                       \
+// Instantiation table for one row width QH (float4 per row): batches of 16, 12, 8 or 4
+// images, y in FP32 (yf = 0) or as the BF16 hi/lo split (yf = 1).
+#define MRA_SWEEP_V3_TABLE(QH)                                     \
+  namespace mra {                                                  \
+  SweepV3Fn sweep_v3_qh##QH(int bi, int yf) {                      \
+    switch (bi * 2 + (yf ? 1 : 0)) {                               \
+      case 32: return k_sweep_v3<QH, 16, 0>;                       \
+      case 33: return k_sweep_v3<QH, 16, 1>;                       \
+      case 24: return k_sweep_v3<QH, 12, 0>;                       \
+      case 25: return k_sweep_v3<QH, 12, 1>;                       \
+      case 16: return k_sweep_v3<QH, 8, 0>;                        \
+      case 17: return k_sweep_v3<QH, 8, 1>;                        \
+      case 8: return k_sweep_v3<QH, 4, 0>;                         \
+      case 9: return k_sweep_v3<QH, 4, 1>;                         \
+      default: return nullptr;                                     \
+    }                                                              \
+  }                                                                \
   }

@@ -50,6 +50,12 @@ _SIGS = {
     "mra_em_run": (c_int, [POINTER(mra_dims), POINTER(mra_em_params)] + [c_void_p] * 4 + [POINTER(c_int32), c_void_p,
                                                                                           c_void_p, c_void_p, c_size_t,
                                                                                           c_void_p]),
+    "mra_em_step_hl": (c_int, [POINTER(mra_dims), POINTER(mra_em_params)] + [c_void_p] * 9 + [c_void_p, c_size_t,
+                                                                                             c_void_p]),
+    "mra_em_run_hl": (c_int, [POINTER(mra_dims), POINTER(mra_em_params)] + [c_void_p] * 4 + [POINTER(c_int32), c_void_p,
+                                                                                             c_void_p, c_void_p,
+                                                                                             c_size_t, c_void_p]),
+    "mra_y_split_bf16": (c_int, [c_void_p, ctypes.c_int64, c_void_p, c_void_p]),
     "mra_loglik_grad": (c_int, [POINTER(mra_dims), c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_double,
                                 c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "mra_sync_workspace_bytes": (c_size_t, [POINTER(mra_dims), c_int32]),
@@ -174,6 +180,27 @@ def mra_em_run(d, prm, y, shift, x_inout, log_rho_inout, stats_out=None, x_traj_
     _check("mra_em_run", load().mra_em_run(ctypes.byref(d), ctypes.byref(prm), _p(y), _p(shift), _p(x_inout),
                                            _p(log_rho_inout), ctypes.byref(it), _p(stats_out), _p(x_traj_out), _p(ws),
                                            ws.numel(), _stream(stream)))
+    return it.value
+
+
+def mra_y_split_bf16(y, y_hl_out, stream=None):
+    """y (complex64, any shape) -> its BF16 hi/lo split in y_hl_out (same byte size, 16-byte groups)."""
+    _check("mra_y_split_bf16", load().mra_y_split_bf16(_p(y), int(y.numel()), _p(y_hl_out), _stream(stream)))
+
+
+def mra_em_step_hl(d, prm, y_hl, shift, x_in, log_rho_in, x_out, log_rho_out, loglik_out=None, step_out=None,
+                   w_out=None, ws=None, stream=None):
+    _check("mra_em_step_hl", load().mra_em_step_hl(ctypes.byref(d), ctypes.byref(prm), _p(y_hl), _p(shift), _p(x_in),
+                                                   _p(log_rho_in), _p(x_out), _p(log_rho_out), _p(loglik_out),
+                                                   _p(step_out), _p(w_out), _p(ws), ws.numel(), _stream(stream)))
+
+
+def mra_em_run_hl(d, prm, y_hl, shift, x_inout, log_rho_inout, stats_out=None, x_traj_out=None, ws=None,
+                  stream=None) -> int:
+    it = c_int32(0)
+    _check("mra_em_run_hl", load().mra_em_run_hl(ctypes.byref(d), ctypes.byref(prm), _p(y_hl), _p(shift),
+                                                 _p(x_inout), _p(log_rho_inout), ctypes.byref(it), _p(stats_out),
+                                                 _p(x_traj_out), _p(ws), ws.numel(), _stream(stream)))
     return it.value
 
 

@@ -17,4 +17,6 @@ from .instances import (  # noqa: F401
     NPIX,
     to_c64,
     c64_round,
+    bf16_split,
+    bf16_merge,
 )

@@ -112,3 +112,29 @@ def to_c64(a: np.ndarray) -> np.ndarray:
 def c64_round(a: np.ndarray) -> np.ndarray:
     """The complex128 values that a complex64 copy of ``a`` holds exactly."""
     return to_c64(a).astype(np.complex128)
+
+
+def _bf16_rne_bits(f: np.ndarray) -> np.ndarray:
+    """uint16 bit patterns of float32 values rounded to the nearest bfloat16, ties to even (finite inputs)."""
+    u = np.ascontiguousarray(f, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = u + 0x7FFF + ((u >> 16) & 1)
+    return (u >> 16).astype(np.uint16)
+
+
+def bf16_split(y: np.ndarray) -> np.ndarray:
+    """The BF16 hi/lo storage of complex64 observations: for each pair of complex values,
+    one 16-byte group with bf16 hi = rn(v) of (re0, im0, re1, im1), then bf16 lo = rn(v - hi)
+    of the same four values.  Returns a uint16 array of shape [count / 2, 8]."""
+    f = to_c64(y).reshape(-1).view(np.float32).reshape(-1, 4)  # [groups, 4]
+    hi = _bf16_rne_bits(f)
+    hi_f = (hi.astype(np.uint32) << 16).view(np.float32)
+    lo = _bf16_rne_bits(f - hi_f)
+    return np.ascontiguousarray(np.concatenate([hi, lo], axis=1))
+
+
+def bf16_merge(groups: np.ndarray, shape) -> np.ndarray:
+    """complex128 values hi + lo held by a BF16 hi/lo split (exact in float32)."""
+    g = np.asarray(groups, dtype=np.uint16).reshape(-1, 8).astype(np.uint32) << 16
+    f = g.view(np.float32)
+    v = (f[:, :4] + f[:, 4:]).astype(np.float32).reshape(-1)
+    return v.view(np.complex64).astype(np.complex128).reshape(shape)
