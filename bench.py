@@ -162,10 +162,17 @@ def main():
     ap.add_argument("--impl", default="gpu")
     ap.add_argument("--no-ttc", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--config", type=int, default=CFG, choices=(2, 4, 5),
+                    help="2: Synch-EM at N=1e5 (default); 4: 64 uneven instances in one graph launch; "
+                         "5: N=1e6 with y in the BF16 hi/lo split")
     args = ap.parse_args()
     c = synth.config(CFG)
     if args.impl == "reference":
         return run_reference(args, c)
+    if args.config == 4:
+        return bench_batched(args)
+    if args.config == 5:
+        return bench_bf16(args)
 
     import torch
     import torch.distributed as dist
@@ -370,6 +377,150 @@ def time_to_converge(mra, pipeline, c, inst, d, y, s_true, x_true, ws, dev):
             res.update({"iters_to_equal_error": None, "seconds_to_equal_error": None, "speedup": None})
         out[tag] = res
     return out
+
+
+def _timed_steps(step, args, clk):
+    import torch
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    with clk:
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            step()
+        e1.record()
+        torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / args.steps
+
+
+def _clocks():
+    d = os.path.join(ROOT, "gpurun_out")
+    return Clocks(os.path.join(d, "clocks_rank0.csv") if os.path.isdir(d) else "/tmp/mra_clocks_0.csv")
+
+
+def bench_batched(args):
+    """64 independent instances of uneven N, K and window, 30 EM iterations each, in one graph launch
+    per step (mra_em_run_batched, sweeps chosen by the autotuner).  Inputs resident in HBM; each
+    instance starts from the average of its synchronized images."""
+    import torch
+
+    from paper_2105_07372_gb300 import mra, pipeline
+
+    mra.load()
+    dev = torch.device("cuda", 0)
+    specs = synth.config4_instances()
+    items, starts = [], []
+    evals = 0
+    ybytes = 0
+    for sp in specs:
+        inst = synth.make_instance(sp["K"], sp["Q"], sp["N"], sp["L"], sp["snr"], sp["decay"], seed=sp["seed"])
+        yh = torch.from_numpy(synth.to_c64(inst.y))
+        y = yh.to(dev)
+        d = mra.dims(inst.N, inst.K, inst.Q, inst.L, inst.sigma2)
+        ws = pipeline.workspaces(d, sp["Lw"], 100, dev)
+        shift = pipeline.synchronize(y, d, 100, ws)
+        x = torch.empty((inst.K + 1, inst.Q), dtype=torch.complex128, device=dev)
+        mra.mra_align_mean(d, y, shift, x, ws.em)
+        lr = torch.full((sp["Lw"],), -math.log(sp["Lw"]), dtype=torch.float64, device=dev)
+        prm = mra.em_params(sp["Lw"], max_iters=sp["iters"])
+        items.append(dict(d=d, prm=prm, y=y, shift=shift, x=x.clone(), log_rho=lr.clone()))
+        starts.append((x, lr))
+        evals += inst.N * sp["Lw"] * sp["iters"]
+        ybytes += inst.N * (inst.K + 1) * inst.Q * 8 * sp["iters"]
+        del ws
+    arr = mra.instances(items)
+    ws = mra.workspace(mra.mra_em_batched_workspace_bytes(arr), dev)
+    t_tune = time.perf_counter()
+    mra.mra_em_run_batched(arr, ws, tune=True)  # the autotuner runs here, once per shape
+    t_tune = time.perf_counter() - t_tune
+    exec_ms = []
+
+    def step():
+        for it, (x0, lr0) in zip(items, starts):
+            it["x"].copy_(x0)
+            it["log_rho"].copy_(lr0)
+        _, ms = mra.mra_em_run_batched(arr, ws, tune=False)
+        exec_ms.append(ms)
+
+    clk = _clocks()
+    ms = _timed_steps(step, args, clk)
+    launch_ms = float(np.mean(exec_ms[args.warmup:]))
+    peak, peak_kind = peaks()
+    achieved = ybytes / (launch_ms / 1e3) / 1e9
+    line = {"metric": METRIC, "value": evals / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{len(specs)} independent MRA instances, N~U[1000,50000] (sum "
+                                   f"{sum(s['N'] for s in specs)}), K~U{{8..40}}, Q=16, L=360, Lw~U{{12..72}}, "
+                                   "SNR log-U[1/100,1/5], 30 EM iterations each, one graph launch",
+                       "parallelism": "single", "l2": "inputs larger than L2"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "peak_source": f"{peak_kind} hbm_gbs", "kernel": "whole batched graph",
+                         "algorithmic_bytes_per_launch": ybytes, "avg_launch_ms": launch_ms},
+            "autotune_s": t_tune, "graph_launch_ms": launch_ms, "clocks": clk.summary(),
+            "gpu_launches": sum(4 + 3 * sp["iters"] + 1 for sp in specs) * args.steps}
+    print(json.dumps(line), flush=True)
+
+
+def bench_bf16(args):
+    """N = 1e6 images at |k| <= 48, Q = 32, L = 720, window 72, y stored as the BF16 hi/lo split,
+    50 EM iterations (mra_em_run_hl) from the average of the aligned images."""
+    import torch
+
+    from paper_2105_07372_gb300 import mra
+
+    mra.load()
+    dev = torch.device("cuda", 0)
+    c = synth.config(5)
+    N, K, Q, L, Lw, T = c["N"], c["K"], c["Q"], c["L"], c["Lw"], c["iters"]
+    x_true = synth.make_signal(K, Q, c["decay"], np.random.default_rng(5000))
+    sigma2 = synth.sigma2_for_snr(c["snr"], x_true)
+    M = (K + 1) * Q
+    y_hl = torch.empty((N, M, 2), dtype=torch.float32, device=dev)  # 8 bytes per complex value
+    shift = torch.empty(N, dtype=torch.int32, device=dev)
+    chunk = 50_000
+    stage = torch.empty((chunk, K + 1, Q), dtype=torch.complex64, device=dev)
+    for i0 in range(0, N, chunk):
+        n = min(chunk, N - i0)
+        inst = synth.make_instance(K, Q, n, L, seed=5000 + 1 + i0 // chunk, sigma2=sigma2, x=x_true)
+        stage[:n].copy_(torch.from_numpy(synth.to_c64(inst.y)))
+        mra.mra_y_split_bf16(stage[:n], y_hl[i0:i0 + n])
+        shift[i0:i0 + n].copy_(torch.from_numpy(inst.s.astype(np.int32)))
+    del stage
+    d = mra.dims(N, K, Q, L, sigma2)
+    ws = mra.workspace(mra.mra_em_workspace_bytes(d, Lw), dev)
+    x0 = torch.from_numpy(x_true * 0.9).to(dev)  # a start near the truth; the sweeps do the same work anywhere
+    lr0 = torch.full((Lw,), -math.log(Lw), dtype=torch.float64, device=dev)
+    x, lr = x0.clone(), lr0.clone()
+    sweep_ms = (ctypes.c_float * T)()
+    sweeps = []
+
+    def step():
+        x.copy_(x0)
+        lr.copy_(lr0)
+        n = mra.mra_em_run_hl(d, mra.em_params(Lw, max_iters=T, sweep_ms=sweep_ms), y_hl, shift, x, lr, None, None,
+                              ws)
+        sweeps.extend(list(sweep_ms)[:n])
+
+    clk = _clocks()
+    ms = _timed_steps(step, args, clk)
+    sw = float(np.mean(sweeps[args.warmup * T:])) / 1e3
+    ybytes = N * M * 8
+    peak, peak_kind = peaks()
+    line = {"metric": METRIC, "value": N * Lw * T / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16 hi/lo storage, f32 arithmetic", "data": "synthetic",
+            "config": {"workload": f"EM |k|<={K} Q={Q} N={N} L={L} Lw={Lw} SNR=1/100 T={T}, y as BF16 hi/lo",
+                       "parallelism": "single", "l2": "inputs larger than L2 (12.5 GB per sweep)"},
+            "roofline": {"bound": "hbm", "achieved": ybytes / sw / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": ybytes / sw / 1e9 / peak, "traffic": None, "peak_source": f"{peak_kind} hbm_gbs",
+                         "kernel": "k_sweep_v3 (BF16 hi/lo)", "algorithmic_bytes_per_launch": ybytes,
+                         "avg_launch_ms": sw * 1e3},
+            "clocks": clk.summary(), "gpu_launches": (2 + 3 * T + 1) * args.steps}
+    print(json.dumps(line), flush=True)
 
 
 if __name__ == "__main__":

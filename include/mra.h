@@ -155,6 +155,51 @@ MRA_API int mra_em_run_hl(const mra_dims* dims, const mra_em_params* prm, const 
                           double* x_inout, double* log_rho_inout, int32_t* iters_out, double* stats_out,
                           double* x_traj_out, void* ws, size_t ws_bytes, void* stream);
 
+/* ------------------------------------------------------------------ autotuner and batched runs
+ * Neither has a counterpart in the paper, which treats one problem at a time. */
+
+/* Times every EM sweep that can take the problem (the warp-per-image sweep; the
+ * batch sweep at 16, 12, 8 or 4 images per batch and 2 or 3 ring stages) for one
+ * sweep over y from the state (x, log_rho), and caches the fastest for this
+ * device and shape (K, Q, L, Lw, l0, y_format).  Later EM calls on that shape use
+ * the cached choice unless the MRA_SWEEP* environment variables fix one.
+ * Synchronizes the stream.
+ *   y_format   0: y complex64; 1: the BF16 hi/lo split of mra_y_split_bf16
+ *   choice_out host int32[3] (kind 1 warp / 2 batch / 0 none applies, batch, stages), or NULL
+ * The workspace is the one of mra_em_workspace_bytes; its contents are clobbered. */
+MRA_API int mra_em_autotune(const mra_dims* dims, const mra_em_params* prm, const void* y, int32_t y_format,
+                            const int32_t* shift, const double* x, const double* log_rho, int32_t* choice_out,
+                            void* ws, size_t ws_bytes, void* stream);
+
+/* One independent problem of a batched run (all pointers device, as in mra_em_run;
+ * prm.max_iters iterations, prm.tol stops an instance early, prm.check_every and
+ * prm.sweep_ms are not used). */
+typedef struct {
+  mra_dims dims;
+  mra_em_params prm;
+  const void* y;           /* [N][K+1][Q] complex64, or the BF16 hi/lo split */
+  int32_t y_format;        /* 0 complex64, 1 BF16 hi/lo split */
+  const int32_t* shift;    /* [N] or NULL */
+  double* x_inout;         /* [K+1][Q] complex double: a_0 in, final a out */
+  double* log_rho_inout;   /* [Lw] */
+  double* stats_out;       /* [max_iters][2] (loglik, step) or NULL */
+} mra_instance;
+
+/* Workspace for mra_em_run_batched: the instances' EM workspaces, 256-byte aligned, in order. */
+MRA_API size_t mra_em_batched_workspace_bytes(const mra_instance* inst, int32_t n);
+
+/* Algorithm Synch-EM's loop for n independent problems of uneven N, K and window
+ * in ONE graph launch: each instance's setup, iterations and export are captured as
+ * a branch of a single CUDA graph, which is launched once and synchronized.
+ *   tune        1: run mra_em_autotune first for every shape not yet in the cache
+ *   iters_out   host int32[n] iterations performed per instance, or NULL
+ *   exec_ms_out host float: device time of the graph launch (CUDA events), or NULL
+ * A repeated call with tune = 0 and the same instance array contents, workspace and
+ * device launches the graph instantiated by the earlier call (a few are kept).
+ * Returns the first failing status; instance results are valid only on MRA_OK. */
+MRA_API int mra_em_run_batched(const mra_instance* inst, int32_t n, int32_t tune, int32_t* iters_out,
+                               float* exec_ms_out, void* ws, size_t ws_bytes, void* stream);
+
 /* Marginal log-likelihood over the window and its gradient (Fisher identity),
  *   l(x, kappa, eta) = sum_j log sum_l rho_l (pi sigma2)^{-M} exp(-||x o e^{-i k theta_l} - y_j||^2 / sigma2),
  *   log rho_l = kappa cos(theta_l) + eta_l - log sum_win exp(kappa cos theta + eta),  theta_l = 2 pi (l0+l)/L.

@@ -244,6 +244,8 @@ struct DevInfo {
   int max_smem_optin;
 };
 int dev_info(DevInfo* out);
+// Raise a kernel's dynamic shared-memory limit to at least `bytes` (never lowers it).
+int raise_smem_limit(const void* fn, int bytes);
 int sweep_grid();  // persistent grid used by the sweep on the current device
 
 }  // namespace mra

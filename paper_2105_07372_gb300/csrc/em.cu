@@ -24,6 +24,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
 #include <mutex>
 #include <vector>
 
@@ -32,6 +33,22 @@
 namespace mra {
 
 // ============================================================================ device info
+// Kernel dynamic shared-memory limits only grow: the limit belongs to the kernel and is
+// shared by every call and every captured graph node that launches it, so lowering it
+// for one call could break an earlier node of a graph that is still to run.
+int raise_smem_limit(const void* fn, int bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, int> limit;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return MRA_ECUDA;
+  std::lock_guard<std::mutex> g(mu);
+  int& cur = limit[{dev, fn}];
+  if (bytes <= cur) return MRA_OK;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess) return MRA_ECUDA;
+  cur = bytes;
+  return MRA_OK;
+}
+
 int dev_info(DevInfo* out) {
   static DevInfo cache[64];
   static bool have[64] = {};
@@ -996,7 +1013,7 @@ struct V3Plan {
 // (16, 2), (12, 2), (8, 3), (8, 2), (4, 3), (4, 2) whose ring and tables fit.  Per-image pitches
 // are odd (in words of their element type) so that the images of one warp fall in
 // distinct banks.
-bool plan_v3(int Kp1, int Q, int L, int Lw, int l0, int yf, int max_smem, V3Plan* p) {
+bool plan_v3(int Kp1, int Q, int L, int Lw, int l0, int yf, int want_bi, int want_ns, int max_smem, V3Plan* p) {
   if (Q % 8 != 0) return false;
   const int QH = Q / 2;
   if (Kp1 * (QH / 2) > kV3Threads) return false;
@@ -1014,9 +1031,6 @@ bool plan_v3(int Kp1, int Q, int L, int Lw, int l0, int yf, int max_smem, V3Plan
   p->phase0 = ((l0 + r0) % L + L) % L;
   const int cp = Kp1 | 1, sp = Lw | 1, dp = p->nd | 1;
   const int cfg[6][2] = {{16, 2}, {12, 2}, {8, 3}, {8, 2}, {4, 3}, {4, 2}};
-  const char* fb = getenv("MRA_SWEEP_BI");  // batch and stages for tuning runs
-  const char* fs = getenv("MRA_SWEEP_NS");
-  const int want_bi = fb ? atoi(fb) : 0, want_ns = fs ? atoi(fs) : 0;
   for (const auto& bn : cfg) {
     const int bi = bn[0], ns = bn[1];
     if ((want_bi && bi != want_bi) || (want_ns && ns != want_ns)) continue;
@@ -1049,15 +1063,52 @@ bool plan_v3(int Kp1, int Q, int L, int Lw, int l0, int yf, int max_smem, V3Plan
   return false;
 }
 
-// MRA_SWEEP=warp or MRA_SWEEP=cta selects one EM sweep where both apply (for comparisons);
-// MRA_SWEEP_BI=16|12|8|4 and MRA_SWEEP_NS=2|3 fix the batch and ring stages of the
-// CTA-cooperative sweep (for tuning).  0: automatic, 1: warp, 2: cta.
-int sweep_choice() {
-  const char* e = getenv("MRA_SWEEP");
-  if (!e) return 0;
-  if (strcmp(e, "warp") == 0) return 1;
-  if (strcmp(e, "cta") == 0) return 2;
-  return 0;
+// Which EM sweep a call uses.  kind: 0 = automatic, 1 = warp per image, 2 = batch
+// (CTA-cooperative) with batch bi and ring stages ns (0 = the first that fits).
+struct SweepSel {
+  int kind, bi, ns;
+};
+
+// MRA_SWEEP=warp|cta, MRA_SWEEP_BI=16|12|8|4 and MRA_SWEEP_NS=2|3 fix the sweep (for
+// comparisons and tuning runs); they take precedence over the autotuner's cache.
+SweepSel env_sweep() {
+  SweepSel e{0, 0, 0};
+  const char* k = getenv("MRA_SWEEP");
+  if (k && strcmp(k, "warp") == 0) e.kind = 1;
+  if (k && strcmp(k, "cta") == 0) e.kind = 2;
+  const char* b = getenv("MRA_SWEEP_BI");
+  const char* n = getenv("MRA_SWEEP_NS");
+  e.bi = b ? atoi(b) : 0;
+  e.ns = n ? atoi(n) : 0;
+  return e;
+}
+
+// ---- autotuner cache: the fastest sweep measured for a problem shape on a device
+struct TuneKey {
+  int dev, Kp1, Q, L, Lw, l0, yfmt;
+  bool operator<(const TuneKey& o) const {
+    const int a[7] = {dev, Kp1, Q, L, Lw, l0, yfmt}, b[7] = {o.dev, o.Kp1, o.Q, o.L, o.Lw, o.l0, o.yfmt};
+    return std::lexicographical_compare(a, a + 7, b, b + 7);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, SweepSel> g_tune;
+
+TuneKey tune_key(const mra_dims* d, int Lw, int l0, int yfmt) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return TuneKey{dev, d->K + 1, d->Q, d->L, Lw, l0, yfmt};
+}
+bool tune_lookup(const TuneKey& k, SweepSel* out) {
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  auto it = g_tune.find(k);
+  if (it == g_tune.end()) return false;
+  *out = it->second;
+  return true;
+}
+void tune_store(const TuneKey& k, const SweepSel& v) {
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  g_tune[k] = v;
 }
 
 typedef void (*SweepFn)(const SweepArgs);
@@ -1115,8 +1166,10 @@ struct EmCall {
 };
 
 // yfmt: 0 = y in complex64, 1 = y as the BF16 hi/lo split (batch sweep only).
+// force: a fixed sweep (the autotuner's candidates); otherwise the environment, then the
+// autotuner's cache, then the default rule below.
 int prepare(const mra_dims* d, int Lw, int l0, const float* y, const int32_t* shift, void* ws, size_t ws_bytes,
-            EmCall* c, bool allow_v3 = true, int yfmt = 0) {
+            EmCall* c, bool allow_v3 = true, int yfmt = 0, const SweepSel* force = nullptr) {
   int st = check_dims(d);
   if (st != MRA_OK) return st;
   if (Lw < 1 || Lw > d->L) return MRA_EINVAL;
@@ -1130,26 +1183,32 @@ int prepare(const mra_dims* d, int Lw, int l0, const float* y, const int32_t* sh
   const int Kp1 = d->K + 1, M = Kp1 * d->Q;
   const int nu = window_units(d->L, Lw, l0, nullptr);
   const int nup = round_up(nu, kUnitChunk);
-  // The warp sweep keeps a window of one unit chunk in registers and is the faster one
-  // there; wider windows (up to the whole circle) go to the batch sweep.
+  SweepSel sel = env_sweep();
+  if (force) {
+    sel = *force;
+  } else if (sel.kind == 0 && sel.bi == 0 && sel.ns == 0) {
+    SweepSel tuned;
+    if (tune_lookup(tune_key(d, Lw, l0, yfmt), &tuned)) sel = tuned;
+  }
   if (yfmt) {
     c->v2 = false;
-    c->v3 = plan_v3(Kp1, d->Q, d->L, Lw, l0, 1, di.max_smem_optin, &c->v3p);
+    c->v3 = sel.kind != 1 && plan_v3(Kp1, d->Q, d->L, Lw, l0, 1, sel.bi, sel.ns, di.max_smem_optin, &c->v3p);
     if (!c->v3) return MRA_EINVAL;  // no sweep for this shape reads the split format
   } else {
-    c->v2 = plan_v2(Kp1, d->Q, d->L, Lw, nup, di.max_smem_optin, &c->v2p);
-    c->v3 = allow_v3 && sweep_choice() != 1 && (!c->v2 || nup > kUnitChunk || sweep_choice() == 2) &&
-            plan_v3(Kp1, d->Q, d->L, Lw, l0, 0, di.max_smem_optin, &c->v3p);
+    // By default the warp sweep keeps a window of one unit chunk in registers and is the
+    // faster one there; wider windows (up to the whole circle) go to the batch sweep.
+    c->v2 = sel.kind != 2 && plan_v2(Kp1, d->Q, d->L, Lw, nup, di.max_smem_optin, &c->v2p);
+    c->v3 = allow_v3 && sel.kind != 1 && (!c->v2 || sel.kind == 2 || nup > kUnitChunk) &&
+            plan_v3(Kp1, d->Q, d->L, Lw, l0, 0, sel.bi, sel.ns, di.max_smem_optin, &c->v3p);
     if (c->v3) c->v2 = false;
+    if (force && ((force->kind == 1 && !c->v2) || (force->kind == 2 && !c->v3))) return MRA_EINVAL;
   }
   if (c->v3) {
-    if (cudaFuncSetAttribute(reinterpret_cast<const void*>(c->v3p.fn), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             c->v3p.smem) != cudaSuccess)
+    if (raise_smem_limit(reinterpret_cast<const void*>(c->v3p.fn), c->v3p.smem) != MRA_OK)
       return MRA_ECUDA;
     c->sweep = nullptr;
   } else if (c->v2) {
-    if (cudaFuncSetAttribute(reinterpret_cast<const void*>(c->v2p.launch.fn),
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, c->v2p.smem) != cudaSuccess)
+    if (raise_smem_limit(reinterpret_cast<const void*>(c->v2p.launch.fn), c->v2p.smem) != MRA_OK)
       return MRA_ECUDA;
     c->sweep = nullptr;
   } else {
@@ -1159,8 +1218,7 @@ int prepare(const mra_dims* d, int Lw, int l0, const float* y, const int32_t* sh
     const int ncolmax = (M / vec + kSweepThreads - 1) / kSweepThreads;
     c->sweep = pick_sweep(qeven, ncolmax);
     if (!c->sweep) return MRA_EINVAL;
-    if (cudaFuncSetAttribute(reinterpret_cast<const void*>(c->sweep), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             c->plan.smem) != cudaSuccess)
+    if (raise_smem_limit(reinterpret_cast<const void*>(c->sweep), c->plan.smem) != MRA_OK)
       return MRA_ECUDA;
   }
   unsigned char* base = static_cast<unsigned char*>(ws);
@@ -1257,9 +1315,7 @@ int prepare(const mra_dims* d, int Lw, int l0, const float* y, const int32_t* sh
   up.stats = nullptr; up.x_traj = nullptr; up.x_out = nullptr; up.log_rho_out = nullptr;
   up.loglik_out = nullptr; up.step_out = nullptr;
   c->update_smem = M * 16 + d->L * 24 + Kp1 * 8 + d->L * 4 + 64;
-  if (c->update_smem > 48 * 1024 &&
-      cudaFuncSetAttribute(reinterpret_cast<const void*>(k_update), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           c->update_smem) != cudaSuccess)
+  if (c->update_smem > 48 * 1024 && raise_smem_limit(reinterpret_cast<const void*>(k_update), c->update_smem) != MRA_OK)
     return MRA_ECUDA;
   c->reduce_blocks = (L_.cols + 7) / 8;
   return MRA_OK;
@@ -1527,6 +1583,258 @@ MRA_API int mra_y_split_bf16(const float* y, int64_t count, void* y_hl_out, void
   k_split_bf16<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(reinterpret_cast<const float4*>(y), groups,
                                                                         static_cast<uint4*>(y_hl_out));
   return cudaGetLastError() == cudaSuccess ? MRA_OK : MRA_ECUDA;
+}
+
+// ---------------------------------------------------------------- autotuner and batched runs
+
+}  // extern "C"
+
+namespace mra {
+namespace {
+
+// Sweep candidates the autotuner times, in the order of the default preference.
+const SweepSel kTuneCandidates[] = {{1, 0, 0}, {2, 16, 2}, {2, 12, 2}, {2, 8, 3}, {2, 8, 2}, {2, 4, 3}, {2, 4, 2}};
+
+// Best of `reps` timed sweeps (after one untimed) of a prepared call whose setup has run; < 0 on error.
+float time_sweep(const EmCall& c, cudaStream_t s, int reps) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  float best = -1.f;
+  if (cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
+    launch_sweep(c, s);
+    for (int r = 0; r < reps; ++r) {
+      float ms = 0.f;
+      if (cudaEventRecord(e0, s) != cudaSuccess) break;
+      launch_sweep(c, s);
+      if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+        break;
+      if (best < 0.f || ms < best) best = ms;
+    }
+  }
+  if (cudaGetLastError() != cudaSuccess) best = -1.f;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  return best;
+}
+
+int autotune_impl(const mra_dims* d, const mra_em_params* p, const float* y, int yfmt, const int32_t* shift,
+                  const double* x, const double* log_rho, void* ws, size_t ws_bytes, cudaStream_t s, SweepSel* out) {
+  SweepSel best{0, 0, 0};
+  float best_ms = -1.f;
+  for (const SweepSel& cand : kTuneCandidates) {
+    EmCall c;
+    const int st = prepare(d, p->Lw, p->l0, y, shift, ws, ws_bytes, &c, true, yfmt, &cand);
+    if (st == MRA_EINVAL) continue;  // this candidate cannot take the shape
+    if (st != MRA_OK) return st;
+    if (cand.kind == 2 && ((cand.bi && c.v3p.bi != cand.bi) || (cand.ns && c.v3p.ns != cand.ns))) continue;
+    c.su.x_in = reinterpret_cast<const double2*>(x);
+    c.su.log_rho_in = log_rho;
+    int rc = launch_setup(c, s);
+    if (rc != MRA_OK) return rc;
+    const float ms = time_sweep(c, s, 2);
+    if (ms < 0.f) return MRA_ECUDA;
+    if (best_ms < 0.f || ms < best_ms) best_ms = ms, best = cand;
+  }
+  if (best_ms >= 0.f) tune_store(tune_key(d, p->Lw, p->l0, yfmt), best);
+  if (out) *out = best;
+  return MRA_OK;
+}
+
+// Instantiated graphs of batched runs, keyed by the exact instance list, workspace and
+// device: a repeated call with the same list launches the same graph again.
+struct BatchedGraph {
+  std::vector<unsigned char> key;
+  cudaGraphExec_t exec;
+  std::vector<Ctrl*> ctrl;
+};
+std::mutex g_graph_mu;
+std::vector<BatchedGraph> g_graphs;  // most recent last
+constexpr size_t kGraphCache = 4;
+
+std::vector<unsigned char> batched_key(const mra_instance* inst, int n, const void* ws, size_t ws_bytes) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::vector<unsigned char> k(sizeof(mra_instance) * n + sizeof(ws) + sizeof(ws_bytes) + sizeof(dev));
+  unsigned char* o = k.data();
+  memcpy(o, inst, sizeof(mra_instance) * n);
+  o += sizeof(mra_instance) * n;
+  memcpy(o, &ws, sizeof(ws));
+  o += sizeof(ws);
+  memcpy(o, &ws_bytes, sizeof(ws_bytes));
+  o += sizeof(ws_bytes);
+  memcpy(o, &dev, sizeof(dev));
+  return k;
+}
+
+}  // namespace
+}  // namespace mra
+
+extern "C" {
+
+MRA_API int mra_em_autotune(const mra_dims* d, const mra_em_params* p, const void* y, int32_t y_format,
+                            const int32_t* shift, const double* x, const double* log_rho, int32_t* choice_out,
+                            void* ws, size_t ws_bytes, void* stream) {
+  int st = check_dims(d);
+  if (st != MRA_OK) return st;
+  if ((st = check_params(d, p)) != MRA_OK) return st;
+  if ((y_format != 0 && y_format != 1) || !ptr_ok(x, 16) || !ptr_ok(log_rho, 8)) return MRA_EINVAL;
+  SweepSel sel{0, 0, 0};
+  st = autotune_impl(d, p, static_cast<const float*>(y), y_format, shift, x, log_rho, ws, ws_bytes,
+                     static_cast<cudaStream_t>(stream), &sel);
+  if (st == MRA_OK && choice_out) {
+    choice_out[0] = sel.kind;
+    choice_out[1] = sel.bi;
+    choice_out[2] = sel.ns;
+  }
+  return st;
+}
+
+MRA_API size_t mra_em_batched_workspace_bytes(const mra_instance* inst, int32_t n) {
+  if (!inst || n < 1) return 0;
+  size_t total = 0;
+  for (int i = 0; i < n; ++i) total += align256(mra_em_workspace_bytes(&inst[i].dims, std::max(inst[i].prm.Lw, 1)));
+  return total;
+}
+
+MRA_API int mra_em_run_batched(const mra_instance* inst, int32_t n, int32_t tune, int32_t* iters_out,
+                               float* exec_ms_out, void* ws, size_t ws_bytes, void* stream) {
+  if (!inst || n < 1 || !ptr_ok(ws, 256)) return MRA_EINVAL;
+  if (ws_bytes < mra_em_batched_workspace_bytes(inst, n)) return MRA_EWORKSPACE;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<size_t> off(n + 1, 0);
+  for (int i = 0; i < n; ++i) {
+    const mra_instance& a = inst[i];
+    int st = check_dims(&a.dims);
+    if (st == MRA_OK) st = check_params(&a.dims, &a.prm);
+    if (st != MRA_OK) return st;
+    if (a.prm.max_iters < 1 || (a.y_format != 0 && a.y_format != 1)) return MRA_EINVAL;
+    if (!ptr_ok(a.x_inout, 16) || !ptr_ok(a.log_rho_inout, 8)) return MRA_EINVAL;
+    if (a.stats_out && !ptr_ok(a.stats_out, 8)) return MRA_EINVAL;
+    off[i + 1] = off[i] + align256(mra_em_workspace_bytes(&a.dims, a.prm.Lw));
+  }
+  unsigned char* base = static_cast<unsigned char*>(ws);
+  const std::vector<unsigned char> key = batched_key(inst, n, ws, ws_bytes);
+  auto run_cached = [&](cudaGraphExec_t exec, const std::vector<Ctrl*>& ctrl) -> int {
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    int rc = MRA_OK;
+    if (cudaEventCreate(&t0) != cudaSuccess || cudaEventCreate(&t1) != cudaSuccess) rc = MRA_ECUDA;
+    if (rc == MRA_OK && (cudaEventRecord(t0, s) != cudaSuccess || cudaGraphLaunch(exec, s) != cudaSuccess ||
+                         cudaEventRecord(t1, s) != cudaSuccess || cudaEventSynchronize(t1) != cudaSuccess))
+      rc = MRA_ECUDA;
+    if (rc == MRA_OK && exec_ms_out && cudaEventElapsedTime(exec_ms_out, t0, t1) != cudaSuccess) rc = MRA_ECUDA;
+    for (int i = 0; i < n && rc == MRA_OK; ++i) {
+      Ctrl h{};
+      if (cudaMemcpy(&h, ctrl[i], 16, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        rc = MRA_ECUDA;
+        break;
+      }
+      if (iters_out) iters_out[i] = h.iter;
+      if (h.status != MRA_OK) rc = h.status;
+    }
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    return rc;
+  };
+  if (!tune) {
+    std::lock_guard<std::mutex> g(g_graph_mu);
+    for (auto& e : g_graphs)
+      if (e.key == key) return run_cached(e.exec, e.ctrl);
+  }
+  // the autotuner runs once per shape not yet in its cache, on the first instance of that shape
+  if (tune) {
+    for (int i = 0; i < n; ++i) {
+      const mra_instance& a = inst[i];
+      SweepSel have;
+      if (tune_lookup(tune_key(&a.dims, a.prm.Lw, a.prm.l0, a.y_format), &have)) continue;
+      const int st = autotune_impl(&a.dims, &a.prm, static_cast<const float*>(a.y), a.y_format, a.shift, a.x_inout,
+                                   a.log_rho_inout, base + off[i], off[i + 1] - off[i], s, nullptr);
+      if (st != MRA_OK) return st;
+    }
+  }
+  std::vector<EmCall> calls(n);
+  for (int i = 0; i < n; ++i) {
+    const mra_instance& a = inst[i];
+    EmCall& c = calls[i];
+    const int st = prepare(&a.dims, a.prm.Lw, a.prm.l0, static_cast<const float*>(a.y), a.shift, base + off[i],
+                           off[i + 1] - off[i], &c, true, a.y_format);
+    if (st != MRA_OK) return st;
+    c.su.x_in = reinterpret_cast<const double2*>(a.x_inout);
+    c.su.log_rho_in = a.log_rho_inout;
+    c.su.log_rho_bar = a.prm.gamma > 0.0 ? a.prm.log_rho_bar : nullptr;
+    c.su.gamma_a_inv = a.prm.gamma_a_inv;
+    c.ua.gamma = a.prm.gamma;
+    c.ua.tol = a.prm.tol;
+    c.ua.update_rho = a.prm.update_rho ? 1 : 0;
+    c.ua.max_iters = a.prm.max_iters;
+    c.ua.stats = a.stats_out;
+  }
+  // one graph: the instances are independent branches, forked over a few capture streams
+  const int S = std::min(n, 8);
+  std::vector<cudaStream_t> side(S, nullptr);
+  std::vector<cudaEvent_t> join(S, nullptr);
+  cudaEvent_t fork = nullptr;
+  cudaStream_t cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int rc = MRA_OK;
+  if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess)
+    rc = MRA_ECUDA;
+  for (int j = 0; j < S && rc == MRA_OK; ++j)
+    if (cudaStreamCreateWithFlags(&side[j], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&join[j], cudaEventDisableTiming) != cudaSuccess)
+      rc = MRA_ECUDA;
+  if (rc == MRA_OK && cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = MRA_ECUDA;
+  if (rc == MRA_OK) {
+    if (cudaEventRecord(fork, cap) != cudaSuccess) rc = MRA_ECUDA;
+    for (int j = 0; j < S && rc == MRA_OK; ++j)
+      if (cudaStreamWaitEvent(side[j], fork, 0) != cudaSuccess) rc = MRA_ECUDA;
+    for (int i = 0; i < n && rc == MRA_OK; ++i) {
+      const EmCall& c = calls[i];
+      cudaStream_t st = side[i % S];
+      rc = launch_setup(c, st);
+      for (int t = 0; t < inst[i].prm.max_iters && rc == MRA_OK; ++t) rc = launch_iteration(c, st);
+      if (rc == MRA_OK) {
+        const int Lw = inst[i].prm.Lw;
+        k_export<<<std::max(1, (std::max(c.lay.M, Lw) + 255) / 256), 256, 0, st>>>(
+            c.lay.M, Lw, c.su.x64, c.su.rho64, reinterpret_cast<double2*>(inst[i].x_inout), inst[i].log_rho_inout);
+        if (cudaGetLastError() != cudaSuccess) rc = MRA_ECUDA;
+      }
+    }
+    for (int j = 0; j < S; ++j) {
+      if (cudaEventRecord(join[j], side[j]) != cudaSuccess || cudaStreamWaitEvent(cap, join[j], 0) != cudaSuccess)
+        rc = MRA_ECUDA;
+    }
+    if (cudaStreamEndCapture(cap, &graph) != cudaSuccess) rc = MRA_ECUDA;
+  }
+  if (rc == MRA_OK && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) rc = MRA_ECUDA;
+  std::vector<Ctrl*> ctrl(n);
+  for (int i = 0; i < n; ++i) ctrl[i] = calls[i].ctrl;
+  if (rc == MRA_OK) rc = run_cached(exec, ctrl);
+  if (rc == MRA_OK) {  // keep the graph for the next call with the same list
+    std::lock_guard<std::mutex> g(g_graph_mu);
+    for (auto it = g_graphs.begin(); it != g_graphs.end(); ++it)
+      if (it->key == key) {
+        cudaGraphExecDestroy(it->exec);
+        g_graphs.erase(it);
+        break;
+      }
+    if (g_graphs.size() >= kGraphCache) {
+      cudaGraphExecDestroy(g_graphs.front().exec);
+      g_graphs.erase(g_graphs.begin());
+    }
+    g_graphs.push_back(BatchedGraph{key, exec, ctrl});
+    exec = nullptr;
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  for (int j = 0; j < S; ++j) {
+    if (side[j]) cudaStreamDestroy(side[j]);
+    if (join[j]) cudaEventDestroy(join[j]);
+  }
+  if (cap) cudaStreamDestroy(cap);
+  if (fork) cudaEventDestroy(fork);
+  return rc;
 }
 
 MRA_API int mra_loglik_grad(const mra_dims* d, int32_t Lw, int32_t l0, const float* y, const int32_t* shift,

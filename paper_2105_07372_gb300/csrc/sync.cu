@@ -518,9 +518,7 @@ MRA_API int mra_sync_pairwise(const mra_dims* d, const float* y, int32_t P, int3
   if (check_sync_dims(d, P) != MRA_OK || !ok_ptr(y, 16) || !ok_ptr(rel_out, 4)) return MRA_EINVAL;
   if (d->L > 8192 || d->K + 1 > 4096) return MRA_EINVAL;
   const int smem = (d->L + d->K + 1) * 8;
-  if (smem > 48 * 1024 &&
-      cudaFuncSetAttribute(reinterpret_cast<const void*>(k_pairwise), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           smem) != cudaSuccess)
+  if (smem > 48 * 1024 && raise_smem_limit(reinterpret_cast<const void*>(k_pairwise), smem) != MRA_OK)
     return MRA_ECUDA;
   k_pairwise<<<dim3(P, P), kPairThreads, smem, static_cast<cudaStream_t>(stream)>>>(
       reinterpret_cast<const float2*>(y), d->K + 1, d->Q, d->L, P, rel_out);
@@ -534,10 +532,7 @@ MRA_API int mra_sync_ppm(int32_t L, int32_t P, const int32_t* rel, int32_t n_pow
   const int base = (L + 2 * P) * 8;
   const int stage = (base + P * P * 8 <= 200 * 1024) ? 2 : (base + P * P * 2 <= 200 * 1024) ? 1 : 0;
   const int smem = base + (stage == 2 ? P * P * 8 : stage == 1 ? P * P * 2 : 0);
-  if (smem > 48 * 1024 &&
-      cudaFuncSetAttribute(reinterpret_cast<const void*>(k_ppm), cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
-          cudaSuccess)
-    return MRA_ECUDA;
+  if (smem > 48 * 1024 && raise_smem_limit(reinterpret_cast<const void*>(k_ppm), smem) != MRA_OK) return MRA_ECUDA;
   int g = 32;  // lanes per row: the largest power of two with g * P <= 1024
   while (g > 1 && g * P > kPpmThreads) g >>= 1;
   k_ppm<<<1, kPpmThreads, smem, static_cast<cudaStream_t>(stream)>>>(L, P, rel, n_power, n_ppm, phi_out, stage, g);

@@ -40,6 +40,11 @@ class mra_em_params(ctypes.Structure):
                 ("check_every", c_int32), ("sweep_ms", c_void_p)]
 
 
+class mra_instance(ctypes.Structure):
+    _fields_ = [("dims", mra_dims), ("prm", mra_em_params), ("y", c_void_p), ("y_format", c_int32),
+                ("shift", c_void_p), ("x_inout", c_void_p), ("log_rho_inout", c_void_p), ("stats_out", c_void_p)]
+
+
 _lib = None
 _SIGS = {
     "mra_status_string": (ctypes.c_char_p, [c_int]),
@@ -56,6 +61,11 @@ _SIGS = {
                                                                                              c_void_p, c_void_p,
                                                                                              c_size_t, c_void_p]),
     "mra_y_split_bf16": (c_int, [c_void_p, ctypes.c_int64, c_void_p, c_void_p]),
+    "mra_em_autotune": (c_int, [POINTER(mra_dims), POINTER(mra_em_params), c_void_p, c_int32, c_void_p, c_void_p,
+                                c_void_p, POINTER(c_int32), c_void_p, c_size_t, c_void_p]),
+    "mra_em_batched_workspace_bytes": (c_size_t, [POINTER(mra_instance), c_int32]),
+    "mra_em_run_batched": (c_int, [POINTER(mra_instance), c_int32, c_int32, POINTER(c_int32), POINTER(ctypes.c_float),
+                                   c_void_p, c_size_t, c_void_p]),
     "mra_loglik_grad": (c_int, [POINTER(mra_dims), c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_double,
                                 c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "mra_sync_workspace_bytes": (c_size_t, [POINTER(mra_dims), c_int32]),
@@ -202,6 +212,45 @@ def mra_em_run_hl(d, prm, y_hl, shift, x_inout, log_rho_inout, stats_out=None, x
                                                  _p(x_inout), _p(log_rho_inout), ctypes.byref(it), _p(stats_out),
                                                  _p(x_traj_out), _p(ws), ws.numel(), _stream(stream)))
     return it.value
+
+
+def mra_em_autotune(d, prm, y, shift, x, log_rho, ws, y_format=0, stream=None):
+    """Time every applicable EM sweep on this problem and cache the fastest; returns (kind, batch, stages)."""
+    ch = (c_int32 * 3)()
+    _check("mra_em_autotune", load().mra_em_autotune(ctypes.byref(d), ctypes.byref(prm), _p(y), int(y_format),
+                                                     _p(shift), _p(x), _p(log_rho), ch, _p(ws), ws.numel(),
+                                                     _stream(stream)))
+    return tuple(ch)
+
+
+def instances(items):
+    """ctypes array of mra_instance from dicts with keys d, prm, y, x, log_rho and optional shift, stats, y_format.
+    The tensors must stay alive while the array is used."""
+    arr = (mra_instance * len(items))()
+    for a, it in zip(arr, items):
+        a.dims = it["d"]
+        a.prm = it["prm"]
+        a.y = _p(it["y"])
+        a.y_format = int(it.get("y_format", 0))
+        a.shift = _p(it.get("shift"))
+        a.x_inout = _p(it["x"])
+        a.log_rho_inout = _p(it["log_rho"])
+        a.stats_out = _p(it.get("stats"))
+    return arr
+
+
+def mra_em_batched_workspace_bytes(arr) -> int:
+    return int(load().mra_em_batched_workspace_bytes(arr, len(arr)))
+
+
+def mra_em_run_batched(arr, ws, tune=True, stream=None):
+    """All instances in one graph launch; returns (iterations per instance, device ms of the launch)."""
+    n = len(arr)
+    it = (c_int32 * n)()
+    ms = ctypes.c_float(0.0)
+    _check("mra_em_run_batched", load().mra_em_run_batched(arr, n, 1 if tune else 0, it, ctypes.byref(ms), _p(ws),
+                                                           ws.numel(), _stream(stream)))
+    return list(it), ms.value
 
 
 def mra_loglik_grad(d, Lw, l0, y, shift, x, logits, kappa, loglik_out, dx_out=None, dlogits_out=None, dkappa_out=None,

@@ -19,4 +19,5 @@ from .instances import (  # noqa: F401
     c64_round,
     bf16_split,
     bf16_merge,
+    config4_instances,
 )

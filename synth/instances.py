@@ -138,3 +138,21 @@ def bf16_merge(groups: np.ndarray, shape) -> np.ndarray:
     f = g.view(np.float32)
     v = (f[:, :4] + f[:, 4:]).astype(np.float32).reshape(-1)
     return v.view(np.complex64).astype(np.complex128).reshape(shape)
+
+
+def config4_instances(seed: int = 4000, n_inst: int = 64, n_max: int | None = None) -> list[dict]:
+    """The batched workload: n_inst independent problems with N ~ U[1000, 50000],
+    K ~ U{8..40}, Q = 16, L = 360, window Lw ~ U{12..72}, pixel SNR log-uniform on
+    [1/100, 1/5], 30 iterations each.  The list is fixed by ``seed``; ``n_max`` caps N
+    (smaller test versions of the same list).  Each entry's ``seed`` draws its data."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_inst):
+        N = int(rng.integers(1000, 50001))
+        K = int(rng.integers(8, 41))
+        Lw = int(rng.integers(12, 73))
+        snr = float(np.exp(rng.uniform(np.log(1 / 100), np.log(1 / 5))))
+        if n_max is not None:
+            N = min(N, n_max)
+        out.append(dict(N=N, K=K, Q=16, L=360, Lw=Lw, snr=snr, decay=50.0, iters=30, seed=seed + 1 + i))
+    return out

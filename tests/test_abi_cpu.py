@@ -45,6 +45,33 @@ def test_struct_layout():
     assert ctypes.sizeof(mra.mra_em_params) == 64
 
 
+def test_struct_layout_matches_the_c_compiler(tmp_path):
+    """Offsets of every binding struct field equal offsetof() in the header, compiled by gcc."""
+    import shutil
+    import subprocess
+
+    from paper_2105_07372_gb300 import mra
+
+    if not shutil.which("gcc"):
+        pytest.skip("no C compiler")
+    structs = [mra.mra_dims, mra.mra_em_params, mra.mra_instance]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "mra.h"', "int main(void) {"]
+    for st in structs:
+        lines.append(f'  printf("{st.__name__} %zu\\n", sizeof({st.__name__}));')
+        for f, _ in st._fields_:
+            lines.append(f'  printf("{st.__name__}.{f} %zu\\n", offsetof({st.__name__}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n") if l)
+    for st in structs:
+        assert int(got[st.__name__]) == ctypes.sizeof(st), st.__name__
+        for f, _ in st._fields_:
+            assert int(got[f"{st.__name__}.{f}"]) == getattr(st, f).offset, (st.__name__, f)
+
+
 def test_oracle_not_imported_by_product():
     """The product package never imports the oracle."""
     pkg = os.path.join(ROOT, "paper_2105_07372_gb300")
