@@ -101,3 +101,46 @@ def relerr(x_hat, x, d, stream=None) -> float:
     out = torch.empty(1, dtype=torch.float64, device=x.device)
     mra.mra_relerr(d.K, d.Q, x_hat, x, out, stream)
     return float(out.item())
+
+
+@dataclasses.dataclass
+class PriorFit:
+    kappa: float
+    logits: torch.Tensor  # float64 [Lw] (zeros unless fitted)
+    loglik: float
+    evals: int
+
+
+def fit_prior_ml(y, d, Lw, x, shift=None, l0=None, kappa0=1.0, fit_logits=False, max_iter=50,
+                 ws=None) -> PriorFit:
+    """Von Mises prior on the window by maximum marginal likelihood at fixed x: maximise
+    l(x, kappa, eta) over kappa (and the window logits eta when fit_logits) with L-BFGS, each
+    evaluation one forward and one backward sweep of mra_loglik_grad through the autograd
+    function (the posterior is recomputed, never stored).  The prior family is the von Mises
+    extension of the learned prior of Algorithm 1; Sec. 3.2 defines the marginal likelihood."""
+    from .autograd import marginal_loglik
+
+    if l0 is None:
+        l0 = -(Lw // 2)
+    if ws is None:
+        ws = mra.workspace(mra.mra_em_workspace_bytes(d, Lw), y.device)
+    xd = x.detach()
+    kappa = torch.tensor([float(kappa0)], dtype=torch.float64, device=y.device, requires_grad=True)
+    eta = torch.zeros(Lw, dtype=torch.float64, device=y.device, requires_grad=fit_logits)
+    params = [kappa] + ([eta] if fit_logits else [])
+    opt = torch.optim.LBFGS(params, lr=1.0, max_iter=max_iter, tolerance_grad=1e-9, tolerance_change=1e-12,
+                            line_search_fn="strong_wolfe")
+    n = [0]
+    scale = 1.0 / d.N
+
+    def closure():
+        opt.zero_grad()
+        loss = -marginal_loglik(xd, eta, kappa, y, d, Lw, l0=l0, shift=shift, ws=ws) * scale
+        loss.backward()
+        n[0] += 1
+        return loss
+
+    opt.step(closure)
+    with torch.no_grad():
+        ll = float(marginal_loglik(xd, eta, kappa, y, d, Lw, l0=l0, shift=shift, ws=ws).item())
+    return PriorFit(kappa=float(kappa.item()), logits=eta.detach().clone(), loglik=ll, evals=n[0])
