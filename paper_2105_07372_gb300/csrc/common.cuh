@@ -218,6 +218,38 @@ SweepV3Fn sweep_v3_qh8(int bi, int yf);
 SweepV3Fn sweep_v3_qh12(int bi, int yf);
 SweepV3Fn sweep_v3_qh16(int bi, int yf);
 
+// Arguments of the chunked two-read sweep (sweep4_impl.cuh).
+struct SweepV4Args {
+  const float2* y;
+  const int* shift;
+  int N, Kp1, M, L, Lw;
+  int slot_bytes;  // bytes per warp slot
+  int cp, sp, dp;  // per-image pitches of the c/W, s/w and unit-weight buffers
+  int nd, wrap, r0, d1, phase0;  // as in SweepV3Args
+  int lc;          // log2 of the images per chunk
+  int off_ring, off_x, off_td, off_tf, off_lr, off_c, off_s, off_w2, off_info, off_wl;
+  float two_beta;
+  const float2* x32;
+  const float2* td;
+  const float2* tf32;
+  const float* logrho32;
+  double* part;
+  float* w_out;
+  Ctrl* ctrl;
+};
+struct SweepV4Launch {
+  void (*fn)(const SweepV4Args);
+  int threads;
+  int ctas_per_sm;
+};
+// QV = float4 per lane per row (Q / 8); MR = rows per quad ((K+1+7)/8, at most 7);
+// cpsm = resident CTAs per SM (1: 512 threads, 2: 256 threads each; 256 threads and one
+// CTA per SM for the largest per-lane accumulators).
+SweepV4Launch sweep_v4_q1(int MR, int cpsm);
+SweepV4Launch sweep_v4_q2(int MR, int cpsm);
+SweepV4Launch sweep_v4_q3(int MR, int cpsm);
+SweepV4Launch sweep_v4_q4(int MR, int cpsm);
+
 // Mirror units of a window: offsets o and -o (mod L) share cos/sin.  Writes the
 // (a, b) index pairs in window order of a; returns the number of units.
 __host__ __device__ inline int window_units(int L, int Lw, int l0, int2* out) {
@@ -241,8 +273,10 @@ __host__ __device__ inline int window_units(int L, int Lw, int l0, int2* out) {
 // Device properties cached per device.
 struct DevInfo {
   int sms;
-  int max_smem_optin;
+  int max_smem_optin;  // per CTA
+  int smem_per_sm;     // shared memory of one SM (shared by its resident CTAs)
 };
+constexpr int kMaxCtasPerSm = 2;  // the EM partial-sum layout has room for this many CTAs per SM
 int dev_info(DevInfo* out);
 // Raise a kernel's dynamic shared-memory limit to at least `bytes` (never lowers it).
 int raise_smem_limit(const void* fn, int bytes);

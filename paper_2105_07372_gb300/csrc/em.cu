@@ -57,12 +57,15 @@ int dev_info(DevInfo* out) {
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return MRA_ECUDA;
   std::lock_guard<std::mutex> lk(mu);
   if (!have[dev]) {
-    int sms = 0, smem = 0;
+    int sms = 0, smem = 0, smem_sm = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return MRA_ECUDA;
     if (cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
       return MRA_ECUDA;
+    if (cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess)
+      return MRA_ECUDA;
     cache[dev].sms = sms;
     cache[dev].max_smem_optin = smem;
+    cache[dev].smem_per_sm = smem_sm;
     have[dev] = true;
   }
   *out = cache[dev];
@@ -72,7 +75,7 @@ int dev_info(DevInfo* out) {
 int sweep_grid() {
   DevInfo d;
   if (dev_info(&d) != MRA_OK) return -1;
-  return d.sms;  // one persistent CTA per SM (the tile ring fills shared memory)
+  return d.sms;  // one persistent CTA per SM (the chunked sweep may run two)
 }
 
 // ============================================================================ kernels
@@ -1063,8 +1066,78 @@ bool plan_v3(int Kp1, int Q, int L, int Lw, int l0, int yf, int want_bi, int wan
   return false;
 }
 
+struct V4Plan {
+  SweepV4Launch launch;
+  int lc, slot_bytes, cp, sp, dp, nd, wrap, r0, d1, phase0, smem, grid;
+  int off_ring, off_x, off_td, off_tf, off_lr, off_c, off_s, off_w2, off_info, off_wl;
+};
+
+// Shared-memory plan of the chunked two-read sweep for one launch shape: one slot per
+// warp and the largest chunk of 128, 64, 32 or 16 images (or want_c) whose transform
+// buffers fit in max_smem.
+bool plan_v4_shape(int Kp1, int Q, int L, int Lw, int l0, int want_c, int max_smem, const SweepV4Launch& ln,
+                   V4Plan* p) {
+  const int NW = ln.threads / 32;
+  const int M = Kp1 * Q;
+  const int slot = al16(M * 8);
+  p->wrap = Lw == L ? 1 : 0;
+  p->nd = p->wrap ? L / 2 + 1 : Lw;
+  int r0 = (-l0) % L;
+  if (r0 < 0) r0 += L;
+  if (r0 >= Lw) r0 = Lw / 2;
+  p->r0 = r0;
+  p->d1 = p->wrap ? L / 2 : std::max(r0, Lw - 1 - r0);
+  p->phase0 = ((l0 + r0) % L + L) % L;
+  const int cp = Kp1 | 1, sp = Lw | 1, dp = p->nd | 1;
+  for (int lc = 7; lc >= 4; --lc) {
+    const int c = 1 << lc;
+    if ((want_c && c != want_c) || c > ln.threads) continue;
+    int o = 128;  // mbarriers, one per warp
+    p->off_ring = o; o += NW * slot;
+    p->off_x = o; o += al16(M * 8);
+    p->off_td = o; o += al16(Kp1 * dp * 8);
+    p->off_tf = o; o += al16(L * 8);
+    p->off_lr = o; o += al16(Lw * 4);
+    p->off_c = o; o += al16(c * cp * 8);
+    p->off_s = o; o += al16(c * sp * 4);
+    p->off_w2 = o; o += al16(c * dp * 8);
+    p->off_info = o; o += al16(c * 16);
+    p->off_wl = o; o += al16(4 * NW * sp * 4);
+    if (o + 1024 <= max_smem) {
+      p->launch = ln;
+      p->lc = lc;
+      p->slot_bytes = slot;
+      p->cp = cp; p->sp = sp; p->dp = dp;
+      p->smem = o;
+      return true;
+    }
+  }
+  return false;
+}
+
+// Two CTAs per SM (each with half the shared memory, so that one can stream while the
+// other transforms) where the plan fits, else one; want_cpsm fixes the choice.
+bool plan_v4(int Kp1, int Q, int L, int Lw, int l0, int want_c, int want_cpsm, const DevInfo& di, V4Plan* p) {
+  if (Q % 8 != 0 || Q / 8 > 4) return false;
+  const int QV = Q / 8, MR = (Kp1 + 7) / 8;
+  if (MR > 7) return false;
+  for (int cpsm = kMaxCtasPerSm; cpsm >= 1; --cpsm) {
+    if (want_cpsm && cpsm != want_cpsm) continue;
+    const SweepV4Launch ln = QV == 1 ? sweep_v4_q1(MR, cpsm) : QV == 2 ? sweep_v4_q2(MR, cpsm)
+                           : QV == 3 ? sweep_v4_q3(MR, cpsm) : sweep_v4_q4(MR, cpsm);
+    if (!ln.fn) continue;
+    const int max_smem = std::min(di.max_smem_optin, di.smem_per_sm / cpsm - 1024);
+    if (plan_v4_shape(Kp1, Q, L, Lw, l0, want_c, max_smem, ln, p)) {
+      p->grid = di.sms * cpsm;
+      return true;
+    }
+  }
+  return false;
+}
+
 // Which EM sweep a call uses.  kind: 0 = automatic, 1 = warp per image, 2 = batch
-// (CTA-cooperative) with batch bi and ring stages ns (0 = the first that fits).
+// (CTA-cooperative) with batch bi and ring stages ns (0 = the first that fits),
+// 3 = chunked two-read with bi images per chunk and ns CTAs per SM (0 = first that fits).
 struct SweepSel {
   int kind, bi, ns;
 };
@@ -1076,6 +1149,7 @@ SweepSel env_sweep() {
   const char* k = getenv("MRA_SWEEP");
   if (k && strcmp(k, "warp") == 0) e.kind = 1;
   if (k && strcmp(k, "cta") == 0) e.kind = 2;
+  if (k && strcmp(k, "chunk") == 0) e.kind = 3;
   const char* b = getenv("MRA_SWEEP_BI");
   const char* n = getenv("MRA_SWEEP_NS");
   e.bi = b ? atoi(b) : 0;
@@ -1158,10 +1232,14 @@ struct EmCall {
   bool v3;  // CTA-cooperative sweep over image batches
   V3Plan v3p;
   SweepV3Args sa3;
+  bool v4;  // chunked two-read sweep
+  V4Plan v4p;
+  SweepV4Args sa4;
   void set_w_out(float* w) {
     sa.w_out = w;
     sa2.w_out = w;
     sa3.w_out = w;
+    sa4.w_out = w;
   }
 };
 
@@ -1178,7 +1256,9 @@ int prepare(const mra_dims* d, int Lw, int l0, const float* y, const int32_t* sh
   DevInfo di;
   if ((st = dev_info(&di)) != MRA_OK) return st;
   const int G = di.sms;
-  c->lay = em_layout(d->N, d->K, d->Q, d->L, Lw, G);
+  // partial sums have room for kMaxCtasPerSm CTAs per SM; lay.G is the launch grid
+  c->lay = em_layout(d->N, d->K, d->Q, d->L, Lw, G * kMaxCtasPerSm);
+  c->lay.G = G;
   if (ws_bytes < c->lay.total) return MRA_EWORKSPACE;
   const int Kp1 = d->K + 1, M = Kp1 * d->Q;
   const int nu = window_units(d->L, Lw, l0, nullptr);
@@ -1190,6 +1270,7 @@ int prepare(const mra_dims* d, int Lw, int l0, const float* y, const int32_t* sh
     SweepSel tuned;
     if (tune_lookup(tune_key(d, Lw, l0, yfmt), &tuned)) sel = tuned;
   }
+  c->v4 = false;
   if (yfmt) {
     c->v2 = false;
     c->v3 = sel.kind != 1 && plan_v3(Kp1, d->Q, d->L, Lw, l0, 1, sel.bi, sel.ns, di.max_smem_optin, &c->v3p);
@@ -1201,9 +1282,22 @@ int prepare(const mra_dims* d, int Lw, int l0, const float* y, const int32_t* sh
     c->v3 = allow_v3 && sel.kind != 1 && (!c->v2 || sel.kind == 2 || nup > kUnitChunk) &&
             plan_v3(Kp1, d->Q, d->L, Lw, l0, 0, sel.bi, sel.ns, di.max_smem_optin, &c->v3p);
     if (c->v3) c->v2 = false;
-    if (force && ((force->kind == 1 && !c->v2) || (force->kind == 2 && !c->v3))) return MRA_EINVAL;
+    // The chunked two-read sweep runs when chosen (environment or autotuner): it leads on
+    // sharp posteriors and ties the warp sweep on broad ones.
+    if (allow_v3 && sel.kind == 3) {
+      c->v4 = plan_v4(Kp1, d->Q, d->L, Lw, l0, sel.bi, sel.ns, di, &c->v4p);
+      if (c->v4) {
+        c->v2 = c->v3 = false;
+        c->lay.G = c->v4p.grid;
+      }
+    }
+    if (force && ((force->kind == 1 && !c->v2) || (force->kind == 2 && !c->v3) || (force->kind == 3 && !c->v4)))
+      return MRA_EINVAL;
   }
-  if (c->v3) {
+  if (c->v4) {
+    if (raise_smem_limit(reinterpret_cast<const void*>(c->v4p.launch.fn), c->v4p.smem) != MRA_OK) return MRA_ECUDA;
+    c->sweep = nullptr;
+  } else if (c->v3) {
     if (raise_smem_limit(reinterpret_cast<const void*>(c->v3p.fn), c->v3p.smem) != MRA_OK)
       return MRA_ECUDA;
     c->sweep = nullptr;
@@ -1284,6 +1378,25 @@ int prepare(const mra_dims* d, int Lw, int l0, const float* y, const int32_t* sh
   w.w_out = nullptr;
   w.ctrl = c->ctrl;
 
+  SweepV4Args& v4 = c->sa4;
+  const V4Plan& q4 = c->v4p;
+  v4.y = s.y;
+  v4.shift = shift;
+  v4.N = d->N; v4.Kp1 = Kp1; v4.M = M; v4.L = d->L; v4.Lw = Lw;
+  v4.slot_bytes = q4.slot_bytes; v4.cp = q4.cp; v4.sp = q4.sp; v4.dp = q4.dp;
+  v4.nd = q4.nd; v4.wrap = q4.wrap; v4.r0 = q4.r0; v4.d1 = q4.d1; v4.phase0 = q4.phase0; v4.lc = q4.lc;
+  v4.off_ring = q4.off_ring; v4.off_x = q4.off_x; v4.off_td = q4.off_td; v4.off_tf = q4.off_tf;
+  v4.off_lr = q4.off_lr; v4.off_c = q4.off_c; v4.off_s = q4.off_s; v4.off_w2 = q4.off_w2;
+  v4.off_info = q4.off_info; v4.off_wl = q4.off_wl;
+  v4.two_beta = s.two_beta;
+  v4.x32 = s.x32;
+  v4.td = reinterpret_cast<const float2*>(base + L_.td);
+  v4.tf32 = s.tf32;
+  v4.logrho32 = s.logrho32;
+  v4.part = s.part;
+  v4.w_out = nullptr;
+  v4.ctrl = c->ctrl;
+
   SetupArgs& u = c->su;
   u.N = d->N; u.Kp1 = Kp1; u.Q = d->Q; u.M = M; u.L = d->L; u.Lw = Lw;
   u.l0 = l0; u.twp = L_.twp; u.kp4 = L_.kp4; u.sigma2 = d->sigma2;
@@ -1300,7 +1413,7 @@ int prepare(const mra_dims* d, int Lw, int l0, const float* y, const int32_t* sh
   u.units = reinterpret_cast<int2*>(base + L_.units);
   u.tu = reinterpret_cast<float2*>(base + L_.tu);
   u.td = reinterpret_cast<float2*>(base + L_.td);
-  u.nd = c->v3 ? c->v3p.nd : 0;
+  u.nd = c->v3 ? c->v3p.nd : c->v4 ? c->v4p.nd : 0;
   u.nu = nu;
   u.nup = nup;
   u.ctrl = c->ctrl;
@@ -1325,7 +1438,7 @@ int launch_setup(const EmCall& c, cudaStream_t st) {
   const int n = std::max(std::max(c.su.L, c.su.M), c.su.Lw);
   const int blocks = std::min(1024, (n + 127) / 128);
   k_setup<<<blocks, 128, 0, st>>>(c.su);
-  if (c.v3) {
+  if (c.v3 || c.v4) {
     const int ntd = c.su.Kp1 * c.su.nd;
     k_setup_td<<<std::min(1024, (ntd + 255) / 256), 256, 0, st>>>(c.su);
   } else if (c.v2) {
@@ -1340,7 +1453,9 @@ int launch_setup(const EmCall& c, cudaStream_t st) {
 }
 
 void launch_sweep(const EmCall& c, cudaStream_t st) {
-  if (c.v3)
+  if (c.v4)
+    c.v4p.launch.fn<<<c.lay.G, c.v4p.launch.threads, c.v4p.smem, st>>>(c.sa4);
+  else if (c.v3)
     c.v3p.fn<<<c.lay.G, kV3Threads, c.v3p.smem, st>>>(c.sa3);
   else if (c.v2)
     c.v2p.launch.fn<<<c.lay.G, c.v2p.launch.threads, c.v2p.smem, st>>>(c.sa2);
@@ -1401,7 +1516,7 @@ MRA_API size_t mra_em_workspace_bytes(const mra_dims* d, int32_t Lw) {
   if (check_dims(d) != MRA_OK || Lw < 1) return 0;
   DevInfo di;
   if (dev_info(&di) != MRA_OK) return 0;
-  return em_layout(d->N, d->K, d->Q, d->L, Lw, di.sms).total;
+  return em_layout(d->N, d->K, d->Q, d->L, Lw, di.sms * kMaxCtasPerSm).total;
 }
 
 }  // extern "C"
@@ -1593,7 +1708,9 @@ namespace mra {
 namespace {
 
 // Sweep candidates the autotuner times, in the order of the default preference.
-const SweepSel kTuneCandidates[] = {{1, 0, 0}, {2, 16, 2}, {2, 12, 2}, {2, 8, 3}, {2, 8, 2}, {2, 4, 3}, {2, 4, 2}};
+const SweepSel kTuneCandidates[] = {{1, 0, 0},  {2, 16, 2}, {2, 12, 2}, {2, 8, 3},  {2, 8, 2}, {2, 4, 3},
+                                    {2, 4, 2},  {3, 64, 2}, {3, 32, 2}, {3, 16, 2}, {3, 128, 1},
+                                    {3, 64, 1}, {3, 32, 1}};
 
 // Best of `reps` timed sweeps (after one untimed) of a prepared call whose setup has run; < 0 on error.
 float time_sweep(const EmCall& c, cudaStream_t s, int reps) {
@@ -1627,6 +1744,9 @@ int autotune_impl(const mra_dims* d, const mra_em_params* p, const float* y, int
     if (st == MRA_EINVAL) continue;  // this candidate cannot take the shape
     if (st != MRA_OK) return st;
     if (cand.kind == 2 && ((cand.bi && c.v3p.bi != cand.bi) || (cand.ns && c.v3p.ns != cand.ns))) continue;
+    if (cand.kind == 3 && ((cand.bi && (1 << c.v4p.lc) != cand.bi) ||
+                           (cand.ns && c.v4p.launch.ctas_per_sm != cand.ns)))
+      continue;
     c.su.x_in = reinterpret_cast<const double2*>(x);
     c.su.log_rho_in = log_rho;
     int rc = launch_setup(c, s);
@@ -1963,7 +2083,8 @@ MRA_API int mra_em_step_noalloc(const mra_dims* d, const mra_em_params* p, const
   if ((st = check_params(d, p)) != MRA_OK) return st;
   DevInfo di;
   if ((st = dev_info(&di)) != MRA_OK) return st;
-  if (em_layout(d->N, d->K, d->Q, d->L, p->Lw, di.sms).total > kNoAllocScratchBytes) return MRA_EWORKSPACE;
+  if (em_layout(d->N, d->K, d->Q, d->L, p->Lw, di.sms * kMaxCtasPerSm).total > kNoAllocScratchBytes)
+    return MRA_EWORKSPACE;
   void* scratch = nullptr;
   if ((st = noalloc_scratch(&scratch)) != MRA_OK) return st;
   return mra_em_step(d, p, y, shift, x_in, log_rho_in, x_out, log_rho_out, loglik_out, step_out, w_out, scratch,

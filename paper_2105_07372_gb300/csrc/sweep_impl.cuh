@@ -554,11 +554,12 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR, IPW>::kThreads, 1) k_swee
 
 }  // namespace mra
 
-// Instantiation table for one row width QV: MR = 1..7 rows per quad, IPW = 1 or 2 images per warp.
+// Instantiation table for one row width QV: MR = 1..7 rows per quad, one image per warp
+// (two images per warp measured slower and are not built).
 #define MRA_SWEEP_V2_CASE(QV, MR)                                                                        \
   case MR:                                                                                               \
-    return ipw == 2 ? SweepV2Launch{k_sweep_v2<QV, MR, 2>, SweepV2Shape<QV, MR, 2>::kThreads}             \
-                    : SweepV2Launch{k_sweep_v2<QV, MR, 1>, SweepV2Shape<QV, MR, 1>::kThreads};
+    return ipw == 1 ? SweepV2Launch{k_sweep_v2<QV, MR, 1>, SweepV2Shape<QV, MR, 1>::kThreads}             \
+                    : SweepV2Launch{nullptr, 0};
 #define MRA_SWEEP_V2_TABLE(QV)                     \
   namespace mra {                                 \
   SweepV2Launch sweep_v2_q##QV(int MR, int ipw) { \

@@ -49,9 +49,10 @@ def compare(mra, inst, x, log_rho, Lw, l0=None, shifts=None, **kw):
     return xg, st
 
 
-@pytest.fixture(params=["cta", "warp"])
+@pytest.fixture(params=["cta", "warp", "chunk"])
 def sweep(request, monkeypatch):
-    """Both EM sweeps: the CTA-cooperative batch sweep and the warp-per-image one."""
+    """Every EM sweep: the CTA-cooperative batch sweep, the warp-per-image one and the
+    chunked two-read one (shapes a sweep cannot take fall back to the tile sweep)."""
     monkeypatch.setenv("MRA_SWEEP", request.param)
     return request.param
 
@@ -117,6 +118,17 @@ def test_em_step_batch_sizes(gpu_lib, bi, monkeypatch):
     monkeypatch.setenv("MRA_SWEEP_BI", bi)
     inst = synth.make_instance(7, 8, 1000 + 13, 36, sigma2=1 / (0.3 * 64), decay=20.0, seed=77)
     x0 = synth.random_init(7, 8, 20.0, seed=3)
+    Lw = 11
+    compare(gpu_lib, inst, x0, np.log(np.full(Lw, 1 / Lw)), Lw, shifts=inst.s)
+
+
+@pytest.mark.parametrize("chunk", ["128", "64", "32", "16"])
+def test_em_step_chunk_sizes(gpu_lib, chunk, monkeypatch):
+    """Every chunk size of the two-read sweep, with a ragged last chunk and warps without images."""
+    monkeypatch.setenv("MRA_SWEEP", "chunk")
+    monkeypatch.setenv("MRA_SWEEP_BI", chunk)
+    inst = synth.make_instance(7, 16, 1000 + 7, 36, sigma2=1 / (0.3 * 128), decay=20.0, seed=78)
+    x0 = synth.random_init(7, 16, 20.0, seed=3)
     Lw = 11
     compare(gpu_lib, inst, x0, np.log(np.full(Lw, 1 / Lw)), Lw, shifts=inst.s)
 
