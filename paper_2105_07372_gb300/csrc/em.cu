@@ -581,6 +581,7 @@ __global__ void k_reduce_cols(const double* part, int G, int cols, double* tot, 
 struct UpdateArgs {
   int N, Kp1, Q, M, L, Lw;
   double sigma2, beta, gamma, tol;
+  double ll_const;  // N M log(pi sigma2), computed on the host (an FP64 log is slow on the device)
   int update_rho, max_iters;
   const double* tot;  // [cols + 8]; tot[cols] keeps sum_j ||y_j||^2 from the first iteration
   int cols;
@@ -618,52 +619,75 @@ __device__ __forceinline__ double block_sum_d(double v, double* red) {
   return red[32];
 }
 
-// One CTA: a_{t+1}, rho_{t+1}, log-likelihood at a_t, step; state update.
-// FP64 where the result needs it (a_{t+1}, norms, rho, the step at the chosen rotations);
-// the search over the L grid rotations for the step runs in FP32 and every rotation
-// within FP32 resolution of the best is re-evaluated exactly in FP64.
-__global__ void k_update(const UpdateArgs a) {
+// Shared memory of k_update: xn [M] double2, t64 [L] double2, t32 [L] float2, d32 [Kp1] float2,
+// sc [L] float, then xf [M] float4 (a_{t+1}, a_t in FP32) at a 16-byte boundary.
+__host__ __device__ inline int update_xf_offset(int M, int L, int Kp1) {
+  return (16 * M + 28 * L + 8 * Kp1 + 15) & ~15;
+}
+
+__device__ __forceinline__ float block_sum_f(float v, float* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    float t = lane < nw ? red[lane] : 0.f;
+    t = warp_sum(t);
+    if (lane == 0) red[32] = t;
+  }
+  __syncthreads();
+  return red[32];
+}
+
+// One CTA: a_{t+1}, rho_{t+1}, log-likelihood at a_t, step; state update.  FP64 arithmetic is
+// slow on this part (one FP64 warp instruction holds the SM's FP64 pipe for many cycles), so
+// FP64 is kept to the state a_{t+1} = num / (N + sigma^2 Gamma^-1) and the final likelihood
+// sum; norms, rho and the step run in FP32 (the step as a direct sum of squares, which has no
+// cancellation, to relative accuracy ~1e-6).
+constexpr int kUpdateThreads = 512;
+
+__global__ void __launch_bounds__(kUpdateThreads, 1) k_update(const UpdateArgs a) {
   extern __shared__ __align__(16) unsigned char usmem[];
   if (a.ctrl->done) return;
   double2* xn = reinterpret_cast<double2*>(usmem);            // [M]
-  double2* t64 = xn + a.M;                                      // [L]
+  double2* t64 = xn + a.M;                                      // [L]  (unused: kept for layout)
   float2* t32 = reinterpret_cast<float2*>(t64 + a.L);          // [L]
   float2* d32 = t32 + a.L;                                      // [Kp1]
   float* sc = reinterpret_cast<float*>(d32 + a.Kp1);           // [L]
-  __shared__ double red[33];
-  __shared__ float fred[32];
+  float4* xf = reinterpret_cast<float4*>(usmem + update_xf_offset(a.M, a.L, a.Kp1));  // [M]
+  __shared__ float fred[33];
   __shared__ double ysq_total;
   __shared__ int ncand;
   __shared__ int cand[16];
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   const int iter = a.ctrl->iter;
   if (tid == 0) ncand = 0;
-  for (int l = tid; l < a.L; l += nt) t64[l] = a.tf64[l], t32[l] = a.tf32[l];
+  for (int l = tid; l < a.L; l += nt) t32[l] = a.tf32[l];
 
-  double nx_old = 0.0, nx_new = 0.0;
+  float nx_old = 0.f;
   for (int e = tid; e < a.M; e += nt) {
     const double2 xo = a.x64[e];
-    const double2 v = make_double2(a.tot[2 * e] * a.inv_den[e], a.tot[2 * e + 1] * a.inv_den[e]);
+    const double id = a.inv_den[e];
+    const double2 v = make_double2(a.tot[2 * e] * id, a.tot[2 * e + 1] * id);
     xn[e] = v;
-    nx_old = fma(xo.x, xo.x, fma(xo.y, xo.y, nx_old));
-    nx_new = fma(v.x, v.x, fma(v.y, v.y, nx_new));
+    xf[e] = make_float4((float)v.x, (float)v.y, (float)xo.x, (float)xo.y);
+    nx_old = fmaf((float)xo.x, (float)xo.x, fmaf((float)xo.y, (float)xo.y, nx_old));
   }
-  nx_old = block_sum_d(nx_old, red);
-  nx_new = block_sum_d(nx_new, red);
+  nx_old = block_sum_f(nx_old, fred);
   if (tid == 0) {
     double* keep = const_cast<double*>(a.tot) + a.cols;
     if (iter == 0) keep[0] = a.tot[2 * a.M + a.Lw + 1];
     ysq_total = keep[0];
   }
-  // d_k = sum_q conj(a_{t+1,kq}) a_{t,kq} in FP32 (only used to rank rotations), one warp per row
+  // d_k = sum_q conj(a_{t+1,kq}) a_{t,kq} (FP32, ranks the rotations), one warp per row
   for (int k = warp; k < a.Kp1; k += nw) {
     float dr = 0.f, di = 0.f;
     for (int q = lane; q < a.Q; q += 32) {
-      const double2 u = xn[k * a.Q + q];
-      const float2 v = a.x32[k * a.Q + q];
-      const float ur = (float)u.x, ui = (float)u.y;
-      dr = fmaf(ur, v.x, fmaf(ui, v.y, dr));
-      di = fmaf(ur, v.y, fmaf(-ui, v.x, di));
+      const float4 v = xf[k * a.Q + q];
+      dr = fmaf(v.x, v.z, fmaf(v.y, v.w, dr));
+      di = fmaf(v.x, v.w, fmaf(-v.y, v.z, di));
     }
     dr = warp_sum(dr);
     di = warp_sum(di);
@@ -671,19 +695,21 @@ __global__ void k_update(const UpdateArgs a) {
   }
   __syncthreads();
 
-  // rho update
-  if (a.update_rho) {
-    double v = 0.0;
-    for (int l = tid; l < a.Lw; l += nt) v += a.tot[2 * a.M + l] + a.gamma * a.rhobar64[l];
-    const double tsum = block_sum_d(v, red);
-    for (int l = tid; l < a.Lw; l += nt) {
-      const double r = (a.tot[2 * a.M + l] + a.gamma * a.rhobar64[l]) / tsum;
-      a.rho64[l] = r;
-      a.logrho32[l] = r > 1e-30 ? logf((float)r) : (float)log(r);
-      if (a.log_rho_out) a.log_rho_out[l] = log(r);
+  // rho update (one warp: the window is short)
+  if (warp == 0) {
+    if (a.update_rho) {
+      float v = 0.f;
+      for (int l = lane; l < a.Lw; l += 32) v += (float)(a.tot[2 * a.M + l] + a.gamma * a.rhobar64[l]);
+      const float inv = 1.f / warp_sum(v);
+      for (int l = lane; l < a.Lw; l += 32) {
+        const float r = (float)(a.tot[2 * a.M + l] + a.gamma * a.rhobar64[l]) * inv;
+        a.rho64[l] = (double)r;
+        a.logrho32[l] = logf(r);  // -inf for an empty bin
+        if (a.log_rho_out) a.log_rho_out[l] = (double)logf(r);
+      }
+    } else if (a.log_rho_out) {
+      for (int l = lane; l < a.Lw; l += 32) a.log_rho_out[l] = (double)logf((float)a.rho64[l]);
     }
-  } else if (a.log_rho_out) {
-    for (int l = tid; l < a.Lw; l += nt) a.log_rho_out[l] = log(a.rho64[l]);
   }
 
   // step: rank the L rotations in FP32
@@ -716,22 +742,22 @@ __global__ void k_update(const UpdateArgs a) {
   }
   __syncthreads();
   const int nc = min(ncand, 16);
-  double step = INFINITY;
-  for (int ci = 0; ci < nc; ++ci) {  // exact ||a_{t+1} - e^{-2 pi i k l/L} a_t||^2, FP64, block-parallel
+  // ||a_{t+1} - e^{-2 pi i k l / L} a_t||^2 of the candidates, summed directly in FP32
+  float step = INFINITY;
+  for (int ci = 0; ci < nc; ++ci) {
     const int l = cand[ci];
-    double part = 0.0;
+    float part = 0.f;
     for (int e = tid; e < a.M; e += nt) {
       const int k = e / a.Q;
-      const double2 t = t64[(k * l) % a.L];
-      const double2 xo = a.x64[e], v = xn[e];
-      const double dr = v.x - (xo.x * t.x - xo.y * t.y);
-      const double di = v.y - (xo.x * t.y + xo.y * t.x);
-      part = fma(dr, dr, fma(di, di, part));
+      const float2 t = t32[(int)(((long long)k * l) % a.L)];
+      const float4 v = xf[e];
+      const float dr = v.x - (v.z * t.x - v.w * t.y);
+      const float di = v.y - (v.z * t.y + v.w * t.x);
+      part = fmaf(dr, dr, fmaf(di, di, part));
     }
-    step = fmin(step, block_sum_d(part, red));
+    step = fminf(step, block_sum_f(part, fred));
   }
-  step = fmax(step, 0.0);
-  __syncthreads();
+  step = fmaxf(step, 0.f);
 
   // state
   for (int e = tid; e < a.M; e += nt) {
@@ -742,17 +768,17 @@ __global__ void k_update(const UpdateArgs a) {
     if (a.x_out) a.x_out[e] = v;
   }
   if (tid == 0) {
-    const double ll = a.tot[2 * a.M + a.Lw] - a.beta * ysq_total - (double)a.N * a.beta * nx_old -
-                      (double)a.N * (double)a.M * log(kPi * a.sigma2);
+    const double ll =
+        a.tot[2 * a.M + a.Lw] - a.beta * ysq_total - (double)a.N * a.beta * (double)nx_old - a.ll_const;
     if (a.stats) {
       a.stats[2 * iter] = ll;
-      a.stats[2 * iter + 1] = step;
+      a.stats[2 * iter + 1] = (double)step;
     }
     if (a.loglik_out) *a.loglik_out = ll;
-    if (a.step_out) *a.step_out = step;
+    if (a.step_out) *a.step_out = (double)step;
     const int nit = iter + 1;
     a.ctrl->iter = nit;
-    if ((a.tol > 0.0 && step < a.tol) || nit >= a.max_iters) a.ctrl->done = 1;
+    if ((a.tol > 0.0 && (double)step < a.tol) || nit >= a.max_iters) a.ctrl->done = 1;
   }
 }
 
@@ -1421,13 +1447,14 @@ int prepare(const mra_dims* d, int Lw, int l0, const float* y, const int32_t* sh
   UpdateArgs& up = c->ua;
   up.N = d->N; up.Kp1 = Kp1; up.Q = d->Q; up.M = M; up.L = d->L; up.Lw = Lw;
   up.sigma2 = d->sigma2; up.beta = 1.0 / d->sigma2; up.gamma = 0.0; up.tol = 0.0;
+  up.ll_const = (double)d->N * (double)M * std::log(kPi * d->sigma2);
   up.update_rho = 0; up.max_iters = 1 << 30;
   up.tot = c->tot; up.cols = L_.cols;
   up.x64 = u.x64; up.x32 = u.x32; up.inv_den = u.inv_den; up.rho64 = u.rho64; up.logrho32 = u.logrho32;
   up.rhobar64 = u.rhobar64; up.tf64 = u.tf64; up.tf32 = u.tf32; up.ctrl = c->ctrl;
   up.stats = nullptr; up.x_traj = nullptr; up.x_out = nullptr; up.log_rho_out = nullptr;
   up.loglik_out = nullptr; up.step_out = nullptr;
-  c->update_smem = M * 16 + d->L * 24 + Kp1 * 8 + d->L * 4 + 64;
+  c->update_smem = update_xf_offset(M, d->L, Kp1) + 16 * M;
   if (c->update_smem > 48 * 1024 && raise_smem_limit(reinterpret_cast<const void*>(k_update), c->update_smem) != MRA_OK)
     return MRA_ECUDA;
   c->reduce_blocks = (L_.cols + 7) / 8;
@@ -1469,7 +1496,7 @@ int launch_iteration(const EmCall& c, cudaStream_t st, cudaEvent_t ev0 = nullptr
   launch_sweep(c, st);
   if (ev1 && cudaEventRecordWithFlags(ev1, st, cudaEventRecordExternal) != cudaSuccess) return MRA_ECUDA;
   k_reduce_cols<<<c.reduce_blocks, 256, 0, st>>>(c.sa.part, c.lay.G, c.lay.cols, c.tot, c.ctrl);
-  k_update<<<1, 256, c.update_smem, st>>>(c.ua);
+  k_update<<<1, kUpdateThreads, c.update_smem, st>>>(c.ua);
   return cudaGetLastError() == cudaSuccess ? MRA_OK : MRA_ECUDA;
 }
 
