@@ -423,7 +423,8 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR, IPW>::kThreads, 1) k_swee
           if (valid[i]) wlw[l] += w;
           if (wo) wo[l] = w;
         }
-        if (lane == 0 && valid[i]) ll_acc += (double)vref[i] + (double)mx + (double)logf(z);
+        // one FP64 add per image (FP64 instructions are costly here); the FP32 term is exact to ~1e-7
+        if (lane == 0 && valid[i]) ll_acc += (double)(vref[i] + (mx + __logf(z)));
       }
       __syncwarp();
 
