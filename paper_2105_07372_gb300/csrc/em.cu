@@ -1734,6 +1734,8 @@ MRA_API int mra_y_split_bf16(const float* y, int64_t count, void* y_hl_out, void
 namespace mra {
 namespace {
 
+constexpr int kBatchedImagesPerCta = 64;
+
 // Sweep candidates the autotuner times, in the order of the default preference.
 const SweepSel kTuneCandidates[] = {{1, 0, 0},  {2, 16, 2}, {2, 12, 2}, {2, 8, 3},  {2, 8, 2}, {2, 4, 3},
                                     {2, 4, 2},  {3, 64, 2}, {3, 32, 2}, {3, 16, 2}, {3, 128, 1},
@@ -1905,6 +1907,13 @@ MRA_API int mra_em_run_batched(const mra_instance* inst, int32_t n, int32_t tune
     const int st = prepare(&a.dims, a.prm.Lw, a.prm.l0, static_cast<const float*>(a.y), a.shift, base + off[i],
                            off[i + 1] - off[i], &c, true, a.y_format);
     if (st != MRA_OK) return st;
+    // a small instance takes few SMs (about one persistent CTA per kBatchedImagesPerCta images),
+    // so that the sweeps of several instances run side by side
+    if (c.v2 || c.v3 || c.v4) {
+      const int cap = std::max(1, (a.dims.N + kBatchedImagesPerCta - 1) / kBatchedImagesPerCta);
+      if (cap < c.lay.G) c.lay.G = cap;
+      c.sa2.G = c.lay.G;  // the warp sweep's partial-sum stride is its launch grid
+    }
     c.su.x_in = reinterpret_cast<const double2*>(a.x_inout);
     c.su.log_rho_in = a.log_rho_inout;
     c.su.log_rho_bar = a.prm.gamma > 0.0 ? a.prm.log_rho_bar : nullptr;
@@ -1916,7 +1925,7 @@ MRA_API int mra_em_run_batched(const mra_instance* inst, int32_t n, int32_t tune
     c.ua.stats = a.stats_out;
   }
   // one graph: the instances are independent branches, forked over a few capture streams
-  const int S = std::min(n, 8);
+  const int S = std::min(n, 32);  // capture streams: concurrent instance chains
   std::vector<cudaStream_t> side(S, nullptr);
   std::vector<cudaEvent_t> join(S, nullptr);
   cudaEvent_t fork = nullptr;
