@@ -299,6 +299,15 @@ MRA_API int mra_em_step_noalloc(const mra_dims* dims, const mra_em_params* prm, 
  * (MRA_OK or MRA_ETIMEOUT), then clear it. */
 MRA_API int mra_ws_status(void* ws, void* stream);
 
+/* Self-test of the device-side failure detection (no counterpart in the paper).
+ * Launches one thread that waits on an mbarrier nothing arrives on, bounded by
+ * limit_us microseconds (the same bounded wait every streaming kernel uses, whose
+ * limit there is 2 s); when it gives up it writes MRA_ETIMEOUT, else MRA_OK.  The
+ * wait ends by itself: no fault, the context stays usable.
+ *   limit_us   1 .. 2,000,000
+ *   status_out device int32[1], written by the kernel */
+MRA_API int mra_selftest_wait_timeout(int32_t limit_us, int32_t* status_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

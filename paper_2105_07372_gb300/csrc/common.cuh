@@ -96,13 +96,16 @@ constexpr uint32_t kSuspendHintNs = 50000;  // one suspension; the time limit is
 // Wait for the phase with the given parity; false if it did not complete within kWaitLimitNs.
 // Waiting threads are suspended rather than spinning, so they take no issue slots from the
 // warps that have work.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait_bounded_ns(uint64_t* bar, uint32_t parity, unsigned long long limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = globaltimer_ns();
   while (true) {
     if (mbar_try_wait_suspend(bar, parity, kSuspendHintNs)) return true;
-    if (globaltimer_ns() - t0 > kWaitLimitNs) return false;
+    if (globaltimer_ns() - t0 > limit_ns) return false;
   }
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  return mbar_wait_bounded_ns(bar, parity, kWaitLimitNs);
 }
 // One-dimensional bulk copy global -> shared, completion counted on bar (bytes, addresses: multiples of 16).
 __device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src_gmem, uint32_t bytes, uint64_t* bar) {

@@ -2127,6 +2127,25 @@ MRA_API int mra_em_step_noalloc(const mra_dims* d, const mra_em_params* p, const
                      kNoAllocScratchBytes, stream);
 }
 
+// Self-test of the bounded waits: one thread waits on an mbarrier that nothing arrives on,
+// with a limit of limit_ns, and records MRA_ETIMEOUT when the wait gives up.
+__global__ void k_selftest_wait(unsigned long long limit_ns, int* status) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_barrier_init();
+    const bool ok = mbar_wait_bounded_ns(&bar, 0u, limit_ns);
+    *status = ok ? (int)MRA_OK : (int)MRA_ETIMEOUT;
+  }
+}
+
+MRA_API int mra_selftest_wait_timeout(int32_t limit_us, int32_t* status_out, void* stream) {
+  if (limit_us < 1 || limit_us > 2000000 || !ptr_ok(status_out, 4)) return MRA_EINVAL;
+  k_selftest_wait<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>((unsigned long long)limit_us * 1000ull,
+                                                                  reinterpret_cast<int*>(status_out));
+  return cudaGetLastError() == cudaSuccess ? MRA_OK : MRA_ECUDA;
+}
+
 MRA_API int mra_ws_status(void* ws, void* stream) {
   if (!ptr_ok(ws, 256)) return MRA_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -80,6 +80,7 @@ _SIGS = {
     "mra_fit_prior": (c_int, [c_int32, c_int32, c_int32, c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
     "mra_relerr": (c_int, [c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
     "mra_ws_status": (c_int, [c_void_p, c_void_p]),
+    "mra_selftest_wait_timeout": (c_int, [c_int32, c_void_p, c_void_p]),
 }
 
 
@@ -302,3 +303,9 @@ def mra_relerr(K, Q, x_hat, x, err_out, stream=None):
 
 def mra_ws_status(ws, stream=None) -> int:
     return int(load().mra_ws_status(_p(ws), _stream(stream)))
+
+
+def mra_selftest_wait_timeout(limit_us, status_out, stream=None):
+    """Run the bounded-wait self-test; status_out (device int32[1]) receives MRA_ETIMEOUT (-4) or MRA_OK."""
+    _check("mra_selftest_wait_timeout", load().mra_selftest_wait_timeout(int(limit_us), _p(status_out),
+                                                                         _stream(stream)))
