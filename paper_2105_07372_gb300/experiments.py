@@ -1,0 +1,148 @@
+"""Synthetic reproductions of the paper's parameter studies (Sec. 4: prior weighting,
+window width, signal prior) on one device, through the library's calls only.
+
+    gamma_study      iterations to the stopping tolerance and relative error of Synch-EM
+                     for prior weights gamma (Sec. 4, "Prior weighting")
+    bw_study         relative error of Synch-EM for window widths BW (Sec. 4,
+                     "Performance with different BW"), with a signal prior
+    signal_prior_study
+                     relative error and iterations of Synch-EM and full-search EM for the
+                     decay parameter of Gamma_a = diag((4 e^{-k/beta})^2) (Sec. 4,
+                     "Performance with signal prior"), and without a signal prior
+
+Each trial draws a fresh instance (observation model of Eq. MRA_Model_FB), runs
+Synchronize and Match, learns the window prior from one trial of Algorithm 1 on the
+same instance (its rotations are known, as in the paper's Monte-Carlo learning) and
+runs EM to tol = 1e-5 or T iterations.  The paper's BW = 2 h corresponds to the window
+Lw = BW + 1 (offsets -h .. h).  Results are means over trials.
+
+    python -m paper_2105_07372_gb300.experiments gamma|bw|prior [--n N] [--trials R]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+
+import numpy as np
+import torch
+
+from . import mra, pipeline
+
+
+def _instance(K, Q, N, L, snr, decay, seed, dev):
+    import synth  # the seeded generator of the observation model (data only)
+
+    inst = synth.make_instance(K, Q, N, L, snr, decay, seed=seed)
+    y = torch.from_numpy(synth.to_c64(inst.y)).to(dev)
+    return inst, y, torch.from_numpy(inst.s.astype(np.int32)).to(dev), torch.from_numpy(inst.x).to(dev)
+
+
+def gamma_inv(K, Q, beta, dev):
+    """Diagonal of Gamma_a^{-1} for Gamma_a = diag((4 e^{-k/beta})^2) over the stored [K+1][Q] entries."""
+    k = np.arange(K + 1, dtype=np.float64)[:, None] * np.ones((1, Q))
+    return torch.from_numpy((1.0 / (4.0 * np.exp(-k / beta)) ** 2).ravel()).to(dev)
+
+
+def synch_em_trial(y, s_true, x_true, d, *, Lw, gamma, P=100, tol=1e-5, T=1000, gamma_a_inv=None, ws=None):
+    """Synchronize and Match, one trial of Algorithm 1, Synch-EM to tol: (iterations, relative error)."""
+    if ws is None:
+        ws = pipeline.workspaces(d, Lw, P, y.device)
+    shift = pipeline.synchronize(y, d, P, ws)
+    log_prior, _, _ = pipeline.learn_prior(y, d, s_true, shift, x_true, Lw, -(Lw // 2), 0, ws)
+    x = torch.empty((d.K + 1, d.Q), dtype=torch.complex128, device=y.device)
+    mra.mra_align_mean(d, y, shift, x, ws.em)
+    log_rho = log_prior.clone()
+    prm = mra.em_params(Lw, gamma=gamma, log_rho_bar=log_prior, gamma_a_inv=gamma_a_inv, tol=tol, max_iters=T,
+                        check_every=25)
+    n = mra.mra_em_run(d, prm, y, shift, x, log_rho, None, None, ws.em)
+    return n, pipeline.relerr(x, x_true, d)
+
+
+def full_em_trial(y, x_true, d, x0, *, tol=1e-5, T=1000, gamma_a_inv=None, ws=None):
+    """Full-search EM from x0 to tol: (iterations, relative error)."""
+    if ws is None:
+        ws = mra.workspace(mra.mra_em_workspace_bytes(d, d.L), y.device)
+    x = x0.clone()
+    log_rho = torch.full((d.L,), -math.log(d.L), dtype=torch.float64, device=y.device)
+    prm = mra.em_params(d.L, l0=0, gamma=0.0, gamma_a_inv=gamma_a_inv, tol=tol, max_iters=T, check_every=25)
+    n = mra.mra_em_run(d, prm, y, None, x, log_rho, None, None, ws)
+    return n, pipeline.relerr(x, x_true, d)
+
+
+def gamma_study(snrs=(1 / 20, 1 / 50, 1 / 100), gammas=(0.0, 1.0, 10.0, 100.0), *, K=32, Q=24, N=5000, L=360,
+                BW=36, trials=3, decay=400.0, seed=6000, dev="cuda"):
+    out = []
+    Lw = BW + 1
+    for si, snr in enumerate(snrs):
+        rows = {g: [] for g in gammas}
+        for t in range(trials):
+            inst, y, s, x = _instance(K, Q, N, L, snr, decay, seed + 100 * si + t, dev)
+            d = mra.dims(N, K, Q, L, inst.sigma2)
+            ws = pipeline.workspaces(d, Lw, 100, dev)
+            for g in gammas:
+                rows[g].append(synch_em_trial(y, s, x, d, Lw=Lw, gamma=g, ws=ws))
+        for g in gammas:
+            it, err = np.mean([r[0] for r in rows[g]]), np.mean([r[1] for r in rows[g]])
+            out.append({"snr": snr, "gamma": g, "iters": float(it), "relerr": float(err)})
+    return out
+
+
+def bw_study(snrs=(1 / 20, 1 / 50), bws=(8, 16, 24, 32, 48, 64), *, K=32, Q=24, N=10000, L=360, trials=2,
+             decay=400.0, beta=8.0, gamma=100.0, seed=6500, dev="cuda"):
+    out = []
+    gi = gamma_inv(K, Q, beta, dev)
+    for si, snr in enumerate(snrs):
+        errs = {b: [] for b in bws}
+        for t in range(trials):
+            inst, y, s, x = _instance(K, Q, N, L, snr, decay, seed + 100 * si + t, dev)
+            d = mra.dims(N, K, Q, L, inst.sigma2)
+            for b in bws:
+                errs[b].append(synch_em_trial(y, s, x, d, Lw=b + 1, gamma=gamma, gamma_a_inv=gi)[1])
+        for b in bws:
+            out.append({"snr": snr, "BW": b, "relerr": float(np.mean(errs[b]))})
+    return out
+
+
+def signal_prior_study(snrs=(1 / 20, 1 / 50), betas=(None, 4.0, 8.0, 16.0), *, K=32, Q=24, N=5000, L=360, BW=36,
+                       trials=2, decay=400.0, gamma=100.0, seed=7000, dev="cuda"):
+    import synth
+
+    out = []
+    for si, snr in enumerate(snrs):
+        acc = {b: {"sem": [], "em": []} for b in betas}
+        for t in range(trials):
+            inst, y, s, x = _instance(K, Q, N, L, snr, decay, seed + 100 * si + t, dev)
+            d = mra.dims(N, K, Q, L, inst.sigma2)
+            x0 = torch.from_numpy(synth.random_init(K, Q, decay, seed=seed + 7 * t + si)).to(dev)
+            for b in betas:
+                gi = gamma_inv(K, Q, b, dev) if b is not None else None
+                acc[b]["sem"].append(synch_em_trial(y, s, x, d, Lw=BW + 1, gamma=gamma, gamma_a_inv=gi))
+                acc[b]["em"].append(full_em_trial(y, x, d, x0, gamma_a_inv=gi))
+        for b in betas:
+            for kind in ("sem", "em"):
+                r = acc[b][kind]
+                out.append({"snr": snr, "beta": b, "method": "Synch-EM" if kind == "sem" else "EM",
+                            "iters": float(np.mean([v[0] for v in r])), "relerr": float(np.mean([v[1] for v in r]))})
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("study", choices=("gamma", "bw", "prior"))
+    ap.add_argument("--n", type=int, default=None)
+    ap.add_argument("--trials", type=int, default=None)
+    a = ap.parse_args()
+    kw = {}
+    if a.n:
+        kw["N"] = a.n
+    if a.trials:
+        kw["trials"] = a.trials
+    mra.load()
+    fn = {"gamma": gamma_study, "bw": bw_study, "prior": signal_prior_study}[a.study]
+    for row in fn(**kw):
+        print(json.dumps(row), flush=True)
+
+
+if __name__ == "__main__":
+    main()
