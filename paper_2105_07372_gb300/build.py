@@ -10,7 +10,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmra.so")
-SOURCES = ["em.cu", "sync.cu", "sweep_q1.cu", "sweep_q2.cu", "sweep_q3.cu", "sweep_q4.cu"]
+# one translation unit per sweep family and row width, so that they compile in parallel
+SOURCES = ["em.cu", "sync.cu"] + [f"sweep_v{v}_q{q}.cu" for v in (2, 3, 4) for q in (1, 2, 3, 4)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden", "--expt-relaxed-constexpr"]
 
@@ -49,7 +50,7 @@ def build_library(force: bool = False, verbose: bool = False, extra: list[str] |
             print(r.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+    with cf.ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + ".tmp"
     cmd = [cc, *ARCH, "-shared", *objs, "-o", tmp]

@@ -198,11 +198,13 @@ struct SweepV2Launch {
   void (*fn)(const SweepV2Args);
   int threads;
 };
-// ipw: images each warp carries at once (2 only for windows of at most one unit chunk).
-SweepV2Launch sweep_v2_q1(int MR, int ipw);
-SweepV2Launch sweep_v2_q2(int MR, int ipw);
-SweepV2Launch sweep_v2_q3(int MR, int ipw);
-SweepV2Launch sweep_v2_q4(int MR, int ipw);
+// ipw: images each warp carries at once (only 1 is built); lwc: for a window of one unit
+// chunk, lane-strided passes over it fixed at compile time (1 for Lw <= 32, 2 for Lw <= 64),
+// else 0 (any window).
+SweepV2Launch sweep_v2_q1(int MR, int ipw, int lwc);
+SweepV2Launch sweep_v2_q2(int MR, int ipw, int lwc);
+SweepV2Launch sweep_v2_q3(int MR, int ipw, int lwc);
+SweepV2Launch sweep_v2_q4(int MR, int ipw, int lwc);
 
 // Arguments of the CTA-cooperative sweep (sweep3_impl.cuh), launched with kV3Threads threads.
 constexpr int kV3Threads = 512;

@@ -1004,8 +1004,9 @@ bool plan_v2(int Kp1, int Q, int L, int Lw, int nup, int max_smem, V2Plan* p) {
   const int slot = al16(M * 8);
   const int sp = (Lw + 3) & ~3;
   for (int ipw = 1; ipw >= 1; --ipw) {  // two images per warp measured slower (fewer resident warps)
-    SweepV2Launch ln = QV == 1 ? sweep_v2_q1(MR, ipw) : QV == 2 ? sweep_v2_q2(MR, ipw)
-                     : QV == 3 ? sweep_v2_q3(MR, ipw) : sweep_v2_q4(MR, ipw);
+    const int lwc = nup != kUnitChunk ? 0 : Lw <= 32 ? 1 : Lw <= 64 ? 2 : 0;  // one unit chunk: fixed loops
+    SweepV2Launch ln = QV == 1 ? sweep_v2_q1(MR, ipw, lwc) : QV == 2 ? sweep_v2_q2(MR, ipw, lwc)
+                     : QV == 3 ? sweep_v2_q3(MR, ipw, lwc) : sweep_v2_q4(MR, ipw, lwc);
     if (!ln.fn) continue;
     const int maxw = ln.threads / 32;
     for (int nw = maxw; nw * 2 * ipw >= maxw && nw >= 1; --nw) {

@@ -41,7 +41,10 @@ __device__ __forceinline__ int mod_small(int a, int L, float invL) {
   return m;
 }
 
-template <int QV, int MR, int IPW>
+// LWC: lane-strided passes over the window (ceil(Lw / 32)) fixed at compile time (1 or 2) for a
+// window of one unit chunk (the unit table is then 4 kUC wide), or 0 for any window; the fixed
+// counts let the per-image loops over the window and its units unroll.
+template <int QV, int MR, int IPW, int LWC>
 __global__ void __launch_bounds__(SweepV2Shape<QV, MR, IPW>::kThreads, 1) k_sweep_v2(const SweepV2Args a) {
   extern __shared__ __align__(128) unsigned char smem[];
   constexpr int NT = SweepV2Shape<QV, MR, IPW>::kThreads;
@@ -50,7 +53,20 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR, IPW>::kThreads, 1) k_swee
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nwarps = a.nwarps;  // <= NT/32 (warps beyond it only join the final combination)
   const int r = lane >> 2, j = lane & 3;
-  const int Kp1 = a.Kp1, L = a.L, Lw = a.Lw, NU = a.NU, NUP = a.NUP, M = a.M;
+  const int Kp1 = a.Kp1, L = a.L, Lw = a.Lw, NU = a.NU, M = a.M;
+  const int NUP = LWC > 0 ? 4 * kUC : a.NUP;
+  // f(l) for this lane's window indices l = lane, lane + 32, ...
+  auto for_window = [&](auto&& f) {
+    if constexpr (LWC > 0) {
+#pragma unroll
+      for (int t = 0; t < LWC; ++t) {
+        const int l = lane + 32 * t;
+        if (l < Lw) f(l);
+      }
+    } else {
+      for (int l = lane; l < Lw; l += 32) f(l);
+    }
+  };
   const float invL = 1.0f / (float)L;
   constexpr int row4 = QV * 4;  // float4 per row
 
@@ -334,10 +350,10 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR, IPW>::kThreads, 1) k_swee
         __syncwarp();
         float bv = -INFINITY;
         int bl = 0x7fffffff;
-        for (int l = lane; l < Lw; l += 32) {
+        for_window([&](int l) {
           const float v = sb[l];
           if (v > bv) bv = v, bl = l;
-        }
+        });
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
           const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
@@ -406,23 +422,23 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR, IPW>::kThreads, 1) k_swee
       for (int i = 0; i < IPW; ++i) {
         float* sb = sbuf0 + i * a.sp;
         float mx = -INFINITY;
-        for (int l = lane; l < Lw; l += 32) mx = fmaxf(mx, sb[l]);
+        for_window([&](int l) { mx = fmaxf(mx, sb[l]); });
         mx = warp_max(mx);
         float z = 0.f;
-        for (int l = lane; l < Lw; l += 32) {
+        for_window([&](int l) {
           const float e = expf(sb[l] - mx);
           sb[l] = e;
           z += e;
-        }
+        });
         z = warp_sum(z);
         const float inv = 1.f / z;
         float* wo = (a.w_out && valid[i]) ? a.w_out + (size_t)img[i] * Lw : nullptr;
-        for (int l = lane; l < Lw; l += 32) {
+        for_window([&](int l) {
           const float w = sb[l] * inv;
           sb[l] = w;
           if (valid[i]) wlw[l] += w;
           if (wo) wo[l] = w;
-        }
+        });
         // one FP64 add per image (FP64 instructions are costly here); the FP32 term is exact to ~1e-7
         if (lane == 0 && valid[i]) ll_acc += (double)(vref[i] + (mx + __logf(z)));
       }
@@ -556,23 +572,25 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR, IPW>::kThreads, 1) k_swee
 }  // namespace mra
 
 // Instantiation table for one row width QV: MR = 1..7 rows per quad, one image per warp
-// (two images per warp measured slower and are not built).
-#define MRA_SWEEP_V2_CASE(QV, MR)                                                                        \
-  case MR:                                                                                               \
-    return ipw == 1 ? SweepV2Launch{k_sweep_v2<QV, MR, 1>, SweepV2Shape<QV, MR, 1>::kThreads}             \
-                    : SweepV2Launch{nullptr, 0};
-#define MRA_SWEEP_V2_TABLE(QV)                     \
-  namespace mra {                                 \
-  SweepV2Launch sweep_v2_q##QV(int MR, int ipw) { \
-    switch (MR) {                                  \
-      MRA_SWEEP_V2_CASE(QV, 1)                     \
-      MRA_SWEEP_V2_CASE(QV, 2)                     \
-      MRA_SWEEP_V2_CASE(QV, 3)                     \
-      MRA_SWEEP_V2_CASE(QV, 4)                     \
-      MRA_SWEEP_V2_CASE(QV, 5)                     \
-      MRA_SWEEP_V2_CASE(QV, 6)                     \
-      MRA_SWEEP_V2_CASE(QV, 7)                     \
-      default: return {nullptr, 0};                \
-    }                                              \
-  }                                                \
+// (two images per warp measured slower and are not built), window passes lwc = 1, 2 or any (0).
+#define MRA_SWEEP_V2_CASE(QV, MR)                                                                       \
+  case MR:                                                                                              \
+    if (ipw != 1) return SweepV2Launch{nullptr, 0};                                                     \
+    return lwc == 1 ? SweepV2Launch{k_sweep_v2<QV, MR, 1, 1>, SweepV2Shape<QV, MR, 1>::kThreads}        \
+         : lwc == 2 ? SweepV2Launch{k_sweep_v2<QV, MR, 1, 2>, SweepV2Shape<QV, MR, 1>::kThreads}        \
+                    : SweepV2Launch{k_sweep_v2<QV, MR, 1, 0>, SweepV2Shape<QV, MR, 1>::kThreads};
+#define MRA_SWEEP_V2_TABLE(QV)                              \
+  namespace mra {                                          \
+  SweepV2Launch sweep_v2_q##QV(int MR, int ipw, int lwc) { \
+    switch (MR) {                                          \
+      MRA_SWEEP_V2_CASE(QV, 1)                             \
+      MRA_SWEEP_V2_CASE(QV, 2)                             \
+      MRA_SWEEP_V2_CASE(QV, 3)                             \
+      MRA_SWEEP_V2_CASE(QV, 4)                             \
+      MRA_SWEEP_V2_CASE(QV, 5)                             \
+      MRA_SWEEP_V2_CASE(QV, 6)                             \
+      MRA_SWEEP_V2_CASE(QV, 7)                             \
+      default: return {nullptr, 0};                        \
+    }                                                      \
+  }                                                        \
   }
