@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR, IPW>::kThreads, 1) k_swee
         float cr[IPW], ci[IPW];
 #pragma unroll
         for (int i = 0; i < IPW; ++i) cr[i] = 0.f, ci[i] = 0.f;
-        if (k < Kp1) {
+        if (m < MR - 1 || k < Kp1) {  // rows of all groups but the last exist
 #pragma unroll
           for (int u = 0; u < QV; ++u) {
             const int pidx = k * row4 + j + 4 * u;
@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR, IPW>::kThreads, 1) k_swee
 #pragma unroll
         for (int m = 0; m < MR; ++m) {
           const int k = r + 8 * m;
-          if (k < Kp1) {
+          if (m < MR - 1 || k < Kp1) {  // rows of all groups but the last exist
             const float2* trow = tus + k * NUP + u0 + j;
 #pragma unroll
             for (int t = 0; t < kUC; ++t) {
@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR, IPW>::kThreads, 1) k_swee
 #pragma unroll
         for (int m = 0; m < MR; ++m) {
           const int k = r + 8 * m;
-          if (k < Kp1) {
+          if (m < MR - 1 || k < Kp1) {  // rows of all groups but the last exist
             const float2 tv = tus[k * NUP + um.x];
             pa = fmaf(c[0][m].x, tv.x, pa);
             pb = fmaf(c[0][m].y, tv.y, pb);
@@ -468,7 +468,7 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR, IPW>::kThreads, 1) k_swee
 #pragma unroll
         for (int m = 0; m < MR; ++m) {
           const int k = r + 8 * m;
-          if (k < Kp1) {
+          if (m < MR - 1 || k < Kp1) {  // rows of all groups but the last exist
             const float2* trow = tus + k * NUP + u0 + j;
 #pragma unroll
             for (int t = 0; t < kUC; ++t) {
@@ -507,7 +507,7 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR, IPW>::kThreads, 1) k_swee
 #pragma unroll
     for (int m = 0; m < MR; ++m) {
       const int k = r + 8 * m;
-      if (k < Kp1) {
+      if (m < MR - 1 || k < Kp1) {  // rows of all groups but the last exist
 #pragma unroll
         for (int i = 0; i < IPW; ++i) {
           if (!valid[i]) continue;
@@ -539,7 +539,7 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR, IPW>::kThreads, 1) k_swee
 #pragma unroll
   for (int m = 0; m < MR; ++m) {
     const int k = r + 8 * m;
-    if (k < Kp1) {
+    if (m < MR - 1 || k < Kp1) {  // rows of all groups but the last exist
 #pragma unroll
       for (int u = 0; u < QV; ++u) red4[(size_t)warp * half + k * row4 + j + 4 * u] = acc[m][u];
     }
