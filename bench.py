@@ -119,6 +119,29 @@ class Clocks:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "error": str(e)[:80]}
 
 
+# ------------------------------------------------------------------ replicas across ranks (no data-path collective)
+def replica_seed(rank: int) -> int:
+    """Each rank draws its own independent instance (replicas, weak scaling)."""
+    return 1000 * CFG + rank
+
+
+def max_over_ranks(values, world: int, device):
+    """Elementwise maximum of per-rank timings (one all-reduce of a few floats; no-op at world 1)."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def whole_job_value(world: int, units_per_rank: float, ms: float) -> float:
+    """Units all ranks processed per second, against the slowest rank's time."""
+    return world * units_per_rank / (ms / 1e3)
+
+
 # ------------------------------------------------------------------ CPU oracle (baseline and reference arm)
 def oracle_sample(inst, c, n_img, iters):
     import oracle as O
@@ -197,7 +220,7 @@ def main():
     mra.load()
 
     # ---- inputs resident in HBM (each rank its own independent instance: replicas)
-    inst = synth.make_instance(c["K"], c["Q"], c["N"], c["L"], c["snr"], c["decay"], seed=1000 * CFG + rank)
+    inst = synth.make_instance(c["K"], c["Q"], c["N"], c["L"], c["snr"], c["decay"], seed=replica_seed(rank))
     y_host = torch.from_numpy(synth.to_c64(inst.y)).pin_memory()
     y = y_host.to(dev)
     s_true = torch.from_numpy(inst.s.astype(np.int32)).to(dev)
@@ -260,13 +283,9 @@ def main():
             step(True)
         e1.record(stream)
         barrier()
-    ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks([e0.elapsed_time(e1) / args.steps], world, dev)[0]
     evals_per_step = N * Lw * T
-    value = world * evals_per_step / (ms / 1e3)
+    value = whole_job_value(world, evals_per_step, ms)
 
     # ---- roofline of the dominant kernel (the EM sweep): algorithmic bytes = one read of y
     bytes_per_sweep = N * (K + 1) * Q * 8
@@ -305,8 +324,8 @@ def main():
         e2e_step()
     e1.record(stream)
     barrier()
-    e2e_ms = e0.elapsed_time(e1) / args.steps
-    e2e = {"value": world * evals_per_step / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+    e2e_ms = max_over_ranks([e0.elapsed_time(e1) / args.steps], world, dev)[0]
+    e2e = {"value": whole_job_value(world, evals_per_step, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms}
 
     relerr_final = pipeline.relerr(x, x_true, d)
