@@ -29,6 +29,12 @@ Readings of the paper taken here (each also listed in the design notes):
 
 * Window: ``Lw`` grid offsets l0, l0+1, .., l0+Lw-1 (mod L) with l0 = -floor(Lw/2)
   by default; the paper's [-BW/2, BW/2] is Lw = BW + 1 points.
+* Denser-resolution window (Sec. 3.3): the window's angles are
+  theta_i = 2 pi step (l0 + i) / L with 0 < step <= 1, so Lw rotations cover Lw step
+  grid units.  The paper's example, the range [-pi BW/L, pi BW/L] at spacing
+  pi BW/L^2, is Lw = 2 L + 1, l0 = -L, step = BW / (2 L).  Alignment shifts stay
+  on the grid; the stopping rule still minimises over the L grid rotations.  The
+  learned histogram gives each window angle the value of the nearest grid bin.
 * Sign of the synchronization matrix: the pairwise argmin of
   Eq. (relative_angle_2d_dist) estimates theta_j - theta_i under the model's
   sign, so the matrix whose leading eigenvector has phases theta_i is
@@ -85,10 +91,17 @@ def grid_angle(l, L: int):
     return TWO_PI * np.asarray(l, dtype=np.float64) / L
 
 
-def window_offsets(L: int, Lw: int, l0: int | None = None) -> np.ndarray:
+def window_offsets(L: int, Lw: int, l0: int | None = None, step: float = 1.0) -> np.ndarray:
+    """Window positions in grid units (l0 + i) * step, i = 0..Lw-1 (Sec. 3.3).
+
+    step = 1 is the grid window of the reduced search space; step < 1 is the
+    denser-resolution variant (Sec. 3.3): Lw angles step grid units apart, so the
+    same number of rotations covers a narrower range at a finer resolution.
+    """
     if l0 is None:
         l0 = -(Lw // 2)
-    return l0 + np.arange(Lw)
+    o = l0 + np.arange(Lw)
+    return o if step == 1.0 else o * float(step)
 
 
 def align(y: np.ndarray, shifts: np.ndarray, L: int) -> np.ndarray:
@@ -156,12 +169,13 @@ def step_size(x_new: np.ndarray, x_old: np.ndarray, L: int) -> float:
 
 
 def em_step(y, x, log_rho, L, sigma2, Lw=None, l0=None, gamma=0.0, log_rho_bar=None,
-            gamma_a_inv=None, update_rho=True, shifts=None) -> EMStep:
+            gamma_a_inv=None, update_rho=True, shifts=None, step=1.0) -> EMStep:
     """One iteration of Algorithm Synch-EM (E-step, W_t, a-update, rho-update, step).
 
     y: [N, K+1, Q] observations; ``shifts`` (grid indices) align them first
     (v~_j = v_j e^{+i k theta_hat_j}); x = a_t; log_rho = log rho_t on the window.
     gamma_a_inv: diagonal of Gamma_a^{-1} as [K+1, Q] (None = flat image prior).
+    step: spacing of the window's rotations in grid units (window_offsets).
     """
     y = np.asarray(y, dtype=np.complex128)
     x = np.asarray(x, dtype=np.complex128)
@@ -169,7 +183,7 @@ def em_step(y, x, log_rho, L, sigma2, Lw=None, l0=None, gamma=0.0, log_rho_bar=N
     M = Kp1 * Q
     if Lw is None:
         Lw = np.asarray(log_rho).size
-    offs = window_offsets(L, Lw, l0)
+    offs = window_offsets(L, Lw, l0, step)
     yt = y if shifts is None else align(y, np.asarray(shifts), L)
     # E-step and normalisation
     w, _, lse = posterior(x, yt, log_rho, L, offs, sigma2)
@@ -196,7 +210,7 @@ def em_step(y, x, log_rho, L, sigma2, Lw=None, l0=None, gamma=0.0, log_rho_bar=N
 
 
 def map_objective(y, x, log_rho, L, sigma2, Lw=None, l0=None, gamma=0.0, log_rho_bar=None,
-                  gamma_a_inv=None, shifts=None) -> float:
+                  gamma_a_inv=None, shifts=None, step=1.0) -> float:
     """log p(v|a,rho) + log p(a) + log p(rho) up to constants (Sec. 2.2, Sec. 3.2.2).
 
     log p(a) = -a^H Gamma_a^{-1} a, log p(rho) = -gamma D_KL(rho_bar, rho) = gamma sum rho_bar log rho + const.
@@ -205,7 +219,7 @@ def map_objective(y, x, log_rho, L, sigma2, Lw=None, l0=None, gamma=0.0, log_rho
     N, Kp1, Q = y.shape
     if Lw is None:
         Lw = np.asarray(log_rho).size
-    offs = window_offsets(L, Lw, l0)
+    offs = window_offsets(L, Lw, l0, step)
     yt = y if shifts is None else align(y, np.asarray(shifts), L)
     _, _, lse = posterior(x, yt, log_rho, L, offs, sigma2)
     val = marginal_loglik(lse, Kp1 * Q, sigma2)
@@ -368,18 +382,21 @@ def fit_kappa(mean_cos: float) -> float:
     return float(optimize.brentq(lambda k: vm_ratio(k) - mean_cos, 0.0, hi, xtol=1e-13, rtol=1e-14, maxiter=500))
 
 
-def fit_prior(counts: np.ndarray, L: int, Lw: int, l0: int | None = None, kind: int = 0):
+def fit_prior(counts: np.ndarray, L: int, Lw: int, l0: int | None = None, kind: int = 0, step: float = 1.0):
     """rho_bar (Algorithm 1, pooled over trials) restricted to the window and renormalised.
 
-    kind 0: the learned histogram itself.  kind 1: von Mises fit
-    log rho_bar[l] = kappa cos theta_l - log Z on the window, kappa from A(kappa) = sum_l rho_bar[l] cos(2 pi l/L).
+    kind 0: the learned histogram itself; a window position u (grid units, non-integer
+    for step < 1) takes the value of the grid bin nearest to it, floor(u + 1/2) mod L.
+    kind 1: von Mises fit log rho_bar[l] = kappa cos theta_l - log Z on the window,
+    kappa from A(kappa) = sum_l rho_bar[l] cos(2 pi l/L).
     Returns (log_rho_bar [Lw], kappa).
     """
     counts = np.asarray(counts, dtype=np.float64)
     rho_bar = counts / counts.sum()
-    offs = window_offsets(L, Lw, l0)
+    offs = window_offsets(L, Lw, l0, step)
     if kind == 0:
-        v = rho_bar[np.mod(offs, L)]
+        bins = np.mod(np.floor(np.asarray(offs, dtype=np.float64) + 0.5).astype(np.int64), L)
+        v = rho_bar[bins]
         v = v / v.sum()
         with np.errstate(divide="ignore"):
             return np.log(v), 0.0
@@ -392,33 +409,34 @@ def fit_prior(counts: np.ndarray, L: int, Lw: int, l0: int | None = None, kind: 
 # ----------------------------------------------------------------------------
 # marginal log-likelihood and its gradient (Fisher identity)
 # ----------------------------------------------------------------------------
-def vm_log_rho(logits: np.ndarray, kappa: float, L: int, l0: int | None = None) -> np.ndarray:
+def vm_log_rho(logits: np.ndarray, kappa: float, L: int, l0: int | None = None, step: float = 1.0) -> np.ndarray:
     """log rho_l = kappa cos theta_l + eta_l - log sum_win exp(kappa cos theta + eta)."""
     Lw = np.asarray(logits).size
-    t = kappa * np.cos(grid_angle(window_offsets(L, Lw, l0), L)) + np.asarray(logits, dtype=np.float64)
+    t = kappa * np.cos(grid_angle(window_offsets(L, Lw, l0, step), L)) + np.asarray(logits, dtype=np.float64)
     return t - _logsumexp(t, axis=0)
 
 
-def loglik(y, x, logits, kappa, L, sigma2, l0=None, shifts=None) -> float:
+def loglik(y, x, logits, kappa, L, sigma2, l0=None, shifts=None, step=1.0) -> float:
     y = np.asarray(y, dtype=np.complex128)
     N, Kp1, Q = y.shape
     Lw = np.asarray(logits).size
-    offs = window_offsets(L, Lw, l0)
+    offs = window_offsets(L, Lw, l0, step)
     yt = y if shifts is None else align(y, np.asarray(shifts), L)
-    _, _, lse = posterior(np.asarray(x, dtype=np.complex128), yt, vm_log_rho(logits, kappa, L, l0), L, offs, sigma2)
+    _, _, lse = posterior(np.asarray(x, dtype=np.complex128), yt, vm_log_rho(logits, kappa, L, l0, step), L, offs,
+                          sigma2)
     return marginal_loglik(lse, Kp1 * Q, sigma2)
 
 
-def loglik_grad(y, x, logits, kappa, L, sigma2, l0=None, shifts=None):
+def loglik_grad(y, x, logits, kappa, L, sigma2, l0=None, shifts=None, step=1.0):
     """(loglik, dx, dlogits, dkappa).  dx = dl/dRe x + i dl/dIm x = (2/sigma^2)(num - N x),
     dl/deta_l = W[l] - N rho_l, dl/dkappa = sum_l (W[l] - N rho_l) cos theta_l."""
     y = np.asarray(y, dtype=np.complex128)
     x = np.asarray(x, dtype=np.complex128)
     N, Kp1, Q = y.shape
     Lw = np.asarray(logits).size
-    offs = window_offsets(L, Lw, l0)
+    offs = window_offsets(L, Lw, l0, step)
     yt = y if shifts is None else align(y, np.asarray(shifts), L)
-    lr = vm_log_rho(logits, kappa, L, l0)
+    lr = vm_log_rho(logits, kappa, L, l0, step)
     w, _, lse = posterior(x, yt, lr, L, offs, sigma2)
     W = w.sum(axis=0)
     back = np.exp(1j * np.outer(grid_angle(offs, L), kbar(Kp1 - 1)))

@@ -50,16 +50,17 @@ def _dist2_loops(x, v, theta):
     return s
 
 
-@pytest.mark.parametrize("Lw,l0", [(5, -2), (3, -1), (4, 0)])
-def test_posterior_and_loglik_by_joint_enumeration(Lw, l0):
-    """Enumerate all Lw^N joint rotations: marginals equal w_jl, log-sum equals the log-likelihood."""
+@pytest.mark.parametrize("Lw,l0,step", [(5, -2, 1.0), (3, -1, 1.0), (4, 0, 1.0), (5, -2, 0.37), (4, -3, 0.5)])
+def test_posterior_and_loglik_by_joint_enumeration(Lw, l0, step):
+    """Enumerate all Lw^N joint rotations: marginals equal w_jl, log-sum equals the log-likelihood.
+    step < 1: the denser window's angles 2 pi step (l0 + i) / L, off the grid."""
     inst = tiny(seed=3)
     L, N, sigma2 = inst.L, inst.N, inst.sigma2
     x = synth.make_signal(inst.K, inst.Q, 4.0, np.random.default_rng(9))
     rng = np.random.default_rng(5)
     rho = rng.random(Lw) + 0.1
     rho /= rho.sum()
-    offs = [l0 + i for i in range(Lw)]
+    offs = [(l0 + i) * step for i in range(Lw)]
     M = (inst.K + 1) * inst.Q
     logp = {}
     for combo in itertools.product(range(Lw), repeat=N):
@@ -75,7 +76,7 @@ def test_posterior_and_loglik_by_joint_enumeration(Lw, l0):
         p = math.exp(v - mx) / Z
         for j, li in enumerate(combo):
             marg[j, li] += p
-    st = O.em_step(inst.y, x, np.log(rho), L, sigma2, Lw=Lw, l0=l0)
+    st = O.em_step(inst.y, x, np.log(rho), L, sigma2, Lw=Lw, l0=l0, step=step)
     np.testing.assert_allclose(st.w, marg, atol=1e-12)
     assert abs(st.loglik - (mx + math.log(Z))) < 1e-9 * abs(st.loglik)
 
@@ -92,8 +93,8 @@ def _Q(a, w, y, log_rho, offs, L, sigma2, gamma_a_inv):
     return val
 
 
-@pytest.mark.parametrize("with_prior", [False, True])
-def test_mstep_maximises_Q(with_prior):
+@pytest.mark.parametrize("with_prior,step", [(False, 1.0), (True, 1.0), (False, 0.45)])
+def test_mstep_maximises_Q(with_prior, step):
     inst = tiny(seed=11, N=4, L=6)
     L, sigma2 = inst.L, inst.sigma2
     Lw, l0 = 4, -2
@@ -103,8 +104,8 @@ def test_mstep_maximises_Q(with_prior):
     if with_prior:
         k = np.arange(inst.K + 1)[:, None] * np.ones((1, inst.Q))
         gi = 1.0 / (4.0 * np.exp(-k / 8.0)) ** 2
-    st = O.em_step(inst.y, x, lr, L, sigma2, Lw=Lw, l0=l0, gamma_a_inv=gi)
-    offs = O.window_offsets(L, Lw, l0)
+    st = O.em_step(inst.y, x, lr, L, sigma2, Lw=Lw, l0=l0, gamma_a_inv=gi, step=step)
+    offs = [(l0 + i) * step for i in range(Lw)]
     q0 = _Q(st.x, st.w, inst.y, lr, offs, L, sigma2, gi)
     rng = np.random.default_rng(4)
     h = 1e-5
@@ -390,3 +391,107 @@ def test_step_is_zero_for_grid_rotation():
     L = 40
     assert O.step_size(O.rotate(x, 2 * np.pi * 13 / L), x, L) < 1e-26
     assert O.step_size(x + 0.1, x, L) > 0
+
+
+# --------------------------------------------------------------------------- denser-resolution window (Sec. 3.3)
+@pytest.mark.parametrize("m", [2, 3, 4])
+def test_dense_window_on_grid_points_equals_grid_window(m):
+    """A window of step 1/m whose prior is zero off the grid points is the grid window:
+    same weights there (zero elsewhere), same a_{t+1}, likelihood and rho_{t+1}."""
+    inst = synth.make_instance(K=4, Q=3, N=40, L=30, sigma2=soft(0.4, 4, 3), decay=6.0, seed=31)
+    L, sigma2 = inst.L, inst.sigma2
+    Lw, l0 = 7, -3
+    rng = np.random.default_rng(8)
+    x = synth.make_signal(inst.K, inst.Q, 6.0, np.random.default_rng(6))
+    rho = rng.random(Lw) + 0.2
+    rho /= rho.sum()
+    rb = rng.random(Lw) + 0.1
+    rb /= rb.sum()
+    g = O.em_step(inst.y, x, np.log(rho), L, sigma2, Lw=Lw, l0=l0, gamma=3.0, log_rho_bar=np.log(rb),
+                  shifts=inst.s)
+    Lwd = m * (Lw - 1) + 1
+    lrd = np.full(Lwd, -np.inf)
+    lrd[::m] = np.log(rho)
+    lrbd = np.full(Lwd, -np.inf)
+    lrbd[::m] = np.log(rb)
+    d = O.em_step(inst.y, x, lrd, L, sigma2, Lw=Lwd, l0=m * l0, gamma=3.0, log_rho_bar=lrbd, shifts=inst.s,
+                  step=1.0 / m)
+    tol = 1e-12
+    np.testing.assert_allclose(d.w[:, ::m], g.w, atol=tol)
+    off = np.ones(Lwd, dtype=bool)
+    off[::m] = False
+    assert np.all(d.w[:, off] == 0.0)
+    assert np.max(np.abs(d.x - g.x)) <= tol * np.max(np.abs(g.x))
+    assert abs(d.loglik - g.loglik) <= tol * abs(g.loglik)
+    np.testing.assert_allclose(np.exp(d.log_rho[::m]), np.exp(g.log_rho), atol=tol)
+    assert abs(d.step - g.step) <= tol * max(1.0, g.step)
+
+
+def test_dense_window_noise_free_recovers_off_grid_rotations():
+    """Images rotated by off-grid angles of the window and nearly noise free: each posterior is one-hot at its
+    angle and the M-step returns the signal (the rotation is undone exactly at non-grid angles)."""
+    K, Q, L, N = 6, 4, 36, 30
+    Lw, l0, step = 21, -10, 0.3
+    rng = np.random.default_rng(13)
+    x = synth.make_signal(K, Q, 8.0, np.random.default_rng(14))
+    idx = rng.integers(0, Lw, N)
+    ang = 2 * math.pi * step * (l0 + idx) / L
+    y = np.stack([x * np.exp(-1j * np.arange(K + 1) * a)[:, None] for a in ang])
+    sigma2 = 1e-5 * float(np.sum(np.abs(x) ** 2))
+    st = O.em_step(y, x, np.log(np.full(Lw, 1.0 / Lw)), L, sigma2, Lw=Lw, l0=l0, step=step)
+    np.testing.assert_allclose(st.w, np.eye(Lw)[idx], atol=1e-12)
+    assert np.max(np.abs(st.x - x)) < 1e-12 * np.max(np.abs(x))
+    np.testing.assert_allclose(st.W, np.bincount(idx, minlength=Lw), atol=1e-10)
+
+
+@pytest.mark.parametrize("kappa,l0", [(0.7, 0), (3.0, -80), (9.0, 17)])
+def test_dense_von_mises_normaliser_is_bessel(kappa, l0):
+    """n equally spaced angles around the whole circle (Lw step = L): sum exp(kappa cos theta) = n I0(kappa) up to
+    aliasing terms 2 n I_n(kappa), below 1e-100 here; the window prior is kappa cos theta - log(n I0(kappa))."""
+    from scipy import special
+
+    L, step = 40, 0.25
+    n = int(L / step)
+    lr = O.vm_log_rho(np.zeros(n), kappa, L, l0=l0, step=step)
+    th = 2 * math.pi * step * (l0 + np.arange(n)) / L
+    np.testing.assert_allclose(lr, kappa * np.cos(th) - math.log(n * special.i0(kappa)), atol=1e-12)
+
+
+def test_dense_histogram_prior_takes_nearest_grid_bin():
+    """Counts 3 : 1 in bins 0 and 1 of L = 12; window positions -2 .. 2 grid units at step 1/4.
+    floor(u + 1/2) puts [-1/2, 1/2) in bin 0 and [1/2, 3/2) in bin 1: four positions each, the
+    others empty, so the window prior is 3/16 on the first four and 1/16 on the next four."""
+    counts = np.zeros(12, dtype=np.int64)
+    counts[0], counts[1] = 3, 1
+    lp, _ = O.fit_prior(counts, 12, 17, l0=-8, kind=0, step=0.25)
+    want = np.zeros(17)
+    want[6:10] = 3 / 16   # u = -0.5, -0.25, 0, 0.25
+    want[10:14] = 1 / 16  # u = 0.5, 0.75, 1, 1.25
+    np.testing.assert_allclose(np.exp(lp), want, atol=1e-15)
+    # step 1 reads the grid bins themselves
+    lp1, _ = O.fit_prior(counts, 12, 5, l0=-2, kind=0)
+    np.testing.assert_allclose(np.exp(lp1), [0, 0, 0.75, 0.25, 0], atol=1e-15)
+
+
+def test_dense_loglik_gradient_central_differences():
+    inst = synth.make_instance(K=3, Q=2, N=20, L=24, sigma2=soft(0.5, 3, 2), decay=6.0, seed=19)
+    L, Lw, l0, step = inst.L, 9, -4, 0.6
+    rng = np.random.default_rng(2)
+    x = synth.random_init(inst.K, inst.Q, 6.0, seed=5)
+    eta = 0.3 * rng.standard_normal(Lw)
+    kappa = 1.5
+    kw = dict(l0=l0, step=step)
+    ll, dx, de, dk = O.loglik_grad(inst.y, x, eta, kappa, L, inst.sigma2, **kw)
+    h = 1e-6
+    for k in range(inst.K + 1):
+        for q in range(inst.Q):
+            for part, unit in ((0, 1.0), (1, 1j)):
+                e = np.zeros_like(x)
+                e[k, q] = unit * h
+                g = (O.loglik(inst.y, x + e, eta, kappa, L, inst.sigma2, **kw)
+                     - O.loglik(inst.y, x - e, eta, kappa, L, inst.sigma2, **kw)) / (2 * h)
+                an = dx[k, q].real if part == 0 else dx[k, q].imag
+                assert abs(g - an) <= 1e-6 * max(1.0, abs(an))
+    g = (O.loglik(inst.y, x, eta, kappa + h, L, inst.sigma2, **kw)
+         - O.loglik(inst.y, x, eta, kappa - h, L, inst.sigma2, **kw)) / (2 * h)
+    assert abs(g - dk) <= 1e-6 * max(1.0, abs(dk))
