@@ -23,7 +23,13 @@
  * Window.  The EM searches the Lw offsets l0, l0+1, ..., l0+Lw-1 (mod L)
  *   around the synchronized estimate (Sec. 3.3); the paper's band [-BW/2,
  *   BW/2] is Lw = BW + 1, l0 = -BW/2.  Arrays over the window are [Lw], index i
- *   meaning offset l0 + i.
+ *   meaning offset l0 + i, the rotation theta_i = 2 pi step (l0 + i) / L.
+ *   step = 1 is the grid; 0 < step < 1 is the denser-resolution window of
+ *   Sec. 3.3 (the same number of rotations over a narrower range): its angles
+ *   lie off the grid, it must span less than the circle ((Lw - 1) step < L,
+ *   Lw <= 65536, |l0| <= 2^24) and Lw may exceed L.  The paper's example range
+ *   [-pi BW/L, pi BW/L] at spacing pi BW/L^2 is Lw = 2 L + 1, l0 = -L,
+ *   step = BW / (2 L).  Alignment shifts and the stopping rule stay on the grid.
  * Alignment.  Where an entry point takes shift (device int32 [N] or NULL),
  *   image j is used as y_j o exp(+2 pi i k shift[j] / L) (the alignment step
  *   before Eq. synch_initialization), folded into the kernels; y is never
@@ -75,8 +81,8 @@ typedef struct {
 
 /* Parameters of Algorithm Synch-EM (inputs L, rho_bar, BW, gamma, Gamma_a, tol, T). */
 typedef struct {
-  int32_t Lw;                /* window size, 1 <= Lw <= L */
-  int32_t l0;                /* first window offset (any integer; taken mod L) */
+  int32_t Lw;                /* window size, 1 <= Lw <= L on the grid (see Window above for step < 1) */
+  int32_t l0;                /* first window offset (|l0| <= 2^30; taken mod L on the grid) */
   double gamma;              /* prior weight gamma >= 0 of p(rho) ~ exp(-gamma KL(rho_bar, rho)) */
   const double* log_rho_bar; /* device [Lw] log rho_bar on the window (-inf allowed); may be NULL if gamma == 0 */
   const double* gamma_a_inv; /* device [(K+1)*Q] diagonal of Gamma_a^{-1} (>= 0), or NULL for a flat image prior */
@@ -87,6 +93,8 @@ typedef struct {
   float* sweep_ms;           /* mra_em_run: host [max_iters] device time (ms) of each iteration's sweep over y,
                                 from CUDA events recorded around the sweep kernel; NULL = not timed.  When set,
                                 the run synchronizes after every graph launch. */
+  double step;               /* spacing of the window's rotations in grid units, 0 < step <= 1 (0 is read as 1,
+                                the grid): theta_i = 2 pi step (l0 + i) / L (Sec. 3.3, denser resolution) */
 } mra_em_params;
 
 MRA_API const char* mra_status_string(int status);
@@ -202,7 +210,8 @@ MRA_API int mra_em_run_batched(const mra_instance* inst, int32_t n, int32_t tune
 
 /* Marginal log-likelihood over the window and its gradient (Fisher identity),
  *   l(x, kappa, eta) = sum_j log sum_l rho_l (pi sigma2)^{-M} exp(-||x o e^{-i k theta_l} - y_j||^2 / sigma2),
- *   log rho_l = kappa cos(theta_l) + eta_l - log sum_win exp(kappa cos theta + eta),  theta_l = 2 pi (l0+l)/L.
+ *   log rho_l = kappa cos(theta_l) + eta_l - log sum_win exp(kappa cos theta + eta),
+ *   theta_l = 2 pi step (l0+l)/L (step as in mra_em_params; 0 is read as 1).
  * The posterior is recomputed in one pass over y (never stored).
  *   x       [K+1][Q] complex double
  *   logits  [Lw] double eta (window logits)
@@ -210,9 +219,10 @@ MRA_API int mra_em_run_batched(const mra_instance* inst, int32_t n, int32_t tune
  *   dx_out  [K+1][Q] complex double dl/dRe x + i dl/dIm x = (2/sigma2)(sum_j sum_l w_jl e^{+i k theta_l} y_j - N x), or NULL
  *   dlogits_out [Lw] double dl/deta_l = W_l - N rho_l, or NULL
  *   dkappa_out  [1] double sum_l (W_l - N rho_l) cos theta_l, or NULL */
-MRA_API int mra_loglik_grad(const mra_dims* dims, int32_t Lw, int32_t l0, const float* y, const int32_t* shift,
-                            const double* x, const double* logits, double kappa, double* loglik_out, double* dx_out,
-                            double* dlogits_out, double* dkappa_out, void* ws, size_t ws_bytes, void* stream);
+MRA_API int mra_loglik_grad(const mra_dims* dims, int32_t Lw, int32_t l0, double step, const float* y,
+                            const int32_t* shift, const double* x, const double* logits, double kappa,
+                            double* loglik_out, double* dx_out, double* dlogits_out, double* dkappa_out, void* ws,
+                            size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------ synchronization */
 
@@ -261,12 +271,14 @@ MRA_API int mra_prior_hist(const mra_dims* dims, const float* y, const int32_t* 
                            const double* x_true, int32_t* hist_inout, int32_t* center_out, void* ws, size_t ws_bytes,
                            void* stream);
 
-/* rho_bar from pooled residual counts (Algorithm 1, averaged over trials), on the window.
- *   kind 0: log_prior_out[i] = log(rho_bar[(l0+i) mod L] / sum over the window)   (the learned histogram)
+/* rho_bar from pooled residual counts (Algorithm 1, averaged over trials), on the window of
+ * positions u_i = step (l0 + i) grid units (step as in mra_em_params; 0 is read as 1).
+ *   kind 0: log_prior_out[i] = log(rho_bar[b_i] / sum over the window), b_i = floor(u_i + 1/2) mod L,
+ *           the grid bin nearest to u_i ((l0+i) mod L on the grid)   (the learned histogram)
  *   kind 1: von Mises fit, kappa solving I1(kappa)/I0(kappa) = sum_s rho_bar[s] cos(2 pi s/L)
- *           (0 if that mean is <= 0), log_prior_out[i] = kappa cos(2 pi (l0+i)/L) - log Z
+ *           (0 if that mean is <= 0), log_prior_out[i] = kappa cos(2 pi u_i / L) - log Z
  *   counts [L] int32, log_prior_out [Lw] double, kappa_out [1] double or NULL. */
-MRA_API int mra_fit_prior(int32_t L, int32_t Lw, int32_t l0, const int32_t* counts, int32_t kind,
+MRA_API int mra_fit_prior(int32_t L, int32_t Lw, int32_t l0, double step, const int32_t* counts, int32_t kind,
                           double* log_prior_out, double* kappa_out, void* stream);
 
 /* Relative error up to rotation (Sec. 2.2): min over continuous theta of

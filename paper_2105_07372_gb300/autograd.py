@@ -17,30 +17,31 @@ from . import mra
 
 class MarginalLogLik(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, x, eta, kappa, y, shift, d, Lw, l0, ws):
+    def forward(ctx, x, eta, kappa, y, shift, d, Lw, l0, ws, step):
         ll = torch.empty(1, dtype=torch.float64, device=y.device)
         mra.mra_loglik_grad(d, Lw, l0, y, shift, x.detach().contiguous(), eta.detach().contiguous(),
-                            float(kappa.detach().item()), ll, None, None, None, ws)
+                            float(kappa.detach().item()), ll, None, None, None, ws, step=step)
         ctx.save_for_backward(x, eta, kappa)
-        ctx.extra = (y, shift, d, Lw, l0, ws)
+        ctx.extra = (y, shift, d, Lw, l0, ws, step)
         return ll[0]
 
     @staticmethod
     def backward(ctx, g):
         x, eta, kappa = ctx.saved_tensors
-        y, shift, d, Lw, l0, ws = ctx.extra
+        y, shift, d, Lw, l0, ws, step = ctx.extra
         ll = torch.empty(1, dtype=torch.float64, device=y.device)
         dx = torch.empty_like(x)
         de = torch.empty_like(eta)
         dk = torch.empty(1, dtype=torch.float64, device=y.device)
         mra.mra_loglik_grad(d, Lw, l0, y, shift, x.detach().contiguous(), eta.detach().contiguous(),
-                            float(kappa.detach().item()), ll, dx, de, dk, ws)
-        return g * dx, g * de, (g * dk).reshape(kappa.shape), None, None, None, None, None, None
+                            float(kappa.detach().item()), ll, dx, de, dk, ws, step=step)
+        return g * dx, g * de, (g * dk).reshape(kappa.shape), None, None, None, None, None, None, None
 
 
-def marginal_loglik(x, eta, kappa, y, d, Lw, l0=None, shift=None, ws=None):
+def marginal_loglik(x, eta, kappa, y, d, Lw, l0=None, shift=None, ws=None, step=1.0):
+    """step: spacing of the window's rotations in grid units (theta_l = 2 pi step (l0 + l) / L)."""
     if l0 is None:
         l0 = -(Lw // 2)
     if ws is None:
         ws = mra.workspace(mra.mra_em_workspace_bytes(d, Lw), y.device)
-    return MarginalLogLik.apply(x, eta, kappa, y, shift, d, Lw, l0, ws)
+    return MarginalLogLik.apply(x, eta, kappa, y, shift, d, Lw, l0, ws, float(step))

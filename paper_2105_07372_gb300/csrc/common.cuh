@@ -27,6 +27,8 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 __device__ __forceinline__ float2 cmul_conj_b(float2 a, float2 b) {  // a * conj(b)
   return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
 }
+// e^{-i t sgn(dr)} from a distance-unit table entry (cos t - 1, -sin t) taken at |dr|.
+__device__ __forceinline__ float2 td_rot(float2 t, int dr) { return make_float2(1.f + t.x, dr >= 0 ? t.y : -t.y); }
 __device__ __forceinline__ double2 zmul(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
@@ -136,7 +138,7 @@ struct EmLayout {
   int kp4;      // K+1 rounded up to a multiple of 4 (rows of the table)
   int cols;     // 2M + Lw + 2 reduced columns
   int nup;      // mirror units padded to a multiple of kUnitChunk
-  size_t ctrl, tf32, tf64, tw, x32, x64, inv_den, logrho32, rho64, rhobar64, units, tu, td, part, tot, total;
+  size_t ctrl, tf32, tf64, tw, tw64, x32, x64, inv_den, logrho32, rho64, rhobar64, units, tu, td, part, tot, total;
 };
 
 __host__ __device__ inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
@@ -158,6 +160,7 @@ inline EmLayout em_layout(int N, int K, int Q, int L, int Lw, int G) {
   l.tf32 = o;      o = align256(o + sizeof(float2) * L);
   l.tf64 = o;      o = align256(o + sizeof(double2) * L);
   l.tw = o;        o = align256(o + sizeof(float2) * (size_t)l.kp4 * l.twp);
+  l.tw64 = o;      o = align256(o + sizeof(double2) * (size_t)l.kp4 * l.twp);
   l.x32 = o;       o = align256(o + sizeof(float2) * l.M);
   l.x64 = o;       o = align256(o + sizeof(double2) * l.M);
   l.inv_den = o;   o = align256(o + sizeof(double) * l.M);
@@ -181,12 +184,18 @@ struct SweepV2Args {
   int nwarps;      // active warps per CTA
   int slot_bytes;  // bytes per ring slot
   int sp;          // per-warp row pitch (floats) of the s/w and W[l] buffers
-  int off_ring, off_x, off_tu, off_tf, off_lr, off_units, off_lmap, off_s, off_wl;
+  int off_ring, off_x, off_tu, off_tf, off_lr, off_units, off_s, off_wl;
   float two_beta;
   int align_only;  // 1: weights are 1 at offset 0 (align and average)
+  int wrap;        // 1: the window is the whole grid circle (Lw == L), distances wrap
+  int l0m;         // l0 mod L (grid windows)
+  int nd;          // distance units in td: L/2 + 1 when wrapping, else Lw
   const float2* x32;
   const float2* tu;    // [Kp1][NUP] e^{-i k theta} of each mirror unit's first offset
   const int2* units;   // [NUP] window indices (a, b), b = -1 for a unit without mirror
+  const float2* td;    // [Kp1][nd] (cos t - 1, -sin t), t = 2 pi k d step / L (global)
+  const float2* tw;    // dense window only (else null): [Kp1][twp] e^{-i k theta_{l0+i}} (global)
+  int twp;
   const float2* tf32;
   const float* logrho32;
   double* part;
@@ -219,13 +228,16 @@ struct SweepV3Args {
   int wrap;        // 1: the window is the whole circle (Lw == L), indices wrap
   int r0, d1;      // first reference (window index) and the distance pass 1 covers
   int fsplit;      // threads per forward item (1 or 2)
-  int phase0;      // (l0 + r0) mod L
+  int phase0;      // (l0 + r0) mod L on the grid; 0 for a dense window (the reference's
+                   // rotation is then the window twiddle tw[k][r0])
   int off_ring, off_x, off_xr, off_td, off_tf, off_lr, off_c, off_s, off_w2, off_info, off_wl;
   float two_beta;
   double two_beta_d;
   const float2* x32;
-  const float2* td;  // [Kp1][nd] (cos 2 pi k d / L - 1, -sin 2 pi k d / L)
+  const float2* td;  // [Kp1][nd] (cos t - 1, -sin t), t = 2 pi k d step / L
   const float2* tf32;
+  const float2* tw;  // dense window only (else null): [Kp1][twp] e^{-i k theta_{l0+i}}
+  int twp;
   const float* logrho32;
   double* part;
   float* w_out;
@@ -253,6 +265,8 @@ struct SweepV4Args {
   const float2* x32;
   const float2* td;
   const float2* tf32;
+  const float2* tw;  // as in SweepV3Args
+  int twp;
   const float* logrho32;
   double* part;
   float* w_out;
@@ -272,15 +286,23 @@ SweepV4Launch sweep_v4_q3(int MR, int cpsm);
 SweepV4Launch sweep_v4_q4(int MR, int cpsm);
 
 // Mirror units of a window: offsets o and -o (mod L) share cos/sin.  Writes the
-// (a, b) index pairs in window order of a; returns the number of units.
-__host__ __device__ inline int window_units(int L, int Lw, int l0, int2* out) {
+// (a, b) index pairs in window order of a; returns the number of units.  A dense window
+// (angles step != 1 grid units apart) pairs positions l0 + i and -(l0 + i) without the
+// modular wrap, which holds only on the grid.
+__host__ __device__ inline int window_units(int L, int Lw, int l0, bool dense, int2* out) {
   int nu = 0;
   for (int i = 0; i < Lw; ++i) {
-    int off = (l0 + i) % L;
-    if (off < 0) off += L;
-    const int moff = (L - off) % L;
-    int im = (moff - l0) % L;
-    if (im < 0) im += L;
+    int im;
+    if (dense) {
+      im = -2 * l0 - i;
+      if (im < 0) im = Lw;  // no mirror
+    } else {
+      int off = (l0 + i) % L;
+      if (off < 0) off += L;
+      const int moff = (L - off) % L;
+      im = (moff - l0) % L;
+      if (im < 0) im += L;
+    }
     if (im < Lw && im != i) {
       if (im < i) continue;  // covered by the unit of its mirror
       if (out) out[nu] = make_int2(i, im);
@@ -291,6 +313,17 @@ __host__ __device__ inline int window_units(int L, int Lw, int l0, int2* out) {
   }
   return nu;
 }
+// A window of Lw rotations 2 pi step (l0 + i) / L: on the grid (step 1) 1 <= Lw <= L; a dense
+// window has 0 < step < 1 and spans less than the circle, (Lw - 1) step < L, so that no two of
+// its rotations coincide.
+inline bool window_ok(int L, int Lw, int l0, double step) {
+  if (L < 1 || Lw < 1 || l0 < -(1 << 30) || l0 > (1 << 30)) return false;
+  if (step == 1.0) return Lw <= L;
+  if (!(step > 0.0 && step < 1.0)) return false;
+  if (Lw > (1 << 16) || l0 < -(1 << 24) || l0 > (1 << 24)) return false;
+  return (double)(Lw - 1) * step < (double)L;
+}
+
 // Device properties cached per device.
 struct DevInfo {
   int sms;

@@ -82,6 +82,8 @@ int sweep_grid() {
 struct SetupArgs {
   int N, Kp1, Q, M, L, Lw, l0, twp, kp4;
   double sigma2;
+  double step;  // spacing of the window's rotations in grid units (1 = the grid)
+  int dense;    // step != 1: window angles 2 pi step (l0 + i) / L off the grid
   const double2* x_in;
   const double* log_rho_in;   // may be null (loglik mode)
   const double* log_rho_bar;  // may be null
@@ -89,6 +91,7 @@ struct SetupArgs {
   float2* tf32;
   double2* tf64;
   float2* tw;
+  double2* tw64;  // the window twiddles in FP64 (tile sweep)
   float2* x32;
   double2* x64;
   double* inv_den;
@@ -138,26 +141,38 @@ __global__ void k_setup(const SetupArgs a) {
   }
 }
 
-// Window twiddles Tw[k][i] = e^{-i k theta_{l0+i}} = T[(k (l0+i)) mod L], zero padded to [kp4][twp].
+// e^{-i k theta} at window position pos of a dense window, theta = 2 pi step pos / L (FP64).
+__device__ inline double2 dense_twiddle(int k, int pos, double step, int L) {
+  double s, c;
+  sincospi(2.0 * step * (double)((long long)k * pos) / (double)L, &s, &c);
+  return make_double2(c, -s);
+}
+
+// Window twiddles Tw[k][i] = e^{-i k theta_{l0+i}}, zero padded to [kp4][twp], in FP32 and FP64:
+// T[(k (l0+i)) mod L] on the grid, the FP64 angle for a dense window.
 __global__ void k_setup_tw(const SetupArgs a) {
   const int n = a.kp4 * a.twp;
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
     const int k = idx / a.twp, i = idx - k * a.twp;
-    float2 v = make_float2(0.f, 0.f);
+    double2 v = make_double2(0.0, 0.0);
     if (k < a.Kp1 && i < a.Lw) {
-      int off = (a.l0 + i) % a.L;
-      if (off < 0) off += a.L;
-      const int m = (int)(((long long)k * off) % a.L);
-      v = a.tf32[m];
+      if (a.dense) {
+        v = dense_twiddle(k, a.l0 + i, a.step, a.L);
+      } else {
+        int off = (a.l0 + i) % a.L;
+        if (off < 0) off += a.L;
+        v = a.tf64[(int)(((long long)k * off) % a.L)];
+      }
     }
-    a.tw[idx] = v;
+    a.tw[idx] = make_float2((float)v.x, (float)v.y);
+    a.tw64[idx] = v;
   }
 }
 
 // Mirror units of the window (one thread: integer bookkeeping over Lw entries).
 __global__ void k_setup_units(const SetupArgs a) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    const int nu = window_units(a.L, a.Lw, a.l0, a.units);
+    const int nu = window_units(a.L, a.Lw, a.l0, a.dense != 0, a.units);
     for (int u = nu; u < a.nup; ++u) a.units[u] = make_int2(0, -1);
   }
 }
@@ -169,36 +184,45 @@ __global__ void k_setup_tu(const SetupArgs a) {
     const int k = idx / a.nup, u = idx - k * a.nup;
     float2 v = make_float2(0.f, 0.f);
     if (u < a.nu) {
-      int off = (a.l0 + a.units[u].x) % a.L;
-      if (off < 0) off += a.L;
-      v = a.tf32[(int)(((long long)k * off) % a.L)];
+      if (a.dense) {
+        const double2 t = dense_twiddle(k, a.l0 + a.units[u].x, a.step, a.L);
+        v = make_float2((float)t.x, (float)t.y);
+      } else {
+        int off = (a.l0 + a.units[u].x) % a.L;
+        if (off < 0) off += a.L;
+        v = a.tf32[(int)(((long long)k * off) % a.L)];
+      }
     }
     a.tu[idx] = v;
   }
 }
 
-// Distance-unit table of the batch sweep: (cos t - 1, -sin t), t = 2 pi k d / L, with
+// Distance-unit table of the batch sweep: (cos t - 1, -sin t), t = 2 pi k d step / L, with
 // cos t - 1 = -2 sin^2(t / 2) so that small angles keep their relative precision (FP64).
 __global__ void k_setup_td(const SetupArgs a) {
   const int n = a.Kp1 * a.nd;
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
     const int k = idx / a.nd, d = idx - k * a.nd;
-    const int m = (int)(((long long)k * d) % a.L);
+    // t / (2 pi): reduced exactly on the grid
+    const double h = a.dense ? a.step * (double)((long long)k * d) / (double)a.L
+                             : (double)(int)(((long long)k * d) % a.L) / (double)a.L;
     double sh, ch, s, c;
-    sincospi((double)m / (double)a.L, &sh, &ch);
-    sincospi(2.0 * (double)m / (double)a.L, &s, &c);
+    sincospi(h, &sh, &ch);
+    sincospi(2.0 * h, &s, &c);
     a.td[idx] = make_float2((float)(-2.0 * sh * sh), (float)(-s));
   }
 }
 
-// log rho_l = kappa cos theta_l + eta_l - log sum exp(...) over the window (one CTA, FP64).
-__global__ void k_setup_vm(int L, int Lw, int l0, double kappa, const double* eta, double* rho64, float* logrho32) {
+// log rho_l = kappa cos theta_l + eta_l - log sum exp(...) over the window (one CTA, FP64),
+// theta_l = 2 pi step (l0 + l) / L.
+__global__ void k_setup_vm(int L, int Lw, int l0, double step, double kappa, const double* eta, double* rho64,
+                           float* logrho32) {
   __shared__ double red[32];
   __shared__ double bc;
   const int tid = threadIdx.x;
   double mx = -INFINITY;
   for (int i = tid; i < Lw; i += blockDim.x) {
-    const double t = kappa * cospi(2.0 * (double)(l0 + i) / (double)L) + eta[i];
+    const double t = kappa * cospi(2.0 * step * (double)(l0 + i) / (double)L) + eta[i];
     mx = fmax(mx, t);
   }
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -212,7 +236,7 @@ __global__ void k_setup_vm(int L, int Lw, int l0, double kappa, const double* et
   __syncthreads();
   const double m = bc;
   double s = 0.0;
-  for (int i = tid; i < Lw; i += blockDim.x) s += exp(kappa * cospi(2.0 * (double)(l0 + i) / (double)L) + eta[i] - m);
+  for (int i = tid; i < Lw; i += blockDim.x) s += exp(kappa * cospi(2.0 * step * (double)(l0 + i) / (double)L) + eta[i] - m);
   s = warp_sum_d(s);
   __syncthreads();
   if ((tid & 31) == 0) red[tid >> 5] = s;
@@ -225,7 +249,7 @@ __global__ void k_setup_vm(int L, int Lw, int l0, double kappa, const double* et
   __syncthreads();
   const double lz = bc;
   for (int i = tid; i < Lw; i += blockDim.x) {
-    const double lr = kappa * cospi(2.0 * (double)(l0 + i) / (double)L) + eta[i] - lz;
+    const double lr = kappa * cospi(2.0 * step * (double)(l0 + i) / (double)L) + eta[i] - lz;
     rho64[i] = exp(lr);
     logrho32[i] = (float)lr;
   }
@@ -239,10 +263,12 @@ struct SweepArgs {
   int slot_bytes;  // bytes per image slot in shared memory
   int cp;          // row pitch (complex) of the c and W tiles
   int sp;          // row pitch (floats) of the s / w tile
-  int off_ybuf, off_x, off_tw, off_tf, off_c, off_s, off_w, off_wl, off_lr;
+  int off_ybuf, off_x, off_tw, off_tf, off_c, off_s, off_s64, off_w, off_wl, off_lr;
   float two_beta;
+  double two_beta_d;
   const float2* x32;
   const float2* tw;
+  const double2* tw64;
   const float2* tf32;
   const float* logrho32;
   double* part;  // [cols][G]
@@ -269,6 +295,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1) k_em_sweep(const SweepArgs a
   float2* tfs = reinterpret_cast<float2*>(smem + a.off_tf);
   float2* cs = reinterpret_cast<float2*>(smem + a.off_c);
   float* ss = reinterpret_cast<float*>(smem + a.off_s);
+  double* ss64 = reinterpret_cast<double*>(smem + a.off_s64);
   float2* wsm = reinterpret_cast<float2*>(smem + a.off_w);
   float* wl = reinterpret_cast<float*>(smem + a.off_wl);
   float* lrs = reinterpret_cast<float*>(smem + a.off_lr);
@@ -402,29 +429,32 @@ __global__ void __launch_bounds__(kSweepThreads, 1) k_em_sweep(const SweepArgs a
     }
     __syncthreads();
 
-    // ---- P2: s_jl = log rho_l + 2 beta Re sum_k c_jk Tw[k][l], four window offsets per item
+    // ---- P2: s_jl = log rho_l + 2 beta Re sum_k c_jk Tw[k][l], four window offsets per item, in FP64
+    // with the FP64 twiddles: this general fallback sweep has no peak-relative pass, and FP32
+    // rounding of sums of size 2 beta |c| would move the weights by more than 1e-5
     {
       int b = tid % B, lq = tid / B;
       for (int i = tid; i < B * nlq; i += NT) {
         if (b < nb) {
-          float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+          double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
           const float2* cr = cs + b * a.cp;
-          const float2* tcol = tws + 4 * lq;
+          const double2* tcol = a.tw64 + 4 * lq;
           for (int k = 0; k < Kp1; ++k) {
-            const float2 c = cr[k];
-            const float4 t01 = *reinterpret_cast<const float4*>(tcol + k * a.twp);
-            const float4 t23 = *reinterpret_cast<const float4*>(tcol + k * a.twp + 2);
-            s0 = fmaf(c.x, t01.x, s0); s0 = fmaf(-c.y, t01.y, s0);
-            s1 = fmaf(c.x, t01.z, s1); s1 = fmaf(-c.y, t01.w, s1);
-            s2 = fmaf(c.x, t23.x, s2); s2 = fmaf(-c.y, t23.y, s2);
-            s3 = fmaf(c.x, t23.z, s3); s3 = fmaf(-c.y, t23.w, s3);
+            const float2 cf = cr[k];
+            const double cx = (double)cf.x, cy = (double)cf.y;
+            const double2 t0 = tcol[k * a.twp], t1 = tcol[k * a.twp + 1];
+            const double2 t2 = tcol[k * a.twp + 2], t3 = tcol[k * a.twp + 3];
+            s0 = fma(cx, t0.x, s0); s0 = fma(-cy, t0.y, s0);
+            s1 = fma(cx, t1.x, s1); s1 = fma(-cy, t1.y, s1);
+            s2 = fma(cx, t2.x, s2); s2 = fma(-cy, t2.y, s2);
+            s3 = fma(cx, t3.x, s3); s3 = fma(-cy, t3.y, s3);
           }
-          float* srow = ss + b * a.sp;
+          double* srow = ss64 + b * a.sp;
           const int l = 4 * lq;
-          srow[l] = fmaf(a.two_beta, s0, lrs[l]);
-          if (l + 1 < Lw) srow[l + 1] = fmaf(a.two_beta, s1, lrs[l + 1]);
-          if (l + 2 < Lw) srow[l + 2] = fmaf(a.two_beta, s2, lrs[l + 2]);
-          if (l + 3 < Lw) srow[l + 3] = fmaf(a.two_beta, s3, lrs[l + 3]);
+          srow[l] = fma(a.two_beta_d, s0, (double)lrs[l]);
+          if (l + 1 < Lw) srow[l + 1] = fma(a.two_beta_d, s1, (double)lrs[l + 1]);
+          if (l + 2 < Lw) srow[l + 2] = fma(a.two_beta_d, s2, (double)lrs[l + 2]);
+          if (l + 3 < Lw) srow[l + 3] = fma(a.two_beta_d, s3, (double)lrs[l + 3]);
         }
         b += dB;
         lq += dK;
@@ -436,12 +466,13 @@ __global__ void __launch_bounds__(kSweepThreads, 1) k_em_sweep(const SweepArgs a
     // ---- P3: normalise over the window (one warp per image)
     for (int b = warp; b < nb; b += kSweepWarps) {
       float* srow = ss + b * a.sp;
-      float m = -INFINITY;
-      for (int l = lane; l < Lw; l += 32) m = fmaxf(m, srow[l]);
-      m = warp_max(m);
+      const double* s64 = ss64 + b * a.sp;
+      double m = -INFINITY;
+      for (int l = lane; l < Lw; l += 32) m = fmax(m, s64[l]);
+      for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
       float z = 0.f;
       for (int l = lane; l < Lw; l += 32) {
-        const float e = expf(srow[l] - m);
+        const float e = expf((float)(s64[l] - m));
         srow[l] = e;
         z += e;
       }
@@ -455,7 +486,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1) k_em_sweep(const SweepArgs a
         wlw[l] += w;
         if (wo) wo[l] = w;
       }
-      if (lane == 0) ll_acc += (double)m + (double)logf(z);
+      if (lane == 0) ll_acc += m + (double)logf(z);
     }
     __syncthreads();
 
@@ -792,6 +823,7 @@ __global__ void k_export(int M, int Lw, const double2* x64, const double* rho64,
 
 struct GradArgs {
   int N, M, L, Lw, l0;
+  double step;
   double sigma2, beta, kappa;
   const double* tot;
   int cols;
@@ -818,7 +850,7 @@ __global__ void k_grad(const GradArgs a) {
   for (int l = tid; l < a.Lw; l += nt) {
     const double g = a.tot[2 * a.M + l] - (double)a.N * a.rho64[l];
     if (a.dlogits_out) a.dlogits_out[l] = g;
-    dk += g * cospi(2.0 * (double)(a.l0 + l) / (double)a.L);
+    dk += g * cospi(2.0 * a.step * (double)(a.l0 + l) / (double)a.L);
   }
   dk = block_sum_d(dk, red);
   if (tid == 0) {
@@ -951,7 +983,7 @@ namespace {
 
 struct SweepPlan {
   int B, slot_bytes, cp, sp, smem;
-  int off_ybuf, off_x, off_tw, off_tf, off_c, off_s, off_w, off_wl, off_lr;
+  int off_ybuf, off_x, off_tw, off_tf, off_c, off_s, off_s64, off_w, off_wl, off_lr;
 };
 
 inline int al16(int v) { return (v + 15) & ~15; }
@@ -972,6 +1004,7 @@ bool plan_sweep(int Kp1, int Q, int L, int Lw, int max_smem, SweepPlan* p) {
     p->off_tf = o; o += al16(L * 8);
     p->off_c = o; o += al16(B * cp * 8);
     p->off_s = o; o += al16(B * sp * 4);
+    p->off_s64 = o; o += al16(B * sp * 8);
     p->off_w = o; o += al16(B * cp * 8);
     p->off_wl = o; o += al16(kSweepWarps * Lw * 4);
     p->off_lr = o; o += al16(Lw * 4);
@@ -990,7 +1023,7 @@ bool plan_sweep(int Kp1, int Q, int L, int Lw, int max_smem, SweepPlan* p) {
 struct V2Plan {
   SweepV2Launch launch;
   int nwarps, slot_bytes, sp, smem;
-  int off_ring, off_x, off_tu, off_tf, off_lr, off_units, off_lmap, off_s, off_wl;
+  int off_ring, off_x, off_tu, off_tf, off_lr, off_units, off_s, off_wl;
 };
 
 // Shared-memory plan of the warp-streaming sweep: each warp carries ipw images
@@ -1017,7 +1050,6 @@ bool plan_v2(int Kp1, int Q, int L, int Lw, int nup, int max_smem, V2Plan* p) {
       p->off_tf = o; o += al16(L * 8);
       p->off_lr = o; o += al16(Lw * 4);
       p->off_units = o; o += al16(nup * 8);
-      p->off_lmap = o; o += al16(Lw * 8);
       p->off_s = o; o += al16(maxw * ipw * sp * 4);
       p->off_wl = o; o += al16(maxw * sp * 4);
       if (o + 1024 <= max_smem) {
@@ -1043,7 +1075,8 @@ struct V3Plan {
 // (16, 2), (12, 2), (8, 3), (8, 2), (4, 3), (4, 2) whose ring and tables fit.  Per-image pitches
 // are odd (in words of their element type) so that the images of one warp fall in
 // distinct banks.
-bool plan_v3(int Kp1, int Q, int L, int Lw, int l0, int yf, int want_bi, int want_ns, int max_smem, V3Plan* p) {
+bool plan_v3(int Kp1, int Q, int L, int Lw, int l0, bool dense, int yf, int want_bi, int want_ns, int max_smem,
+             V3Plan* p) {
   if (Q % 8 != 0) return false;
   const int QH = Q / 2;
   if (Kp1 * (QH / 2) > kV3Threads) return false;
@@ -1051,14 +1084,14 @@ bool plan_v3(int Kp1, int Q, int L, int Lw, int l0, int yf, int want_bi, int wan
   int words = (M * 8 + 15) / 16;
   if (words % 2 == 0) ++words;
   const int slot = words * 16;
-  p->wrap = Lw == L ? 1 : 0;
+  p->wrap = !dense && Lw == L ? 1 : 0;
   p->nd = p->wrap ? L / 2 + 1 : Lw;
-  int r0 = (-l0) % L;
-  if (r0 < 0) r0 += L;
-  if (r0 >= Lw) r0 = Lw / 2;  // rotation 0 outside the window: start from its centre
+  int r0 = dense ? -l0 : (-l0) % L;  // the window index of rotation 0
+  if (r0 < 0) r0 += dense ? Lw : L;
+  if (r0 >= Lw || r0 < 0) r0 = Lw / 2;  // rotation 0 outside the window: start from its centre
   p->r0 = r0;
   p->d1 = p->wrap ? L / 2 : std::max(r0, Lw - 1 - r0);
-  p->phase0 = ((l0 + r0) % L + L) % L;
+  p->phase0 = dense ? 0 : ((l0 + r0) % L + L) % L;
   const int cp = Kp1 | 1, sp = Lw | 1, dp = p->nd | 1;
   const int cfg[6][2] = {{16, 2}, {12, 2}, {8, 3}, {8, 2}, {4, 3}, {4, 2}};
   for (const auto& bn : cfg) {
@@ -1102,19 +1135,19 @@ struct V4Plan {
 // Shared-memory plan of the chunked two-read sweep for one launch shape: one slot per
 // warp and the largest chunk of 128, 64, 32 or 16 images (or want_c) whose transform
 // buffers fit in max_smem.
-bool plan_v4_shape(int Kp1, int Q, int L, int Lw, int l0, int want_c, int max_smem, const SweepV4Launch& ln,
-                   V4Plan* p) {
+bool plan_v4_shape(int Kp1, int Q, int L, int Lw, int l0, bool dense, int want_c, int max_smem,
+                   const SweepV4Launch& ln, V4Plan* p) {
   const int NW = ln.threads / 32;
   const int M = Kp1 * Q;
   const int slot = al16(M * 8);
-  p->wrap = Lw == L ? 1 : 0;
+  p->wrap = !dense && Lw == L ? 1 : 0;
   p->nd = p->wrap ? L / 2 + 1 : Lw;
-  int r0 = (-l0) % L;
-  if (r0 < 0) r0 += L;
-  if (r0 >= Lw) r0 = Lw / 2;
+  int r0 = dense ? -l0 : (-l0) % L;  // the window index of rotation 0
+  if (r0 < 0) r0 += dense ? Lw : L;
+  if (r0 >= Lw || r0 < 0) r0 = Lw / 2;
   p->r0 = r0;
   p->d1 = p->wrap ? L / 2 : std::max(r0, Lw - 1 - r0);
-  p->phase0 = ((l0 + r0) % L + L) % L;
+  p->phase0 = dense ? 0 : ((l0 + r0) % L + L) % L;
   const int cp = Kp1 | 1, sp = Lw | 1, dp = p->nd | 1;
   for (int lc = 7; lc >= 4; --lc) {
     const int c = 1 << lc;
@@ -1144,7 +1177,8 @@ bool plan_v4_shape(int Kp1, int Q, int L, int Lw, int l0, int want_c, int max_sm
 
 // Two CTAs per SM (each with half the shared memory, so that one can stream while the
 // other transforms) where the plan fits, else one; want_cpsm fixes the choice.
-bool plan_v4(int Kp1, int Q, int L, int Lw, int l0, int want_c, int want_cpsm, const DevInfo& di, V4Plan* p) {
+bool plan_v4(int Kp1, int Q, int L, int Lw, int l0, bool dense, int want_c, int want_cpsm, const DevInfo& di,
+             V4Plan* p) {
   if (Q % 8 != 0 || Q / 8 > 4) return false;
   const int QV = Q / 8, MR = (Kp1 + 7) / 8;
   if (MR > 7) return false;
@@ -1154,7 +1188,7 @@ bool plan_v4(int Kp1, int Q, int L, int Lw, int l0, int want_c, int want_cpsm, c
                            : QV == 3 ? sweep_v4_q3(MR, cpsm) : sweep_v4_q4(MR, cpsm);
     if (!ln.fn) continue;
     const int max_smem = std::min(di.max_smem_optin, di.smem_per_sm / cpsm - 1024);
-    if (plan_v4_shape(Kp1, Q, L, Lw, l0, want_c, max_smem, ln, p)) {
+    if (plan_v4_shape(Kp1, Q, L, Lw, l0, dense, want_c, max_smem, ln, p)) {
       p->grid = di.sms * cpsm;
       return true;
     }
@@ -1187,18 +1221,21 @@ SweepSel env_sweep() {
 // ---- autotuner cache: the fastest sweep measured for a problem shape on a device
 struct TuneKey {
   int dev, Kp1, Q, L, Lw, l0, yfmt;
+  double step;
   bool operator<(const TuneKey& o) const {
     const int a[7] = {dev, Kp1, Q, L, Lw, l0, yfmt}, b[7] = {o.dev, o.Kp1, o.Q, o.L, o.Lw, o.l0, o.yfmt};
-    return std::lexicographical_compare(a, a + 7, b, b + 7);
+    if (std::lexicographical_compare(a, a + 7, b, b + 7)) return true;
+    if (std::lexicographical_compare(b, b + 7, a, a + 7)) return false;
+    return step < o.step;
   }
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, SweepSel> g_tune;
 
-TuneKey tune_key(const mra_dims* d, int Lw, int l0, int yfmt) {
+TuneKey tune_key(const mra_dims* d, int Lw, int l0, double step, int yfmt) {
   int dev = 0;
   cudaGetDevice(&dev);
-  return TuneKey{dev, d->K + 1, d->Q, d->L, Lw, l0, yfmt};
+  return TuneKey{dev, d->K + 1, d->Q, d->L, Lw, l0, yfmt, step};
 }
 bool tune_lookup(const TuneKey& k, SweepSel* out) {
   std::lock_guard<std::mutex> g(g_tune_mu);
@@ -1273,11 +1310,13 @@ struct EmCall {
 // yfmt: 0 = y in complex64, 1 = y as the BF16 hi/lo split (batch sweep only).
 // force: a fixed sweep (the autotuner's candidates); otherwise the environment, then the
 // autotuner's cache, then the default rule below.
-int prepare(const mra_dims* d, int Lw, int l0, const float* y, const int32_t* shift, void* ws, size_t ws_bytes,
-            EmCall* c, bool allow_v3 = true, int yfmt = 0, const SweepSel* force = nullptr) {
+// step: spacing of the window's rotations in grid units (1 = the grid, see window_ok).
+int prepare(const mra_dims* d, int Lw, int l0, double step, const float* y, const int32_t* shift, void* ws,
+            size_t ws_bytes, EmCall* c, bool allow_v3 = true, int yfmt = 0, const SweepSel* force = nullptr) {
   int st = check_dims(d);
   if (st != MRA_OK) return st;
-  if (Lw < 1 || Lw > d->L) return MRA_EINVAL;
+  if (!window_ok(d->L, Lw, l0, step)) return MRA_EINVAL;
+  const bool dense = step != 1.0;
   if (!ptr_ok(y, 16) || !ptr_ok(ws, 256)) return MRA_EINVAL;
   if (shift && !ptr_ok(shift, 4)) return MRA_EINVAL;
   DevInfo di;
@@ -1288,31 +1327,31 @@ int prepare(const mra_dims* d, int Lw, int l0, const float* y, const int32_t* sh
   c->lay.G = G;
   if (ws_bytes < c->lay.total) return MRA_EWORKSPACE;
   const int Kp1 = d->K + 1, M = Kp1 * d->Q;
-  const int nu = window_units(d->L, Lw, l0, nullptr);
+  const int nu = window_units(d->L, Lw, l0, dense, nullptr);
   const int nup = round_up(nu, kUnitChunk);
   SweepSel sel = env_sweep();
   if (force) {
     sel = *force;
   } else if (sel.kind == 0 && sel.bi == 0 && sel.ns == 0) {
     SweepSel tuned;
-    if (tune_lookup(tune_key(d, Lw, l0, yfmt), &tuned)) sel = tuned;
+    if (tune_lookup(tune_key(d, Lw, l0, step, yfmt), &tuned)) sel = tuned;
   }
   c->v4 = false;
   if (yfmt) {
     c->v2 = false;
-    c->v3 = sel.kind != 1 && plan_v3(Kp1, d->Q, d->L, Lw, l0, 1, sel.bi, sel.ns, di.max_smem_optin, &c->v3p);
+    c->v3 = sel.kind != 1 && plan_v3(Kp1, d->Q, d->L, Lw, l0, dense, 1, sel.bi, sel.ns, di.max_smem_optin, &c->v3p);
     if (!c->v3) return MRA_EINVAL;  // no sweep for this shape reads the split format
   } else {
     // By default the warp sweep keeps a window of one unit chunk in registers and is the
     // faster one there; wider windows (up to the whole circle) go to the batch sweep.
     c->v2 = sel.kind != 2 && plan_v2(Kp1, d->Q, d->L, Lw, nup, di.max_smem_optin, &c->v2p);
     c->v3 = allow_v3 && sel.kind != 1 && (!c->v2 || sel.kind == 2 || nup > kUnitChunk) &&
-            plan_v3(Kp1, d->Q, d->L, Lw, l0, 0, sel.bi, sel.ns, di.max_smem_optin, &c->v3p);
+            plan_v3(Kp1, d->Q, d->L, Lw, l0, dense, 0, sel.bi, sel.ns, di.max_smem_optin, &c->v3p);
     if (c->v3) c->v2 = false;
     // The chunked two-read sweep runs when chosen (environment or autotuner): it leads on
     // sharp posteriors and ties the warp sweep on broad ones.
     if (allow_v3 && sel.kind == 3) {
-      c->v4 = plan_v4(Kp1, d->Q, d->L, Lw, l0, sel.bi, sel.ns, di, &c->v4p);
+      c->v4 = plan_v4(Kp1, d->Q, d->L, Lw, l0, dense, sel.bi, sel.ns, di, &c->v4p);
       if (c->v4) {
         c->v2 = c->v3 = false;
         c->lay.G = c->v4p.grid;
@@ -1354,11 +1393,13 @@ int prepare(const mra_dims* d, int Lw, int l0, const float* y, const int32_t* sh
   s.twp = L_.twp;
   s.slot_bytes = c->plan.slot_bytes; s.cp = c->plan.cp; s.sp = c->plan.sp;
   s.off_ybuf = c->plan.off_ybuf; s.off_x = c->plan.off_x; s.off_tw = c->plan.off_tw; s.off_tf = c->plan.off_tf;
-  s.off_c = c->plan.off_c; s.off_s = c->plan.off_s; s.off_w = c->plan.off_w; s.off_wl = c->plan.off_wl;
+  s.off_c = c->plan.off_c; s.off_s = c->plan.off_s; s.off_s64 = c->plan.off_s64; s.off_w = c->plan.off_w; s.off_wl = c->plan.off_wl;
   s.off_lr = c->plan.off_lr;
   s.two_beta = (float)(2.0 / d->sigma2);
+  s.two_beta_d = 2.0 / d->sigma2;
   s.x32 = reinterpret_cast<const float2*>(base + L_.x32);
   s.tw = reinterpret_cast<const float2*>(base + L_.tw);
+  s.tw64 = reinterpret_cast<const double2*>(base + L_.tw64);
   s.tf32 = reinterpret_cast<const float2*>(base + L_.tf32);
   s.logrho32 = reinterpret_cast<const float*>(base + L_.logrho32);
   s.part = reinterpret_cast<double*>(base + L_.part);
@@ -1372,9 +1413,15 @@ int prepare(const mra_dims* d, int Lw, int l0, const float* y, const int32_t* sh
   v.N = d->N; v.Kp1 = Kp1; v.M = M; v.L = d->L; v.Lw = Lw; v.NU = nu; v.NUP = nup;
   v.nwarps = c->v2p.nwarps; v.slot_bytes = c->v2p.slot_bytes; v.sp = c->v2p.sp;
   v.off_ring = c->v2p.off_ring; v.off_x = c->v2p.off_x; v.off_tu = c->v2p.off_tu; v.off_tf = c->v2p.off_tf;
-  v.off_lr = c->v2p.off_lr; v.off_units = c->v2p.off_units; v.off_lmap = c->v2p.off_lmap; v.off_s = c->v2p.off_s; v.off_wl = c->v2p.off_wl;
+  v.off_lr = c->v2p.off_lr; v.off_units = c->v2p.off_units; v.off_s = c->v2p.off_s; v.off_wl = c->v2p.off_wl;
   v.two_beta = s.two_beta;
   v.align_only = 0;
+  v.wrap = !dense && Lw == d->L ? 1 : 0;
+  v.l0m = ((l0 % d->L) + d->L) % d->L;
+  v.nd = v.wrap ? d->L / 2 + 1 : Lw;
+  v.td = reinterpret_cast<const float2*>(base + L_.td);
+  v.tw = dense ? s.tw : nullptr;
+  v.twp = L_.twp;
   v.x32 = s.x32;
   v.tu = reinterpret_cast<const float2*>(base + L_.tu);
   v.units = reinterpret_cast<const int2*>(base + L_.units);
@@ -1400,6 +1447,8 @@ int prepare(const mra_dims* d, int Lw, int l0, const float* y, const int32_t* sh
   w.x32 = s.x32;
   w.td = reinterpret_cast<const float2*>(base + L_.td);
   w.tf32 = s.tf32;
+  w.tw = dense ? s.tw : nullptr;
+  w.twp = L_.twp;
   w.logrho32 = s.logrho32;
   w.part = s.part;
   w.w_out = nullptr;
@@ -1419,6 +1468,8 @@ int prepare(const mra_dims* d, int Lw, int l0, const float* y, const int32_t* sh
   v4.x32 = s.x32;
   v4.td = reinterpret_cast<const float2*>(base + L_.td);
   v4.tf32 = s.tf32;
+  v4.tw = w.tw;
+  v4.twp = L_.twp;
   v4.logrho32 = s.logrho32;
   v4.part = s.part;
   v4.w_out = nullptr;
@@ -1427,10 +1478,12 @@ int prepare(const mra_dims* d, int Lw, int l0, const float* y, const int32_t* sh
   SetupArgs& u = c->su;
   u.N = d->N; u.Kp1 = Kp1; u.Q = d->Q; u.M = M; u.L = d->L; u.Lw = Lw;
   u.l0 = l0; u.twp = L_.twp; u.kp4 = L_.kp4; u.sigma2 = d->sigma2;
+  u.step = step; u.dense = dense ? 1 : 0;
   u.x_in = nullptr; u.log_rho_in = nullptr; u.log_rho_bar = nullptr; u.gamma_a_inv = nullptr;
   u.tf32 = reinterpret_cast<float2*>(base + L_.tf32);
   u.tf64 = reinterpret_cast<double2*>(base + L_.tf64);
   u.tw = reinterpret_cast<float2*>(base + L_.tw);
+  u.tw64 = reinterpret_cast<double2*>(base + L_.tw64);
   u.x32 = reinterpret_cast<float2*>(base + L_.x32);
   u.x64 = reinterpret_cast<double2*>(base + L_.x64);
   u.inv_den = reinterpret_cast<double*>(base + L_.inv_den);
@@ -1440,7 +1493,7 @@ int prepare(const mra_dims* d, int Lw, int l0, const float* y, const int32_t* sh
   u.units = reinterpret_cast<int2*>(base + L_.units);
   u.tu = reinterpret_cast<float2*>(base + L_.tu);
   u.td = reinterpret_cast<float2*>(base + L_.td);
-  u.nd = c->v3 ? c->v3p.nd : c->v4 ? c->v4p.nd : 0;
+  u.nd = c->v3 ? c->v3p.nd : c->v4 ? c->v4p.nd : c->v2 ? v.nd : 0;
   u.nu = nu;
   u.nup = nup;
   u.ctrl = c->ctrl;
@@ -1469,10 +1522,20 @@ int launch_setup(const EmCall& c, cudaStream_t st) {
   if (c.v3 || c.v4) {
     const int ntd = c.su.Kp1 * c.su.nd;
     k_setup_td<<<std::min(1024, (ntd + 255) / 256), 256, 0, st>>>(c.su);
+    if (c.su.dense) {  // the rotation to each image's reference
+      const int ntw = c.su.kp4 * c.su.twp;
+      k_setup_tw<<<std::min(1024, (ntw + 255) / 256), 256, 0, st>>>(c.su);
+    }
   } else if (c.v2) {
     k_setup_units<<<1, 32, 0, st>>>(c.su);
     const int ntu = c.su.Kp1 * c.su.nup;
     k_setup_tu<<<std::min(1024, (ntu + 255) / 256), 256, 0, st>>>(c.su);
+    const int ntd = c.su.Kp1 * c.su.nd;  // pass 2 around each image's peak
+    k_setup_td<<<std::min(1024, (ntd + 255) / 256), 256, 0, st>>>(c.su);
+    if (c.su.dense) {  // the rotation to each image's peak
+      const int ntw = c.su.kp4 * c.su.twp;
+      k_setup_tw<<<std::min(1024, (ntw + 255) / 256), 256, 0, st>>>(c.su);
+    }
   } else {
     const int ntw = c.su.kp4 * c.su.twp;
     k_setup_tw<<<std::min(1024, (ntw + 255) / 256), 256, 0, st>>>(c.su);
@@ -1501,9 +1564,12 @@ int launch_iteration(const EmCall& c, cudaStream_t st, cudaEvent_t ev0 = nullptr
   return cudaGetLastError() == cudaSuccess ? MRA_OK : MRA_ECUDA;
 }
 
+// The window's rotation spacing: step (0 is read as 1, the grid).
+double param_step(const mra_em_params* p) { return p->step == 0.0 ? 1.0 : p->step; }
+
 int check_params(const mra_dims* d, const mra_em_params* p) {
   if (!p) return MRA_EINVAL;
-  if (p->Lw < 1 || p->Lw > d->L) return MRA_EINVAL;
+  if (!window_ok(d->L, p->Lw, p->l0, param_step(p))) return MRA_EINVAL;
   if (!(p->gamma >= 0.0) || !isfinite(p->gamma)) return MRA_EINVAL;
   if (p->gamma > 0.0 && !ptr_ok(p->log_rho_bar, 8)) return MRA_EINVAL;
   if (p->gamma_a_inv && !ptr_ok(p->gamma_a_inv, 8)) return MRA_EINVAL;
@@ -1560,7 +1626,7 @@ static int em_step_impl(const mra_dims* d, const mra_em_params* p, const float* 
     return MRA_EINVAL;
   if (w_out && !ptr_ok(w_out, 4)) return MRA_EINVAL;
   EmCall c;
-  if ((st = prepare(d, p->Lw, p->l0, y, shift, ws, ws_bytes, &c, true, yfmt)) != MRA_OK) return st;
+  if ((st = prepare(d, p->Lw, p->l0, param_step(p), y, shift, ws, ws_bytes, &c, true, yfmt)) != MRA_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   c.su.x_in = reinterpret_cast<const double2*>(x_in);
   c.su.log_rho_in = log_rho_in;
@@ -1588,7 +1654,7 @@ static int em_run_impl(const mra_dims* d, const mra_em_params* p, const float* y
   if (stats_out && !ptr_ok(stats_out, 8)) return MRA_EINVAL;
   if (x_traj_out && !ptr_ok(x_traj_out, 16)) return MRA_EINVAL;
   EmCall c;
-  if ((st = prepare(d, p->Lw, p->l0, y, shift, ws, ws_bytes, &c, true, yfmt)) != MRA_OK) return st;
+  if ((st = prepare(d, p->Lw, p->l0, param_step(p), y, shift, ws, ws_bytes, &c, true, yfmt)) != MRA_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   c.su.x_in = reinterpret_cast<const double2*>(x_inout);
   c.su.log_rho_in = log_rho_inout;
@@ -1770,7 +1836,7 @@ int autotune_impl(const mra_dims* d, const mra_em_params* p, const float* y, int
   float best_ms = -1.f;
   for (const SweepSel& cand : kTuneCandidates) {
     EmCall c;
-    const int st = prepare(d, p->Lw, p->l0, y, shift, ws, ws_bytes, &c, true, yfmt, &cand);
+    const int st = prepare(d, p->Lw, p->l0, param_step(p), y, shift, ws, ws_bytes, &c, true, yfmt, &cand);
     if (st == MRA_EINVAL) continue;  // this candidate cannot take the shape
     if (st != MRA_OK) return st;
     if (cand.kind == 2 && ((cand.bi && c.v3p.bi != cand.bi) || (cand.ns && c.v3p.ns != cand.ns))) continue;
@@ -1785,7 +1851,7 @@ int autotune_impl(const mra_dims* d, const mra_em_params* p, const float* y, int
     if (ms < 0.f) return MRA_ECUDA;
     if (best_ms < 0.f || ms < best_ms) best_ms = ms, best = cand;
   }
-  if (best_ms >= 0.f) tune_store(tune_key(d, p->Lw, p->l0, yfmt), best);
+  if (best_ms >= 0.f) tune_store(tune_key(d, p->Lw, p->l0, param_step(p), yfmt), best);
   if (out) *out = best;
   return MRA_OK;
 }
@@ -1895,7 +1961,7 @@ MRA_API int mra_em_run_batched(const mra_instance* inst, int32_t n, int32_t tune
     for (int i = 0; i < n; ++i) {
       const mra_instance& a = inst[i];
       SweepSel have;
-      if (tune_lookup(tune_key(&a.dims, a.prm.Lw, a.prm.l0, a.y_format), &have)) continue;
+      if (tune_lookup(tune_key(&a.dims, a.prm.Lw, a.prm.l0, param_step(&a.prm), a.y_format), &have)) continue;
       const int st = autotune_impl(&a.dims, &a.prm, static_cast<const float*>(a.y), a.y_format, a.shift, a.x_inout,
                                    a.log_rho_inout, base + off[i], off[i + 1] - off[i], s, nullptr);
       if (st != MRA_OK) return st;
@@ -1905,7 +1971,7 @@ MRA_API int mra_em_run_batched(const mra_instance* inst, int32_t n, int32_t tune
   for (int i = 0; i < n; ++i) {
     const mra_instance& a = inst[i];
     EmCall& c = calls[i];
-    const int st = prepare(&a.dims, a.prm.Lw, a.prm.l0, static_cast<const float*>(a.y), a.shift, base + off[i],
+    const int st = prepare(&a.dims, a.prm.Lw, a.prm.l0, param_step(&a.prm), static_cast<const float*>(a.y), a.shift, base + off[i],
                            off[i + 1] - off[i], &c, true, a.y_format);
     if (st != MRA_OK) return st;
     // a small instance takes few SMs (about one persistent CTA per kBatchedImagesPerCta images),
@@ -1994,23 +2060,25 @@ MRA_API int mra_em_run_batched(const mra_instance* inst, int32_t n, int32_t tune
   return rc;
 }
 
-MRA_API int mra_loglik_grad(const mra_dims* d, int32_t Lw, int32_t l0, const float* y, const int32_t* shift,
-                            const double* x, const double* logits, double kappa, double* loglik_out, double* dx_out,
-                            double* dlogits_out, double* dkappa_out, void* ws, size_t ws_bytes, void* stream) {
+MRA_API int mra_loglik_grad(const mra_dims* d, int32_t Lw, int32_t l0, double step, const float* y,
+                            const int32_t* shift, const double* x, const double* logits, double kappa,
+                            double* loglik_out, double* dx_out, double* dlogits_out, double* dkappa_out, void* ws,
+                            size_t ws_bytes, void* stream) {
   int st = check_dims(d);
   if (st != MRA_OK) return st;
+  if (step == 0.0) step = 1.0;
   if (!ptr_ok(x, 16) || !ptr_ok(logits, 8) || !isfinite(kappa)) return MRA_EINVAL;
   if (dx_out && !ptr_ok(dx_out, 16)) return MRA_EINVAL;
   EmCall c;
-  if ((st = prepare(d, Lw, l0, y, shift, ws, ws_bytes, &c)) != MRA_OK) return st;
+  if ((st = prepare(d, Lw, l0, step, y, shift, ws, ws_bytes, &c)) != MRA_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   c.su.x_in = reinterpret_cast<const double2*>(x);
   if ((st = launch_setup(c, s)) != MRA_OK) return st;
-  k_setup_vm<<<1, 256, 0, s>>>(d->L, Lw, l0, kappa, logits, c.su.rho64, c.su.logrho32);
+  k_setup_vm<<<1, 256, 0, s>>>(d->L, Lw, l0, step, kappa, logits, c.su.rho64, c.su.logrho32);
   launch_sweep(c, s);
   k_reduce_cols<<<c.reduce_blocks, 256, 0, s>>>(c.sa.part, c.lay.G, c.lay.cols, c.tot, c.ctrl);
   GradArgs g;
-  g.N = d->N; g.M = c.lay.M; g.L = d->L; g.Lw = Lw; g.l0 = l0;
+  g.N = d->N; g.M = c.lay.M; g.L = d->L; g.Lw = Lw; g.l0 = l0; g.step = step;
   g.sigma2 = d->sigma2; g.beta = 1.0 / d->sigma2; g.kappa = kappa;
   g.tot = c.tot; g.cols = c.lay.cols;
   g.x64 = c.su.x64; g.rho64 = c.su.rho64;
@@ -2024,7 +2092,7 @@ MRA_API int mra_loglik_grad(const mra_dims* d, int32_t Lw, int32_t l0, const flo
 
 static int align_into_tot(const mra_dims* d, const float* y, const int32_t* shift, void* ws, size_t ws_bytes,
                           cudaStream_t s, EmCall* c) {
-  int st = prepare(d, 1, 0, y, shift, ws, ws_bytes, c, /*allow_v3=*/false);  // align mode lives in the warp sweep
+  int st = prepare(d, 1, 0, 1.0, y, shift, ws, ws_bytes, c, /*allow_v3=*/false);  // align mode lives in the warp sweep
   if (st != MRA_OK) return st;
   const bool qeven = (d->Q % 2) == 0;
   const int M = c->lay.M, vec = qeven ? 2 : 1;

@@ -258,6 +258,7 @@ __global__ void __launch_bounds__(kV3Threads, 1) k_sweep_v3(const SweepV3Args a)
         }
         float2 c = make_float2((p0.x + p0.y) + (p1.x + p1.y), (q0.x + q0.y) + (q1.x + q1.y));
         if (ph != 0) c = cmul(c, tfs[(k * ph) % L]);
+        if (a.tw) c = cmul(c, a.tw[k * a.twp + r0]);  // dense window: the first reference's angle
         cbuf[ii * cp + k] = c;
         if (want_ysq) ysq_acc += (double)(sq0 + sq1);
       }
@@ -299,10 +300,16 @@ __global__ void __launch_bounds__(kV3Threads, 1) k_sweep_v3(const SweepV3Args a)
         const float shiftv = srow[p] - lrs[p];
         __syncwarp();
         for (int l = lane; l < Lw; l += 32) srow[l] -= shiftv;
-        int dr = (p - r0) % L;
-        if (dr < 0) dr += L;
-        for (int k = lane; k < Kp1; k += 32) cbuf[i * cp + k] = cmul(cbuf[i * cp + k], tfs[(k * dr) % L]);
-        if (lane == 0) info[i] = make_int4((ph1 + dr) % L, p, (int)dist, (int)dist);
+        if (a.tw) {  // dense window: p - r0 window steps, from the distance-unit table
+          const int dr = p - r0, ad = dr < 0 ? -dr : dr;
+          for (int k = lane; k < Kp1; k += 32) cbuf[i * cp + k] = cmul(cbuf[i * cp + k], td_rot(td[k * dp + ad], dr));
+          if (lane == 0) info[i] = make_int4(ph1, p, (int)dist, (int)dist);
+        } else {
+          int dr = (p - r0) % L;
+          if (dr < 0) dr += L;
+          for (int k = lane; k < Kp1; k += 32) cbuf[i * cp + k] = cmul(cbuf[i * cp + k], tfs[(k * dr) % L]);
+          if (lane == 0) info[i] = make_int4((ph1 + dr) % L, p, (int)dist, (int)dist);
+        }
       } else if (lane == 0) {
         info[i] = make_int4(ph1, p, (int)dist, -1);
       }
@@ -368,6 +375,7 @@ __global__ void __launch_bounds__(kV3Threads, 1) k_sweep_v3(const SweepV3Args a)
         if (d <= f.z) v0 = __ffma2_rn(wr[d], trow[d], v0);
         float2 W = make_float2(1.f + (v0.x + v1.x), v0.y + v1.y);
         if (f.x != 0) W = cmul_conj_b(W, tfs[(k * f.x) % L]);
+        if (a.tw) W = cmul_conj_b(W, a.tw[k * a.twp + f.y]);  // dense window: the reference's angle
         cbuf[ii * cp + k] = W;
       }
     }

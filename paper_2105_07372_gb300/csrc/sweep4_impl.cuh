@@ -213,6 +213,7 @@ __global__ void __launch_bounds__(NTH, MINB) k_sweep_v4(const SweepV4Args a) {
         if (j == 0 && k < Kp1) {
           float2 c = make_float2(cr, ci);
           if (ph != 0) c = cmul(c, tfs[(k * ph) % L]);
+          if (a.tw) c = cmul(c, a.tw[k * a.twp + r0]);  // dense window: the first reference's angle
           cbuf[li * cp + k] = c;
         }
       }
@@ -311,10 +312,16 @@ __global__ void __launch_bounds__(NTH, MINB) k_sweep_v4(const SweepV4Args a) {
         if (own) {
           if (p != r0) {
             for (int l = sub; l < Lw; l += 8) srow[l] -= shiftv;
-            int dr = (p - r0) % L;
-            if (dr < 0) dr += L;
-            for (int k = sub; k < Kp1; k += 8) cbuf[i * cp + k] = cmul(cbuf[i * cp + k], tfs[(k * dr) % L]);
-            if (sub == 0) info[i] = make_int4((ph1 + dr) % L, p, dist, dist);
+            if (a.tw) {  // dense window: p - r0 window steps, from the distance-unit table
+              const int dr = p - r0, ad = dr < 0 ? -dr : dr;
+              for (int k = sub; k < Kp1; k += 8) cbuf[i * cp + k] = cmul(cbuf[i * cp + k], td_rot(td[k * dp + ad], dr));
+              if (sub == 0) info[i] = make_int4(ph1, p, dist, dist);
+            } else {
+              int dr = (p - r0) % L;
+              if (dr < 0) dr += L;
+              for (int k = sub; k < Kp1; k += 8) cbuf[i * cp + k] = cmul(cbuf[i * cp + k], tfs[(k * dr) % L]);
+              if (sub == 0) info[i] = make_int4((ph1 + dr) % L, p, dist, dist);
+            }
           } else if (sub == 0) {
             info[i] = make_int4(ph1, p, dist, -1);
           }
@@ -387,6 +394,7 @@ __global__ void __launch_bounds__(NTH, MINB) k_sweep_v4(const SweepV4Args a) {
             if (k < Kp1) {
               float2 W = make_float2(1.f + v[u].x, v[u].y);
               if (f.x != 0) W = cmul_conj_b(W, tfs[(k * f.x) % L]);
+              if (a.tw) W = cmul_conj_b(W, a.tw[k * a.twp + f.y]);  // dense window: the reference's angle
               cbuf[ii * cp + k] = W;
             }
           }

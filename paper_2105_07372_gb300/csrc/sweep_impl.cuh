@@ -17,9 +17,11 @@
 //   back          W_k = sum_l w_l e^{+i k theta_l} = sum_units (w_+ + w_-) cos + i (w_- - w_+) sin
 //   accumulate    num_kq += W_k y_kq into per-lane FP32 registers
 //
-// FP32 log-weights reach 2 beta S ~ hundreds; to keep their differences accurate a
-// first pass locates each image's peak rotation and the per-quad partial sums are
-// re-expressed relative to the peak's partial before the cross-quad sums.
+// FP32 log-weights reach 2 beta S ~ thousands, and FP32 rounding of such sums (and of the
+// twiddles) would move the normalised weights by more than 1e-5.  So pass 1 (above) only
+// locates each image's peak rotation l* and how far from it the weights matter; pass 2
+// recomputes those values as differences S(l* +- d) - S(l*) from c rotated to the peak and
+// an FP64-built table of (cos t - 1, -sin t), whose terms vanish near the peak.
 // The CTA combines its warps' sums once at the end and writes FP64 partials.
 #pragma once
 #include "common.cuh"
@@ -54,6 +56,7 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR, IPW>::kThreads, 1) k_swee
   const int nwarps = a.nwarps;  // <= NT/32 (warps beyond it only join the final combination)
   const int r = lane >> 2, j = lane & 3;
   const int Kp1 = a.Kp1, L = a.L, Lw = a.Lw, NU = a.NU, M = a.M;
+  const bool wrap = a.wrap != 0;
   const int NUP = LWC > 0 ? 4 * kUC : a.NUP;
   // f(l) for this lane's window indices l = lane, lane + 32, ...
   auto for_window = [&](auto&& f) {
@@ -77,7 +80,6 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR, IPW>::kThreads, 1) k_swee
   const float2* tfs = reinterpret_cast<const float2*>(smem + a.off_tf);  // [L]
   const float* lrs = reinterpret_cast<const float*>(smem + a.off_lr);    // [Lw]
   const int2* uab = reinterpret_cast<const int2*>(smem + a.off_units);   // [NUP] (a, b) window indices, b < 0: single
-  const int2* lmap = reinterpret_cast<const int2*>(smem + a.off_lmap);   // [Lw] (unit, -1 first offset / +1 mirror)
   float* sbuf0 = reinterpret_cast<float*>(smem + a.off_s) + warp * IPW * a.sp;  // per warp [IPW][sp]
   float* wlw = reinterpret_cast<float*>(smem + a.off_wl) + warp * a.sp;          // per warp [sp]
 
@@ -93,15 +95,7 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR, IPW>::kThreads, 1) k_swee
     float* lrw = reinterpret_cast<float*>(smem + a.off_lr);
     for (int i = tid; i < Lw; i += NT) lrw[i] = a.logrho32[i];
     int2* uw = reinterpret_cast<int2*>(smem + a.off_units);
-    int2* lw = reinterpret_cast<int2*>(smem + a.off_lmap);
-    for (int i = tid; i < NUP; i += NT) {
-      const int2 ab = a.units[i];
-      uw[i] = ab;
-      if (i < NU && ab.x >= 0 && ab.x < Lw) {
-        lw[ab.x] = make_int2(i, -1);
-        if (ab.y >= 0 && ab.y < Lw) lw[ab.y] = make_int2(i, 1);
-      }
-    }
+    for (int i = tid; i < NUP; i += NT) uw[i] = a.units[i];
     float* wl0 = reinterpret_cast<float*>(smem + a.off_wl);
     for (int i = tid; i < a.sp * (NT / 32); i += NT) wl0[i] = 0.f;
     if (tid < 2 * nwarps) mbar_init(&bar[tid], 1);
@@ -245,7 +239,8 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR, IPW>::kThreads, 1) k_swee
         }
       }
 
-      // ---- forward transform over mirror units (chunks of 4 * kUC units)
+      // ---- forward transform, pass 1 over mirror units (chunks of 4 * kUC units): the peak l* and
+      // the distance D from it beyond which every value is more than 40 below the peak's
       auto quad_sum = [&](float v) {
         v += __shfl_xor_sync(0xffffffffu, v, 4);
         v += __shfl_xor_sync(0xffffffffu, v, 8);
@@ -275,25 +270,39 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR, IPW>::kThreads, 1) k_swee
           }
         }
       };
+      // D from the lowest and highest window index whose value is within 40 of the peak (the
+      // whole half circle when the window is all of it)
+      auto peak_dist = [&](int p, int lo, int hi) {
+        if (wrap) return L / 2;
+        lo = __reduce_min_sync(0xffffffffu, lo);
+        hi = __reduce_max_sync(0xffffffffu, hi);
+        return max(p - lo, hi - p);
+      };
       float vref[IPW];  // FP32 log-weight at the peak l* (absolute)
+      int peak[IPW], dist[IPW];
       if (NUP == 4 * kUC) {
         float A[IPW][kUC], Bv[IPW][kUC];
         partials(0, A, Bv);
 #pragma unroll
         for (int i = 0; i < IPW; ++i) {
+          float sa[kUC], sm[kUC];  // values at each unit's first offset and at its mirror
+          int2 abt[kUC];
           float bv = -INFINITY;
           int bl = 0x7fffffff;
 #pragma unroll
           for (int t = 0; t < kUC; ++t) {
             const int u = j + 4 * t;
             const float At = quad_sum(A[i][t]), Bt = quad_sum(Bv[i][t]);
+            sa[t] = -INFINITY, sm[t] = -INFINITY;
+            abt[t] = make_int2(0, 0);
             if (u < NU) {
               const int2 ab = uab[u];
-              const float sa = fmaf(two_beta, At - Bt, lrs[ab.x]);
-              if (sa > bv || (sa == bv && ab.x < bl)) bv = sa, bl = ab.x;
+              abt[t] = ab;
+              sa[t] = fmaf(two_beta, At - Bt, lrs[ab.x]);
+              if (sa[t] > bv || (sa[t] == bv && ab.x < bl)) bv = sa[t], bl = ab.x;
               if (ab.y >= 0) {
-                const float sb = fmaf(two_beta, At + Bt, lrs[ab.y]);
-                if (sb > bv || (sb == bv && ab.y < bl)) bv = sb, bl = ab.y;
+                sm[t] = fmaf(two_beta, At + Bt, lrs[ab.y]);
+                if (sm[t] > bv || (sm[t] == bv && ab.y < bl)) bv = sm[t], bl = ab.y;
               }
             }
           }
@@ -305,27 +314,15 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR, IPW>::kThreads, 1) k_swee
           }
           if (bl >= Lw) bl = 0;  // only if every log-weight is -inf
           vref[i] = bv;
-          const int2 um = lmap[bl];  // (unit, -1 for its first offset / +1 for the mirror)
-          const int tstar = um.x >> 2, jstar = um.x & 3;
-          float pa = A[i][0], pb = Bv[i][0];
+          peak[i] = bl;
+          const float thr = bv - 40.f;
+          int lo = bl, hi = bl;
 #pragma unroll
-          for (int t = 1; t < kUC; ++t)
-            if (t == tstar) pa = A[i][t], pb = Bv[i][t];
-          float pr = um.y < 0 ? pa - pb : pa + pb;
-          pr = __shfl_sync(0xffffffffu, pr, (lane & ~3) | jstar);
-          const float lr_ref = lrs[bl];
-          float* sb = sbuf0 + i * a.sp;
-#pragma unroll
-          for (int t = 0; t < kUC; ++t) {
-            const float da = quad_sum((A[i][t] - Bv[i][t]) - pr);
-            const float db = quad_sum((A[i][t] + Bv[i][t]) - pr);
-            const int u = j + 4 * t;
-            if (r == 0 && u < NU) {
-              const int2 ab = uab[u];
-              sb[ab.x] = fmaf(two_beta, da, lrs[ab.x] - lr_ref);
-              if (ab.y >= 0) sb[ab.y] = fmaf(two_beta, db, lrs[ab.y] - lr_ref);
-            }
+          for (int t = 0; t < kUC; ++t) {  // sa, sm are -inf where a unit or its mirror is absent
+            if (sa[t] >= thr) lo = min(lo, abt[t].x), hi = max(hi, abt[t].x);
+            if (sm[t] >= thr) lo = min(lo, abt[t].y), hi = max(hi, abt[t].y);
           }
+          dist[i] = peak_dist(bl, lo, hi);
         }
       } else if constexpr (IPW == 1) {
         float* sb = sbuf0;
@@ -362,71 +359,115 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR, IPW>::kThreads, 1) k_swee
         }
         if (bl >= Lw) bl = 0;
         vref[0] = bv;
-        const int2 um = lmap[bl];
-        float pa = 0.f, pb = 0.f;  // the peak's quad partial, same arithmetic as partials()
+        peak[0] = bl;
+        const float thr = bv - 40.f;
+        int lo = bl, hi = bl;
+        for_window([&](int l) {
+          if (sb[l] >= thr) lo = min(lo, l), hi = max(hi, l);
+        });
+        dist[0] = peak_dist(bl, lo, hi);
+        __syncwarp();  // pass 2 rewrites sb
+      }
+
+      // ---- pass 2: the values within D of the peak, relative to it, from c rotated to the peak,
+      // c'_k = c_k e^{-i k theta_l*}, and the distance-unit table (cos t - 1, -sin t),
+      // t = 2 pi k d step / L: S(l* + d) - S(l*) = A_d - B_d and S(l* - d) - S(l*) = A_d + B_d with
+      // A_d = sum c'.x (cos t - 1), B_d = sum c'.y (-sin t).  The terms are small near the peak,
+      // so the FP32 differences keep their precision however large 2 beta |c| is.  Values
+      // farther than D are more than 40 below the peak: their weights (< e^-40) are taken as 0.
 #pragma unroll
-        for (int m = 0; m < MR; ++m) {
-          const int k = r + 8 * m;
-          if (m < MR - 1 || k < Kp1) {  // rows of all groups but the last exist
-            const float2 tv = tus[k * NUP + um.x];
-            pa = fmaf(c[0][m].x, tv.x, pa);
-            pb = fmaf(c[0][m].y, tv.y, pb);
+      for (int i = 0; i < IPW; ++i) {
+        const int p = peak[i], D = dist[i];
+        float2 cq[MR];
+        if (a.tw) {  // dense window: the window twiddle table (global, L1-resident)
+#pragma unroll
+          for (int m = 0; m < MR; ++m) {
+            const int k = r + 8 * m;
+            cq[m] = (m < MR - 1 || k < Kp1) ? cmul(c[i][m], a.tw[k * a.twp + p]) : make_float2(0.f, 0.f);
+          }
+        } else {
+          int op = a.l0m + p;
+          if (op >= L) op -= L;
+          int ph = mod_small(r * op, L, invL);
+          const int pst = mod_small(8 * op, L, invL);
+#pragma unroll
+          for (int m = 0; m < MR; ++m) {
+            cq[m] = cmul(c[i][m], tfs[ph]);
+            ph += pst;
+            if (ph >= L) ph -= L;
           }
         }
-        const float pr = um.y < 0 ? pa - pb : pa + pb;
-        const float lr_ref = lrs[bl];
-        for (int u0 = 0; u0 < NUP; u0 += 4 * kUC) {  // pass 2 where the weights are not negligible
-          bool sig = false;
+        float* sb = sbuf0 + i * a.sp;
+        const float lr_ref = lrs[p];
+        // one slot per lane and distance chunk: d = d0 + j (+ 4 t), four distances per quad
+        auto emit = [&](int d, float Ad, float Bd) {
+          const float da = quad_sum(Ad - Bd), db = quad_sum(Ad + Bd);
+          if (r == 0 && d <= D) {
+            int la = p + d, lb = p - d;
+            if (wrap) {
+              if (la >= L) la -= L;
+              if (lb < 0) lb += L;
+            }
+            if (wrap || la < Lw) sb[la] = fmaf(two_beta, da, lrs[la] - lr_ref);
+            if (d > 0 && (wrap ? 2 * d != L : lb >= 0)) sb[lb] = fmaf(two_beta, db, lrs[lb] - lr_ref);
+          }
+        };
+        const int nd1 = a.nd - 1;
+        const float2* trow0 = a.td + r * a.nd;  // row k = r; row r + 8 m is 8 m nd further
+        if (D < 4) {  // the usual case: one distance per lane
+          const float2* tp = trow0 + min(j, nd1);
+          float Ad = 0.f, Bd = 0.f;
 #pragma unroll
-          for (int t = 0; t < kUC; ++t) {
-            const int u = u0 + j + 4 * t;
-            if (u < NU) {
-              const int2 ab = uab[u];
-              sig |= sb[ab.x] >= bv - 40.f;
-              if (ab.y >= 0) sig |= sb[ab.y] >= bv - 40.f;
+          for (int m = 0; m < MR; ++m) {
+            if (m < MR - 1 || r + 8 * m < Kp1) {
+              const float2 tv = tp[8 * m * a.nd];
+              Ad = fmaf(cq[m].x, tv.x, Ad);
+              Bd = fmaf(cq[m].y, tv.y, Bd);
             }
           }
-          sig = __any_sync(0xffffffffu, sig);
-          __syncwarp();
-          if (sig) {
-            float A[1][kUC], Bv[1][kUC];
-            partials(u0, A, Bv);
+          emit(j, Ad, Bd);
+        } else {
+          for (int d0 = 0; d0 <= D; d0 += 4 * kUC) {
+            const int nt = min(kUC, (D - d0) / 4 + 1);  // slots t holding some d <= D
+            float Ad[kUC], Bd[kUC];
 #pragma unroll
-            for (int t = 0; t < kUC; ++t) {
-              const float da = quad_sum((A[0][t] - Bv[0][t]) - pr);
-              const float db = quad_sum((A[0][t] + Bv[0][t]) - pr);
-              const int u = u0 + j + 4 * t;
-              if (r == 0 && u < NU) {
-                const int2 ab = uab[u];
-                sb[ab.x] = fmaf(two_beta, da, lrs[ab.x] - lr_ref);
-                if (ab.y >= 0) sb[ab.y] = fmaf(two_beta, db, lrs[ab.y] - lr_ref);
+            for (int t = 0; t < kUC; ++t) Ad[t] = 0.f, Bd[t] = 0.f;
+#pragma unroll
+            for (int m = 0; m < MR; ++m) {
+              if (m < MR - 1 || r + 8 * m < Kp1) {
+                const float2* tr = trow0 + 8 * m * a.nd;
+#pragma unroll
+                for (int t = 0; t < kUC; ++t) {
+                  if (t < nt) {
+                    const float2 tv = tr[min(d0 + j + 4 * t, nd1)];
+                    Ad[t] = fmaf(cq[m].x, tv.x, Ad[t]);
+                    Bd[t] = fmaf(cq[m].y, tv.y, Bd[t]);
+                  }
+                }
               }
             }
-          } else if (r == 0) {
 #pragma unroll
-            for (int t = 0; t < kUC; ++t) {
-              const int u = u0 + j + 4 * t;
-              if (u < NU) {
-                const int2 ab = uab[u];
-                sb[ab.x] -= bv;
-                if (ab.y >= 0) sb[ab.y] -= bv;
-              }
-            }
+            for (int t = 0; t < kUC; ++t)
+              if (t < nt) emit(d0 + j + 4 * t, Ad[t], Bd[t]);
           }
         }
       }
       __syncwarp();
 
-      // ---- normalisation over the window (values are relative to the peak)
+      // ---- normalisation over the window (values within D of the peak, relative to it; 0 beyond)
 #pragma unroll
       for (int i = 0; i < IPW; ++i) {
         float* sb = sbuf0 + i * a.sp;
+        const int p = peak[i], D = dist[i];
+        auto near = [&](int l) { return wrap || (l >= p - D && l <= p + D); };
         float mx = -INFINITY;
-        for_window([&](int l) { mx = fmaxf(mx, sb[l]); });
+        for_window([&](int l) {
+          if (near(l)) mx = fmaxf(mx, sb[l]);
+        });
         mx = warp_max(mx);
         float z = 0.f;
         for_window([&](int l) {
-          const float e = expf(sb[l] - mx);
+          const float e = near(l) ? expf(sb[l] - mx) : 0.f;
           sb[l] = e;
           z += e;
         });

@@ -312,7 +312,19 @@ __device__ double vm_A(double kappa) {
   return s1 / s0;
 }
 
-__global__ void k_fit_prior(int L, int Lw, int l0, const int* counts, int kind, double* log_prior, double* kappa_out) {
+// Grid bin of window position i: (l0 + i) mod L on the grid, else the bin nearest to step (l0 + i).
+__device__ inline int prior_bin(int L, int l0, int i, double step) {
+  long long b;
+  if (step == 1.0)
+    b = (long long)l0 + i;
+  else
+    b = (long long)floor(__dadd_rn(__dmul_rn(step, (double)(l0 + i)), 0.5));  // rounded product, then the add
+  b %= L;
+  return (int)(b < 0 ? b + L : b);
+}
+
+__global__ void k_fit_prior(int L, int Lw, int l0, double step, const int* counts, int kind, double* log_prior,
+                            double* kappa_out) {
   __shared__ double red[32];
   __shared__ double bc[2];
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -334,17 +346,9 @@ __global__ void k_fit_prior(int L, int Lw, int l0, const int* counts, int kind, 
   mc = bsum(mc);
   if (kind == 0) {
     double wsum = 0.0;
-    for (int i = tid; i < Lw; i += nt) {
-      int s = (l0 + i) % L;
-      if (s < 0) s += L;
-      wsum += (double)counts[s];
-    }
+    for (int i = tid; i < Lw; i += nt) wsum += (double)counts[prior_bin(L, l0, i, step)];
     wsum = bsum(wsum);
-    for (int i = tid; i < Lw; i += nt) {
-      int s = (l0 + i) % L;
-      if (s < 0) s += L;
-      log_prior[i] = log((double)counts[s] / wsum);
-    }
+    for (int i = tid; i < Lw; i += nt) log_prior[i] = log((double)counts[prior_bin(L, l0, i, step)] / wsum);
     if (tid == 0 && kappa_out) *kappa_out = 0.0;
     return;
   }
@@ -365,7 +369,7 @@ __global__ void k_fit_prior(int L, int Lw, int l0, const int* counts, int kind, 
   __syncthreads();
   const double kap = bc[0];
   double mx = -INFINITY;
-  for (int i = tid; i < Lw; i += nt) mx = fmax(mx, kap * cospi(2.0 * (double)(l0 + i) / (double)L));
+  for (int i = tid; i < Lw; i += nt) mx = fmax(mx, kap * cospi(2.0 * step * (double)(l0 + i) / (double)L));
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   __syncthreads();
   if ((tid & 31) == 0) red[tid >> 5] = mx;
@@ -378,10 +382,10 @@ __global__ void k_fit_prior(int L, int Lw, int l0, const int* counts, int kind, 
   __syncthreads();
   const double m = bc[1];
   double z = 0.0;
-  for (int i = tid; i < Lw; i += nt) z += exp(kap * cospi(2.0 * (double)(l0 + i) / (double)L) - m);
+  for (int i = tid; i < Lw; i += nt) z += exp(kap * cospi(2.0 * step * (double)(l0 + i) / (double)L) - m);
   z = bsum(z);
   const double lz = m + log(z);
-  for (int i = tid; i < Lw; i += nt) log_prior[i] = kap * cospi(2.0 * (double)(l0 + i) / (double)L) - lz;
+  for (int i = tid; i < Lw; i += nt) log_prior[i] = kap * cospi(2.0 * step * (double)(l0 + i) / (double)L) - lz;
   if (tid == 0 && kappa_out) *kappa_out = kap;
 }
 
@@ -568,12 +572,14 @@ MRA_API int mra_sync(const mra_dims* d, const float* y, int32_t P, int32_t n_pow
   return mra_sync_match(d, y, P, phi, shift_out, ws, ws_bytes, stream);
 }
 
-MRA_API int mra_fit_prior(int32_t L, int32_t Lw, int32_t l0, const int32_t* counts, int32_t kind,
+MRA_API int mra_fit_prior(int32_t L, int32_t Lw, int32_t l0, double step, const int32_t* counts, int32_t kind,
                           double* log_prior_out, double* kappa_out, void* stream) {
-  if (L < 1 || Lw < 1 || Lw > L || (kind != 0 && kind != 1) || !ok_ptr(counts, 4) || !ok_ptr(log_prior_out, 8))
-    return MRA_EINVAL;
+  if (step == 0.0) step = 1.0;
+  if (L < 1 || (kind != 0 && kind != 1) || !ok_ptr(counts, 4) || !ok_ptr(log_prior_out, 8)) return MRA_EINVAL;
+  if (!window_ok(L, Lw, l0, step)) return MRA_EINVAL;
   if (kappa_out && !ok_ptr(kappa_out, 8)) return MRA_EINVAL;
-  k_fit_prior<<<1, 256, 0, static_cast<cudaStream_t>(stream)>>>(L, Lw, l0, counts, kind, log_prior_out, kappa_out);
+  k_fit_prior<<<1, 256, 0, static_cast<cudaStream_t>(stream)>>>(L, Lw, l0, step, counts, kind, log_prior_out,
+                                                                kappa_out);
   return cudaGetLastError() == cudaSuccess ? MRA_OK : MRA_ECUDA;
 }
 

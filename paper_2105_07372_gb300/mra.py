@@ -37,7 +37,7 @@ class mra_dims(ctypes.Structure):
 class mra_em_params(ctypes.Structure):
     _fields_ = [("Lw", c_int32), ("l0", c_int32), ("gamma", c_double), ("log_rho_bar", c_void_p),
                 ("gamma_a_inv", c_void_p), ("update_rho", c_int32), ("tol", c_double), ("max_iters", c_int32),
-                ("check_every", c_int32), ("sweep_ms", c_void_p)]
+                ("check_every", c_int32), ("sweep_ms", c_void_p), ("step", c_double)]
 
 
 class mra_instance(ctypes.Structure):
@@ -66,8 +66,8 @@ _SIGS = {
     "mra_em_batched_workspace_bytes": (c_size_t, [POINTER(mra_instance), c_int32]),
     "mra_em_run_batched": (c_int, [POINTER(mra_instance), c_int32, c_int32, POINTER(c_int32), POINTER(ctypes.c_float),
                                    c_void_p, c_size_t, c_void_p]),
-    "mra_loglik_grad": (c_int, [POINTER(mra_dims), c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_double,
-                                c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "mra_loglik_grad": (c_int, [POINTER(mra_dims), c_int32, c_int32, c_double, c_void_p, c_void_p, c_void_p, c_void_p,
+                                c_double, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "mra_sync_workspace_bytes": (c_size_t, [POINTER(mra_dims), c_int32]),
     "mra_sync_pairwise": (c_int, [POINTER(mra_dims), c_void_p, c_int32, c_void_p, c_void_p]),
     "mra_sync_ppm": (c_int, [c_int32, c_int32, c_void_p, c_int32, c_int32, c_void_p, c_void_p]),
@@ -77,7 +77,7 @@ _SIGS = {
     "mra_align_mean": (c_int, [POINTER(mra_dims), c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "mra_prior_hist": (c_int, [POINTER(mra_dims), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                c_size_t, c_void_p]),
-    "mra_fit_prior": (c_int, [c_int32, c_int32, c_int32, c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
+    "mra_fit_prior": (c_int, [c_int32, c_int32, c_int32, c_double, c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
     "mra_relerr": (c_int, [c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
     "mra_ws_status": (c_int, [c_void_p, c_void_p]),
     "mra_selftest_wait_timeout": (c_int, [c_int32, c_void_p, c_void_p]),
@@ -140,13 +140,14 @@ def dims(N: int, K: int, Q: int, L: int, sigma2: float) -> mra_dims:
 
 def em_params(Lw: int, l0: int | None = None, gamma: float = 0.0, log_rho_bar=None, gamma_a_inv=None,
               update_rho: bool = True, tol: float = 0.0, max_iters: int = 1, check_every: int | None = None,
-              sweep_ms=None):
-    """sweep_ms: optional host ctypes float array [max_iters] that receives each sweep's device time."""
+              sweep_ms=None, step: float = 1.0):
+    """sweep_ms: optional host ctypes float array [max_iters] that receives each sweep's device time.
+    step: spacing of the window's rotations in grid units (1 = the grid, < 1 the denser window)."""
     if l0 is None:
         l0 = -(Lw // 2)
     p = mra_em_params(int(Lw), int(l0), float(gamma), _p(log_rho_bar), _p(gamma_a_inv), 1 if update_rho else 0,
                       float(tol), int(max_iters), int(check_every if check_every else max_iters),
-                      ctypes.cast(sweep_ms, c_void_p) if sweep_ms is not None else None)
+                      ctypes.cast(sweep_ms, c_void_p) if sweep_ms is not None else None, float(step))
     p._keep = (log_rho_bar, gamma_a_inv, sweep_ms)  # keep buffers alive with the struct
     return p
 
@@ -255,8 +256,9 @@ def mra_em_run_batched(arr, ws, tune=True, stream=None):
 
 
 def mra_loglik_grad(d, Lw, l0, y, shift, x, logits, kappa, loglik_out, dx_out=None, dlogits_out=None, dkappa_out=None,
-                    ws=None, stream=None):
-    _check("mra_loglik_grad", load().mra_loglik_grad(ctypes.byref(d), int(Lw), int(l0), _p(y), _p(shift), _p(x),
+                    ws=None, stream=None, step=1.0):
+    _check("mra_loglik_grad", load().mra_loglik_grad(ctypes.byref(d), int(Lw), int(l0), float(step), _p(y), _p(shift),
+                                                     _p(x),
                                                      _p(logits), float(kappa), _p(loglik_out), _p(dx_out),
                                                      _p(dlogits_out), _p(dkappa_out), _p(ws), ws.numel(),
                                                      _stream(stream)))
@@ -292,9 +294,9 @@ def mra_prior_hist(d, y, shift_true, shift_est, x_true, hist_inout, center_out=N
                                                    _stream(stream)))
 
 
-def mra_fit_prior(L, Lw, l0, counts, kind, log_prior_out, kappa_out=None, stream=None):
-    _check("mra_fit_prior", load().mra_fit_prior(int(L), int(Lw), int(l0), _p(counts), int(kind), _p(log_prior_out),
-                                                 _p(kappa_out), _stream(stream)))
+def mra_fit_prior(L, Lw, l0, counts, kind, log_prior_out, kappa_out=None, stream=None, step=1.0):
+    _check("mra_fit_prior", load().mra_fit_prior(int(L), int(Lw), int(l0), float(step), _p(counts), int(kind),
+                                                 _p(log_prior_out), _p(kappa_out), _stream(stream)))
 
 
 def mra_relerr(K, Q, x_hat, x, err_out, stream=None):

@@ -44,15 +44,17 @@ def synchronize(y, d, P, ws: Workspaces, n_power=50, n_ppm=100, stream=None) -> 
     return shift
 
 
-def learn_prior(y, d, shift_true, shift_est, x_true, Lw, l0=None, kind=0, ws: Workspaces | None = None, stream=None):
-    """One Monte-Carlo trial of Algorithm 1 on a synthetic instance whose truth is known, then the window prior."""
+def learn_prior(y, d, shift_true, shift_est, x_true, Lw, l0=None, kind=0, ws: Workspaces | None = None, stream=None,
+                step=1.0):
+    """One Monte-Carlo trial of Algorithm 1 on a synthetic instance whose truth is known, then the window prior
+    (on the window of rotations 2 pi step (l0 + i) / L)."""
     if l0 is None:
         l0 = -(Lw // 2)
     hist = torch.zeros(d.L, dtype=torch.int32, device=y.device)
     mra.mra_prior_hist(d, y, shift_true, shift_est, x_true, hist, None, ws.em, stream)
     log_prior = torch.empty(Lw, dtype=torch.float64, device=y.device)
     kappa = torch.empty(1, dtype=torch.float64, device=y.device)
-    mra.mra_fit_prior(d.L, Lw, l0, hist, kind, log_prior, kappa, stream)
+    mra.mra_fit_prior(d.L, Lw, l0, hist, kind, log_prior, kappa, stream, step=step)
     return log_prior, kappa, hist
 
 
@@ -71,15 +73,16 @@ def window_for_mass(hist: torch.Tensor, L: int, mass: float) -> int:
 
 
 def synch_em(y, d, *, P, Lw, iters, gamma, log_rho_bar, ws: Workspaces, shift=None, tol=0.0, check_every=None,
-             stats=True, x_traj=None, stream=None) -> SynchEMResult:
-    """Steps 1-4 given the learned window prior log_rho_bar [Lw] (float64 device tensor)."""
+             stats=True, x_traj=None, stream=None, l0=None, step=1.0) -> SynchEMResult:
+    """Steps 1-4 given the learned window prior log_rho_bar [Lw] (float64 device tensor); step < 1 searches
+    the denser window of rotations 2 pi step (l0 + i) / L."""
     if shift is None:
         shift = synchronize(y, d, P, ws, stream=stream)
     x = torch.empty((d.K + 1, d.Q), dtype=torch.complex128, device=y.device)
     mra.mra_align_mean(d, y, shift, x, ws.em, stream)
     log_rho = log_rho_bar.clone()
-    prm = mra.em_params(Lw, gamma=gamma, log_rho_bar=log_rho_bar, update_rho=True, tol=tol, max_iters=iters,
-                        check_every=check_every or iters)
+    prm = mra.em_params(Lw, l0=l0, gamma=gamma, log_rho_bar=log_rho_bar, update_rho=True, tol=tol, max_iters=iters,
+                        check_every=check_every or iters, step=step)
     st = torch.empty((iters, 2), dtype=torch.float64, device=y.device) if stats else None
     n = mra.mra_em_run(d, prm, y, shift, x, log_rho, st, x_traj, ws.em, stream)
     return SynchEMResult(x=x, log_rho=log_rho, shift=shift, iters=n, stats=st)
@@ -112,7 +115,7 @@ class PriorFit:
 
 
 def fit_prior_ml(y, d, Lw, x, shift=None, l0=None, kappa0=1.0, fit_logits=False, max_iter=50,
-                 ws=None) -> PriorFit:
+                 ws=None, step=1.0) -> PriorFit:
     """Von Mises prior on the window by maximum marginal likelihood at fixed x: maximise
     l(x, kappa, eta) over kappa (and the window logits eta when fit_logits) with L-BFGS, each
     evaluation one forward and one backward sweep of mra_loglik_grad through the autograd
@@ -135,12 +138,12 @@ def fit_prior_ml(y, d, Lw, x, shift=None, l0=None, kappa0=1.0, fit_logits=False,
 
     def closure():
         opt.zero_grad()
-        loss = -marginal_loglik(xd, eta, kappa, y, d, Lw, l0=l0, shift=shift, ws=ws) * scale
+        loss = -marginal_loglik(xd, eta, kappa, y, d, Lw, l0=l0, shift=shift, ws=ws, step=step) * scale
         loss.backward()
         n[0] += 1
         return loss
 
     opt.step(closure)
     with torch.no_grad():
-        ll = float(marginal_loglik(xd, eta, kappa, y, d, Lw, l0=l0, shift=shift, ws=ws).item())
+        ll = float(marginal_loglik(xd, eta, kappa, y, d, Lw, l0=l0, shift=shift, ws=ws, step=step).item())
     return PriorFit(kappa=float(kappa.item()), logits=eta.detach().clone(), loglik=ll, evals=n[0])

@@ -16,6 +16,9 @@ Recipe (one instance):
   ||I||_F^2 equals the two-sided coefficient energy |a_0|^2 + 2 sum_{k>0} |a_k|^2,
   so sigma^2 = (|x_0|^2 + 2 sum_{k>0} |x_k|^2) / (16641 SNR).
 * observation ``y_i = x o exp(-2 pi i k s_i / L) + eps_i`` (Eq. MRA_Model_FB).
+* ``offgrid=True``: continuous rotations r_i = s_i + f_i grid units with f_i uniform on
+  [-1/2, 1/2); ``s_i`` is then the nearest grid point and ``rot`` holds r_i (the
+  workload of the denser-resolution window, Sec. 3.3).
 
 The generator uses numpy's PCG64 stream seeded per instance.
 """
@@ -80,11 +83,12 @@ class Instance:
     x: np.ndarray  # complex128 [K+1, Q]
     s: np.ndarray  # int64 [N]
     y: np.ndarray  # complex128 [N, K+1, Q]
+    rot: np.ndarray | None = None  # float64 [N] exact rotations in grid units (offgrid instances)
 
 
 def make_instance(K: int, Q: int, N: int, L: int, snr: float | None = None, decay: float = 50.0,
                   seed: int = 0, sigma2: float | None = None, shifts: np.ndarray | None = None,
-                  x: np.ndarray | None = None) -> Instance:
+                  x: np.ndarray | None = None, offgrid: bool = False) -> Instance:
     """Draw one instance.  ``sigma2`` overrides ``snr``; ``sigma2 = 0`` is noise free."""
     rng = np.random.default_rng(seed)
     if x is None:
@@ -95,13 +99,16 @@ def make_instance(K: int, Q: int, N: int, L: int, snr: float | None = None, deca
         s = rng.integers(0, L, size=N).astype(np.int64)
     else:
         s = np.asarray(shifts, dtype=np.int64)
+    rot = None
+    if offgrid:
+        rot = s + rng.uniform(-0.5, 0.5, size=N)
     k = np.arange(K + 1, dtype=np.float64)
-    phase = np.exp(-2j * np.pi * np.outer(s, k) / L)  # [N, K+1]
+    phase = np.exp(-2j * np.pi * np.outer(s if rot is None else rot, k) / L)  # [N, K+1]
     y = x[None, :, :] * phase[:, :, None]
     if sigma2 > 0:
         noise = rng.standard_normal((N, K + 1, Q)) + 1j * rng.standard_normal((N, K + 1, Q))
         y = y + noise * np.sqrt(sigma2 / 2.0)
-    return Instance(K=K, Q=Q, N=N, L=L, sigma2=float(sigma2), x=x, s=s, y=y)
+    return Instance(K=K, Q=Q, N=N, L=L, sigma2=float(sigma2), x=x, s=s, y=y, rot=rot)
 
 
 def to_c64(a: np.ndarray) -> np.ndarray:

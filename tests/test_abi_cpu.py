@@ -42,7 +42,7 @@ def test_struct_layout():
 
     assert ctypes.sizeof(mra.mra_dims) == 24
     assert mra.mra_em_params.tol.offset == 40 and mra.mra_em_params.sweep_ms.offset == 56
-    assert ctypes.sizeof(mra.mra_em_params) == 64
+    assert ctypes.sizeof(mra.mra_em_params) == 72
 
 
 def test_struct_layout_matches_the_c_compiler(tmp_path):

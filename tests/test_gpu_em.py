@@ -261,3 +261,15 @@ def test_errors_are_status_codes(gpu_lib):
     assert e.value.status == -1
     with pytest.raises(mra.MraError):
         mra.mra_em_step(mra.dims(10, 2, 3, 8, 0.1), mra.em_params(4), y, None, x, lr, x, lr, ws=ws)  # M odd
+
+
+@pytest.mark.parametrize("snr", [1 / 50, 1 / 20, 1 / 10])
+@pytest.mark.parametrize("K,Q,N,L,Lw", [(32, 24, 2000, 360, 37), (12, 16, 1500, 90, 31), (6, 6, 1200, 60, 21)])
+def test_em_step_weights_across_snr(gpu_lib, sweep, snr, K, Q, N, L, Lw):
+    """Weights within 1e-5 where the posterior is spread over a few rotations and 2 beta |c| is in the
+    thousands: log-weights of that size lose the precision in plain FP32 sums, which the sweeps avoid by
+    recomputing the values near each image's peak from peak-relative terms (rows of Q = 6 take the tile
+    sweep, which forms them in FP64)."""
+    inst = synth.make_instance(K, Q, N, L, snr, 400.0 if K > 20 else 50.0, seed=3100 + K)
+    x0 = O.align_mean(synth.c64_round(inst.y), inst.s, inst.L)
+    compare(gpu_lib, inst, x0, np.log(np.full(Lw, 1 / Lw)), Lw, shifts=inst.s)
