@@ -40,11 +40,27 @@ METRIC = "EM image-rotation evals/s"
 UNIT = "evals/s"
 
 
+def dense_config():
+    """The denser-resolution window of Sec. 3.3 on the Synch-EM workload: the range [-pi BW/L, pi BW/L]
+    (BW = 36) sampled at spacing pi BW/L^2, i.e. Lw = 2 L + 1 rotations 0.05 grid units apart, on images
+    whose rotations are continuous (off the grid)."""
+    c = synth.config(CFG)
+    c.update(Lw=2 * c["L"] + 1, l0=-c["L"], step=36 / (2 * c["L"]), offgrid=True)
+    return c
+
+
 def workload_config(c):
-    return {"workload": f"Synch-EM |k|<={c['K']} Q={c['Q']} N={c['N']} L={c['L']} Lw={c['Lw']} "
-                        f"SNR=1/{round(1 / c['snr'])} T={c['iters']} P={c['P']} gamma={c['gamma']}",
-            "K": c["K"], "Q": c["Q"], "N": c["N"], "L": c["L"], "Lw": c["Lw"], "iters": c["iters"], "P": c["P"],
-            "snr": c["snr"], "l2": "inputs larger than L2 (y is 633.6 MB per sweep)"}
+    dense = c.get("step", 1.0) != 1.0
+    name = "Synch-EM dense window" if dense else "Synch-EM"
+    w = (f"Lw={c['Lw']} step={c['step']:g} (range {(c['Lw'] - 1) * c['step']:g} grid units, off-grid rotations)"
+         if dense else f"Lw={c['Lw']}")
+    out = {"workload": f"{name} |k|<={c['K']} Q={c['Q']} N={c['N']} L={c['L']} {w} "
+                       f"SNR=1/{round(1 / c['snr'])} T={c['iters']} P={c['P']} gamma={c['gamma']}",
+           "K": c["K"], "Q": c["Q"], "N": c["N"], "L": c["L"], "Lw": c["Lw"], "iters": c["iters"], "P": c["P"],
+           "snr": c["snr"], "l2": "inputs larger than L2 (y is 633.6 MB per sweep)"}
+    if dense:
+        out.update(step=c["step"], l0=c["l0"])
+    return out
 
 
 def peaks():
@@ -54,6 +70,12 @@ def peaks():
         return float(p["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def fp32_alu_peak_tflops():
+    """FP32 CUDA-core peak of a GB300 from its unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop (FMA)
+    x 2.07 GHz maximum SM clock."""
+    return 152 * 128 * 2 * 2.07e9 / 1e12
 
 
 def traffic_kernel():
@@ -153,7 +175,7 @@ def oracle_sample(inst, c, n_img, iters):
     lr = np.log(np.full(Lw, 1.0 / Lw))
     t0 = time.perf_counter()
     for _ in range(iters):
-        st = O.em_step(y64, x, lr, inst.L, inst.sigma2, Lw=Lw, shifts=s)
+        st = O.em_step(y64, x, lr, inst.L, inst.sigma2, Lw=Lw, shifts=s, l0=c.get("l0"), step=c.get("step", 1.0))
         x, lr = st.x, st.log_rho
     dt = time.perf_counter() - t0
     return n_img * Lw * iters / dt, dt
@@ -163,8 +185,9 @@ def run_reference(args, c):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    inst = synth.make_instance(c["K"], c["Q"], 6000, c["L"], c["snr"], c["decay"], seed=1000 * CFG)
-    n_img = 1500
+    inst = synth.make_instance(c["K"], c["Q"], 6000, c["L"], c["snr"], c["decay"], seed=1000 * CFG,
+                               offgrid=c.get("offgrid", False))
+    n_img = 1500 if c["Lw"] <= 64 else max(100, 1500 * 37 // c["Lw"])
     for _ in range(args.warmup):
         oracle_sample(inst, c, 200, 1)
     vals = []
@@ -193,16 +216,17 @@ def main():
     ap.add_argument("--impl", default="gpu")
     ap.add_argument("--no-ttc", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--config", type=int, default=CFG, choices=(2, 4, 5),
+    ap.add_argument("--config", default=str(CFG), choices=("2", "4", "5", "dense"),
                     help="2: Synch-EM at N=1e5 (default); 4: 64 uneven instances in one graph launch; "
-                         "5: N=1e6 with y in the BF16 hi/lo split")
+                         "5: N=1e6 with y in the BF16 hi/lo split; dense: the workload of 2 with the "
+                         "denser-resolution window (2L+1 rotations over BW = 36) on off-grid rotations")
     args = ap.parse_args()
-    c = synth.config(CFG)
+    c = dense_config() if args.config == "dense" else synth.config(CFG)
     if args.impl == "reference":
         return run_reference(args, c)
-    if args.config == 4:
+    if args.config == "4":
         return bench_batched(args)
-    if args.config == 5:
+    if args.config == "5":
         return bench_bf16(args)
 
     import torch
@@ -220,7 +244,8 @@ def main():
     mra.load()
 
     # ---- inputs resident in HBM (each rank its own independent instance: replicas)
-    inst = synth.make_instance(c["K"], c["Q"], c["N"], c["L"], c["snr"], c["decay"], seed=replica_seed(rank))
+    inst = synth.make_instance(c["K"], c["Q"], c["N"], c["L"], c["snr"], c["decay"], seed=replica_seed(rank),
+                               offgrid=c.get("offgrid", False))
     y_host = torch.from_numpy(synth.to_c64(inst.y)).pin_memory()
     y = y_host.to(dev)
     s_true = torch.from_numpy(inst.s.astype(np.int32)).to(dev)
@@ -228,7 +253,8 @@ def main():
     N, K, Q, L, Lw, T, P = c["N"], c["K"], c["Q"], c["L"], c["Lw"], c["iters"], c["P"]
     d = mra.dims(N, K, Q, L, inst.sigma2)
     ws = pipeline.workspaces(d, Lw, P, dev)
-    l0 = -(Lw // 2)
+    l0 = c.get("l0", -(Lw // 2))
+    wstep = c.get("step", 1.0)
     shift = torch.empty(N, dtype=torch.int32, device=dev)
     hist = torch.zeros(L, dtype=torch.int32, device=dev)
     log_prior = torch.empty(Lw, dtype=torch.float64, device=dev)
@@ -243,11 +269,11 @@ def main():
         mra.mra_sync(d, y, P, 50, 100, shift, ws.sync)
         hist.zero_()
         mra.mra_prior_hist(d, y, s_true, shift, x_true, hist, None, ws.em)
-        mra.mra_fit_prior(L, Lw, l0, hist, 0, log_prior, kappa)
+        mra.mra_fit_prior(L, Lw, l0, hist, 0, log_prior, kappa, step=wstep)
         mra.mra_align_mean(d, y, shift, x, ws.em)
         log_rho.copy_(log_prior)
         prm = mra.em_params(Lw, l0=l0, gamma=c["gamma"], log_rho_bar=log_prior, max_iters=T,
-                            sweep_ms=sweep_ms if timed_sweeps else None)
+                            sweep_ms=sweep_ms if timed_sweeps else None, step=wstep)
         n = mra.mra_em_run(d, prm, y, shift, x, log_rho, stats, None, ws.em)
         if timed_sweeps:
             sweep_times.extend(list(sweep_ms)[:n])
@@ -263,8 +289,8 @@ def main():
     mra.mra_sync(d, y, P, 50, 100, shift, ws.sync)
     mra.mra_align_mean(d, y, shift, x, ws.em)
     log_rho.copy_(log_prior)
-    tuned = mra.mra_em_autotune(d, mra.em_params(Lw, l0=l0, gamma=c["gamma"], log_rho_bar=log_prior), y, shift, x,
-                                log_rho, ws.em)
+    tuned = mra.mra_em_autotune(d, mra.em_params(Lw, l0=l0, gamma=c["gamma"], log_rho_bar=log_prior, step=wstep), y,
+                                shift, x, log_rho, ws.em)
     torch.cuda.synchronize()
 
     def barrier():
@@ -287,18 +313,31 @@ def main():
     evals_per_step = N * Lw * T
     value = whole_job_value(world, evals_per_step, ms)
 
-    # ---- roofline of the dominant kernel (the EM sweep): algorithmic bytes = one read of y
+    # ---- roofline of the dominant kernel (the EM sweep): algorithmic bytes = one read of y; algorithmic
+    # FP32 flops per image = 8 M (correlation) + 4 Lw (K+1) (window transform) + 4 Lw (K+1) (back
+    # transform) + 8 M (accumulation).  The bound is whichever takes longer at its peak: HBM for the
+    # 36-rotation window, FP32 ALU for the 721-rotation dense window.
     bytes_per_sweep = N * (K + 1) * Q * 8
+    flops_per_sweep = N * (16 * (K + 1) * Q + 8 * Lw * (K + 1))
     avg_sweep_s = float(np.mean(sweep_times)) / 1e3
-    achieved = bytes_per_sweep / avg_sweep_s / 1e9
     peak, peak_kind = peaks()
+    alu_peak = fp32_alu_peak_tflops()
     traffic = traffic_for()
     kernel = {1: "k_sweep_v2", 2: "k_sweep_v3", 3: "k_sweep_v4"}.get(tuned[0], "k_em_sweep")
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic if kernel == traffic_kernel() else None, "peak_source": f"{peak_kind} hbm_gbs",
+    hbm_side = {"achieved": bytes_per_sweep / avg_sweep_s / 1e9, "peak": peak, "unit": "GB/s"}
+    alu_side = {"achieved": flops_per_sweep / avg_sweep_s / 1e12, "peak": alu_peak, "unit": "TFLOP/s"}
+    hbm_bound = bytes_per_sweep / (peak * 1e9) >= flops_per_sweep / (alu_peak * 1e12)
+    dom = hbm_side if hbm_bound else alu_side
+    roofline = {"bound": "hbm" if hbm_bound else "alu", "achieved": dom["achieved"], "peak": dom["peak"],
+                "unit": dom["unit"], "frac": dom["achieved"] / dom["peak"],
+                "traffic": traffic if kernel == traffic_kernel() and wstep == 1.0 else None,
+                "peak_source": f"{peak_kind} hbm_gbs" if hbm_bound else
+                               "derived FP32 CUDA-core peak: 152 SMs x 128 FMA/clk x 2 flop x 2.07 GHz",
+                "other": ({"bound": "alu", **alu_side, "frac": alu_side["achieved"] / alu_peak} if hbm_bound else
+                          {"bound": "hbm", **hbm_side, "frac": hbm_side["achieved"] / peak}),
                 "kernel": kernel, "sweep_choice": {"kind": tuned[0], "batch": tuned[1], "stages_or_ctas": tuned[2]},
-                "algorithmic_bytes_per_launch": bytes_per_sweep, "avg_launch_ms": avg_sweep_s * 1e3,
-                "launches_timed": len(sweep_times)}
+                "algorithmic_bytes_per_launch": bytes_per_sweep, "algorithmic_flops_per_launch": flops_per_sweep,
+                "avg_launch_ms": avg_sweep_s * 1e3, "launches_timed": len(sweep_times)}
     em_ms = float(np.sum(sweep_times)) / args.steps
 
     # ---- end to end through the public API with host buffers (H2D of the step's inputs, D2H of its result)
@@ -332,13 +371,13 @@ def main():
 
     # ---- time to converge against full-search EM at equal error (same GPU, same instance)
     ttc = None
-    if not args.no_ttc and rank == 0:
+    if not args.no_ttc and rank == 0 and wstep == 1.0:
         ttc = time_to_converge(mra, pipeline, c, inst, d, y, s_true, x_true, ws, dev)
 
     # ---- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        n_img, iters = 4000, 3
+        n_img, iters = (4000, 3) if Lw <= 64 else (max(200, 4000 * 37 // Lw), 2)
         v, dt = oracle_sample(inst, c, n_img, iters)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"oracle em_step (FP64 numpy) on {n_img} of the {N} images, {iters} iterations, "

@@ -1026,9 +1026,9 @@ struct V2Plan {
   int off_ring, off_x, off_tu, off_tf, off_lr, off_units, off_s, off_wl;
 };
 
-// Shared-memory plan of the warp-streaming sweep: each warp carries ipw images
-// (2 when the window fits one unit chunk) in a two-stage ring; as many warps as
-// fit, at least enough that the ring can hold every warp's sums at the end.
+// Shared-memory plan of the warp-streaming sweep: each warp carries one image per stage of a
+// two-stage ring; as many warps as fit, at least enough that the ring can hold every warp's
+// sums at the end.
 bool plan_v2(int Kp1, int Q, int L, int Lw, int nup, int max_smem, V2Plan* p) {
   if (Q % 8 != 0 || Q / 8 > 4) return false;
   const int QV = Q / 8, MR = (Kp1 + 7) / 8;
@@ -1036,8 +1036,10 @@ bool plan_v2(int Kp1, int Q, int L, int Lw, int nup, int max_smem, V2Plan* p) {
   const int M = Kp1 * Q;
   const int slot = al16(M * 8);
   const int sp = (Lw + 3) & ~3;
-  for (int ipw = 1; ipw >= 1; --ipw) {  // two images per warp measured slower (fewer resident warps)
-    const int lwc = nup != kUnitChunk ? 0 : Lw <= 32 ? 1 : Lw <= 64 ? 2 : 0;  // one unit chunk: fixed loops
+  const int ipw = 1;  // two images per warp measured slower (fewer resident warps)
+  const int lwc0 = nup != kUnitChunk ? 0 : Lw <= 32 ? 1 : Lw <= 64 ? 2 : 0;  // one unit chunk: fixed loops
+  // a window whose unit table does not fit next to the rings reads it from global memory (lwc -1)
+  for (int lwc : {lwc0, lwc0 == 0 ? -1 : lwc0}) {
     SweepV2Launch ln = QV == 1 ? sweep_v2_q1(MR, ipw, lwc) : QV == 2 ? sweep_v2_q2(MR, ipw, lwc)
                      : QV == 3 ? sweep_v2_q3(MR, ipw, lwc) : sweep_v2_q4(MR, ipw, lwc);
     if (!ln.fn) continue;
@@ -1046,7 +1048,7 @@ bool plan_v2(int Kp1, int Q, int L, int Lw, int nup, int max_smem, V2Plan* p) {
       int o = al16(2 * maxw * 8);
       p->off_ring = o; o += 2 * ipw * nw * slot;
       p->off_x = o; o += al16(M * 8);
-      p->off_tu = o; o += al16(Kp1 * nup * 8);
+      p->off_tu = o; o += lwc >= 0 ? al16(Kp1 * nup * 8) : 0;
       p->off_tf = o; o += al16(L * 8);
       p->off_lr = o; o += al16(Lw * 4);
       p->off_units = o; o += al16(nup * 8);

@@ -44,8 +44,10 @@ __device__ __forceinline__ int mod_small(int a, int L, float invL) {
 }
 
 // LWC: lane-strided passes over the window (ceil(Lw / 32)) fixed at compile time (1 or 2) for a
-// window of one unit chunk (the unit table is then 4 kUC wide), or 0 for any window; the fixed
-// counts let the per-image loops over the window and its units unroll.
+// window of one unit chunk; 0 for any window; -1 for any window with the unit twiddle table read
+// from global memory (windows whose table does not fit in shared memory next to the rings).
+// The fixed counts let the per-image loops over the window and its units unroll (the unit
+// table is then 4 kUC wide).
 template <int QV, int MR, int IPW, int LWC>
 __global__ void __launch_bounds__(SweepV2Shape<QV, MR, IPW>::kThreads, 1) k_sweep_v2(const SweepV2Args a) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -76,7 +78,7 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR, IPW>::kThreads, 1) k_swee
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);  // [NT/32][2]
   unsigned char* ring = smem + a.off_ring;            // [nwarps][2][IPW][slot]
   const float4* xs4 = reinterpret_cast<const float4*>(smem + a.off_x);
-  const float2* tus = reinterpret_cast<const float2*>(smem + a.off_tu);  // [Kp1][NUP]
+  const float2* tus = LWC >= 0 ? reinterpret_cast<const float2*>(smem + a.off_tu) : a.tu;  // [Kp1][NUP]
   const float2* tfs = reinterpret_cast<const float2*>(smem + a.off_tf);  // [L]
   const float* lrs = reinterpret_cast<const float*>(smem + a.off_lr);    // [Lw]
   const int2* uab = reinterpret_cast<const int2*>(smem + a.off_units);   // [NUP] (a, b) window indices, b < 0: single
@@ -88,8 +90,10 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR, IPW>::kThreads, 1) k_swee
     float4* x4w = reinterpret_cast<float4*>(smem + a.off_x);
     const float4* xg = reinterpret_cast<const float4*>(a.x32);
     for (int i = tid; i < M / 2; i += NT) x4w[i] = xg[i];
-    float2* tuw = reinterpret_cast<float2*>(smem + a.off_tu);
-    for (int i = tid; i < Kp1 * NUP; i += NT) tuw[i] = a.tu[i];
+    if constexpr (LWC >= 0) {
+      float2* tuw = reinterpret_cast<float2*>(smem + a.off_tu);
+      for (int i = tid; i < Kp1 * NUP; i += NT) tuw[i] = a.tu[i];
+    }
     float2* tfw = reinterpret_cast<float2*>(smem + a.off_tf);
     for (int i = tid; i < L; i += NT) tfw[i] = a.tf32[i];
     float* lrw = reinterpret_cast<float*>(smem + a.off_lr);
@@ -613,13 +617,15 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR, IPW>::kThreads, 1) k_swee
 }  // namespace mra
 
 // Instantiation table for one row width QV: MR = 1..7 rows per quad, one image per warp
-// (two images per warp measured slower and are not built), window passes lwc = 1, 2 or any (0).
+// (two images per warp measured slower and are not built), window passes lwc = 1, 2 or any (0;
+// -1 with the unit table in global memory).
 #define MRA_SWEEP_V2_CASE(QV, MR)                                                                       \
   case MR:                                                                                              \
     if (ipw != 1) return SweepV2Launch{nullptr, 0};                                                     \
-    return lwc == 1 ? SweepV2Launch{k_sweep_v2<QV, MR, 1, 1>, SweepV2Shape<QV, MR, 1>::kThreads}        \
-         : lwc == 2 ? SweepV2Launch{k_sweep_v2<QV, MR, 1, 2>, SweepV2Shape<QV, MR, 1>::kThreads}        \
-                    : SweepV2Launch{k_sweep_v2<QV, MR, 1, 0>, SweepV2Shape<QV, MR, 1>::kThreads};
+    return lwc == 1  ? SweepV2Launch{k_sweep_v2<QV, MR, 1, 1>, SweepV2Shape<QV, MR, 1>::kThreads}       \
+         : lwc == 2  ? SweepV2Launch{k_sweep_v2<QV, MR, 1, 2>, SweepV2Shape<QV, MR, 1>::kThreads}       \
+         : lwc == -1 ? SweepV2Launch{k_sweep_v2<QV, MR, 1, -1>, SweepV2Shape<QV, MR, 1>::kThreads}      \
+                     : SweepV2Launch{k_sweep_v2<QV, MR, 1, 0>, SweepV2Shape<QV, MR, 1>::kThreads};
 #define MRA_SWEEP_V2_TABLE(QV)                              \
   namespace mra {                                          \
   SweepV2Launch sweep_v2_q##QV(int MR, int ipw, int lwc) { \

@@ -9,6 +9,10 @@ window width, signal prior) on one device, through the library's calls only.
                      relative error and iterations of Synch-EM and full-search EM for the
                      decay parameter of Gamma_a = diag((4 e^{-k/beta})^2) (Sec. 4,
                      "Performance with signal prior"), and without a signal prior
+    dense_study      relative error of Synch-EM on images with continuous (off-grid) rotations
+                     for the grid window and the denser-resolution window (Sec. 3.3): the
+                     same number of rotations over a narrower range, or the same range at a
+                     finer spacing
 
 Each trial draws a fresh instance (observation model of Eq. MRA_Model_FB), runs
 Synchronize and Match, learns the window prior from one trial of Algorithm 1 on the
@@ -16,7 +20,7 @@ same instance (its rotations are known, as in the paper's Monte-Carlo learning) 
 runs EM to tol = 1e-5 or T iterations.  The paper's BW = 2 h corresponds to the window
 Lw = BW + 1 (offsets -h .. h).  Results are means over trials.
 
-    python -m paper_2105_07372_gb300.experiments gamma|bw|prior [--n N] [--trials R]
+    python -m paper_2105_07372_gb300.experiments gamma|bw|prior|dense [--n N] [--trials R]
 """
 from __future__ import annotations
 
@@ -30,10 +34,10 @@ import torch
 from . import mra, pipeline
 
 
-def _instance(K, Q, N, L, snr, decay, seed, dev):
+def _instance(K, Q, N, L, snr, decay, seed, dev, offgrid=False):
     import synth  # the seeded generator of the observation model (data only)
 
-    inst = synth.make_instance(K, Q, N, L, snr, decay, seed=seed)
+    inst = synth.make_instance(K, Q, N, L, snr, decay, seed=seed, offgrid=offgrid)
     y = torch.from_numpy(synth.to_c64(inst.y)).to(dev)
     return inst, y, torch.from_numpy(inst.s.astype(np.int32)).to(dev), torch.from_numpy(inst.x).to(dev)
 
@@ -44,17 +48,20 @@ def gamma_inv(K, Q, beta, dev):
     return torch.from_numpy((1.0 / (4.0 * np.exp(-k / beta)) ** 2).ravel()).to(dev)
 
 
-def synch_em_trial(y, s_true, x_true, d, *, Lw, gamma, P=100, tol=1e-5, T=1000, gamma_a_inv=None, ws=None):
-    """Synchronize and Match, one trial of Algorithm 1, Synch-EM to tol: (iterations, relative error)."""
+def synch_em_trial(y, s_true, x_true, d, *, Lw, gamma, P=100, tol=1e-5, T=1000, gamma_a_inv=None, ws=None,
+                   step=1.0, shift=None):
+    """Synchronize and Match, one trial of Algorithm 1, Synch-EM to tol: (iterations, relative error).
+    step < 1: the denser window of Lw rotations step grid units apart; shift: reuse a synchronization."""
     if ws is None:
         ws = pipeline.workspaces(d, Lw, P, y.device)
-    shift = pipeline.synchronize(y, d, P, ws)
-    log_prior, _, _ = pipeline.learn_prior(y, d, s_true, shift, x_true, Lw, -(Lw // 2), 0, ws)
+    if shift is None:
+        shift = pipeline.synchronize(y, d, P, ws)
+    log_prior, _, _ = pipeline.learn_prior(y, d, s_true, shift, x_true, Lw, -(Lw // 2), 0, ws, step=step)
     x = torch.empty((d.K + 1, d.Q), dtype=torch.complex128, device=y.device)
     mra.mra_align_mean(d, y, shift, x, ws.em)
     log_rho = log_prior.clone()
     prm = mra.em_params(Lw, gamma=gamma, log_rho_bar=log_prior, gamma_a_inv=gamma_a_inv, tol=tol, max_iters=T,
-                        check_every=25)
+                        check_every=25, step=step)
     n = mra.mra_em_run(d, prm, y, shift, x, log_rho, None, None, ws.em)
     return n, pipeline.relerr(x, x_true, d)
 
@@ -127,9 +134,32 @@ def signal_prior_study(snrs=(1 / 20, 1 / 50), betas=(None, 4.0, 8.0, 16.0), *, K
     return out
 
 
+def dense_study(snrs=(1 / 5, 1 / 20, 1 / 50), *, K=32, Q=24, N=10000, L=360, trials=2, decay=400.0,
+                windows=((37, 1.0), (37, 0.25), (145, 0.25)), gamma=100.0, seed=8000, dev="cuda"):
+    """Images rotated by continuous angles (off the grid).  For each window (Lw, step): relative error and
+    iterations of Synch-EM from one shared synchronization per trial; (37, 1) is the grid window BW = 36,
+    (37, 1/4) the same number of rotations over a quarter of the range, (145, 1/4) the same range at a
+    quarter of the spacing."""
+    out = []
+    for si, snr in enumerate(snrs):
+        acc = {w: [] for w in windows}
+        for t in range(trials):
+            inst, y, s, x = _instance(K, Q, N, L, snr, decay, seed + 100 * si + t, dev, offgrid=True)
+            d = mra.dims(N, K, Q, L, inst.sigma2)
+            ws = pipeline.workspaces(d, max(w[0] for w in windows), 100, dev)
+            shift = pipeline.synchronize(y, d, 100, ws)
+            for (Lw, step) in windows:
+                acc[(Lw, step)].append(synch_em_trial(y, s, x, d, Lw=Lw, gamma=gamma, ws=ws, step=step, shift=shift))
+        for (Lw, step) in windows:
+            r = acc[(Lw, step)]
+            out.append({"snr": snr, "Lw": Lw, "step": step, "range_grid_units": (Lw - 1) * step,
+                        "iters": float(np.mean([v[0] for v in r])), "relerr": float(np.mean([v[1] for v in r]))})
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("study", choices=("gamma", "bw", "prior"))
+    ap.add_argument("study", choices=("gamma", "bw", "prior", "dense"))
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--trials", type=int, default=None)
     a = ap.parse_args()
@@ -139,7 +169,7 @@ def main():
     if a.trials:
         kw["trials"] = a.trials
     mra.load()
-    fn = {"gamma": gamma_study, "bw": bw_study, "prior": signal_prior_study}[a.study]
+    fn = {"gamma": gamma_study, "bw": bw_study, "prior": signal_prior_study, "dense": dense_study}[a.study]
     for row in fn(**kw):
         print(json.dumps(row), flush=True)
 

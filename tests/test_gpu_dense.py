@@ -72,6 +72,18 @@ def test_dense_em_step_matches_oracle(gpu_lib, sweep, K, Q, N, L, Lw, l0, step):
     _compare(gpu_lib, inst, x0, lr, Lw, l0, step, shifts=inst.s)
 
 
+def test_dense_paper_example_window_full_workload_shape(gpu_lib):
+    """The paper's example of the denser window at the Synch-EM workload's shape: the range
+    [-pi BW/L, pi BW/L] with BW = 36 at spacing pi BW/L^2 (Lw = 2 L + 1 = 721 rotations 0.05 grid units
+    apart, |k| <= 32, Q = 24, L = 360).  Its unit twiddle table does not fit in shared memory next to the
+    image rings, so the warp sweep reads it from global memory."""
+    K, Q, L = 32, 24, 360
+    inst = synth.make_instance(K, Q, 300, L, snr=1 / 50, decay=400.0, seed=8150, offgrid=True)
+    x0 = O.align_mean(synth.c64_round(inst.y), inst.s, inst.L)
+    Lw = 2 * L + 1
+    _compare(gpu_lib, inst, x0, np.log(np.full(Lw, 1 / Lw)), Lw, -L, 36 / (2 * L), shifts=inst.s)
+
+
 def test_dense_em_step_tile_sweep_odd_rows(gpu_lib):
     """Rows of Q = 6 (not a multiple of 8) take the tile sweep and its window twiddle table."""
     inst = synth.make_instance(5, 6, 800, 40, snr=1 / 3, decay=20.0, seed=8200, offgrid=True)

@@ -38,3 +38,14 @@ def test_flat_signal_prior_limit(gpu_lib):
     n0, e0 = E.synch_em_trial(y, s, x, d, Lw=13, gamma=10.0, T=20)
     n1, e1 = E.synch_em_trial(y, s, x, d, Lw=13, gamma=10.0, T=20, gamma_a_inv=zero)
     assert n0 == n1 and math.isclose(e0, e1, rel_tol=1e-12, abs_tol=1e-15)
+
+
+def test_dense_study_runs_and_finer_spacing_does_not_hurt(gpu_lib):
+    """Off-grid rotations at a high SNR: the window of the same range at a quarter of the spacing holds the grid
+    window's rotations among others, so its error cannot be much larger (it is expected to be smaller)."""
+    from paper_2105_07372_gb300 import experiments as E
+
+    r = E.dense_study(snrs=(1 / 5,), N=2000, trials=1, windows=((37, 1.0), (145, 0.25)))
+    err = {(v["Lw"], v["step"]): v["relerr"] for v in r}
+    assert all(0 < e < 1 for e in err.values())
+    assert err[(145, 0.25)] <= err[(37, 1.0)] + 0.005, err
