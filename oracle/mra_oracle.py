@@ -18,6 +18,8 @@ its own order and notation:
 * rho update (W + gamma rho_bar) / sum(W + gamma rho_bar)              Algorithm "Synch-EM", App. C
 * convergence min_l ||a_{t+1} - e^{-2 pi i kbar l/L} o a_t||^2 < tol    Algorithm "Synch-EM"
 * Synchronize and Match                                               Algorithm "Synchronize and Match"
+* template matching: every image against one reference, O(NLM)        Sec. 2.1.1 (template matching)
+* shift pmf of 1-D template matching with the true signal as reference App. B, Eq. (shift_pmf)
 * learned rotation distribution, centred by theta_c                    Eq. (learned_distribution_formula), Algorithm 1
 * relative error up to rotation                                       Sec. 2.2, relative-error equation
 * likelihood with the (pi sigma^2)^{-M} factor                          Sec. 2.2, likelihood equation
@@ -340,6 +342,44 @@ def synchronize_and_match(y: np.ndarray, P: int, L: int, n_power: int = 50, n_pp
     rel = pairwise_relative(y[:P], L)
     phi = ppm(rel, L, n_power, n_ppm)
     return match(y, P, phi), phi, rel
+
+
+def template_match(y: np.ndarray, ref: np.ndarray, L: int, chunk: int = 16) -> np.ndarray:
+    """Template matching (Sec. 2.1.1): s_j = argmin over the grid of sum_{k,q} |ref - e^{i k theta} v^j|^2,
+    each image against the one reference (the relative rotation of Eq. relative_angle_2d_dist)."""
+    y = np.asarray(y, dtype=np.complex128)
+    ref = np.asarray(ref, dtype=np.complex128)
+    ph = np.exp(1j * np.outer(grid_angle(np.arange(L), L), kbar(y.shape[1] - 1)))  # e^{+i k theta_l} [L, K+1]
+    out = np.empty(y.shape[0], dtype=np.int64)
+    for a in range(0, y.shape[0], chunk):
+        rv = y[a:a + chunk, None, :, :] * ph[None, :, :, None]  # [n, L, K+1, Q]
+        diff = ref[None, None] - rv
+        d = np.sum(diff.real ** 2 + diff.imag ** 2, axis=(2, 3))
+        out[a:a + chunk] = np.argmin(d, axis=1)
+    return out
+
+
+def tm_shift_pmf(x: np.ndarray, sigma: float) -> np.ndarray:
+    """App. B, Eq. (shift_pmf): the approximate pmf of the shift that 1-D template matching with the true
+    signal x as reference estimates for zero-shift observations y ~ N(x, sigma^2 I):
+    p[m] = int N(u; R_xx[m], sigma_c^2) prod_{l != m} Phi((u - R_xx[l]) / sigma_c) du,
+    R_xx[l] = sum_n x[n] x[(n + l) mod L], sigma_c^2 = sigma^2 ||x||^2 (the correlations taken independent)."""
+    from scipy import integrate, stats
+
+    x = np.asarray(x, dtype=np.float64)
+    L = x.size
+    R = np.array([np.dot(x, np.roll(x, -l)) for l in range(L)])  # R[l] = sum_n x[n] x[n + l]
+    sc = float(sigma) * float(np.linalg.norm(x))
+    p = np.empty(L)
+    for m in range(L):
+        others = np.delete(R, m)
+
+        def f(u, m=m, others=others):
+            return stats.norm.pdf(u, R[m], sc) * np.prod(stats.norm.cdf((u - others) / sc))
+
+        lo, hi = R.min() - 12 * sc, R.max() + 12 * sc
+        p[m] = integrate.quad(f, lo, hi, points=sorted(set(R.tolist())), limit=400, epsabs=1e-13, epsrel=1e-11)[0]
+    return p
 
 
 def align_mean(y: np.ndarray, shifts: np.ndarray, L: int) -> np.ndarray:

@@ -21,3 +21,4 @@ from .instances import (  # noqa: F401
     bf16_merge,
     config4_instances,
 )
+from .mra1d import Instance1D, coeffs_1d, make_instance_1d, sigma2_coeff, signal_1d  # noqa: F401,E402

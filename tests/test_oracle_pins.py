@@ -495,3 +495,66 @@ def test_dense_loglik_gradient_central_differences():
     g = (O.loglik(inst.y, x, eta, kappa + h, L, inst.sigma2, **kw)
          - O.loglik(inst.y, x, eta, kappa - h, L, inst.sigma2, **kw)) / (2 * h)
     assert abs(g - dk) <= 1e-6 * max(1.0, abs(dk))
+
+
+# --------------------------------------------------------------------------- template matching, 1-D MRA, App. B
+def test_template_match_noise_free_and_sign():
+    """Images that are the reference rotated by s_j come back with s_j (the sign of the relative rotation)."""
+    K, Q, L = 6, 3, 40
+    ref = synth.make_signal(K, Q, 20.0, np.random.default_rng(21))
+    s = np.random.default_rng(22).integers(0, L, 25)
+    y = np.stack([O.rotate(ref, 2 * np.pi * sj / L) for sj in s])
+    np.testing.assert_array_equal(O.template_match(y, ref, L), s)
+
+
+def test_1d_coefficient_form_preserves_distances_and_shifts():
+    """Parseval in the coefficient form of synth.mra1d: ||roll(x, s) - v||^2 in signal space equals the stored-entry
+    distance after rotating the coefficients by 2 pi s / L, for every s."""
+    rng = np.random.default_rng(5)
+    L = 21
+    x, v = rng.standard_normal(L), rng.standard_normal(L)
+    ax, av = synth.coeffs_1d(x), synth.coeffs_1d(v)
+    for s in range(L):
+        d_sig = float(np.sum((np.roll(x, s) - v) ** 2))
+        diff = O.rotate(ax, 2 * np.pi * s / L) - av
+        assert abs(d_sig - float(np.sum(np.abs(diff) ** 2))) < 1e-10 * max(1.0, d_sig)
+    np.testing.assert_allclose(synth.signal_1d(ax, L), x, atol=1e-13)
+
+
+def test_template_match_1d_against_signal_space_brute_force():
+    """Template matching in the coefficient form equals argmin_l ||ref - roll(v_j, -l)||^2 in signal space."""
+    inst = synth.make_instance_1d(21, 200, 1.5, seed=9)
+    ref = inst.v[0]
+    want = np.array([int(np.argmin([np.sum((ref - np.roll(vj, -l)) ** 2) for l in range(21)])) for vj in inst.v])
+    got = O.template_match(synth.coeffs_1d(inst.v), synth.coeffs_1d(ref), 21)
+    np.testing.assert_array_equal(got, want)
+
+
+def test_tm_shift_pmf_two_point_closed_form():
+    """L = 2: p[0] = P(A_0 > A_1) = Phi((R[0] - R[1]) / (sqrt 2 sigma_c)) for the independent model."""
+    from scipy import stats
+
+    x = np.array([1.3, -0.4])
+    sigma = 0.8
+    R0, R1 = float(x @ x), 2 * x[0] * x[1]
+    sc = sigma * np.linalg.norm(x)
+    p = O.tm_shift_pmf(x, sigma)
+    assert abs(p[0] - stats.norm.cdf((R0 - R1) / (np.sqrt(2) * sc))) < 1e-9
+    assert abs(p.sum() - 1.0) < 1e-9
+
+
+def test_tm_shift_pmf_against_monte_carlo_of_its_model():
+    """The pmf integral against argmax frequencies of independent N(R_xx[l], sigma_c^2) draws (the model App. B
+    integrates), and its symmetry p[m] = p[L - m]."""
+    rng = np.random.default_rng(31)
+    L, sigma = 21, 3.0
+    x = rng.standard_normal(L)
+    p = O.tm_shift_pmf(x, sigma)
+    R = np.array([np.dot(x, np.roll(x, -l)) for l in range(L)])
+    sc = sigma * np.linalg.norm(x)
+    n = 400_000
+    A = R[None, :] + sc * rng.standard_normal((n, L))
+    freq = np.bincount(np.argmax(A, axis=1), minlength=L) / n
+    assert np.all(np.abs(freq - p) <= 5 * np.sqrt(p * (1 - p) / n) + 1e-6), np.abs(freq - p).max()
+    np.testing.assert_allclose(p[1:], p[1:][::-1], atol=1e-9)
+    assert abs(p.sum() - 1.0) < 1e-9
