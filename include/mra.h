@@ -259,6 +259,16 @@ MRA_API int mra_sync(const mra_dims* dims, const float* y, int32_t P, int32_t n_
 MRA_API int mra_align_mean(const mra_dims* dims, const float* y, const int32_t* shift, double* x_out, void* ws,
                            size_t ws_bytes, void* stream);
 
+/* Template matching (Sec. 2.1.1): every image against one reference,
+ *   shift_out[j] = argmin_s sum_{k,q} |ref_kq - e^{2 pi i k s/L} y_jkq|^2   (grid index; smallest s among ties),
+ * the relative rotation of Eq. (relative_angle_2d_dist) with the reference as the first image: aligning
+ * y_j by shift_out[j] (as with the shifts of mra_sync) brings it to the reference's orientation.
+ * O(N L M).  Robust only at high SNR (the paper's point), and the basis of App. B.
+ *   ref [K+1][Q] complex float, 16-byte aligned (for example an observation, or a known signal);
+ *   shift_out [N] int32.  No workspace. */
+MRA_API int mra_template_match(const mra_dims* dims, const float* y, const float* ref, int32_t* shift_out,
+                               void* stream);
+
 /* ------------------------------------------------------------------ rotation prior */
 
 /* One trial of Algorithm 1 (learning the post-synchronization rotation distribution):

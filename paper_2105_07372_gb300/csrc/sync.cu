@@ -5,6 +5,8 @@
 //   ppm       z <- Hz/||Hz|| then z <- phase(Hz) on H_ij = e^{-2 pi i rel_ij / L}     (Eq. cost_synchronization)
 //   match     n*(i) = argmin_{n<P, n != i} ||y_n||^2 - 2 Re <y_i, y_n>, shift_i = phi[n*]
 //             (Algorithm Synchronize and Match) -- an (N x 2M) by (2M x P) product with a fused argmin
+//   template  shift_j = argmax_s Re sum_k C^{j}_k e^{+2 pi i k s/L},  C^{j}_k = sum_q conj(ref_kq) y_jkq
+//             (template matching, Sec. 2.1.1: every image against one reference, O(NLM))
 //   fit_prior rho_bar on the window, optional von Mises fit (Algorithm 1 + concentration fit)
 //   relerr    min_theta ||R_theta x_hat - x|| / ||x|| (Sec. 2.2)
 #include <math.h>
@@ -77,6 +79,71 @@ __global__ void __launch_bounds__(kPairThreads) k_pairwise(const float2* y, int 
       if (rv[w] > b || (rv[w] == b && ri[w] < idx)) b = rv[w], idx = ri[w];
     rel[(size_t)i * P + j] = idx;
     rel[(size_t)j * P + i] = (L - idx) % L;
+  }
+}
+
+// Template matching: a warp per image (grid-stride).  The warp stages its image in shared
+// memory with 16-byte loads, lane k forms C_k against the reference held by the CTA, and the
+// lanes scan the L grid shifts (lane-strided) for the largest Re sum_k C_k e^{+2 pi i k s/L}
+// (smallest s among ties), which is argmin_s sum |ref - e^{i k theta_s} y_j|^2.
+constexpr int kTmThreads = 256;
+__host__ __device__ inline int tm_even(int v) { return (v + 1) & ~1; }
+__global__ void __launch_bounds__(kTmThreads) k_template_match(const float2* y, const float2* ref, int N, int Kp1,
+                                                               int Q, int L, int nwarps, int* shift) {
+  extern __shared__ __align__(16) unsigned char tsm[];
+  // every image buffer starts on a 16-byte boundary (it is filled with 16-byte stores): offsets in
+  // float2 are even (M is even; L and K + 1 are rounded up)
+  const int M = Kp1 * Q;
+  float2* tf = reinterpret_cast<float2*>(tsm);  // [L] e^{-2 pi i m / L}
+  float2* rs = tf + tm_even(L);                 // [M] the reference
+  float2* base = rs + M;                        // per warp: [M] image, then [K + 1] C
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int m = tid; m < L; m += blockDim.x) {
+    double s, c;
+    sincospi(2.0 * (double)m / (double)L, &s, &c);
+    tf[m] = make_float2((float)c, (float)-s);
+  }
+  for (int e = tid; e < M; e += blockDim.x) rs[e] = ref[e];
+  __syncthreads();
+  if (warp >= nwarps) return;
+  float2* img = base + (size_t)warp * (M + tm_even(Kp1));
+  float2* C = img + M;
+  for (int j = blockIdx.x * nwarps + warp; j < N; j += gridDim.x * nwarps) {
+    const float4* src = reinterpret_cast<const float4*>(y + (size_t)j * M);
+    float4* dst = reinterpret_cast<float4*>(img);
+    for (int e = lane; e < M / 2; e += 32) dst[e] = src[e];
+    __syncwarp();
+    for (int k = lane; k < Kp1; k += 32) {
+      float cr = 0.f, ci = 0.f;
+      for (int q = 0; q < Q; ++q) {
+        const float2 a = rs[k * Q + q], b = img[k * Q + q];
+        cr = fmaf(a.x, b.x, cr); cr = fmaf(a.y, b.y, cr);
+        ci = fmaf(a.x, b.y, ci); ci = fmaf(-a.y, b.x, ci);
+      }
+      C[k] = make_float2(cr, ci);
+    }
+    __syncwarp();
+    float best = -INFINITY;
+    int bi = 0x7fffffff;
+    for (int l = lane; l < L; l += 32) {
+      float v = 0.f;
+      int m = 0;
+      for (int k = 0; k < Kp1; ++k) {
+        const float2 t = tf[m], c = C[k];  // Re(C e^{+i phi}) with t = e^{-i phi}
+        v = fmaf(c.x, t.x, v);
+        v = fmaf(c.y, t.y, v);
+        m += l;
+        if (m >= L) m -= L;
+      }
+      if (v > best) best = v, bi = l;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const float ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) best = ov, bi = oi;
+    }
+    if (lane == 0) shift[j] = bi < L ? bi : 0;  // bi >= L only if every value is NaN
+    __syncwarp();  // the image and C buffers are rewritten for the next image
   }
 }
 
@@ -526,6 +593,30 @@ MRA_API int mra_sync_pairwise(const mra_dims* d, const float* y, int32_t P, int3
     return MRA_ECUDA;
   k_pairwise<<<dim3(P, P), kPairThreads, smem, static_cast<cudaStream_t>(stream)>>>(
       reinterpret_cast<const float2*>(y), d->K + 1, d->Q, d->L, P, rel_out);
+  return cudaGetLastError() == cudaSuccess ? MRA_OK : MRA_ECUDA;
+}
+
+MRA_API int mra_template_match(const mra_dims* d, const float* y, const float* ref, int32_t* shift_out,
+                               void* stream) {
+  if (check_sync_dims(d, 1) != MRA_OK || !ok_ptr(y, 16) || !ok_ptr(ref, 16) || !ok_ptr(shift_out, 4))
+    return MRA_EINVAL;
+  if (d->L > 8192) return MRA_EINVAL;
+  DevInfo di;
+  if (dev_info(&di) != MRA_OK) return MRA_ECUDA;
+  const int Kp1 = d->K + 1, M = Kp1 * d->Q;
+  const int fixed = (tm_even(d->L) + M) * 8, per_warp = (M + tm_even(Kp1)) * 8;
+  const int budget = std::min(di.max_smem_optin, 96 * 1024);  // room for two CTAs per SM
+  const int nwarps = std::min(kTmThreads / 32, (budget - fixed) / per_warp);
+  if (nwarps < 1) return MRA_EINVAL;
+  const int smem = fixed + nwarps * per_warp;
+  if (smem > 48 * 1024 &&
+      raise_smem_limit(reinterpret_cast<const void*>(k_template_match), smem) != MRA_OK)
+    return MRA_ECUDA;
+  const long long need = ((long long)d->N + nwarps - 1) / nwarps;
+  const int grid = (int)std::min<long long>(need, (long long)di.sms * 8);
+  k_template_match<<<grid, kTmThreads, smem, static_cast<cudaStream_t>(stream)>>>(
+      reinterpret_cast<const float2*>(y), reinterpret_cast<const float2*>(ref), d->N, Kp1, d->Q, d->L, nwarps,
+      shift_out);
   return cudaGetLastError() == cudaSuccess ? MRA_OK : MRA_ECUDA;
 }
 

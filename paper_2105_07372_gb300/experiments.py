@@ -9,6 +9,12 @@ window width, signal prior) on one device, through the library's calls only.
                      relative error and iterations of Synch-EM and full-search EM for the
                      decay parameter of Gamma_a = diag((4 e^{-k/beta})^2) (Sec. 4,
                      "Performance with signal prior"), and without a signal prior
+    pearson_study    1-D MRA (Sec. 3.1.1): fraction of Pearson coefficients between the shifted
+                     signal's entries and the noise's entries with p < 0.05, before
+                     synchronization, after angular synchronization (PPM over all images) and
+                     after Synchronize and Match
+    degraded_study   1-D MRA: relative error of EM, template matching + EM and PPM
+                     synchronization + EM against SNR (Sec. 3.1.1, degraded performance)
     dense_study      relative error of Synch-EM on images with continuous (off-grid) rotations
                      for the grid window and the denser-resolution window (Sec. 3.3): the
                      same number of rotations over a narrower range, or the same range at a
@@ -20,7 +26,7 @@ same instance (its rotations are known, as in the paper's Monte-Carlo learning) 
 runs EM to tol = 1e-5 or T iterations.  The paper's BW = 2 h corresponds to the window
 Lw = BW + 1 (offsets -h .. h).  Results are means over trials.
 
-    python -m paper_2105_07372_gb300.experiments gamma|bw|prior|dense [--n N] [--trials R]
+    python -m paper_2105_07372_gb300.experiments gamma|bw|prior|dense|pearson|degraded [--n N] [--trials R]
 """
 from __future__ import annotations
 
@@ -157,9 +163,114 @@ def dense_study(snrs=(1 / 5, 1 / 20, 1 / 50), *, K=32, Q=24, N=10000, L=360, tri
     return out
 
 
+# ---------------------------------------------------------------- 1-D MRA through the coefficient form
+def _dims_1d(inst, mra):
+    return mra.dims(inst.N, (inst.L - 1) // 2, 2, inst.L, 2.0 * inst.sigma ** 2)
+
+
+def _coeff_dev(v, dev):
+    import synth
+
+    return torch.from_numpy(synth.to_c64(synth.coeffs_1d(v))).to(dev)
+
+
+def _pearson_fraction(a, b, alpha=0.05):
+    """Fraction of the L x L Pearson coefficients r(a[:, i], b[:, j]) whose two-sided p-value (Student t with N - 2
+    degrees of freedom, t = r sqrt((N - 2) / (1 - r^2))) is below alpha."""
+    from scipy import stats
+
+    n = a.shape[0]
+    az = (a - a.mean(0)) / np.sqrt(((a - a.mean(0)) ** 2).sum(0))
+    bz = (b - b.mean(0)) / np.sqrt(((b - b.mean(0)) ** 2).sum(0))
+    r = np.clip(az.T @ bz, -0.999999, 0.999999)
+    t = r * np.sqrt((n - 2) / (1 - r ** 2))
+    p = 2 * stats.t.sf(np.abs(t), n - 2)
+    return float(np.mean(p < alpha))
+
+
+def _aligned_pair(inst, shat):
+    """(shifted signal after alignment, noise after alignment): roll(x, s - s_hat) and roll(eps, -s_hat)."""
+    L = inst.L
+    idx = (np.arange(L)[None, :] - (inst.s - shat)[:, None]) % L
+    a = inst.x[idx]
+    b = np.stack([np.roll(e, -int(sh)) for e, sh in zip(inst.eps, shat)])
+    return a, b
+
+
+def pearson_study(*, L=21, sigma=2.0, N=1000, trials=20, P=100, seed=9500, dev="cuda"):
+    """Sec. 3.1.1: 1-D MRA with x ~ N(0, I_21), sigma = 2, N = 1000.  Returns the mean fractions of p < 0.05."""
+    import synth
+
+    out = {"before": [], "ppm": [], "synch_and_match": []}
+    for t in range(trials):
+        inst = synth.make_instance_1d(L, N, sigma, seed=seed + t)
+        d = _dims_1d(inst, mra)
+        y = _coeff_dev(inst.v, dev)
+        idx = (np.arange(L)[None, :] - inst.s[:, None]) % L
+        out["before"].append(_pearson_fraction(inst.x[idx], inst.eps))
+        # angular synchronization over all images: pairwise rotations and the projected power method
+        rel = torch.empty((N, N), dtype=torch.int32, device=dev)
+        mra.mra_sync_pairwise(d, y, N, rel)
+        phi = torch.empty(N, dtype=torch.int32, device=dev)
+        mra.mra_sync_ppm(L, N, rel, 50, 100, phi)
+        out["ppm"].append(_pearson_fraction(*_aligned_pair(inst, phi.cpu().numpy().astype(np.int64))))
+        ws = mra.workspace(mra.mra_sync_workspace_bytes(d, P), dev)
+        sh = torch.empty(N, dtype=torch.int32, device=dev)
+        mra.mra_sync(d, y, P, 50, 100, sh, ws)
+        out["synch_and_match"].append(_pearson_fraction(*_aligned_pair(inst, sh.cpu().numpy().astype(np.int64))))
+    return {k: float(np.mean(v)) for k, v in out.items()}
+
+
+def _relerr_1d(xhat, x):
+    """min over cyclic shifts ||roll(xhat, s) - x|| / ||x|| (1-D relative error up to a shift)."""
+    return float(min(np.linalg.norm(np.roll(xhat, s) - x) for s in range(x.size)) / np.linalg.norm(x))
+
+
+def degraded_study(snrs=(1 / 8, 1 / 4, 1 / 2, 1, 2, 4), *, L=21, N=500, trials=10, T=1000, tol=1e-6, seed=9600, dev="cuda"):
+    """Sec. 3.1.1 (degraded performance): relative error of EM from a random start, of template matching (first
+    observation as reference) + EM and of PPM synchronization over all images + EM, each EM over all L shifts with a
+    uniform start, against the SNR ||x||^2 / (L sigma^2)."""
+    import synth
+
+    rows = []
+    for si, snr in enumerate(snrs):
+        acc = {"EM": [], "TM+EM": [], "Synch+EM": []}
+        for t in range(trials):
+            rng = np.random.default_rng(seed + 100 * si + t)
+            x = rng.standard_normal(L)
+            sigma = float(np.linalg.norm(x) / np.sqrt(L * snr))
+            inst = synth.make_instance_1d(L, N, sigma, seed=seed + 100 * si + t, x=x)
+            d = _dims_1d(inst, mra)
+            y = _coeff_dev(inst.v, dev)
+            ws = mra.workspace(mra.mra_em_workspace_bytes(d, L), dev)
+
+            def em_from(x0, shift):
+                xc = x0.clone()
+                lr = torch.full((L,), -np.log(L), dtype=torch.float64, device=dev)
+                prm = mra.em_params(L, l0=0, max_iters=T, tol=tol, check_every=50)
+                mra.mra_em_run(d, prm, y, shift, xc, lr, None, None, ws)
+                return _relerr_1d(synth.signal_1d(xc.cpu().numpy(), L), x)
+
+            x0 = torch.from_numpy(synth.coeffs_1d(rng.standard_normal(L))).to(dev)
+            acc["EM"].append(em_from(x0, None))
+            tm = pipeline.template_match(y, d, y[0])
+            xa = torch.empty_like(x0)
+            mra.mra_align_mean(d, y, tm, xa, ws)
+            acc["TM+EM"].append(em_from(xa, tm))
+            rel = torch.empty((N, N), dtype=torch.int32, device=dev)
+            mra.mra_sync_pairwise(d, y, N, rel)
+            phi = torch.empty(N, dtype=torch.int32, device=dev)
+            mra.mra_sync_ppm(L, N, rel, 50, 100, phi)
+            mra.mra_align_mean(d, y, phi, xa, ws)
+            acc["Synch+EM"].append(em_from(xa, phi))
+        for k, v in acc.items():
+            rows.append({"snr": snr, "method": k, "relerr": float(np.mean(v))})
+    return rows
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("study", choices=("gamma", "bw", "prior", "dense"))
+    ap.add_argument("study", choices=("gamma", "bw", "prior", "dense", "pearson", "degraded"))
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--trials", type=int, default=None)
     a = ap.parse_args()
@@ -169,8 +280,10 @@ def main():
     if a.trials:
         kw["trials"] = a.trials
     mra.load()
-    fn = {"gamma": gamma_study, "bw": bw_study, "prior": signal_prior_study, "dense": dense_study}[a.study]
-    for row in fn(**kw):
+    fn = {"gamma": gamma_study, "bw": bw_study, "prior": signal_prior_study, "dense": dense_study,
+          "pearson": pearson_study, "degraded": degraded_study}[a.study]
+    res = fn(**kw)
+    for row in (res if isinstance(res, list) else [res]):
         print(json.dumps(row), flush=True)
 
 

@@ -72,6 +72,7 @@ _SIGS = {
     "mra_sync_pairwise": (c_int, [POINTER(mra_dims), c_void_p, c_int32, c_void_p, c_void_p]),
     "mra_sync_ppm": (c_int, [c_int32, c_int32, c_void_p, c_int32, c_int32, c_void_p, c_void_p]),
     "mra_sync_match": (c_int, [POINTER(mra_dims), c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "mra_template_match": (c_int, [POINTER(mra_dims), c_void_p, c_void_p, c_void_p, c_void_p]),
     "mra_sync": (c_int, [POINTER(mra_dims), c_void_p, c_int32, c_int32, c_int32, c_void_p, c_void_p, c_size_t,
                          c_void_p]),
     "mra_align_mean": (c_int, [POINTER(mra_dims), c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
@@ -276,6 +277,11 @@ def mra_sync_ppm(L, P, rel, n_power, n_ppm, phi_out, stream=None):
 def mra_sync_match(d, y, P, phi, shift_out, ws, stream=None):
     _check("mra_sync_match", load().mra_sync_match(ctypes.byref(d), _p(y), int(P), _p(phi), _p(shift_out), _p(ws),
                                                    ws.numel(), _stream(stream)))
+
+
+def mra_template_match(d, y, ref, shift_out, stream=None):
+    _check("mra_template_match", load().mra_template_match(ctypes.byref(d), _p(y), _p(ref), _p(shift_out),
+                                                           _stream(stream)))
 
 
 def mra_sync(d, y, P, n_power, n_ppm, shift_out, ws, stream=None):

@@ -44,6 +44,14 @@ def synchronize(y, d, P, ws: Workspaces, n_power=50, n_ppm=100, stream=None) -> 
     return shift
 
 
+def template_match(y, d, ref, stream=None) -> torch.Tensor:
+    """Template matching (Sec. 2.1.1): the shift of every image against the reference ref [K+1, Q] (complex64
+    device tensor; an observation such as y[0], or a known signal)."""
+    shift = torch.empty(d.N, dtype=torch.int32, device=y.device)
+    mra.mra_template_match(d, y, ref.contiguous(), shift, stream)
+    return shift
+
+
 def learn_prior(y, d, shift_true, shift_est, x_true, Lw, l0=None, kind=0, ws: Workspaces | None = None, stream=None,
                 step=1.0):
     """One Monte-Carlo trial of Algorithm 1 on a synthetic instance whose truth is known, then the window prior

@@ -49,3 +49,17 @@ def test_dense_study_runs_and_finer_spacing_does_not_hurt(gpu_lib):
     err = {(v["Lw"], v["step"]): v["relerr"] for v in r}
     assert all(0 < e < 1 for e in err.values())
     assert err[(145, 0.25)] <= err[(37, 1.0)] + 0.005, err
+
+
+def test_pearson_and_degraded_studies_run(gpu_lib):
+    """1-D studies (Sec. 3.1.1) on small runs: before synchronization the fraction of Pearson p-values below 0.05
+    is the test's nominal level (independent entries); synchronization by PPM over all images raises it; the
+    degraded-performance study returns sane errors for its three methods."""
+    from paper_2105_07372_gb300 import experiments as E
+
+    r = E.pearson_study(trials=3)
+    assert 0.02 <= r["before"] <= 0.09, r
+    assert r["ppm"] > r["before"], r
+    rows = E.degraded_study(snrs=(2.0,), trials=2, N=300)
+    assert {v["method"] for v in rows} == {"EM", "TM+EM", "Synch+EM"}
+    assert all(0 <= v["relerr"] < 1.5 for v in rows), rows

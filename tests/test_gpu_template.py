@@ -1,0 +1,103 @@
+"""Template matching (Sec. 2.1.1) on the GPU against the FP64 oracle, in the 2-D coefficient model and in the
+1-D model through its coefficient form, and the App. B shift-pmf approximation against the GPU's template
+matching with the true signal as reference."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import synth
+from gpu_helpers import dev, dev_y, host
+
+pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore::RuntimeWarning")]
+
+
+def _tm(mra, y64, ref64, L, sigma2=1.0):
+    N, Kp1, Q = y64.shape
+    d = mra.dims(N, Kp1 - 1, Q, L, sigma2)
+    out = torch.empty(N, dtype=torch.int32, device="cuda")
+    mra.mra_template_match(d, dev_y(y64), dev_y(ref64[None])[0], out)
+    torch.cuda.synchronize()
+    return host(out).astype(np.int64)
+
+
+def _dist(ref, yj, s, L):
+    d = ref - O.rotate(yj, -2 * np.pi * s / L)
+    return float(np.sum(np.abs(d) ** 2))
+
+
+def _check_against_oracle(y64, ref64, L, got, min_exact=0.995):
+    want = O.template_match(y64, ref64, L)
+    same = got == want
+    assert same.mean() >= min_exact, same.mean()
+    for j in np.nonzero(~same)[0]:  # a near tie resolved the other way in FP32: the choice must be as good
+        dg, dw = _dist(ref64, y64[j], got[j], L), _dist(ref64, y64[j], want[j], L)
+        scale = float(np.sum(np.abs(ref64) ** 2) + np.sum(np.abs(y64[j]) ** 2))
+        assert dg - dw <= 1e-5 * scale, (j, dg, dw)
+
+
+@pytest.mark.parametrize("K,Q,N,L,snr", [(12, 16, 1500, 90, 1 / 5), (32, 24, 800, 360, 1 / 20), (5, 6, 2000, 37, 1 / 2)])
+def test_template_match_matches_oracle(gpu_lib, K, Q, N, L, snr):
+    inst = synth.make_instance(K, Q, N, L, snr, 50.0, seed=9100 + K)
+    y64 = synth.c64_round(inst.y)
+    got = _tm(gpu_lib, y64, y64[0], L)
+    assert got[0] == 0
+    _check_against_oracle(y64, y64[0], L, got)
+
+
+def test_template_match_noise_free_full_size(gpu_lib):
+    """|k| <= 32, Q = 24, L = 360 at N = 100,000: images that are the reference rotated by s_j give s_j exactly."""
+    c = synth.config(2)
+    inst = synth.make_instance(c["K"], c["Q"], c["N"], c["L"], sigma2=0.0, seed=9200)
+    y64 = synth.c64_round(inst.y)
+    got = _tm(gpu_lib, y64, synth.c64_round(inst.x), c["L"])
+    np.testing.assert_array_equal(got, inst.s)
+
+
+def test_template_match_1d_against_signal_space(gpu_lib):
+    """The 1-D model (L = 21, sigma = 2, N = 1000) through its coefficient form: the GPU's shifts against the
+    signal-space argmax of the circular cross-correlation with the first observation."""
+    inst = synth.make_instance_1d(21, 1000, 2.0, seed=9300)
+    a = synth.coeffs_1d(inst.v)
+    got = _tm(gpu_lib, synth.c64_round(a), synth.c64_round(a[0]), 21)
+    _check_against_oracle(synth.c64_round(a), synth.c64_round(a[0]), 21, got)
+
+
+def test_template_match_edge_shapes(gpu_lib):
+    mra = gpu_lib
+    # one image, one grid point; an image equal to the reference
+    inst = synth.make_instance(3, 2, 1, 1, sigma2=0.1, seed=1)
+    assert _tm(mra, synth.c64_round(inst.y), synth.c64_round(inst.y[0]), 1).tolist() == [0]
+    inst = synth.make_instance(3, 2, 40, 17, sigma2=0.3, seed=2)
+    y64 = synth.c64_round(inst.y)
+    _check_against_oracle(y64, y64[5], 17, _tm(mra, y64, y64[5], 17))
+    # the largest stored size (M = 4096) runs with fewer warps per block
+    inst = synth.make_instance(63, 64, 300, 24, sigma2=1e-3, seed=3)
+    y64 = synth.c64_round(inst.y)
+    got = _tm(mra, y64, synth.c64_round(inst.x), 24)
+    np.testing.assert_array_equal(got, O.template_match(y64, synth.c64_round(inst.x), 24))
+    # misaligned reference pointer
+    d = mra.dims(4, 3, 2, 8, 1.0)
+    y = torch.zeros((4, 4, 2), dtype=torch.complex64, device="cuda")
+    buf = torch.zeros(17, dtype=torch.complex64, device="cuda")
+    with pytest.raises(RuntimeError):
+        mra.mra_template_match(d, y, buf[1:], torch.empty(4, dtype=torch.int32, device="cuda"))
+
+
+def test_tm_shift_pmf_against_gpu_template_matching(gpu_lib):
+    """App. B: 1-D template matching with the true signal as reference on 200,000 zero-shift observations
+    (L = 21, sigma = 3).  The GPU's shift histogram equals the signal-space argmax of R_xy on the same draws;
+    the approximate pmf of Eq. (shift_pmf) (independent correlations) is within 0.1 of it in total variation."""
+    rng = np.random.default_rng(9400)
+    L, sigma, n = 21, 3.0, 200_000
+    x = rng.standard_normal(L)
+    inst = synth.make_instance_1d(L, n, sigma, seed=9401, x=x, shifts=np.zeros(n, dtype=np.int64))
+    got = _tm(gpu_lib, synth.c64_round(synth.coeffs_1d(inst.v)), synth.c64_round(synth.coeffs_1d(x)), L)
+    R = np.real(np.fft.ifft(np.conj(np.fft.fft(x))[None, :] * np.fft.fft(inst.v, axis=1), axis=1))
+    want = np.argmax(R, axis=1)
+    assert (got == want).mean() >= 0.999
+    freq = np.bincount(got, minlength=L) / n
+    p = O.tm_shift_pmf(x, sigma)
+    tv = 0.5 * np.abs(freq - p).sum()
+    print(f"\nApp. B approximation vs template matching on the GPU: total variation {tv:.3f}")
+    assert tv < 0.1
