@@ -216,10 +216,11 @@ def main():
     ap.add_argument("--impl", default="gpu")
     ap.add_argument("--no-ttc", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--config", default=str(CFG), choices=("2", "4", "5", "dense"),
+    ap.add_argument("--config", default=str(CFG), choices=("2", "4", "5", "dense", "tm"),
                     help="2: Synch-EM at N=1e5 (default); 4: 64 uneven instances in one graph launch; "
                          "5: N=1e6 with y in the BF16 hi/lo split; dense: the workload of 2 with the "
-                         "denser-resolution window (2L+1 rotations over BW = 36) on off-grid rotations")
+                         "denser-resolution window (2L+1 rotations over BW = 36) on off-grid rotations; tm: "
+                         "template matching of the images of 2 against the first one")
     args = ap.parse_args()
     c = dense_config() if args.config == "dense" else synth.config(CFG)
     if args.impl == "reference":
@@ -228,6 +229,8 @@ def main():
         return bench_batched(args)
     if args.config == "5":
         return bench_bf16(args)
+    if args.config == "tm":
+        return bench_template_match(args)
 
     import torch
     import torch.distributed as dist
@@ -595,6 +598,53 @@ def bench_bf16(args):
                          "kernel": "k_sweep_v3 (BF16 hi/lo)", "algorithmic_bytes_per_launch": ybytes,
                          "avg_launch_ms": sw * 1e3},
             "clocks": clk.summary(), "gpu_launches": (2 + 3 * T + 1) * args.steps}
+    print(json.dumps(line), flush=True)
+
+
+def bench_template_match(args):
+    """Template matching (Sec. 2.1.1) of the Synch-EM workload's images (|k| <= 32, Q = 24, N = 1e5, L = 360,
+    SNR 1/50) against the first observation: one mra_template_match per step, N L image-rotation evaluations."""
+    import torch
+
+    from paper_2105_07372_gb300 import mra
+
+    mra.load()
+    dev = torch.device("cuda", 0)
+    c = synth.config(CFG)
+    N, K, Q, L = c["N"], c["K"], c["Q"], c["L"]
+    inst = synth.make_instance(K, Q, N, L, c["snr"], c["decay"], seed=replica_seed(0))
+    y = torch.from_numpy(synth.to_c64(inst.y)).to(dev)
+    d = mra.dims(N, K, Q, L, inst.sigma2)
+    out = torch.empty(N, dtype=torch.int32, device=dev)
+    ref = y[0].clone()
+
+    def step():
+        mra.mra_template_match(d, y, ref, out)
+
+    clk = _clocks()
+    ms = _timed_steps(step, args, clk)
+    M = (K + 1) * Q
+    ybytes = N * M * 8
+    flops = N * (8 * M + 4 * L * (K + 1))  # correlation + the transform over all L shifts, per image
+    peak, peak_kind = peaks()
+    alu = fp32_alu_peak_tflops()
+    hbm_bound = ybytes / (peak * 1e9) >= flops / (alu * 1e12)
+    ach_h, ach_a = ybytes / (ms / 1e3) / 1e9, flops / (ms / 1e3) / 1e12
+    hit = float((out.cpu().numpy().astype(np.int64) == (inst.s - inst.s[0]) % L).mean())
+    line = {"metric": "template-matching image-rotation evals/s", "value": N * L / (ms / 1e3), "unit": UNIT,
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"template matching |k|<={K} Q={Q} N={N} L={L} SNR=1/{round(1 / c['snr'])}, "
+                                   f"reference = first observation", "parallelism": "single",
+                       "l2": "inputs larger than L2 (633.6 MB per launch)"},
+            "roofline": {"bound": "hbm" if hbm_bound else "alu", "achieved": ach_h if hbm_bound else ach_a,
+                         "peak": peak if hbm_bound else alu, "unit": "GB/s" if hbm_bound else "TFLOP/s",
+                         "frac": ach_h / peak if hbm_bound else ach_a / alu, "traffic": None,
+                         "peak_source": f"{peak_kind} hbm_gbs" if hbm_bound else
+                                        "derived FP32 CUDA-core peak: 152 SMs x 128 FMA/clk x 2 flop x 2.07 GHz",
+                         "kernel": "k_template_match", "algorithmic_bytes_per_launch": ybytes,
+                         "algorithmic_flops_per_launch": flops, "avg_launch_ms": ms},
+            "fraction_true_relative_shift": hit, "clocks": clk.summary(), "gpu_launches": args.steps}
     print(json.dumps(line), flush=True)
 
 

@@ -83,9 +83,11 @@ __global__ void __launch_bounds__(kPairThreads) k_pairwise(const float2* y, int 
 }
 
 // Template matching: a warp per image (grid-stride).  The warp stages its image in shared
-// memory with 16-byte loads, lane k forms C_k against the reference held by the CTA, and the
-// lanes scan the L grid shifts (lane-strided) for the largest Re sum_k C_k e^{+2 pi i k s/L}
-// (smallest s among ties), which is argmin_s sum |ref - e^{i k theta_s} y_j|^2.
+// memory with 16-byte loads, lane k forms C_k against the reference held by the CTA (each lane
+// starts its walk over q at k mod Q, which spreads the lanes over the banks), and the lanes scan
+// the L grid shifts for the largest Re sum_k C_k e^{+2 pi i k s/L} (smallest s among ties), which
+// is argmin_s sum |ref - e^{i k theta_s} y_j|^2.  Shifts s and L - s share cos and sin: with
+// A = sum C.x cos, B = sum C.y (-sin), the values are A + B at s and A - B at L - s.
 constexpr int kTmThreads = 256;
 __host__ __device__ inline int tm_even(int v) { return (v + 1) & ~1; }
 __global__ void __launch_bounds__(kTmThreads) k_template_match(const float2* y, const float2* ref, int N, int Kp1,
@@ -115,27 +117,33 @@ __global__ void __launch_bounds__(kTmThreads) k_template_match(const float2* y, 
     __syncwarp();
     for (int k = lane; k < Kp1; k += 32) {
       float cr = 0.f, ci = 0.f;
-      for (int q = 0; q < Q; ++q) {
+      int q = k % Q;
+      for (int qq = 0; qq < Q; ++qq) {
         const float2 a = rs[k * Q + q], b = img[k * Q + q];
         cr = fmaf(a.x, b.x, cr); cr = fmaf(a.y, b.y, cr);
         ci = fmaf(a.x, b.y, ci); ci = fmaf(-a.y, b.x, ci);
+        if (++q == Q) q = 0;
       }
       C[k] = make_float2(cr, ci);
     }
     __syncwarp();
     float best = -INFINITY;
     int bi = 0x7fffffff;
-    for (int l = lane; l < L; l += 32) {
-      float v = 0.f;
+    auto take = [&](float v, int l) {
+      if (v > best || (v == best && l < bi)) best = v, bi = l;
+    };
+    for (int l = lane; 2 * l <= L; l += 32) {  // the pair {l, L - l}
+      float A = 0.f, B = 0.f;
       int m = 0;
       for (int k = 0; k < Kp1; ++k) {
-        const float2 t = tf[m], c = C[k];  // Re(C e^{+i phi}) with t = e^{-i phi}
-        v = fmaf(c.x, t.x, v);
-        v = fmaf(c.y, t.y, v);
+        const float2 t = tf[m], c = C[k];  // Re(C e^{+i phi}) = A + B with t = e^{-i phi}
+        A = fmaf(c.x, t.x, A);
+        B = fmaf(c.y, t.y, B);
         m += l;
         if (m >= L) m -= L;
       }
-      if (v > best) best = v, bi = l;
+      take(A + B, l);
+      if (l > 0 && 2 * l != L) take(A - B, L - l);
     }
     for (int o = 16; o > 0; o >>= 1) {
       const float ov = __shfl_xor_sync(0xffffffffu, best, o);

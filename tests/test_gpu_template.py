@@ -101,3 +101,30 @@ def test_tm_shift_pmf_against_gpu_template_matching(gpu_lib):
     tv = 0.5 * np.abs(freq - p).sum()
     print(f"\nApp. B approximation vs template matching on the GPU: total variation {tv:.3f}")
     assert tv < 0.1
+
+
+def test_prior_learning_with_template_matching_against_app_b(gpu_lib):
+    """Algorithm 1 with template matching (the true signal as reference) on 1-D data with uniform shifts: the learned
+    residual histogram (mra_prior_hist) against the App. B pmf of the shift error, mirrored by the residual's sign
+    (r = s - s_hat + c); both are symmetric here.  Total variation below 0.1."""
+    mra = gpu_lib
+    rng = np.random.default_rng(9500)
+    L, sigma, n = 21, 3.0, 200_000
+    x = rng.standard_normal(L)
+    inst = synth.make_instance_1d(L, n, sigma, seed=9501, x=x)
+    a = synth.c64_round(synth.coeffs_1d(inst.v))
+    xc = synth.coeffs_1d(x)
+    d = mra.dims(n, (L - 1) // 2, 2, L, synth.sigma2_coeff(sigma))
+    y = dev_y(a)
+    shat = torch.empty(n, dtype=torch.int32, device="cuda")
+    mra.mra_template_match(d, y, dev_y(synth.c64_round(xc)[None])[0], shat)
+    hist = torch.zeros(L, dtype=torch.int32, device="cuda")
+    ws = mra.workspace(mra.mra_em_workspace_bytes(d, 1))
+    mra.mra_prior_hist(d, y, dev(inst.s.astype(np.int32)), shat, dev(xc), hist, None, ws)
+    lp = torch.empty(L, dtype=torch.float64, device="cuda")
+    mra.mra_fit_prior(L, L, 0, hist, 0, lp, None)
+    rho = np.exp(host(lp))
+    p = O.tm_shift_pmf(x, sigma)
+    tv = 0.5 * np.abs(rho - p[(-np.arange(L)) % L]).sum()
+    print(f"\nlearned prior (template matching) vs App. B pmf: total variation {tv:.3f}")
+    assert tv < 0.1
