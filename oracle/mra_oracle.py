@@ -20,6 +20,7 @@ its own order and notation:
 * Synchronize and Match                                               Algorithm "Synchronize and Match"
 * template matching: every image against one reference, O(NLM)        Sec. 2.1.1 (template matching)
 * shift pmf of 1-D template matching with the true signal as reference App. B, Eq. (shift_pmf)
+* Fourier-Bessel coefficients of pixel images by least squares          App. A
 * learned rotation distribution, centred by theta_c                    Eq. (learned_distribution_formula), Algorithm 1
 * relative error up to rotation                                       Sec. 2.2, relative-error equation
 * likelihood with the (pi sigma^2)^{-M} factor                          Sec. 2.2, likelihood equation
@@ -380,6 +381,51 @@ def tm_shift_pmf(x: np.ndarray, sigma: float) -> np.ndarray:
         lo, hi = R.min() - 12 * sc, R.max() + 12 * sc
         p[m] = integrate.quad(f, lo, hi, points=sorted(set(R.tolist())), limit=400, epsabs=1e-13, epsrel=1e-11)[0]
     return p
+
+
+# ----------------------------------------------------------------------------
+# Fourier-Bessel front end, App. A
+# ----------------------------------------------------------------------------
+def fb_design(n: int, K: int, Q: int) -> np.ndarray:
+    """Real least-squares design matrix [n*n, Q + 2KQ] of a real image in the Fourier-Bessel basis (App. A):
+    u^{k,q} = N_{k,q} J_|k|(R_{|k|,q} r/c) e^{ik theta} on r <= c = (n-1)/2, N_{k,q} = 1/(c sqrt(pi) |J_{k+1}(R_{k,q})|),
+    pixels at x = column - c, y = row - c.  With a_{-k} = conj(a_k) the image is
+    sum_q a_0q u^{0q} + sum_{k>=1,q} (2 Re a_kq Re u^{kq} - 2 Im a_kq Im u^{kq}); columns k = 0 (a_0q, real), then
+    per k >= 1 and q the columns of Re a_kq and Im a_kq."""
+    c = (n - 1) / 2.0
+    rows, colsx = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    x = (colsx - c).ravel()
+    y = (rows - c).ravel()
+    r = np.sqrt(x * x + y * y)
+    theta = np.arctan2(y, x)
+    out = np.zeros((n * n, Q + 2 * K * Q))
+    col = 0
+    for k in range(K + 1):
+        R = special.jn_zeros(k, Q)
+        for q in range(Q):
+            Nkq = 1.0 / (c * math.sqrt(math.pi) * abs(special.jv(k + 1, R[q])))
+            f = np.where(r <= c, Nkq * special.jv(k, R[q] * r / c), 0.0)
+            if k == 0:
+                out[:, col] = f
+                col += 1
+            else:
+                out[:, col] = 2.0 * f * np.cos(k * theta)
+                out[:, col + 1] = -2.0 * f * np.sin(k * theta)
+                col += 2
+    return out
+
+
+def fb_project(images: np.ndarray, K: int, Q: int) -> np.ndarray:
+    """Coefficients [N, K+1, Q] (complex, k >= 0) of images [N, n, n] as the least-squares solution of App. A."""
+    images = np.asarray(images, dtype=np.float64)
+    n = images.shape[-1]
+    A = fb_design(n, K, Q)
+    beta = np.linalg.lstsq(A, images.reshape(images.shape[0], -1).T, rcond=None)[0].T  # [N, Q + 2KQ]
+    a = np.zeros((images.shape[0], K + 1, Q), dtype=np.complex128)
+    a[:, 0, :] = beta[:, :Q]
+    ri = beta[:, Q:].reshape(images.shape[0], K, Q, 2)
+    a[:, 1:, :] = ri[..., 0] + 1j * ri[..., 1]
+    return a
 
 
 def align_mean(y: np.ndarray, shifts: np.ndarray, L: int) -> np.ndarray:

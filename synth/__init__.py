@@ -22,3 +22,4 @@ from .instances import (  # noqa: F401
     config4_instances,
 )
 from .mra1d import Instance1D, coeffs_1d, make_instance_1d, sigma2_coeff, signal_1d  # noqa: F401,E402
+from .fb_images import noisy_images, real_params, render, render_matrix  # noqa: F401,E402

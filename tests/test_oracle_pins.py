@@ -558,3 +558,48 @@ def test_tm_shift_pmf_against_monte_carlo_of_its_model():
     assert np.all(np.abs(freq - p) <= 5 * np.sqrt(p * (1 - p) / n) + 1e-6), np.abs(freq - p).max()
     np.testing.assert_allclose(p[1:], p[1:][::-1], atol=1e-9)
     assert abs(p.sum() - 1.0) < 1e-9
+
+
+# --------------------------------------------------------------------------- Fourier-Bessel front end (App. A)
+@pytest.mark.parametrize("k,q", [(0, 1), (0, 7), (3, 2), (12, 5), (30, 20)])
+def test_fb_normalisation_closed_form(k, q):
+    """N_{k,q} makes the continuous basis function unit-norm on the disk: 2 pi int_0^c N^2 J_k(R r/c)^2 r dr = 1
+    (equivalently c^2 J_{k+1}(R)^2 / 2 = int_0^c J_k(R r/c)^2 r dr, the Lommel integral at a zero)."""
+    from scipy import integrate, special
+
+    c = 64.0
+    R = special.jn_zeros(k, q)[-1]
+    Nkq = 1.0 / (c * math.sqrt(math.pi) * abs(special.jv(k + 1, R)))
+    val = 2 * math.pi * integrate.quad(lambda r: (Nkq * special.jv(k, R * r / c)) ** 2 * r, 0, c, limit=400)[0]
+    assert abs(val - 1.0) < 1e-9
+
+
+def test_fb_project_recovers_rendered_coefficients():
+    """Images rendered by the data generator (its own evaluation of the basis) come back through the oracle's least
+    squares: the two implementations of App. A's basis agree."""
+    K, Q, n = 6, 5, 41
+    a = np.stack([synth.make_signal(K, Q, 10.0, np.random.default_rng(s)) for s in range(3)])
+    img = synth.render(a, n)
+    np.testing.assert_allclose(O.fb_project(img, K, Q), a, atol=1e-11)
+
+
+def test_fb_rotation_by_quarter_turn():
+    """Steerability on the pixel grid: the image rotated by pi/2, I'(x, y) = I(y, -x), i.e. I'[iy][ix] =
+    I[n-1-ix][iy], has the coefficients a_k e^{-i k pi/2} (Eq. fb_rotation)."""
+    K, Q, n = 8, 4, 33
+    a = synth.make_signal(K, Q, 20.0, np.random.default_rng(3))
+    img = synth.render(a[None], n)[0]
+    iy, ix = np.mgrid[0:n, 0:n]
+    rot = img[n - 1 - ix, iy]
+    want = a * np.exp(-1j * np.arange(K + 1) * np.pi / 2)[:, None]
+    np.testing.assert_allclose(O.fb_project(rot[None], K, Q)[0], want, atol=1e-11)
+
+
+def test_fb_pixel_noise_is_nearly_white_in_coefficients():
+    """White pixel noise of variance s^2 gives coefficients of variance ~ s^2 per stored complex entry (the discrete
+    basis is nearly orthonormal; App. A): within 3% on average and 10% per entry over 4000 draws."""
+    K, Q, n, s = 4, 4, 41, 1.0
+    noise = np.random.default_rng(8).standard_normal((4000, n, n)) * s
+    v = np.mean(np.abs(O.fb_project(noise, K, Q)) ** 2, axis=0)
+    assert abs(v.mean() - s ** 2) < 0.03
+    assert np.all(np.abs(v - s ** 2) < 0.1)
