@@ -216,11 +216,12 @@ def main():
     ap.add_argument("--impl", default="gpu")
     ap.add_argument("--no-ttc", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--config", default=str(CFG), choices=("2", "4", "5", "dense", "tm"),
+    ap.add_argument("--config", default=str(CFG), choices=("2", "4", "5", "dense", "tm", "fb"),
                     help="2: Synch-EM at N=1e5 (default); 4: 64 uneven instances in one graph launch; "
                          "5: N=1e6 with y in the BF16 hi/lo split; dense: the workload of 2 with the "
                          "denser-resolution window (2L+1 rotations over BW = 36) on off-grid rotations; tm: "
-                         "template matching of the images of 2 against the first one")
+                         "template matching of the images of 2 against the first one; fb: the Fourier-Bessel "
+                         "front end on 10,000 images of 129 x 129 pixels")
     args = ap.parse_args()
     c = dense_config() if args.config == "dense" else synth.config(CFG)
     if args.impl == "reference":
@@ -231,6 +232,8 @@ def main():
         return bench_bf16(args)
     if args.config == "tm":
         return bench_template_match(args)
+    if args.config == "fb":
+        return bench_fb(args)
 
     import torch
     import torch.distributed as dist
@@ -645,6 +648,72 @@ def bench_template_match(args):
                          "kernel": "k_template_match", "algorithmic_bytes_per_launch": ybytes,
                          "algorithmic_flops_per_launch": flops, "avg_launch_ms": ms},
             "fraction_true_relative_shift": hit, "clocks": clk.summary(), "gpu_launches": args.steps}
+    print(json.dumps(line), flush=True)
+
+
+def bench_fb(args):
+    """The Fourier-Bessel front end (App. A) at the paper's image size: N = 10,000 images of 129 x 129 pixels
+    onto |k| <= 32, Q = 24 (the coefficient shape of the Synch-EM workload): one mra_fb_project per step, FP32
+    (TF32 timed beside it); the one-time mra_fb_setup is timed separately."""
+    import torch
+
+    from paper_2105_07372_gb300 import mra, pipeline
+
+    mra.load()
+    dev = torch.device("cuda", 0)
+    n, K, Q, N = 129, 32, 24, 10_000
+    c = synth.config(CFG)
+    A = torch.from_numpy(synth.render_matrix(n, K, Q)).to(dev, torch.float32)  # data generation only
+    x = synth.make_signal(K, Q, c["decay"], np.random.default_rng(11))
+    s = np.random.default_rng(12).integers(0, c["L"], N)
+    a = x[None] * np.exp(-2j * np.pi * np.outer(s, np.arange(K + 1)) / c["L"])[:, :, None]
+    sigma = math.sqrt(synth.sigma2_for_snr(c["snr"], x))
+    coeff = torch.from_numpy(synth.real_params(a)).to(dev, torch.float32)
+    images = (coeff @ A.T).reshape(N, n, n)
+    images += sigma * torch.randn(images.shape, generator=torch.Generator(device=dev).manual_seed(13), device=dev)
+    del A, coeff
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    P = pipeline.fb_projection(n, K, Q, dev)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    y = torch.empty((N, K + 1, Q), dtype=torch.complex64, device=dev)
+
+    def step(tf32=False):
+        mra.mra_fb_project(N, n, K, Q, images, P, y, tf32)
+
+    clk = _clocks()
+    ms = _timed_steps(step, args, clk)
+    ms_tf32 = _timed_steps(lambda: step(True), args, _clocks())
+    flops = 2.0 * N * n * n * 2 * (K + 1) * Q
+    alu = fp32_alu_peak_tflops()
+    bf16 = 1943.5
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            bf16 = float(json.load(f)["bf16_tflops"])
+    except Exception:
+        pass
+    tf32_peak = bf16 * 1.1 / 2.25  # the measured bf16 peak times the nominal TF32 / BF16 ratio
+    step()
+    # white pixel noise of variance sigma^2 stays (nearly) white with the same variance per coefficient (App. A)
+    noise_ratio = float(torch.mean(torch.abs(y.cpu().to(torch.complex128) - torch.from_numpy(a)) ** 2) / sigma ** 2)
+    line = {"metric": "Fourier-Bessel projected images/s", "value": N / (ms / 1e3), "unit": "images/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"Fourier-Bessel front end: N={N} images {n}x{n} onto |k|<={K} Q={Q} "
+                                   f"(SNR 1/{round(1 / c['snr'])})", "parallelism": "single",
+                       "l2": f"inputs larger than L2 ({N * n * n * 4 / 1e6:.0f} MB of pixels per launch)"},
+            "roofline": {"bound": "alu", "achieved": flops / (ms / 1e3) / 1e12, "peak": alu, "unit": "TFLOP/s",
+                         "frac": flops / (ms / 1e3) / 1e12 / alu, "traffic": None,
+                         "peak_source": "derived FP32 CUDA-core peak: 152 SMs x 128 FMA/clk x 2 flop x 2.07 GHz",
+                         "kernel": "cuBLAS SGEMM (mra_fb_project)", "algorithmic_flops_per_launch": flops,
+                         "avg_launch_ms": ms},
+            "tf32": {"ms_per_step": ms_tf32, "images_per_s": N / (ms_tf32 / 1e3),
+                     "achieved_tflops": flops / (ms_tf32 / 1e3) / 1e12, "peak_tflops": tf32_peak,
+                     "peak_source": "measured bf16 x 1.1/2.25 (nominal TF32/BF16)",
+                     "frac": flops / (ms_tf32 / 1e3) / 1e12 / tf32_peak},
+            "setup_s": setup_s, "coefficient_noise_variance_over_pixel_variance": noise_ratio,
+            "clocks": clk.summary(), "gpu_launches": args.steps}
     print(json.dumps(line), flush=True)
 
 

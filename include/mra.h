@@ -269,6 +269,34 @@ MRA_API int mra_align_mean(const mra_dims* dims, const float* y, const int32_t* 
 MRA_API int mra_template_match(const mra_dims* dims, const float* y, const float* ref, int32_t* shift_out,
                                void* stream);
 
+/* ------------------------------------------------------------------ Fourier-Bessel front end (App. A) */
+
+/* From n x n pixel images to the steerable coefficients a_{k,q}, k = 0..K, q = 1..Q, as the least-squares
+ * solution over the sampled Fourier-Bessel basis
+ *   u^{k,q}(r, theta) = N_{k,q} J_|k|(R_{|k|,q} r / c) e^{i k theta} for r <= c = (n - 1)/2, 0 beyond,
+ *   R_{k,q} the q-th positive zero of J_k, N_{k,q} = 1 / (c sqrt(pi) |J_{k+1}(R_{k,q})|),
+ * with a_{-k,q} = conj(a_{k,q}) (real images).  Pixel (row iy, column ix) sits at x = ix - c, y = iy - c,
+ * theta = atan2(y, x); rotating an image by phi multiplies a_{k,q} by e^{-i k phi} (Eq. fb_rotation).
+ * Limits: 3 <= n <= 1024, (K+1) Q even, and the sampling criterion R_{K,Q} <= pi n / 2 (checked as
+ * Q + K/2 + 1/4 <= n/2).
+ *
+ * mra_fb_setup (once per n, K, Q; synchronizes the stream): computes the zeros, the design matrix, its
+ * Gram matrix and inverse (FP64) and writes the projection P [n*n][K+1][Q] complex float: the coefficients
+ * of an image are sum over pixels of image[pixel] * P[pixel].
+ *   P_out      device, 16-byte aligned, n*n*(K+1)*Q complex float
+ *   zeros_out  device [(K+1)][Q] double R_{k,q}, or NULL
+ *   ws         workspace of mra_fb_setup_workspace_bytes(n, K, Q) bytes (about 16 n^2 (Q + 2KQ) bytes)
+ * Returns MRA_ENUMERIC if a zero was not found or the inverse did not converge. */
+MRA_API size_t mra_fb_setup_workspace_bytes(int32_t n, int32_t K, int32_t Q);
+MRA_API int mra_fb_setup(int32_t n, int32_t K, int32_t Q, float* P_out, double* zeros_out, void* ws, size_t ws_bytes,
+                         void* stream);
+
+/* Coefficients of N images: y_out [N][K+1][Q] complex float = images [N][n][n] float times P, one GEMM
+ * (cuBLAS; tf32 != 0 uses TF32 tensor cores, relative error ~1e-3 instead of ~1e-6).  y_out has the
+ * layout every EM and synchronization entry point reads.  All pointers device, 16-byte aligned. */
+MRA_API int mra_fb_project(int32_t N, int32_t n, int32_t K, int32_t Q, const float* images, const float* P,
+                           float* y_out, int32_t tf32, void* stream);
+
 /* ------------------------------------------------------------------ rotation prior */
 
 /* One trial of Algorithm 1 (learning the post-synchronization rotation distribution):

@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmra.so")
 # one translation unit per sweep family and row width, so that they compile in parallel
-SOURCES = ["em.cu", "sync.cu"] + [f"sweep_v{v}_q{q}.cu" for v in (2, 3, 4) for q in (1, 2, 3, 4)]
+SOURCES = ["em.cu", "sync.cu", "fb.cu"] + [f"sweep_v{v}_q{q}.cu" for v in (2, 3, 4) for q in (1, 2, 3, 4)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden", "--expt-relaxed-constexpr"]
 
@@ -53,7 +53,7 @@ def build_library(force: bool = False, verbose: bool = False, extra: list[str] |
     with cf.ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + ".tmp"
-    cmd = [cc, *ARCH, "-shared", *objs, "-o", tmp]
+    cmd = [cc, *ARCH, "-shared", *objs, "-o", tmp, "-lcublas"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

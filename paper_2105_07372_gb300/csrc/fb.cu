@@ -1,0 +1,273 @@
+// Fourier-Bessel front end (App. A): from n x n pixel images to the steerable coefficients
+// a_{k,q} (k = 0..K, q = 1..Q) as the least-squares solution over the sampled basis.
+//
+//   setup    (once per n, K, Q)  Bessel zeros R_{k,q} (scan and bisection of J_k, FP64), the real
+//            design matrix A [n^2 x Mr] (Mr = Q + 2KQ: a_0q, then Re a_kq and Im a_kq of
+//            u^{kq} + u^{-kq}), its Gram G = A^T A (cuBLAS DGEMM), G^{-1} by Newton-Schulz from
+//            the Jacobi start diag(G)^{-1} (DGEMMs; the Jacobi-scaled Gram of the sampled basis is
+//            within ~1% of the identity, so a few steps reach FP64 accuracy), the projection
+//            P = G^{-1} A^T, stored per pixel in the coefficient layout [n^2][K+1][Q] complex FP32.
+//   project  y = images P, one GEMM over all images: [N x n^2] by [n^2 x 2M] (cuBLAS SGEMM, or
+//            TF32 tensor cores on request).  This is a plain library GEMM.
+//
+// Basis (App. A): u^{k,q}(r, theta) = N_{k,q} J_|k|(R_{|k|,q} r / c) e^{i k theta} on r <= c = (n - 1)/2,
+// N_{k,q} = 1 / (c sqrt(pi) |J_{k+1}(R_{k,q})|); pixel (row iy, column ix) at x = ix - c, y = iy - c.
+#include <cublas_v2.h>
+#include <math.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+
+#include "common.cuh"
+
+namespace mra {
+namespace {
+
+// q-th positive zeros of J_k for k = 0..K: a scan at step 0.05 (zeros are ~pi apart) from
+// max(k, 0.05) (the first zero of J_k lies above k) for sign changes, each refined by bisection;
+// also the normalisation N_{k,q}.  One thread per k.
+__global__ void k_fb_zeros(int K, int Q, double c, double* R, double* Nkq, int* status) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k > K) return;
+  const double h = 0.05;
+  double x0 = k == 0 ? h : (double)k;
+  double f0 = jn(k, x0);
+  int found = 0;
+  for (int it = 0; found < Q && it < 400000; ++it) {
+    const double x1 = x0 + h, f1 = jn(k, x1);
+    if ((f0 < 0.0) != (f1 < 0.0)) {
+      double lo = x0, hi = x1, flo = f0;
+      for (int b = 0; b < 80; ++b) {
+        const double mid = 0.5 * (lo + hi), fm = jn(k, mid);
+        if ((fm < 0.0) == (flo < 0.0)) lo = mid, flo = fm; else hi = mid;
+      }
+      const double z = 0.5 * (lo + hi);
+      R[k * Q + found] = z;
+      Nkq[k * Q + found] = 1.0 / (c * sqrt(M_PI) * fabs(jn(k + 1, z)));
+      ++found;
+    }
+    x0 = x1;
+    f0 = f1;
+  }
+  if (found < Q) atomicExch(status, (int)MRA_ENUMERIC);
+}
+
+// At[col][pixel] (row-major [Mr][n^2]): the design matrix column by column.
+__global__ void k_fb_basis(int n, int K, int Q, double c, const double* R, const double* Nkq, double* At) {
+  const long long npix = (long long)n * n, Mr = Q + 2LL * K * Q;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < Mr * npix;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int col = (int)(idx / npix);
+    const int pix = (int)(idx - (long long)col * npix);
+    int k, q, part;
+    if (col < Q) {
+      k = 0, q = col, part = 0;
+    } else {
+      const int j = col - Q;
+      k = 1 + j / (2 * Q);
+      q = (j % (2 * Q)) / 2;
+      part = j & 1;
+    }
+    const double x = (double)(pix % n) - c, y = (double)(pix / n) - c;
+    const double r = sqrt(x * x + y * y);
+    double v = 0.0;
+    if (r <= c) {
+      // J_k(0) = 1 for k = 0 and 0 otherwise (the library's jn is not evaluated at 0 for k >= 2)
+      const double jk = r > 0.0 ? jn(k, R[k * Q + q] * r / c) : (k == 0 ? 1.0 : 0.0);
+      const double f = Nkq[k * Q + q] * jk;
+      if (k == 0) {
+        v = f;
+      } else {
+        double s, co;
+        sincos((double)k * atan2(y, x), &s, &co);
+        v = part == 0 ? 2.0 * f * co : -2.0 * f * s;
+      }
+    }
+    At[idx] = v;
+  }
+}
+
+// X = diag(G)^{-1} (column-major Mr x Mr)
+__global__ void k_fb_jacobi(int Mr, const double* G, double* X) {
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < (long long)Mr * Mr;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % Mr), j = (int)(idx / Mr);
+    X[idx] = i == j ? 1.0 / G[idx] : 0.0;
+  }
+}
+
+// P (column-major [Mr x n^2], i.e. per pixel the Mr real parameters) to the coefficient layout
+// out[pixel][k][q] = (Re, Im) in FP32, Im = 0 for k = 0.
+__global__ void k_fb_scatter(int npix, int K, int Q, const double* P, float2* out) {
+  const int Mr = Q + 2 * K * Q, M = (K + 1) * Q;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < (long long)npix * M;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int pix = (int)(idx / M), e = (int)(idx % M);
+    const int k = e / Q, q = e % Q;
+    const double* p = P + (size_t)pix * Mr;
+    float2 v;
+    if (k == 0) {
+      v = make_float2((float)p[q], 0.f);
+    } else {
+      const int col = Q + 2 * ((k - 1) * Q + q);
+      v = make_float2((float)p[col], (float)p[col + 1]);
+    }
+    out[idx] = v;
+  }
+}
+
+// status = MRA_ENUMERIC if max |T - I| > tol (T column-major Mr x Mr): the iteration did not reach G^{-1}.
+__global__ void k_fb_check(int Mr, const double* T, double tol, int* status) {
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < (long long)Mr * Mr;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % Mr), j = (int)(idx / Mr);
+    const double e = T[idx] - (i == j ? 1.0 : 0.0);
+    if (!(fabs(e) <= tol)) atomicExch(status, (int)MRA_ENUMERIC);
+  }
+}
+
+// One cuBLAS handle per device, created on first use.
+int blas_handle(cublasHandle_t* out) {
+  static std::mutex mu;
+  static std::map<int, cublasHandle_t> handles;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return MRA_ECUDA;
+  std::lock_guard<std::mutex> g(mu);
+  auto it = handles.find(dev);
+  if (it == handles.end()) {
+    cublasHandle_t h;
+    if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) return MRA_ECUDA;
+    it = handles.emplace(dev, h).first;
+  }
+  *out = it->second;
+  return MRA_OK;
+}
+
+struct FbLayout {
+  size_t R, N, status, At, G, X, T, Xn, P, total;
+};
+FbLayout fb_layout(int n, int K, int Q) {
+  const size_t npix = (size_t)n * n, Mr = (size_t)Q + 2 * (size_t)K * Q, zq = (size_t)(K + 1) * Q;
+  FbLayout l;
+  size_t o = 0;
+  l.R = o; o = align256(o + 8 * zq);
+  l.N = o; o = align256(o + 8 * zq);
+  l.status = o; o = align256(o + 16);
+  l.At = o; o = align256(o + 8 * Mr * npix);
+  l.G = o; o = align256(o + 8 * Mr * Mr);
+  l.X = o; o = align256(o + 8 * Mr * Mr);
+  l.T = o; o = align256(o + 8 * Mr * Mr);
+  l.Xn = o; o = align256(o + 8 * Mr * Mr);
+  l.P = o; o = align256(o + 8 * Mr * npix);
+  l.total = o;
+  return l;
+}
+
+bool fb_dims_ok(int n, int K, int Q) {
+  if (n < 3 || n > 1024 || K < 0 || Q < 1 || K > 256 || Q > 256) return false;
+  if (((K + 1) * Q) % 2 != 0) return false;
+  // sampling criterion R_{k,q} <= pi n / 2 (App. A), with McMahon's estimate R_{K,Q} ~ (Q + K/2 - 1/4) pi
+  // plus a margin of half a zero spacing
+  return (double)Q + 0.5 * K + 0.25 <= 0.5 * n;
+}
+
+constexpr int kFbNewtonSteps = 6;  // error ~ delta^(2^6) from a Jacobi start within delta < 0.1
+
+}  // namespace
+}  // namespace mra
+
+using namespace mra;
+
+extern "C" {
+
+MRA_API size_t mra_fb_setup_workspace_bytes(int32_t n, int32_t K, int32_t Q) {
+  if (!fb_dims_ok(n, K, Q)) return 0;
+  return fb_layout(n, K, Q).total;
+}
+
+MRA_API int mra_fb_setup(int32_t n, int32_t K, int32_t Q, float* P_out, double* zeros_out, void* ws, size_t ws_bytes,
+                         void* stream) {
+  if (!fb_dims_ok(n, K, Q)) return MRA_EINVAL;
+  if (!P_out || (reinterpret_cast<uintptr_t>(P_out) % 16) != 0 || !ws || (reinterpret_cast<uintptr_t>(ws) % 256) != 0)
+    return MRA_EINVAL;
+  if (zeros_out && (reinterpret_cast<uintptr_t>(zeros_out) % 8) != 0) return MRA_EINVAL;
+  const FbLayout L_ = fb_layout(n, K, Q);
+  if (ws_bytes < L_.total) return MRA_EWORKSPACE;
+  cublasHandle_t h;
+  if (blas_handle(&h) != MRA_OK) return MRA_ECUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cublasSetStream(h, s) != CUBLAS_STATUS_SUCCESS) return MRA_ECUDA;
+  unsigned char* b = static_cast<unsigned char*>(ws);
+  double* R = reinterpret_cast<double*>(b + L_.R);
+  double* Nkq = reinterpret_cast<double*>(b + L_.N);
+  int* status = reinterpret_cast<int*>(b + L_.status);
+  double* At = reinterpret_cast<double*>(b + L_.At);
+  double* G = reinterpret_cast<double*>(b + L_.G);
+  double* X = reinterpret_cast<double*>(b + L_.X);
+  double* T = reinterpret_cast<double*>(b + L_.T);
+  double* Xn = reinterpret_cast<double*>(b + L_.Xn);
+  double* P = reinterpret_cast<double*>(b + L_.P);
+  const int npix = n * n, Mr = Q + 2 * K * Q;
+  const double c = 0.5 * (n - 1);
+  if (cudaMemsetAsync(status, 0, 16, s) != cudaSuccess) return MRA_ECUDA;
+  k_fb_zeros<<<(K + 1 + 63) / 64, 64, 0, s>>>(K, Q, c, R, Nkq, status);
+  k_fb_basis<<<2048, 256, 0, s>>>(n, K, Q, c, R, Nkq, At);
+  if (cudaGetLastError() != cudaSuccess) return MRA_ECUDA;
+  // A is column-major [npix x Mr] (At row-major); G = A^T A
+  const double one = 1.0, zero = 0.0, two = 2.0, mone = -1.0;
+  if (cublasDgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, Mr, Mr, npix, &one, At, npix, At, npix, &zero, G, Mr) !=
+      CUBLAS_STATUS_SUCCESS)
+    return MRA_ECUDA;
+  k_fb_jacobi<<<1024, 256, 0, s>>>(Mr, G, X);
+  for (int it = 0; it < kFbNewtonSteps; ++it) {  // X <- 2X - X G X
+    if (cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, Mr, Mr, Mr, &one, G, Mr, X, Mr, &zero, T, Mr) !=
+        CUBLAS_STATUS_SUCCESS)
+      return MRA_ECUDA;
+    if (cudaMemcpyAsync(Xn, X, sizeof(double) * Mr * Mr, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return MRA_ECUDA;
+    if (cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, Mr, Mr, Mr, &mone, X, Mr, T, Mr, &two, Xn, Mr) !=
+        CUBLAS_STATUS_SUCCESS)
+      return MRA_ECUDA;
+    std::swap(X, Xn);
+  }
+  // G X must be the identity to FP64 accuracy (the sampled basis is far from singular for n, K, Q
+  // within the sampling criterion; otherwise the setup reports MRA_ENUMERIC)
+  if (cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, Mr, Mr, Mr, &one, G, Mr, X, Mr, &zero, T, Mr) != CUBLAS_STATUS_SUCCESS)
+    return MRA_ECUDA;
+  k_fb_check<<<1024, 256, 0, s>>>(Mr, T, 1e-10, status);
+  // P = X A^T, column-major [Mr x npix]
+  if (cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_T, Mr, npix, Mr, &one, X, Mr, At, npix, &zero, P, Mr) !=
+      CUBLAS_STATUS_SUCCESS)
+    return MRA_ECUDA;
+  k_fb_scatter<<<2048, 256, 0, s>>>(npix, K, Q, P, reinterpret_cast<float2*>(P_out));
+  if (zeros_out &&
+      cudaMemcpyAsync(zeros_out, R, sizeof(double) * (K + 1) * Q, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return MRA_ECUDA;
+  if (cudaGetLastError() != cudaSuccess) return MRA_ECUDA;
+  int st = 0;
+  if (cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return MRA_ECUDA;
+  return st;
+}
+
+MRA_API int mra_fb_project(int32_t N, int32_t n, int32_t K, int32_t Q, const float* images, const float* P,
+                           float* y_out, int32_t tf32, void* stream) {
+  if (N < 1 || !fb_dims_ok(n, K, Q)) return MRA_EINVAL;
+  if (!images || !P || !y_out || (reinterpret_cast<uintptr_t>(images) % 16) != 0 ||
+      (reinterpret_cast<uintptr_t>(P) % 16) != 0 || (reinterpret_cast<uintptr_t>(y_out) % 16) != 0)
+    return MRA_EINVAL;
+  cublasHandle_t h;
+  if (blas_handle(&h) != MRA_OK) return MRA_ECUDA;
+  if (cublasSetStream(h, static_cast<cudaStream_t>(stream)) != CUBLAS_STATUS_SUCCESS) return MRA_ECUDA;
+  const int npix = n * n, two_m = 2 * (K + 1) * Q;
+  const float one = 1.f, zero = 0.f;
+  // row-major y [N x 2M] = images [N x npix] P [npix x 2M]  <=>  column-major y^T = P^T images^T
+  const cublasStatus_t r = cublasGemmEx(h, CUBLAS_OP_N, CUBLAS_OP_N, two_m, N, npix, &one, P, CUDA_R_32F, two_m,
+                                        images, CUDA_R_32F, npix, &zero, y_out, CUDA_R_32F, two_m,
+                                        tf32 ? CUBLAS_COMPUTE_32F_FAST_TF32 : CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
+  return r == CUBLAS_STATUS_SUCCESS ? MRA_OK : MRA_ECUDA;
+}
+
+}  // extern "C"

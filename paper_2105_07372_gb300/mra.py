@@ -73,6 +73,9 @@ _SIGS = {
     "mra_sync_ppm": (c_int, [c_int32, c_int32, c_void_p, c_int32, c_int32, c_void_p, c_void_p]),
     "mra_sync_match": (c_int, [POINTER(mra_dims), c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "mra_template_match": (c_int, [POINTER(mra_dims), c_void_p, c_void_p, c_void_p, c_void_p]),
+    "mra_fb_setup_workspace_bytes": (c_size_t, [c_int32, c_int32, c_int32]),
+    "mra_fb_setup": (c_int, [c_int32, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "mra_fb_project": (c_int, [c_int32, c_int32, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
     "mra_sync": (c_int, [POINTER(mra_dims), c_void_p, c_int32, c_int32, c_int32, c_void_p, c_void_p, c_size_t,
                          c_void_p]),
     "mra_align_mean": (c_int, [POINTER(mra_dims), c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
@@ -277,6 +280,20 @@ def mra_sync_ppm(L, P, rel, n_power, n_ppm, phi_out, stream=None):
 def mra_sync_match(d, y, P, phi, shift_out, ws, stream=None):
     _check("mra_sync_match", load().mra_sync_match(ctypes.byref(d), _p(y), int(P), _p(phi), _p(shift_out), _p(ws),
                                                    ws.numel(), _stream(stream)))
+
+
+def mra_fb_setup_workspace_bytes(n, K, Q) -> int:
+    return int(load().mra_fb_setup_workspace_bytes(int(n), int(K), int(Q)))
+
+
+def mra_fb_setup(n, K, Q, P_out, zeros_out, ws, stream=None):
+    _check("mra_fb_setup", load().mra_fb_setup(int(n), int(K), int(Q), _p(P_out), _p(zeros_out), _p(ws), ws.numel(),
+                                               _stream(stream)))
+
+
+def mra_fb_project(N, n, K, Q, images, P, y_out, tf32=False, stream=None):
+    _check("mra_fb_project", load().mra_fb_project(int(N), int(n), int(K), int(Q), _p(images), _p(P), _p(y_out),
+                                                   1 if tf32 else 0, _stream(stream)))
 
 
 def mra_template_match(d, y, ref, shift_out, stream=None):

@@ -44,6 +44,23 @@ def synchronize(y, d, P, ws: Workspaces, n_power=50, n_ppm=100, stream=None) -> 
     return shift
 
 
+def fb_projection(n, K, Q, device="cuda", stream=None):
+    """The Fourier-Bessel projection of App. A for n x n images onto k = 0..K, q = 1..Q: a complex64 tensor
+    [n*n, K+1, Q] (set up once; mra_fb_setup)."""
+    P = torch.empty((n * n, K + 1, Q), dtype=torch.complex64, device=device)
+    ws = mra.workspace(mra.mra_fb_setup_workspace_bytes(n, K, Q), device)
+    mra.mra_fb_setup(n, K, Q, P, None, ws, stream)
+    return P
+
+
+def fb_coefficients(images, P, K, Q, tf32=False, stream=None) -> torch.Tensor:
+    """Coefficients [N, K+1, Q] (complex64) of images [N, n, n] (float32): the observations y of Eq. MRA_Model_FB."""
+    N, n = images.shape[0], images.shape[-1]
+    y = torch.empty((N, K + 1, Q), dtype=torch.complex64, device=images.device)
+    mra.mra_fb_project(N, n, K, Q, images.contiguous(), P, y, tf32, stream)
+    return y
+
+
 def template_match(y, d, ref, stream=None) -> torch.Tensor:
     """Template matching (Sec. 2.1.1): the shift of every image against the reference ref [K+1, Q] (complex64
     device tensor; an observation such as y[0], or a known signal)."""
