@@ -24,33 +24,56 @@
 namespace mra {
 namespace {
 
-// q-th positive zeros of J_k for k = 0..K: a scan at step 0.05 (zeros are ~pi apart) from
-// max(k, 0.05) (the first zero of J_k lies above k) for sign changes, each refined by bisection;
-// also the normalisation N_{k,q}.  One thread per k.
+// q-th positive zeros of J_k for k = 0..K, one warp per k: the grid x_j = x0 + j h (h = 0.05; zeros
+// are ~pi apart) from x0 = max(k, h) (the first zero of J_k lies above k) up to beyond McMahon's
+// estimate of the Q-th zero, split into 32 consecutive runs of grid intervals; each lane counts the
+// sign changes in its run, a warp prefix sum orders them, and each lane then bisects its own
+// changes (80 halvings) into R[k][q]; also the normalisation N_{k,q}.
 __global__ void k_fb_zeros(int K, int Q, double c, double* R, double* Nkq, int* status) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (k > K) return;
   const double h = 0.05;
-  double x0 = k == 0 ? h : (double)k;
-  double f0 = jn(k, x0);
-  int found = 0;
-  for (int it = 0; found < Q && it < 400000; ++it) {
-    const double x1 = x0 + h, f1 = jn(k, x1);
-    if ((f0 < 0.0) != (f1 < 0.0)) {
-      double lo = x0, hi = x1, flo = f0;
-      for (int b = 0; b < 80; ++b) {
-        const double mid = 0.5 * (lo + hi), fm = jn(k, mid);
-        if ((fm < 0.0) == (flo < 0.0)) lo = mid, flo = fm; else hi = mid;
+  const double x0 = k == 0 ? h : (double)k;
+  const double xmax = (Q + 0.5 * k + 2.0) * M_PI + 2.0;
+  const long long nint = (long long)((xmax - x0) / h) + 1;  // grid intervals scanned
+  const long long per = (nint + 31) / 32;
+  const long long j0 = lane * per, j1 = min(nint, j0 + per);
+  auto count = [&](bool write, int base) {
+    int n = 0;
+    if (j0 >= j1) return 0;
+    double xa = x0 + (double)j0 * h, fa = jn(k, xa);
+    for (long long j = j0; j < j1; ++j) {
+      const double xb = x0 + (double)(j + 1) * h, fb = jn(k, xb);
+      if ((fa < 0.0) != (fb < 0.0)) {
+        if (write && base + n < Q) {
+          double lo = xa, hi = xb, flo = fa;
+          for (int it = 0; it < 80; ++it) {
+            const double mid = 0.5 * (lo + hi), fm = jn(k, mid);
+            if ((fm < 0.0) == (flo < 0.0)) lo = mid, flo = fm; else hi = mid;
+          }
+          const double z = 0.5 * (lo + hi);
+          R[k * Q + base + n] = z;
+          Nkq[k * Q + base + n] = 1.0 / (c * sqrt(M_PI) * fabs(jn(k + 1, z)));
+        }
+        ++n;
       }
-      const double z = 0.5 * (lo + hi);
-      R[k * Q + found] = z;
-      Nkq[k * Q + found] = 1.0 / (c * sqrt(M_PI) * fabs(jn(k + 1, z)));
-      ++found;
+      xa = xb, fa = fb;
     }
-    x0 = x1;
-    f0 = f1;
+    return n;
+  };
+  const int mine = count(false, 0);
+  int incl = mine;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
   }
-  if (found < Q) atomicExch(status, (int)MRA_ENUMERIC);
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  if (total < Q) {
+    if (lane == 0) atomicExch(status, (int)MRA_ENUMERIC);
+    return;
+  }
+  if (incl - mine < Q) count(true, incl - mine);
 }
 
 // At[col][pixel] (row-major [Mr][n^2]): the design matrix column by column.
@@ -211,7 +234,7 @@ MRA_API int mra_fb_setup(int32_t n, int32_t K, int32_t Q, float* P_out, double* 
   const int npix = n * n, Mr = Q + 2 * K * Q;
   const double c = 0.5 * (n - 1);
   if (cudaMemsetAsync(status, 0, 16, s) != cudaSuccess) return MRA_ECUDA;
-  k_fb_zeros<<<(K + 1 + 63) / 64, 64, 0, s>>>(K, Q, c, R, Nkq, status);
+  k_fb_zeros<<<(K + 1 + 3) / 4, 128, 0, s>>>(K, Q, c, R, Nkq, status);  // a warp per k
   k_fb_basis<<<2048, 256, 0, s>>>(n, K, Q, c, R, Nkq, At);
   if (cudaGetLastError() != cudaSuccess) return MRA_ECUDA;
   // A is column-major [npix x Mr] (At row-major); G = A^T A

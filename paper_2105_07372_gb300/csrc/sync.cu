@@ -90,6 +90,7 @@ __global__ void __launch_bounds__(kPairThreads) k_pairwise(const float2* y, int 
 // A = sum C.x cos, B = sum C.y (-sin), the values are A + B at s and A - B at L - s.
 constexpr int kTmThreads = 256;
 __host__ __device__ inline int tm_even(int v) { return (v + 1) & ~1; }
+constexpr int kTmReseed = 8;
 __global__ void __launch_bounds__(kTmThreads) k_template_match(const float2* y, const float2* ref, int N, int Kp1,
                                                                int Q, int L, int nwarps, int* shift) {
   extern __shared__ __align__(16) unsigned char tsm[];
@@ -132,18 +133,48 @@ __global__ void __launch_bounds__(kTmThreads) k_template_match(const float2* y, 
     auto take = [&](float v, int l) {
       if (v > best || (v == best && l < bi)) best = v, bi = l;
     };
-    for (int l = lane; 2 * l <= L; l += 32) {  // the pair {l, L - l}
-      float A = 0.f, B = 0.f;
-      int m = 0;
-      for (int k = 0; k < Kp1; ++k) {
-        const float2 t = tf[m], c = C[k];  // Re(C e^{+i phi}) = A + B with t = e^{-i phi}
-        A = fmaf(c.x, t.x, A);
-        B = fmaf(c.y, t.y, B);
-        m += l;
-        if (m >= L) m -= L;
+    // four pairs {l, L - l} per lane at a time (l = lane + 32 (i0 + g)); the twiddle e^{-2 pi i k l / L} steps
+    // from k to k + 1 by one complex product with e^{-2 pi i l / L} and is reloaded from the table every
+    // kTmReseed rows (bounded rounding drift; table reads of different lanes meet in the same banks)
+    const int npair = L / 2 + 1;
+    for (int i0 = 0; lane + 32 * i0 < npair; i0 += 4) {
+      float A[4], B[4];
+      float2 t[4], w[4];
+      int l[4], m[4], m8[4];
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        l[g] = min(lane + 32 * (i0 + g), npair - 1);
+        w[g] = tf[l[g]];
+        m[g] = 0;
+        m8[g] = (int)(((long long)kTmReseed * l[g]) % L);
+        A[g] = 0.f, B[g] = 0.f;
       }
-      take(A + B, l);
-      if (l > 0 && 2 * l != L) take(A - B, L - l);
+      for (int k0 = 0; k0 < Kp1; k0 += kTmReseed) {
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          t[g] = tf[m[g]];
+          m[g] += m8[g];
+          if (m[g] >= L) m[g] -= L;
+        }
+        const int k1 = min(k0 + kTmReseed, Kp1);
+        for (int k = k0; k < k1; ++k) {
+          const float2 c = C[k];  // Re(C e^{+i phi}) = A + B with t = e^{-i phi}
+#pragma unroll
+          for (int g = 0; g < 4; ++g) {
+            A[g] = fmaf(c.x, t[g].x, A[g]);
+            B[g] = fmaf(c.y, t[g].y, B[g]);
+            t[g] = cmul(t[g], w[g]);
+          }
+        }
+      }
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        const int lg = lane + 32 * (i0 + g);
+        if (lg < npair) {
+          take(A[g] + B[g], lg);
+          if (lg > 0 && 2 * lg != L) take(A[g] - B[g], L - lg);
+        }
+      }
     }
     for (int o = 16; o > 0; o >>= 1) {
       const float ov = __shfl_xor_sync(0xffffffffu, best, o);
