@@ -495,6 +495,20 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR, IPW>::kThreads, 1) k_swee
 #pragma unroll
         for (int m = 0; m < MR; ++m) W[i][m] = make_float2(0.f, 0.f);
       for (int u0 = 0; u0 < NUP; u0 += 4 * kUC) {
+        if constexpr (LWC <= 0 && IPW == 1) {
+          // wide windows: skip chunks whose units all lie farther than D from the peak (zero weights)
+          const int p = peak[0], D = dist[0];
+          bool act = wrap;
+#pragma unroll
+          for (int t = 0; t < kUC; ++t) {
+            const int u = u0 + j + 4 * t;
+            if (u < NU) {
+              const int2 ab = uab[u];
+              act |= (ab.x >= p - D && ab.x <= p + D) || (ab.y >= 0 && ab.y >= p - D && ab.y <= p + D);
+            }
+          }
+          if (!__any_sync(0xffffffffu, act)) continue;
+        }
         float sw[IPW][kUC], dw[IPW][kUC];
 #pragma unroll
         for (int t = 0; t < kUC; ++t) {
