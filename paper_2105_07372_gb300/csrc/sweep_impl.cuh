@@ -2,9 +2,10 @@
 //
 // Each warp owns a private shared-memory ring filled by bulk copies (one image
 // per copy, IPW images per ring stage, two stages) and runs its images through
-// every stage with warp-level synchronisation only.  With IPW = 2 the warp
-// carries two images at once: the x and twiddle loads are shared by both and
-// the two images give independent instruction streams.
+// every stage with warp-level synchronisation only.  The code is written for IPW
+// images carried at once (the x and twiddle loads shared by them), but only
+// IPW = 1 is built: two images per warp measured slower (fewer resident warps),
+// and the peak-relative second pass and the wide-window paths handle one image.
 //
 //   lanes form 8 quads; quad r owns the rows k = r, r+8, r+16, ...; lane j of a
 //   quad owns the float4 columns j, j+4, ... of those rows (QV of them per row).
