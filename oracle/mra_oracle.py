@@ -21,6 +21,8 @@ its own order and notation:
 * template matching: every image against one reference, O(NLM)        Sec. 2.1.1 (template matching)
 * shift pmf of 1-D template matching with the true signal as reference App. B, Eq. (shift_pmf)
 * Fourier-Bessel coefficients of pixel images by least squares          App. A
+* steerable PCA of the coefficients (data-driven radial basis per k)   App. A (sPCA; details are the
+  cited method's, restated in the readings below)
 * learned rotation distribution, centred by theta_c                    Eq. (learned_distribution_formula), Algorithm 1
 * relative error up to rotation                                       Sec. 2.2, relative-error equation
 * likelihood with the (pi sigma^2)^{-M} factor                          Sec. 2.2, likelihood equation
@@ -56,6 +58,13 @@ Readings of the paper taken here (each also listed in the design notes):
   the EM window and rho_0 = rho_bar refer to.  This is -Delta_theta_bar of
   Algorithm 1 under the paper's rotation sign.
 * rho_bar on the window is the restriction of rho_bar renormalised to sum 1.
+* Steerable PCA: for every angular index k the uncentred second moment C_k = (1/N) sum_i a_ik a_ik^H
+  over the Q radial entries (uncentred also at k = 0, so that the mean image's direction is kept),
+  its eigenvectors kept where the eigenvalue exceeds the noise-only spectrum's upper edge
+  sigma^2 (1 + sqrt(Q/N))^2 (Marchenko-Pastur); coefficients b_ik = U_k^H a_ik.  Each eigenvector's
+  phase makes its largest-magnitude entry real positive; eigenvalues descend.  The output is
+  [K'+1, Q'] with K' the largest k that keeps a component and Q' the largest kept count (made even
+  with (K'+1) when needed), zero where a k keeps fewer.
 * Relative error: the stored k > 0 entries count twice (the k < 0 half of a
   real image), the angle is continuous (fine grid then golden section).
 
@@ -426,6 +435,58 @@ def fb_project(images: np.ndarray, K: int, Q: int) -> np.ndarray:
     ri = beta[:, Q:].reshape(images.shape[0], K, Q, 2)
     a[:, 1:, :] = ri[..., 0] + 1j * ri[..., 1]
     return a
+
+
+def _phase_fix(U: np.ndarray) -> np.ndarray:
+    """Columns scaled by a unit phase so that each column's largest-magnitude entry is real positive."""
+    U = U.copy()
+    for j in range(U.shape[1]):
+        i = int(np.argmax(np.abs(U[:, j])))
+        U[:, j] *= np.conj(U[i, j]) / abs(U[i, j])
+    return U
+
+
+@dataclasses.dataclass
+class SPCA:
+    bases: list          # per k: [Q, Q_k] complex, kept eigenvectors (columns)
+    eigs: list           # per k: [Q] eigenvalues, descending
+    counts: np.ndarray   # [K+1] kept per k
+    K2: int
+    Q2: int
+
+
+def spca_fit(a: np.ndarray, sigma2: float) -> SPCA:
+    """Steerable PCA of coefficients a [N, K+1, Q] with noise variance sigma2 per entry (readings above)."""
+    a = np.asarray(a, dtype=np.complex128)
+    N, Kp1, Q = a.shape
+    edge = sigma2 * (1.0 + math.sqrt(Q / N)) ** 2
+    bases, eigs, counts = [], [], []
+    for k in range(Kp1):
+        A = a[:, k, :]                      # [N, Q]
+        C = A.T @ A.conj() / N              # sum_i a_ik a_ik^H / N  (entry (q, q') = mean a_q conj(a_q'))
+        w, U = np.linalg.eigh(C)
+        order = np.argsort(-w, kind="stable")
+        w, U = w[order], _phase_fix(U[:, order])
+        keep = int(np.sum(w > edge))
+        bases.append(U[:, :keep])
+        eigs.append(w)
+        counts.append(keep)
+    counts = np.array(counts)
+    K2 = int(np.max(np.nonzero(counts)[0])) if np.any(counts) else 0
+    Q2 = int(max(counts.max(), 1))
+    if ((K2 + 1) * Q2) % 2:
+        Q2 += 1
+    return SPCA(bases=bases, eigs=eigs, counts=counts, K2=K2, Q2=Q2)
+
+
+def spca_project(a: np.ndarray, fit: SPCA) -> np.ndarray:
+    """b [N, K'+1, Q'] with b_ik = U_k^H a_ik in the first counts[k] entries of row k, zero elsewhere."""
+    a = np.asarray(a, dtype=np.complex128)
+    out = np.zeros((a.shape[0], fit.K2 + 1, fit.Q2), dtype=np.complex128)
+    for k in range(fit.K2 + 1):
+        U = fit.bases[k]
+        out[:, k, :U.shape[1]] = a[:, k, :] @ U.conj()
+    return out
 
 
 def align_mean(y: np.ndarray, shifts: np.ndarray, L: int) -> np.ndarray:

@@ -603,3 +603,56 @@ def test_fb_pixel_noise_is_nearly_white_in_coefficients():
     v = np.mean(np.abs(O.fb_project(noise, K, Q)) ** 2, axis=0)
     assert abs(v.mean() - s ** 2) < 0.03
     assert np.all(np.abs(v - s ** 2) < 0.1)
+
+
+# --------------------------------------------------------------------------- steerable PCA (App. A)
+def _lowrank(N, K, Q, r, var, sigma2, seed):
+    """a_ik = sum_{j<r} z_ikj u_kj + noise with known orthonormal u_k [Q, r] and E|z|^2 = var[j]."""
+    rng = np.random.default_rng(seed)
+    U = []
+    a = np.zeros((N, K + 1, Q), dtype=np.complex128)
+    for k in range(K + 1):
+        M = rng.standard_normal((Q, r)) + 1j * rng.standard_normal((Q, r))
+        Uk, _ = np.linalg.qr(M)
+        U.append(Uk)
+        z = (rng.standard_normal((N, r)) + 1j * rng.standard_normal((N, r))) * np.sqrt(np.asarray(var) / 2)
+        a[:, k, :] = z @ Uk.T
+    a += (rng.standard_normal(a.shape) + 1j * rng.standard_normal(a.shape)) * math.sqrt(sigma2 / 2)
+    return a, U
+
+
+def test_spca_recovers_known_low_rank_subspaces():
+    """Rank 2 per k with variances 5 and 2 over unit noise: two components kept at every k, their span is the true
+    one (principal angles below 0.05), eigenvalues var + sigma^2 within 5%, U^H U = I, max entries real positive."""
+    N, K, Q = 20000, 4, 10
+    a, U = _lowrank(N, K, Q, 2, [5.0, 2.0], 1.0, seed=41)
+    f = O.spca_fit(a, 1.0)
+    np.testing.assert_array_equal(f.counts, 2)
+    assert (f.K2, f.Q2) == (K, 2)
+    for k in range(K + 1):
+        B = f.bases[k]
+        s = np.linalg.svd(B.conj().T @ U[k], compute_uv=False)
+        assert np.all(s > np.cos(0.05))
+        np.testing.assert_allclose(f.eigs[k][:2], [6.0, 3.0], rtol=0.05)
+        np.testing.assert_allclose(B.conj().T @ B, np.eye(2), atol=1e-12)
+        for j in range(2):
+            i = int(np.argmax(np.abs(B[:, j])))
+            assert abs(B[i, j].imag) < 1e-12 and B[i, j].real > 0
+
+
+def test_spca_is_steerable_and_scalar_case():
+    """Rotating every image (a_ik e^{-i k theta_i}) leaves each C_k unchanged, so b rotates the same way; with Q = 1
+    the basis is [1] and b = a wherever mean |a_k|^2 exceeds sigma^2 (1 + 1/sqrt N)^2."""
+    N, K, Q = 3000, 5, 6
+    a, _ = _lowrank(N, K, Q, 1, [4.0], 0.5, seed=42)
+    th = np.random.default_rng(43).uniform(0, 2 * np.pi, N)
+    ph = np.exp(-1j * np.outer(th, np.arange(K + 1)))[:, :, None]
+    f, fr = O.spca_fit(a, 0.5), O.spca_fit(a * ph, 0.5)
+    b, br = O.spca_project(a, f), O.spca_project(a * ph, fr)
+    np.testing.assert_allclose(br, b * ph[:, : f.K2 + 1], atol=1e-10)
+    a1 = a[:, :, :1]
+    f1 = O.spca_fit(a1, 0.5)
+    keep = np.mean(np.abs(a1[:, :, 0]) ** 2, axis=0) > 0.5 * (1 + 1 / math.sqrt(N)) ** 2
+    np.testing.assert_array_equal(f1.counts, keep.astype(int))
+    b1 = O.spca_project(a1, f1)
+    np.testing.assert_allclose(b1[:, :, 0], a1[:, : f1.K2 + 1, 0] * keep[None, : f1.K2 + 1], atol=1e-13)
