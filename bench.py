@@ -694,7 +694,22 @@ def bench_fb(args):
     except Exception:
         pass
     tf32_peak = bf16 * 1.1 / 2.25  # the measured bf16 peak times the nominal TF32 / BF16 ratio
+    # steerable PCA of the projected coefficients: the fit (second moments on the GPU, eigenvectors on the
+    # host) once, then the reduced coefficients by CGEMM
     step()
+    d = mra.dims(N, K, Q, c["L"], sigma ** 2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    yr, d2, basis, counts = pipeline.spca(y, d)
+    torch.cuda.synchronize()
+    spca_s = time.perf_counter() - t0
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.steps):
+        mra.mra_spca_project(d, y, d2.K, d2.Q, basis, yr)
+    ev1.record()
+    torch.cuda.synchronize()
+    spca_proj_ms = ev0.elapsed_time(ev1) / args.steps
     # white pixel noise of variance sigma^2 stays (nearly) white with the same variance per coefficient (App. A)
     noise_ratio = float(torch.mean(torch.abs(y.cpu().to(torch.complex128) - torch.from_numpy(a)) ** 2) / sigma ** 2)
     line = {"metric": "Fourier-Bessel projected images/s", "value": N / (ms / 1e3), "unit": "images/s", "n_gpus": 1,
@@ -713,6 +728,8 @@ def bench_fb(args):
                      "peak_source": "measured bf16 x 1.1/2.25 (nominal TF32/BF16)",
                      "frac": flops / (ms_tf32 / 1e3) / 1e12 / tf32_peak},
             "setup_s": setup_s, "coefficient_noise_variance_over_pixel_variance": noise_ratio,
+            "spca": {"fit_s": spca_s, "project_ms": spca_proj_ms, "reduced_shape": [d2.K + 1, d2.Q],
+                     "kept_per_k": [int(v) for v in counts]},
             "clocks": clk.summary(), "gpu_launches": args.steps}
     print(json.dumps(line), flush=True)
 

@@ -297,6 +297,31 @@ MRA_API int mra_fb_setup(int32_t n, int32_t K, int32_t Q, float* P_out, double* 
 MRA_API int mra_fb_project(int32_t N, int32_t n, int32_t K, int32_t Q, const float* images, const float* P,
                            float* y_out, int32_t tf32, void* stream);
 
+/* Steerable PCA of coefficients (App. A: a data-driven radial basis per angular index k that keeps
+ * steerability).  For every k the uncentred second moment C_k = (1/N) sum_i a_ik a_ik^H over the Q
+ * radial entries (FP32 GEMM over the images), its eigenvectors on the host (FP64 Jacobi), kept where the
+ * eigenvalue exceeds sigma2 (1 + sqrt(Q/N))^2 (dims->sigma2 is the coefficients' noise variance).  Each
+ * kept eigenvector's largest-magnitude entry is real positive; eigenvalues descend.  The reduced
+ * coefficients b_ik = U_k^H a_ik have shape [K2+1][Q2]: K2 the largest k that keeps a component, Q2 the
+ * largest count (plus one if (K2+1) Q2 would be odd); entries beyond a k's count are zero.  Rotations
+ * still multiply b_ik by e^{-i k theta} and white noise stays white with the same variance.
+ *
+ * mra_spca_fit (synchronizes the stream): y [N][K+1][Q] complex float (device);
+ *   basis_out device [K+1][Q][Q] complex float (column c of block k = the c-th eigenvector of C_k, zero
+ *   beyond the kept count); eig_out host [K+1][Q] double or NULL; counts_out host [K+1] int32 or NULL;
+ *   K2_out, Q2_out host; ws of mra_spca_workspace_bytes(dims) bytes.
+ * mra_spca_project: y_out [N][K2+1][Q2] complex float = the reduced coefficients of y. */
+MRA_API size_t mra_spca_workspace_bytes(const mra_dims* dims);
+MRA_API int mra_spca_fit(const mra_dims* dims, const float* y, float* basis_out, double* eig_out, int32_t* counts_out,
+                         int32_t* K2_out, int32_t* Q2_out, void* ws, size_t ws_bytes, void* stream);
+MRA_API int mra_spca_project(const mra_dims* dims, const float* y, int32_t K2, int32_t Q2, const float* basis,
+                             float* y_out, void* stream);
+
+/* Eigen-decomposition of a Hermitian n x n matrix (HOST pointers, column-major complex double, n <= 512):
+ * w [n] descending, V [n][n] eigenvectors as columns, each with its largest-magnitude entry real positive.
+ * FP64 cyclic Jacobi on the real symmetric embedding.  Used by mra_spca_fit; no GPU needed. */
+MRA_API int mra_hermitian_eig(int32_t n, const double* A, double* w, double* V);
+
 /* ------------------------------------------------------------------ rotation prior */
 
 /* One trial of Algorithm 1 (learning the post-synchronization rotation distribution):

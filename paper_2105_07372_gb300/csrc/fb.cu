@@ -294,3 +294,207 @@ MRA_API int mra_fb_project(int32_t N, int32_t n, int32_t K, int32_t Q, const flo
 }
 
 }  // extern "C"
+
+// ============================================================================ steerable PCA
+// For every angular index k: the uncentred second moment C_k = (1/N) sum_i a_ik a_ik^H over the Q
+// radial entries (one strided-batched cuBLAS CGEMM over all images), its eigen-decomposition on
+// the host (C++, FP64: cyclic Jacobi on the real symmetric embedding [[Re C, -Im C], [Im C, Re C]],
+// whose eigenvectors (x; y) are the complex eigenvectors x + i y, each twice; a complex Gram-Schmidt
+// pass keeps one of each pair), the eigenvectors whose eigenvalue exceeds the noise-only edge
+// sigma^2 (1 + sqrt(Q/N))^2, and the projection b_ik = U_k^H a_ik (a second strided-batched CGEMM).
+#include <complex>
+#include <vector>
+
+namespace mra {
+namespace {
+
+typedef std::complex<double> cd;
+
+// Eigen-decomposition of a Hermitian n x n matrix A (column-major): w descending, V's columns the
+// eigenvectors, each scaled so that its largest-magnitude entry is real positive.
+int herm_eig(int n, const cd* A, double* w, cd* V) {
+  const int m = 2 * n;
+  std::vector<double> S((size_t)m * m), E((size_t)m * m, 0.0);
+  for (int j = 0; j < n; ++j)
+    for (int i = 0; i < n; ++i) {
+      const cd a = A[(size_t)j * n + i];  // row i, column j
+      S[(size_t)j * m + i] = a.real();
+      S[(size_t)(j + n) * m + i] = -a.imag();
+      S[(size_t)j * m + i + n] = a.imag();
+      S[(size_t)(j + n) * m + i + n] = a.real();
+    }
+  for (int i = 0; i < m; ++i) E[(size_t)i * m + i] = 1.0;
+  auto s_at = [&](int i, int j) -> double& { return S[(size_t)j * m + i]; };
+  double norm = 0.0;
+  for (double v : S) norm += v * v;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0;
+    for (int j = 0; j < m; ++j)
+      for (int i = 0; i < j; ++i) off += s_at(i, j) * s_at(i, j);
+    if (off <= 1e-30 * norm) break;
+    for (int p = 0; p < m - 1; ++p)
+      for (int q = p + 1; q < m; ++q) {
+        const double apq = s_at(p, q);
+        if (apq == 0.0) continue;
+        const double theta = (s_at(q, q) - s_at(p, p)) / (2.0 * apq);
+        const double t = (theta >= 0.0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < m; ++k) {  // columns p, q
+          const double skp = s_at(k, p), skq = s_at(k, q);
+          s_at(k, p) = c * skp - s * skq;
+          s_at(k, q) = s * skp + c * skq;
+        }
+        for (int k = 0; k < m; ++k) {  // rows p, q
+          const double spk = s_at(p, k), sqk = s_at(q, k);
+          s_at(p, k) = c * spk - s * sqk;
+          s_at(q, k) = s * spk + c * sqk;
+        }
+        for (int k = 0; k < m; ++k) {
+          const double ekp = E[(size_t)p * m + k], ekq = E[(size_t)q * m + k];
+          E[(size_t)p * m + k] = c * ekp - s * ekq;
+          E[(size_t)q * m + k] = s * ekp + c * ekq;
+        }
+      }
+  }
+  std::vector<int> order(m);
+  for (int i = 0; i < m; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return s_at(x, x) > s_at(y, y); });
+  std::vector<cd> U;  // accepted complex eigenvectors, n each
+  std::vector<double> lam;
+  for (int idx = 0; idx < m && (int)lam.size() < n; ++idx) {
+    const int j = order[idx];
+    std::vector<cd> u(n);
+    for (int i = 0; i < n; ++i) u[i] = cd(E[(size_t)j * m + i], E[(size_t)j * m + i + n]);
+    for (size_t v = 0; v < lam.size(); ++v) {
+      cd dot = 0.0;
+      for (int i = 0; i < n; ++i) dot += std::conj(U[v * n + i]) * u[i];
+      for (int i = 0; i < n; ++i) u[i] -= dot * U[v * n + i];
+    }
+    double r = 0.0;
+    for (int i = 0; i < n; ++i) r += std::norm(u[i]);
+    r = std::sqrt(r);
+    if (r < 0.5) continue;  // the partner of an accepted vector
+    for (int i = 0; i < n; ++i) u[i] /= r;
+    double l = 0.0;  // Rayleigh quotient u^H A u
+    for (int jj = 0; jj < n; ++jj) {
+      cd au = 0.0;
+      for (int i = 0; i < n; ++i) au += A[(size_t)i * n + jj] * u[i];  // (A u)_jj = sum_i A[jj][i] u_i
+      l += (std::conj(u[jj]) * au).real();
+    }
+    U.insert(U.end(), u.begin(), u.end());
+    lam.push_back(l);
+  }
+  if ((int)lam.size() < n) return MRA_ENUMERIC;
+  std::vector<int> ord(n);
+  for (int i = 0; i < n; ++i) ord[i] = i;
+  std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return lam[x] > lam[y]; });
+  for (int c = 0; c < n; ++c) {
+    const cd* u = &U[(size_t)ord[c] * n];
+    int imax = 0;
+    for (int i = 1; i < n; ++i)
+      if (std::abs(u[i]) > std::abs(u[imax])) imax = i;
+    const cd ph = std::conj(u[imax]) / std::abs(u[imax]);
+    for (int i = 0; i < n; ++i) V[(size_t)c * n + i] = u[i] * ph;
+    w[c] = lam[ord[c]];
+  }
+  return MRA_OK;
+}
+
+}  // namespace
+}  // namespace mra
+
+extern "C" {
+
+MRA_API int mra_hermitian_eig(int32_t n, const double* A, double* w, double* V) {
+  if (n < 1 || n > 512 || !A || !w || !V) return MRA_EINVAL;
+  return herm_eig(n, reinterpret_cast<const cd*>(A), w, reinterpret_cast<cd*>(V));
+}
+
+MRA_API size_t mra_spca_workspace_bytes(const mra_dims* d) {
+  if (!d || d->K < 0 || d->Q < 1 || d->Q > 512) return 0;
+  return align256(sizeof(float) * 2 * (size_t)(d->K + 1) * d->Q * d->Q);
+}
+
+MRA_API int mra_spca_fit(const mra_dims* d, const float* y, float* basis_out, double* eig_out, int32_t* counts_out,
+                         int32_t* K2_out, int32_t* Q2_out, void* ws, size_t ws_bytes, void* stream) {
+  if (!d || d->N < 1 || d->K < 0 || d->Q < 1 || d->Q > 512 || !(d->sigma2 >= 0.0)) return MRA_EINVAL;
+  if (!y || (reinterpret_cast<uintptr_t>(y) % 16) != 0 || !basis_out ||
+      (reinterpret_cast<uintptr_t>(basis_out) % 8) != 0 || !ws || !K2_out || !Q2_out)
+    return MRA_EINVAL;
+  const int Kp1 = d->K + 1, Q = d->Q, M = Kp1 * Q, N = d->N;
+  if (M % 2 != 0) return MRA_EINVAL;
+  if (ws_bytes < mra_spca_workspace_bytes(d)) return MRA_EWORKSPACE;
+  cublasHandle_t h;
+  if (blas_handle(&h) != MRA_OK) return MRA_ECUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cublasSetStream(h, s) != CUBLAS_STATUS_SUCCESS) return MRA_ECUDA;
+  // C_k = B B^H / N with B = a[:, k, :]^T (column-major Q x N, leading dimension M): entry (q, q') is the
+  // mean of a_q conj(a_q')
+  const cuComplex alpha = make_cuComplex(1.f / (float)N, 0.f), beta = make_cuComplex(0.f, 0.f);
+  cuComplex* D = static_cast<cuComplex*>(ws);
+  if (cublasCgemmStridedBatched(h, CUBLAS_OP_N, CUBLAS_OP_C, Q, Q, N, &alpha,
+                                reinterpret_cast<const cuComplex*>(y), M, Q, reinterpret_cast<const cuComplex*>(y),
+                                M, Q, &beta, D, Q, (long long)Q * Q, Kp1) != CUBLAS_STATUS_SUCCESS)
+    return MRA_ECUDA;
+  std::vector<cuComplex> Dh((size_t)Kp1 * Q * Q);
+  if (cudaMemcpyAsync(Dh.data(), D, sizeof(cuComplex) * Dh.size(), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return MRA_ECUDA;
+  const double edge = d->sigma2 * (1.0 + std::sqrt((double)Q / N)) * (1.0 + std::sqrt((double)Q / N));
+  std::vector<cd> C((size_t)Q * Q), V((size_t)Q * Q);
+  std::vector<double> w(Q);
+  std::vector<cuComplex> Bh((size_t)Kp1 * Q * Q);
+  int K2 = 0, Q2 = 1;
+  for (int k = 0; k < Kp1; ++k) {
+    for (size_t e = 0; e < (size_t)Q * Q; ++e) {
+      const cuComplex v = Dh[(size_t)k * Q * Q + e];
+      C[e] = cd(v.x, v.y);
+    }
+    const int st = herm_eig(Q, C.data(), w.data(), V.data());
+    if (st != MRA_OK) return st;
+    int keep = 0;
+    while (keep < Q && w[keep] > edge) ++keep;
+    if (counts_out) counts_out[k] = keep;
+    if (eig_out)
+      for (int q = 0; q < Q; ++q) eig_out[(size_t)k * Q + q] = w[q];
+    if (keep > 0) K2 = k, Q2 = std::max(Q2, keep);
+    for (int c = 0; c < Q; ++c)
+      for (int i = 0; i < Q; ++i) {
+        const cd v = c < keep ? V[(size_t)c * Q + i] : cd(0.0, 0.0);
+        Bh[((size_t)k * Q + c) * Q + i] = make_cuComplex((float)v.real(), (float)v.imag());
+      }
+  }
+  if (((K2 + 1) * Q2) % 2) ++Q2;
+  *K2_out = K2;
+  *Q2_out = Q2;
+  if (cudaMemcpyAsync(basis_out, Bh.data(), sizeof(cuComplex) * Bh.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return MRA_ECUDA;
+  return MRA_OK;
+}
+
+MRA_API int mra_spca_project(const mra_dims* d, const float* y, int32_t K2, int32_t Q2, const float* basis,
+                             float* y_out, void* stream) {
+  if (!d || d->N < 1 || d->K < 0 || d->Q < 1 || d->Q > 512 || K2 < 0 || K2 > d->K || Q2 < 1 || Q2 > d->Q + 1)
+    return MRA_EINVAL;
+  if (!y || !basis || !y_out || (reinterpret_cast<uintptr_t>(y) % 16) != 0 ||
+      (reinterpret_cast<uintptr_t>(basis) % 8) != 0 || (reinterpret_cast<uintptr_t>(y_out) % 16) != 0)
+    return MRA_EINVAL;
+  const int Q = d->Q, M = (d->K + 1) * Q, M2 = (K2 + 1) * Q2, N = d->N;
+  if (M2 % 2 != 0) return MRA_EINVAL;
+  cublasHandle_t h;
+  if (blas_handle(&h) != MRA_OK) return MRA_ECUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cublasSetStream(h, s) != CUBLAS_STATUS_SUCCESS) return MRA_ECUDA;
+  const cuComplex one = make_cuComplex(1.f, 0.f), zero = make_cuComplex(0.f, 0.f);
+  const int qc = std::min(Q2, Q);  // basis columns used (a padding column beyond Q stays zero)
+  if (Q2 > Q && cudaMemsetAsync(y_out, 0, sizeof(cuComplex) * (size_t)N * M2, s) != cudaSuccess) return MRA_ECUDA;
+  // out_k (column-major qc x N, leading dimension M2) = U_k^H (qc x Q) a[:, k, :]^T (Q x N, leading dimension M)
+  if (cublasCgemmStridedBatched(h, CUBLAS_OP_C, CUBLAS_OP_N, qc, N, Q, &one, reinterpret_cast<const cuComplex*>(basis),
+                                Q, (long long)Q * Q, reinterpret_cast<const cuComplex*>(y), M, Q, &zero,
+                                reinterpret_cast<cuComplex*>(y_out), M2, Q2, K2 + 1) != CUBLAS_STATUS_SUCCESS)
+    return MRA_ECUDA;
+  return MRA_OK;
+}
+
+}  // extern "C"

@@ -76,6 +76,11 @@ _SIGS = {
     "mra_fb_setup_workspace_bytes": (c_size_t, [c_int32, c_int32, c_int32]),
     "mra_fb_setup": (c_int, [c_int32, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "mra_fb_project": (c_int, [c_int32, c_int32, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
+    "mra_spca_workspace_bytes": (c_size_t, [POINTER(mra_dims)]),
+    "mra_spca_fit": (c_int, [POINTER(mra_dims), c_void_p, c_void_p, c_void_p, c_void_p, POINTER(c_int32),
+                             POINTER(c_int32), c_void_p, c_size_t, c_void_p]),
+    "mra_spca_project": (c_int, [POINTER(mra_dims), c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p]),
+    "mra_hermitian_eig": (c_int, [c_int32, c_void_p, c_void_p, c_void_p]),
     "mra_sync": (c_int, [POINTER(mra_dims), c_void_p, c_int32, c_int32, c_int32, c_void_p, c_void_p, c_size_t,
                          c_void_p]),
     "mra_align_mean": (c_int, [POINTER(mra_dims), c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
@@ -294,6 +299,40 @@ def mra_fb_setup(n, K, Q, P_out, zeros_out, ws, stream=None):
 def mra_fb_project(N, n, K, Q, images, P, y_out, tf32=False, stream=None):
     _check("mra_fb_project", load().mra_fb_project(int(N), int(n), int(K), int(Q), _p(images), _p(P), _p(y_out),
                                                    1 if tf32 else 0, _stream(stream)))
+
+
+def mra_spca_workspace_bytes(d) -> int:
+    return int(load().mra_spca_workspace_bytes(ctypes.byref(d)))
+
+
+def mra_spca_fit(d, y, basis_out, ws, stream=None):
+    """Returns (K2, Q2, counts [K+1] numpy int32, eigenvalues [K+1, Q] numpy float64)."""
+    import numpy as np
+
+    counts = np.zeros(d.K + 1, dtype=np.int32)
+    eigs = np.zeros((d.K + 1, d.Q), dtype=np.float64)
+    K2, Q2 = c_int32(0), c_int32(0)
+    _check("mra_spca_fit", load().mra_spca_fit(ctypes.byref(d), _p(y), _p(basis_out), eigs.ctypes.data,
+                                               counts.ctypes.data, ctypes.byref(K2), ctypes.byref(Q2), _p(ws),
+                                               ws.numel(), _stream(stream)))
+    return K2.value, Q2.value, counts, eigs
+
+
+def mra_spca_project(d, y, K2, Q2, basis, y_out, stream=None):
+    _check("mra_spca_project", load().mra_spca_project(ctypes.byref(d), _p(y), int(K2), int(Q2), _p(basis),
+                                                       _p(y_out), _stream(stream)))
+
+
+def mra_hermitian_eig(A):
+    """Host eigen-decomposition of a Hermitian numpy matrix: (w descending, V columns)."""
+    import numpy as np
+
+    A = np.asfortranarray(np.asarray(A, dtype=np.complex128))
+    n = A.shape[0]
+    w = np.zeros(n, dtype=np.float64)
+    V = np.zeros((n, n), dtype=np.complex128, order="F")
+    _check("mra_hermitian_eig", load().mra_hermitian_eig(n, A.ctypes.data, w.ctypes.data, V.ctypes.data))
+    return w, V
 
 
 def mra_template_match(d, y, ref, shift_out, stream=None):

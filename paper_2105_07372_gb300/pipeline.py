@@ -61,6 +61,17 @@ def fb_coefficients(images, P, K, Q, tf32=False, stream=None) -> torch.Tensor:
     return y
 
 
+def spca(y, d, stream=None):
+    """Steerable PCA (App. A) of coefficients y [N, K+1, Q] with noise variance d.sigma2: returns
+    (y_reduced [N, K2+1, Q2] complex64, dims of the reduced problem, basis [K+1, Q, Q], counts [K+1])."""
+    basis = torch.empty((d.K + 1, d.Q, d.Q), dtype=torch.complex64, device=y.device)
+    ws = mra.workspace(mra.mra_spca_workspace_bytes(d), y.device)
+    K2, Q2, counts, _ = mra.mra_spca_fit(d, y, basis, ws, stream)
+    out = torch.empty((d.N, K2 + 1, Q2), dtype=torch.complex64, device=y.device)
+    mra.mra_spca_project(d, y, K2, Q2, basis, out, stream)
+    return out, mra.dims(d.N, K2, Q2, d.L, d.sigma2), basis, counts
+
+
 def template_match(y, d, ref, stream=None) -> torch.Tensor:
     """Template matching (Sec. 2.1.1): the shift of every image against the reference ref [K+1, Q] (complex64
     device tensor; an observation such as y[0], or a known signal)."""
