@@ -331,7 +331,7 @@ int herm_eig(int n, const cd* A, double* w, cd* V) {
     double off = 0.0;
     for (int j = 0; j < m; ++j)
       for (int i = 0; i < j; ++i) off += s_at(i, j) * s_at(i, j);
-    if (off <= 1e-30 * norm) break;
+    if (off <= 1e-26 * norm) break;  // off-diagonal part below 1e-13 of the matrix (rounding level after that)
     for (int p = 0; p < m - 1; ++p)
       for (int q = p + 1; q < m; ++q) {
         const double apq = s_at(p, q);
