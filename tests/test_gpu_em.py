@@ -91,10 +91,12 @@ def test_em_step_full_search_and_signal_prior(gpu_lib, sweep):
 
 @pytest.mark.parametrize("K,Q,N,L,Lw", [(5, 3, 77, 30, 7), (0, 2, 40, 12, 5), (3, 4, 1, 16, 16), (7, 6, 33, 50, 1),
                                         (12, 10, 500, 90, 13), (4, 8, 1, 16, 16), (6, 16, 301, 40, 9),
-                                        (48, 32, 203, 72, 72), (63, 8, 150, 128, 20)])
+                                        (48, 32, 203, 72, 72), (63, 8, 150, 128, 20), (63, 64, 90, 40, 9),
+                                        (127, 32, 60, 256, 15)])
 def test_em_step_shapes_and_edges(gpu_lib, sweep, K, Q, N, L, Lw):
     """Odd Q (float2 path), K = 0, N = 1, Lw = L, Lw = 1, ragged tiles and batches, the
-    largest rows (M = 1568) and the most rows (64) of the batch sweep."""
+    largest rows (M = 1568) and the most rows (64) of the batch sweep, and the largest
+    stored size M = 4096 (wide rows and many rows: the tile sweep)."""
     inst = synth.make_instance(K, Q, N, L, sigma2=1 / (0.3 * (K + 1) * Q), decay=20.0, seed=K * 100 + N)
     x0 = synth.random_init(K, Q, 20.0, seed=3)
     compare(gpu_lib, inst, x0, np.log(np.full(Lw, 1 / Lw)), Lw, shifts=inst.s, update_rho=(Lw % 2 == 1))
