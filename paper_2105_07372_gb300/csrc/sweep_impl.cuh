@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR, IPW>::kThreads, 1) k_swee
     int img[IPW];
     bool valid[IPW];
     const float4* y4[IPW];
-    int ph0[IPW], phstep[IPW];
+    int ph0[IPW], phstep[IPW], sjv[IPW];
 #pragma unroll
     for (int i = 0; i < IPW; ++i) {
       img[i] = gw + (p * IPW + i) * GW;
@@ -166,6 +166,7 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR, IPW>::kThreads, 1) k_swee
         sj = a.shift[img[i]] % L;
         if (sj < 0) sj += L;
       }
+      sjv[i] = sj;
       ph0[i] = mod_small(r * sj, L, invL);
       phstep[i] = mod_small(8 * sj, L, invL);
     }
@@ -490,26 +491,14 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR, IPW>::kThreads, 1) k_swee
       }
       __syncwarp();
 
-      // ---- back transform (twiddle loads shared by the IPW images)
+      if constexpr (LWC > 0) {
+      // ---- back transform of a one-chunk window over its units (shared-memory twiddles, loads shared by
+      // the IPW images); wider windows use the distance units around the peak (below)
 #pragma unroll
       for (int i = 0; i < IPW; ++i)
 #pragma unroll
         for (int m = 0; m < MR; ++m) W[i][m] = make_float2(0.f, 0.f);
       for (int u0 = 0; u0 < NUP; u0 += 4 * kUC) {
-        if constexpr (LWC <= 0 && IPW == 1) {
-          // wide windows: skip chunks whose units all lie farther than D from the peak (zero weights)
-          const int p = peak[0], D = dist[0];
-          bool act = wrap;
-#pragma unroll
-          for (int t = 0; t < kUC; ++t) {
-            const int u = u0 + j + 4 * t;
-            if (u < NU) {
-              const int2 ab = uab[u];
-              act |= (ab.x >= p - D && ab.x <= p + D) || (ab.y >= 0 && ab.y >= p - D && ab.y <= p + D);
-            }
-          }
-          if (!__any_sync(0xffffffffu, act)) continue;
-        }
         float sw[IPW][kUC], dw[IPW][kUC];
 #pragma unroll
         for (int t = 0; t < kUC; ++t) {
@@ -560,6 +549,105 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR, IPW>::kThreads, 1) k_swee
             if (ph >= L) ph -= L;
           }
         }
+      }
+      } else {
+      // ---- back transform around the peak, on the distance units as in pass 2:
+      // W_k = e^{+i k (theta_hat_j + theta_l*)} (1 + sum_{d>=1} [(w_{l*+d} + w_{l*-d}) (cos t - 1)
+      //        + i (w_{l*-d} - w_{l*+d}) (-sin t)]),  t = 2 pi k d step / L  (sum_l w_l = 1),
+      // over d <= D only (weights beyond D are zero): one distance per lane in the usual D < 4.
+#pragma unroll
+      for (int i = 0; i < IPW; ++i) {
+        const int p = peak[i], D = dist[i];
+        const float* sb = sbuf0 + i * a.sp;
+        auto wpair = [&](int d) {  // (w_{p+d} + w_{p-d}, w_{p-d} - w_{p+d}) for 1 <= d <= D
+          float wa = 0.f, wb = 0.f;
+          if (d >= 1 && d <= D) {
+            int la = p + d, lb = p - d;
+            if (wrap) {
+              if (la >= L) la -= L;
+              if (lb < 0) lb += L;
+              wa = sb[la];
+              if (2 * d != L) wb = sb[lb];
+            } else {
+              if (la < Lw) wa = sb[la];
+              if (lb >= 0) wb = sb[lb];
+            }
+          }
+          return make_float2(wa + wb, wb - wa);
+        };
+#pragma unroll
+        for (int m = 0; m < MR; ++m) W[i][m] = make_float2(0.f, 0.f);
+        const int nd1 = a.nd - 1;
+        const float2* trow0 = a.td + r * a.nd;  // row k = r; row r + 8 m is 8 m nd further
+        if (D < 4) {
+          const float2 sw = wpair(j);
+          const float2* tp = trow0 + min(j, nd1);
+#pragma unroll
+          for (int m = 0; m < MR; ++m) {
+            if (m < MR - 1 || r + 8 * m < Kp1) {
+              const float2 tv = tp[8 * m * a.nd];
+              W[i][m].x = fmaf(sw.x, tv.x, W[i][m].x);
+              W[i][m].y = fmaf(sw.y, tv.y, W[i][m].y);
+            }
+          }
+        } else {
+          for (int d0 = 0; d0 <= D; d0 += 4 * kUC) {
+            const int nt = min(kUC, (D - d0) / 4 + 1);
+#pragma unroll
+            for (int t = 0; t < kUC; ++t) {
+              if (t < nt) {
+                const int d = d0 + j + 4 * t;
+                const float2 sw = wpair(d);
+#pragma unroll
+                for (int m = 0; m < MR; ++m) {
+                  if (m < MR - 1 || r + 8 * m < Kp1) {
+                    const float2 tv = trow0[8 * m * a.nd + min(d, nd1)];
+                    W[i][m].x = fmaf(sw.x, tv.x, W[i][m].x);
+                    W[i][m].y = fmaf(sw.y, tv.y, W[i][m].y);
+                  }
+                }
+              }
+            }
+          }
+        }
+#pragma unroll
+        for (int m = 0; m < MR; ++m) {
+          W[i][m].x += __shfl_xor_sync(0xffffffffu, W[i][m].x, 1);
+          W[i][m].y += __shfl_xor_sync(0xffffffffu, W[i][m].y, 1);
+          W[i][m].x += __shfl_xor_sync(0xffffffffu, W[i][m].x, 2);
+          W[i][m].y += __shfl_xor_sync(0xffffffffu, W[i][m].y, 2);
+          W[i][m].x += 1.f;
+        }
+        if (a.tw) {  // dense window: the peak's angle from the window table, then the shift
+#pragma unroll
+          for (int m = 0; m < MR; ++m) {
+            const int k = r + 8 * m;
+            if (m < MR - 1 || k < Kp1) W[i][m] = cmul_conj_b(W[i][m], a.tw[k * a.twp + p]);
+          }
+          if (a.shift) {
+            int ph = ph0[i];
+#pragma unroll
+            for (int m = 0; m < MR; ++m) {
+              W[i][m] = cmul_conj_b(W[i][m], tfs[ph]);
+              ph += phstep[i];
+              if (ph >= L) ph -= L;
+            }
+          }
+        } else {  // grid: one rotation by theta_hat_j + theta_l*, i.e. by (s_j + l0 + l*) mod L
+          int op = a.l0m + p;
+          if (op >= L) op -= L;
+          int q = sjv[i] + op;
+          if (q >= L) q -= L;
+          int ph = mod_small(r * q, L, invL);
+          const int pst = mod_small(8 * q, L, invL);
+#pragma unroll
+          for (int m = 0; m < MR; ++m) {
+            W[i][m] = cmul_conj_b(W[i][m], tfs[ph]);
+            ph += pst;
+            if (ph >= L) ph -= L;
+          }
+        }
+      }
       }
     }
 
