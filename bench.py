@@ -576,6 +576,9 @@ def bench_bf16(args):
     x0 = torch.from_numpy(x_true * 0.9).to(dev)  # a start near the truth; the sweeps do the same work anywhere
     lr0 = torch.full((Lw,), -math.log(Lw), dtype=torch.float64, device=dev)
     x, lr = x0.clone(), lr0.clone()
+    # the autotuner times the sweeps that read the split format (batch and chunked) from the start state
+    tuned = mra.mra_em_autotune(d, mra.em_params(Lw), y_hl, shift, x, lr, ws, y_format=1)
+    x, lr = x0.clone(), lr0.clone()
     sweep_ms = (ctypes.c_float * T)()
     sweeps = []
 
@@ -598,7 +601,9 @@ def bench_bf16(args):
                        "parallelism": "single", "l2": "inputs larger than L2 (12.5 GB per sweep)"},
             "roofline": {"bound": "hbm", "achieved": ybytes / sw / 1e9, "peak": peak, "unit": "GB/s",
                          "frac": ybytes / sw / 1e9 / peak, "traffic": None, "peak_source": f"{peak_kind} hbm_gbs",
-                         "kernel": "k_sweep_v3 (BF16 hi/lo)", "algorithmic_bytes_per_launch": ybytes,
+                         "kernel": {2: "k_sweep_v3", 3: "k_sweep_v4"}.get(tuned[0], "?") + " (BF16 hi/lo)",
+                         "sweep_choice": {"kind": tuned[0], "batch": tuned[1], "stages_or_ctas": tuned[2]},
+                         "algorithmic_bytes_per_launch": ybytes,
                          "avg_launch_ms": sw * 1e3},
             "clocks": clk.summary(), "gpu_launches": (2 + 3 * T + 1) * args.steps}
     print(json.dumps(line), flush=True)

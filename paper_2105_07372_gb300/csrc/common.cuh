@@ -27,6 +27,24 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 __device__ __forceinline__ float2 cmul_conj_b(float2 a, float2 b) {  // a * conj(b)
   return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
 }
+// Two complex values of y at float4 index f of an image: FP32 (YF = 0), or the BF16
+// hi/lo split (YF = 1) whose 16-byte group f holds bf16 hi of (re, im, re, im) and then
+// bf16 lo of the same four values; hi + lo is exact in FP32.
+template <int YF>
+__device__ __forceinline__ float4 load_y4(const float4* img, int f) {
+  if constexpr (YF == 0) {
+    return img[f];
+  } else {
+    const uint4 v = reinterpret_cast<const uint4*>(img)[f];
+    const float2 h0 = make_float2(__uint_as_float(v.x << 16), __uint_as_float(v.x & 0xffff0000u));
+    const float2 h1 = make_float2(__uint_as_float(v.y << 16), __uint_as_float(v.y & 0xffff0000u));
+    const float2 l0 = make_float2(__uint_as_float(v.z << 16), __uint_as_float(v.z & 0xffff0000u));
+    const float2 l1 = make_float2(__uint_as_float(v.w << 16), __uint_as_float(v.w & 0xffff0000u));
+    const float2 a = __fadd2_rn(h0, l0), b = __fadd2_rn(h1, l1);
+    return make_float4(a.x, a.y, b.x, b.y);
+  }
+}
+
 // e^{-i t sgn(dr)} from a distance-unit table entry (cos t - 1, -sin t) taken at |dr|.
 __device__ __forceinline__ float2 td_rot(float2 t, int dr) { return make_float2(1.f + t.x, dr >= 0 ? t.y : -t.y); }
 __device__ __forceinline__ double2 zmul(double2 a, double2 b) {
@@ -280,10 +298,15 @@ struct SweepV4Launch {
 // QV = float4 per lane per row (Q / 8); MR = rows per quad ((K+1+7)/8, at most 7);
 // cpsm = resident CTAs per SM (1: 512 threads, 2: 256 threads each; 256 threads and one
 // CTA per SM for the largest per-lane accumulators).
-SweepV4Launch sweep_v4_q1(int MR, int cpsm);
-SweepV4Launch sweep_v4_q2(int MR, int cpsm);
-SweepV4Launch sweep_v4_q3(int MR, int cpsm);
-SweepV4Launch sweep_v4_q4(int MR, int cpsm);
+// yf: 1 for y stored as the BF16 hi/lo split (load_y4), one translation unit per (QV, yf).
+SweepV4Launch sweep_v4_q1_f0(int MR, int cpsm);
+SweepV4Launch sweep_v4_q2_f0(int MR, int cpsm);
+SweepV4Launch sweep_v4_q3_f0(int MR, int cpsm);
+SweepV4Launch sweep_v4_q4_f0(int MR, int cpsm);
+SweepV4Launch sweep_v4_q1_f1(int MR, int cpsm);
+SweepV4Launch sweep_v4_q2_f1(int MR, int cpsm);
+SweepV4Launch sweep_v4_q3_f1(int MR, int cpsm);
+SweepV4Launch sweep_v4_q4_f1(int MR, int cpsm);
 
 // Mirror units of a window: offsets o and -o (mod L) share cos/sin.  Writes the
 // (a, b) index pairs in window order of a; returns the number of units.  A dense window

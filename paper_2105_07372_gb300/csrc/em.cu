@@ -1179,15 +1179,18 @@ bool plan_v4_shape(int Kp1, int Q, int L, int Lw, int l0, bool dense, int want_c
 
 // Two CTAs per SM (each with half the shared memory, so that one can stream while the
 // other transforms) where the plan fits, else one; want_cpsm fixes the choice.
-bool plan_v4(int Kp1, int Q, int L, int Lw, int l0, bool dense, int want_c, int want_cpsm, const DevInfo& di,
-             V4Plan* p) {
+bool plan_v4(int Kp1, int Q, int L, int Lw, int l0, bool dense, int yf, int want_c, int want_cpsm,
+             const DevInfo& di, V4Plan* p) {
   if (Q % 8 != 0 || Q / 8 > 4) return false;
   const int QV = Q / 8, MR = (Kp1 + 7) / 8;
   if (MR > 7) return false;
   for (int cpsm = kMaxCtasPerSm; cpsm >= 1; --cpsm) {
     if (want_cpsm && cpsm != want_cpsm) continue;
-    const SweepV4Launch ln = QV == 1 ? sweep_v4_q1(MR, cpsm) : QV == 2 ? sweep_v4_q2(MR, cpsm)
-                           : QV == 3 ? sweep_v4_q3(MR, cpsm) : sweep_v4_q4(MR, cpsm);
+    const SweepV4Launch ln =
+        yf ? (QV == 1 ? sweep_v4_q1_f1(MR, cpsm) : QV == 2 ? sweep_v4_q2_f1(MR, cpsm)
+              : QV == 3 ? sweep_v4_q3_f1(MR, cpsm) : sweep_v4_q4_f1(MR, cpsm))
+           : (QV == 1 ? sweep_v4_q1_f0(MR, cpsm) : QV == 2 ? sweep_v4_q2_f0(MR, cpsm)
+              : QV == 3 ? sweep_v4_q3_f0(MR, cpsm) : sweep_v4_q4_f0(MR, cpsm));
     if (!ln.fn) continue;
     const int max_smem = std::min(di.max_smem_optin, di.smem_per_sm / cpsm - 1024);
     if (plan_v4_shape(Kp1, Q, L, Lw, l0, dense, want_c, max_smem, ln, p)) {
@@ -1339,10 +1342,16 @@ int prepare(const mra_dims* d, int Lw, int l0, double step, const float* y, cons
     if (tune_lookup(tune_key(d, Lw, l0, step, yfmt), &tuned)) sel = tuned;
   }
   c->v4 = false;
-  if (yfmt) {
+  if (yfmt) {  // the batch sweep reads the split format, and the chunked sweep when chosen
     c->v2 = false;
-    c->v3 = sel.kind != 1 && plan_v3(Kp1, d->Q, d->L, Lw, l0, dense, 1, sel.bi, sel.ns, di.max_smem_optin, &c->v3p);
-    if (!c->v3) return MRA_EINVAL;  // no sweep for this shape reads the split format
+    if (sel.kind == 3) {
+      c->v3 = false;
+      c->v4 = plan_v4(Kp1, d->Q, d->L, Lw, l0, dense, 1, sel.bi, sel.ns, di, &c->v4p);
+      if (c->v4) c->lay.G = c->v4p.grid;
+    } else {
+      c->v3 = sel.kind != 1 && plan_v3(Kp1, d->Q, d->L, Lw, l0, dense, 1, sel.bi, sel.ns, di.max_smem_optin, &c->v3p);
+    }
+    if (!c->v3 && !c->v4) return MRA_EINVAL;  // no sweep for this shape reads the split format
   } else {
     // By default the warp sweep keeps a window of one unit chunk in registers and is the
     // faster one there; wider windows (up to the whole circle) go to the batch sweep.
@@ -1353,7 +1362,7 @@ int prepare(const mra_dims* d, int Lw, int l0, double step, const float* y, cons
     // The chunked two-read sweep runs when chosen (environment or autotuner): it leads on
     // sharp posteriors and ties the warp sweep on broad ones.
     if (allow_v3 && sel.kind == 3) {
-      c->v4 = plan_v4(Kp1, d->Q, d->L, Lw, l0, dense, sel.bi, sel.ns, di, &c->v4p);
+      c->v4 = plan_v4(Kp1, d->Q, d->L, Lw, l0, dense, 0, sel.bi, sel.ns, di, &c->v4p);
       if (c->v4) {
         c->v2 = c->v3 = false;
         c->lay.G = c->v4p.grid;

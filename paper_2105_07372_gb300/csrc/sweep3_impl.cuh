@@ -32,23 +32,6 @@
 
 namespace mra {
 
-// Two complex values of y at float4 index f of an image: FP32 (YF = 0), or the BF16
-// hi/lo split (YF = 1) whose 16-byte group f holds bf16 hi of (re, im, re, im) and then
-// bf16 lo of the same four values; hi + lo is exact in FP32.
-template <int YF>
-__device__ __forceinline__ float4 load_y4(const float4* img, int f) {
-  if constexpr (YF == 0) {
-    return img[f];
-  } else {
-    const uint4 v = reinterpret_cast<const uint4*>(img)[f];
-    const float2 h0 = make_float2(__uint_as_float(v.x << 16), __uint_as_float(v.x & 0xffff0000u));
-    const float2 h1 = make_float2(__uint_as_float(v.y << 16), __uint_as_float(v.y & 0xffff0000u));
-    const float2 l0 = make_float2(__uint_as_float(v.z << 16), __uint_as_float(v.z & 0xffff0000u));
-    const float2 l1 = make_float2(__uint_as_float(v.w << 16), __uint_as_float(v.w & 0xffff0000u));
-    const float2 a = __fadd2_rn(h0, l0), b = __fadd2_rn(h1, l1);
-    return make_float4(a.x, a.y, b.x, b.y);
-  }
-}
 
 // window indices of distance unit d around the reference p (-1 where absent)
 __device__ __forceinline__ int2 unit_pair(int p, int d, int Lw, int L, bool wrap) {

@@ -52,7 +52,7 @@ __device__ __forceinline__ void bulk_g2s_hint(void* dst_smem, const void* src_gm
       : "memory");
 }
 
-template <int QV, int MR, int NTH, int MINB>
+template <int QV, int MR, int NTH, int MINB, int YF>
 __global__ void __launch_bounds__(NTH, MINB) k_sweep_v4(const SweepV4Args a) {
   extern __shared__ __align__(128) unsigned char smem[];
   constexpr int NT = NTH;
@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(NTH, MINB) k_sweep_v4(const SweepV4Args a) {
           for (int u = 0; u < QV; ++u) {
             const int pidx = k * row4 + j + 4 * u;
             const float4 xv = xs4[pidx];
-            const float4 yv = y4[pidx];
+            const float4 yv = load_y4<YF>(y4, pidx);
             cr = fmaf(yv.x, xv.x, cr); cr = fmaf(yv.y, xv.y, cr);
             ci = fmaf(yv.x, xv.y, ci); ci = fmaf(-yv.y, xv.x, ci);
             cr = fmaf(yv.z, xv.z, cr); cr = fmaf(yv.w, xv.w, cr);
@@ -415,7 +415,7 @@ __global__ void __launch_bounds__(NTH, MINB) k_sweep_v4(const SweepV4Args a) {
           const float2 w = cbuf[li * cp + k];
 #pragma unroll
           for (int u = 0; u < QV; ++u) {
-            const float4 yv = y4[k * row4 + j + 4 * u];
+            const float4 yv = load_y4<YF>(y4, k * row4 + j + 4 * u);
             float4& q = acc[m][u];
             q.x = fmaf(w.x, yv.x, q.x); q.x = fmaf(-w.y, yv.y, q.x);
             q.y = fmaf(w.x, yv.y, q.y); q.y = fmaf(w.y, yv.x, q.y);
@@ -474,28 +474,28 @@ __global__ void __launch_bounds__(NTH, MINB) k_sweep_v4(const SweepV4Args a) {
 
 }  // namespace mra
 
-// Instantiation table for one row width QV (float4 per lane per row): MR = 1..7 rows per
-// quad; one CTA of 512 threads or two of 256 per SM (256 threads and one CTA per SM for
+// Instantiation table for one row width QV (float4 per lane per row) and y format YF: MR = 1..7
+// rows per quad; one CTA of 512 threads or two of 256 per SM (256 threads and one CTA per SM for
 // the largest per-lane accumulators).
-#define MRA_SWEEP_V4_CASE(QV, MR)                                                    \
-  case MR:                                                                           \
-    if (SweepV4Shape<QV, MR>::kBig)                                                  \
-      return cpsm == 1 ? SweepV4Launch{k_sweep_v4<QV, MR, 256, 1>, 256, 1}           \
-                       : SweepV4Launch{nullptr, 0, 0};                               \
-    return cpsm == 1 ? SweepV4Launch{k_sweep_v4<QV, MR, 512, 1>, 512, 1}             \
-                     : SweepV4Launch{k_sweep_v4<QV, MR, 256, 2>, 256, 2};
-#define MRA_SWEEP_V4_TABLE(QV)                     \
-  namespace mra {                                  \
-  SweepV4Launch sweep_v4_q##QV(int MR, int cpsm) { \
-    switch (MR) {                                  \
-      MRA_SWEEP_V4_CASE(QV, 1)                     \
-      MRA_SWEEP_V4_CASE(QV, 2)                     \
-      MRA_SWEEP_V4_CASE(QV, 3)                     \
-      MRA_SWEEP_V4_CASE(QV, 4)                     \
-      MRA_SWEEP_V4_CASE(QV, 5)                     \
-      MRA_SWEEP_V4_CASE(QV, 6)                     \
-      MRA_SWEEP_V4_CASE(QV, 7)                     \
-      default: return {nullptr, 0, 0};             \
-    }                                              \
-  }                                                \
+#define MRA_SWEEP_V4_CASE(QV, MR, YF)                                                    \
+  case MR:                                                                               \
+    if (SweepV4Shape<QV, MR>::kBig)                                                      \
+      return cpsm == 1 ? SweepV4Launch{k_sweep_v4<QV, MR, 256, 1, YF>, 256, 1}           \
+                       : SweepV4Launch{nullptr, 0, 0};                                   \
+    return cpsm == 1 ? SweepV4Launch{k_sweep_v4<QV, MR, 512, 1, YF>, 512, 1}             \
+                     : SweepV4Launch{k_sweep_v4<QV, MR, 256, 2, YF>, 256, 2};
+#define MRA_SWEEP_V4_TABLE(QV, YF)                           \
+  namespace mra {                                            \
+  SweepV4Launch sweep_v4_q##QV##_f##YF(int MR, int cpsm) {   \
+    switch (MR) {                                            \
+      MRA_SWEEP_V4_CASE(QV, 1, YF)                           \
+      MRA_SWEEP_V4_CASE(QV, 2, YF)                           \
+      MRA_SWEEP_V4_CASE(QV, 3, YF)                           \
+      MRA_SWEEP_V4_CASE(QV, 4, YF)                           \
+      MRA_SWEEP_V4_CASE(QV, 5, YF)                           \
+      MRA_SWEEP_V4_CASE(QV, 6, YF)                           \
+      MRA_SWEEP_V4_CASE(QV, 7, YF)                           \
+      default: return {nullptr, 0, 0};                       \
+    }                                                        \
+  }                                                          \
   }

@@ -1,0 +1,4 @@
+// Chunked two-read EM sweep for rows of 8 coefficients (1 float4 per lane per row), y as the BF16 hi/lo split.
+#include "sweep4_impl.cuh"
+
+MRA_SWEEP_V4_TABLE(1, 1)

@@ -1,0 +1,4 @@
+// Chunked two-read EM sweep for rows of 16 coefficients (2 float4 per lane per row), y in FP32.
+#include "sweep4_impl.cuh"
+
+MRA_SWEEP_V4_TABLE(2, 0)

@@ -31,8 +31,15 @@ def test_split_kernel_is_bit_exact(gpu_lib):
     np.testing.assert_array_equal(host(out), want)
 
 
+@pytest.fixture(params=["cta", "chunk"])
+def sweep(request, monkeypatch):
+    """Both sweeps that read the split format: the CTA batch sweep and the chunked two-read sweep."""
+    monkeypatch.setenv("MRA_SWEEP", request.param)
+    return request.param
+
+
 @pytest.mark.parametrize("N,L,window", [(2000, 720, True), (600, 180, False)])
-def test_em_step_hl_config5_shapes(gpu_lib, N, L, window):
+def test_em_step_hl_config5_shapes(gpu_lib, sweep, N, L, window):
     """|k| <= 48, Q = 32: the window of 72 around aligned images at L = 720, or the whole grid
     of L = 180 (the oracle's literal distances over 720 rotations would need tens of GB)."""
     mra = gpu_lib
@@ -66,7 +73,7 @@ def test_em_step_hl_config5_shapes(gpu_lib, N, L, window):
           f"x {rel_err(host(xo), full.x):.2e} w {np.max(np.abs(host(w) - full.w)):.2e}")
 
 
-def test_em_run_hl_first_10k_images_of_config5(gpu_lib):
+def test_em_run_hl_first_10k_images_of_config5(gpu_lib, sweep):
     """The first 10,000 images of the largest workload: two EM iterations on the window."""
     mra = gpu_lib
     c = synth.config(5)
