@@ -302,14 +302,16 @@ __global__ void k_refnorm(const float* y, int D, int P, float* nrm) {
 // Matching: 128 queries x 128 references per tile, 16 real coordinates per step,
 // 8 x 8 outputs per thread; score = ||y_n||^2 - 2 <y_i, y_n>, running argmin per query.
 // The next step's coordinates are fetched into registers while the current step
-// computes from the other shared-memory buffer.
+// computes from the other shared-memory buffer.  Lanes run over query groups and warps
+// over reference groups, so that a warp whose reference columns all lie beyond P (the
+// second half of the last tile when P is not a multiple of 128) skips those products.
 constexpr int kMT = 128, kKC = 16;
 __global__ void __launch_bounds__(256) k_match(const float* y, int N, int D, int P, const float* nrm, const int* phi,
                                                int* shift_out) {
   __shared__ __align__(16) float As[2][kKC][kMT + 4];
   __shared__ __align__(16) float Bs[2][kKC][kMT + 4];
   const int tid = threadIdx.x;
-  const int tr = tid & 15, tq = tid >> 4;
+  const int tq = tid & 15, tr = tid >> 4;  // a warp holds tr = 2w, 2w + 1
   const int q0 = blockIdx.x * kMT;
   const int lrow = tid >> 1, lh = (tid & 1) * 8;  // loader: row and 8-coordinate half of a step
   float bestv[8];
@@ -346,6 +348,9 @@ __global__ void __launch_bounds__(256) k_match(const float* y, int N, int D, int
     for (int u = 0; u < 8; ++u)
 #pragma unroll
       for (int v = 0; v < 8; ++v) acc[u][v] = 0.f;
+    // reference columns of this warp: r0 + 8w .. r0 + 8w + 7 in each half (warp-uniform tests)
+    const int wc = r0 + 8 * (tid >> 5);
+    const bool lo_on = wc < P, hi_on = wc + 64 < P;
     fetch(0);
     int buf = 0;
     for (int kc = 0; kc < D; kc += kKC, buf ^= 1) {
@@ -360,10 +365,18 @@ __global__ void __launch_bounds__(256) k_match(const float* y, int N, int D, int
         const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][64 + tr * 4]);
         const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
         const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+        if (lo_on) {
 #pragma unroll
-        for (int u = 0; u < 8; ++u)
+          for (int u = 0; u < 8; ++u)
 #pragma unroll
-          for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
+            for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
+        }
+        if (hi_on) {
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+#pragma unroll
+            for (int v = 4; v < 8; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
+        }
       }
     }
     __syncthreads();  // the buffers are refilled by the next reference tile
@@ -380,18 +393,27 @@ __global__ void __launch_bounds__(256) k_match(const float* y, int N, int D, int
       }
     }
   }
-  // reduce over the 16 threads (same tq) that share these queries: lanes differ in tr
+  // reduce over the 16 threads (one per tr, in different warps) that share each query, through
+  // shared memory (the tile buffers are free after the last barrier of the reference loop)
+  float* rv = &As[0][0][0];                      // [16][kMT]
+  int* ri = reinterpret_cast<int*>(&Bs[0][0][0]);  // [16][kMT]
 #pragma unroll
   for (int u = 0; u < 8; ++u) {
-    float bv = bestv[u];
-    int bi = besti[u];
-    for (int o = 8; o > 0; o >>= 1) {
-      const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    const int ql = u < 4 ? tq * 4 + u : 64 + tq * 4 + (u - 4);
+    rv[tr * kMT + ql] = bestv[u];
+    ri[tr * kMT + ql] = besti[u];
+  }
+  __syncthreads();
+  if (tid < kMT) {
+    float bv = rv[tid];
+    int bi = ri[tid];
+    for (int t = 1; t < 16; ++t) {
+      const float ov = rv[t * kMT + tid];
+      const int oi = ri[t * kMT + tid];
       if (ov < bv || (ov == bv && oi < bi)) bv = ov, bi = oi;
     }
-    const int q = q0 + (u < 4 ? tq * 4 + u : 64 + tq * 4 + (u - 4));
-    if (tr == 0 && q < N) shift_out[q] = (bi < P) ? phi[bi] : 0;
+    const int q = q0 + tid;
+    if (q < N) shift_out[q] = (bi < P) ? phi[bi] : 0;
   }
 }
 
