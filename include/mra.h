@@ -63,7 +63,7 @@ extern "C" {
 
 typedef enum {
   MRA_OK = 0,
-  MRA_EINVAL = -1,     /* bad dimensions, NULL or misaligned pointer, window > L, ... */
+  MRA_EINVAL = -1,     /* bad dimensions, NULL or misaligned pointer, a window the limits exclude, ... */
   MRA_ENOMEM = -2,     /* a host-side allocation inside the library failed */
   MRA_ECUDA = -3,      /* a CUDA runtime call failed (launch, copy, graph) */
   MRA_ETIMEOUT = -4,   /* a bounded device-side wait ran out; the kernel returned early */
