@@ -26,6 +26,7 @@ import json  # noqa: E402
 import math  # noqa: E402
 import subprocess  # noqa: E402
 import sys  # noqa: E402
+import tempfile  # noqa: E402
 import time  # noqa: E402
 
 import numpy as np  # noqa: E402
@@ -307,8 +308,7 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    clk = Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv") if os.path.isdir(
-        os.path.join(ROOT, "gpurun_out")) else f"/tmp/mra_clocks_{rank}.csv")
+    clk = _clocks(rank)
     with clk:
         barrier()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -504,9 +504,10 @@ def _timed_steps(step, args, clk):
     return e0.elapsed_time(e1) / args.steps
 
 
-def _clocks():
-    d = os.path.join(ROOT, "gpurun_out")
-    return Clocks(os.path.join(d, "clocks_rank0.csv") if os.path.isdir(d) else "/tmp/mra_clocks_0.csv")
+def _clocks(rank=0):
+    """The clock samples go to $MRA_CLOCKS_DIR (kept for inspection) or to the temporary directory."""
+    d = os.environ.get("MRA_CLOCKS_DIR") or tempfile.gettempdir()
+    return Clocks(os.path.join(d, f"mra_clocks_rank{rank}.csv"))
 
 
 def bench_batched(args):
