@@ -299,8 +299,8 @@ def main():
     mra.mra_sync(d, y, P, 50, 100, shift, ws.sync)
     mra.mra_align_mean(d, y, shift, x, ws.em)
     log_rho.copy_(log_prior)
-    tuned = mra.mra_em_autotune(d, mra.em_params(Lw, l0=l0, gamma=c["gamma"], log_rho_bar=log_prior, step=wstep), y,
-                                shift, x, log_rho, ws.em)
+    tuned = _effective_choice(mra.mra_em_autotune(
+        d, mra.em_params(Lw, l0=l0, gamma=c["gamma"], log_rho_bar=log_prior, step=wstep), y, shift, x, log_rho, ws.em))
     torch.cuda.synchronize()
 
     def barrier():
@@ -504,6 +504,14 @@ def _timed_steps(step, args, clk):
     return e0.elapsed_time(e1) / args.steps
 
 
+def _effective_choice(tuned):
+    """The sweep the timed steps use: MRA_SWEEP (with MRA_SWEEP_BI / _NS) overrides the autotuner's choice."""
+    kind = {"warp": 1, "cta": 2, "chunk": 3}.get(os.environ.get("MRA_SWEEP", ""))
+    if kind is None:
+        return tuned
+    return [kind, int(os.environ.get("MRA_SWEEP_BI", 0) or 0), int(os.environ.get("MRA_SWEEP_NS", 0) or 0)]
+
+
 def _clocks(rank=0):
     """The clock samples go to $MRA_CLOCKS_DIR (kept for inspection) or to the temporary directory."""
     d = os.environ.get("MRA_CLOCKS_DIR") or tempfile.gettempdir()
@@ -605,7 +613,7 @@ def bench_bf16(args):
     lr0 = torch.full((Lw,), -math.log(Lw), dtype=torch.float64, device=dev)
     x, lr = x0.clone(), lr0.clone()
     # the autotuner times the sweeps that read the split format (batch and chunked) from the start state
-    tuned = mra.mra_em_autotune(d, mra.em_params(Lw), y_hl, shift, x, lr, ws, y_format=1)
+    tuned = _effective_choice(mra.mra_em_autotune(d, mra.em_params(Lw), y_hl, shift, x, lr, ws, y_format=1))
     x, lr = x0.clone(), lr0.clone()
     sweep_ms = (ctypes.c_float * T)()
     sweeps = []

@@ -142,7 +142,8 @@ struct Ctrl {
   int status;  // MRA_OK or MRA_ETIMEOUT, set by kernels
   int done;    // em_run: converged flag, makes the remaining kernels of a graph return at entry
   int iter;    // em_run: iterations performed
-  int pad[61];
+  unsigned sched[2];  // wide-window warp sweep: next image and finished warps (zero between launches)
+  int pad[59];
 };
 
 __host__ __device__ inline int round_up(int v, int m) { return (v + m - 1) / m * m; }

@@ -24,6 +24,11 @@
 //                               (the weights sum to 1; those beyond D_i are below e^-40 of the peak)
 //   accumulate   thread (k, p): num_kq += sum_i W_ik y_ikq for two float4 columns of row k
 //
+// The distance-unit table sits in shared memory, or (TDG, for windows whose table does not fit
+// next to the ring) stays in global memory, read through the read-only path: the (unit, image)
+// items put the images on the fastest thread index, so a warp's table loads cover a few units and
+// serve all of its images.
+//
 // Packed FP32 FMAs (f32x2) carry (re, im) pairs.  Per-thread FP32 column sums are folded
 // into FP64 every 32 batches; the CTA writes FP64 partials [column][CTA] at the end, in the
 // same layout as the other sweeps.
@@ -45,7 +50,7 @@ __device__ __forceinline__ int2 unit_pair(int p, int d, int Lw, int L, bool wrap
   return make_int2(p + d < Lw ? p + d : -1, (d > 0 && p - d >= 0) ? p - d : -1);
 }
 
-template <int QH, int BI, int YF>
+template <int QH, int BI, int YF, bool TDG = false>
 __global__ void __launch_bounds__(kV3Threads, 1) k_sweep_v3(const SweepV3Args a) {
   extern __shared__ __align__(128) unsigned char smem[];
   constexpr int NT = kV3Threads;
@@ -66,7 +71,12 @@ __global__ void __launch_bounds__(kV3Threads, 1) k_sweep_v3(const SweepV3Args a)
   unsigned char* ring = smem + a.off_ring;                                // [NS][BI][slot]
   const float4* xs4 = reinterpret_cast<const float4*>(smem + a.off_x);   // [M/2]  (x.re, x.im) pairs
   const float4* xr4 = reinterpret_cast<const float4*>(smem + a.off_xr);  // [M/2]  (x.im, -x.re) pairs
-  const float2* td = reinterpret_cast<const float2*>(smem + a.off_td);   // [Kp1][dp]
+  const float2* td = TDG ? a.td : reinterpret_cast<const float2*>(smem + a.off_td);  // [Kp1][tdp]
+  const int tdp = TDG ? a.nd : dp;
+  auto tld = [&](const float2* t, int i) {
+    if constexpr (TDG) return __ldg(t + i);
+    else return t[i];
+  };
   const float2* tfs = reinterpret_cast<const float2*>(smem + a.off_tf);  // [L]
   const float* lrs = reinterpret_cast<const float*>(smem + a.off_lr);    // [Lw]
   float2* cbuf = reinterpret_cast<float2*>(smem + a.off_c);              // [BI][cp]: c, later W
@@ -85,10 +95,12 @@ __global__ void __launch_bounds__(kV3Threads, 1) k_sweep_v3(const SweepV3Args a)
       xw[i] = v;
       xrw[i] = make_float4(v.y, -v.x, v.w, -v.z);
     }
-    float2* tw = reinterpret_cast<float2*>(smem + a.off_td);
-    for (int idx = tid; idx < Kp1 * dp; idx += NT) {
-      const int k = idx / dp, d = idx - k * dp;
-      tw[idx] = d < a.nd ? a.td[k * a.nd + d] : make_float2(0.f, 0.f);
+    if constexpr (!TDG) {
+      float2* tw = reinterpret_cast<float2*>(smem + a.off_td);
+      for (int idx = tid; idx < Kp1 * dp; idx += NT) {
+        const int k = idx / dp, d = idx - k * dp;
+        tw[idx] = d < a.nd ? a.td[k * a.nd + d] : make_float2(0.f, 0.f);
+      }
     }
     float2* tfw = reinterpret_cast<float2*>(smem + a.off_tf);
     for (int i = tid; i < L; i += NT) tfw[i] = a.tf32[i];
@@ -154,10 +166,10 @@ __global__ void __launch_bounds__(kV3Threads, 1) k_sweep_v3(const SweepV3Args a)
       const int kst = 2 << fsh;
       int k = fsub;
       for (; k + (kst >> 1) < Kp1; k += kst) {
-        ab0 = __ffma2_rn(cr[k], tcol[k * dp], ab0);
-        ab1 = __ffma2_rn(cr[k + (kst >> 1)], tcol[(k + (kst >> 1)) * dp], ab1);
+        ab0 = __ffma2_rn(cr[k], tld(tcol, k * tdp), ab0);
+        ab1 = __ffma2_rn(cr[k + (kst >> 1)], tld(tcol, (k + (kst >> 1)) * tdp), ab1);
       }
-      if (k < Kp1) ab0 = __ffma2_rn(cr[k], tcol[k * dp], ab0);
+      if (k < Kp1) ab0 = __ffma2_rn(cr[k], tld(tcol, k * tdp), ab0);
       float A = ab0.x + ab1.x, B = ab0.y + ab1.y;
       if (fsh) {
         A += __shfl_xor_sync(fmask, A, 1);
@@ -285,7 +297,8 @@ __global__ void __launch_bounds__(kV3Threads, 1) k_sweep_v3(const SweepV3Args a)
         for (int l = lane; l < Lw; l += 32) srow[l] -= shiftv;
         if (a.tw) {  // dense window: p - r0 window steps, from the distance-unit table
           const int dr = p - r0, ad = dr < 0 ? -dr : dr;
-          for (int k = lane; k < Kp1; k += 32) cbuf[i * cp + k] = cmul(cbuf[i * cp + k], td_rot(td[k * dp + ad], dr));
+          for (int k = lane; k < Kp1; k += 32)
+            cbuf[i * cp + k] = cmul(cbuf[i * cp + k], td_rot(tld(td, k * tdp + ad), dr));
           if (lane == 0) info[i] = make_int4(ph1, p, (int)dist, (int)dist);
         } else {
           int dr = (p - r0) % L;
@@ -349,13 +362,13 @@ __global__ void __launch_bounds__(kV3Threads, 1) k_sweep_v3(const SweepV3Args a)
       const int4 f = info[ii];
       for (int k = it0; k < Kp1; k += ISTEP) {
         float2 v0 = make_float2(0.f, 0.f), v1 = v0;
-        const float2* trow = td + k * dp;
+        const float2* trow = td + k * tdp;
         int d = 0;
         for (; d + 1 <= f.z; d += 2) {
-          v0 = __ffma2_rn(wr[d], trow[d], v0);
-          v1 = __ffma2_rn(wr[d + 1], trow[d + 1], v1);
+          v0 = __ffma2_rn(wr[d], tld(trow, d), v0);
+          v1 = __ffma2_rn(wr[d + 1], tld(trow, d + 1), v1);
         }
-        if (d <= f.z) v0 = __ffma2_rn(wr[d], trow[d], v0);
+        if (d <= f.z) v0 = __ffma2_rn(wr[d], tld(trow, d), v0);
         float2 W = make_float2(1.f + (v0.x + v1.x), v0.y + v1.y);
         if (f.x != 0) W = cmul_conj_b(W, tfs[(k * f.x) % L]);
         if (a.tw) W = cmul_conj_b(W, a.tw[k * a.twp + f.y]);  // dense window: the reference's angle
@@ -417,7 +430,8 @@ __global__ void __launch_bounds__(kV3Threads, 1) k_sweep_v3(const SweepV3Args a)
 }  // namespace mra
 
 // Instantiation table for one row width QH (float4 per row): batches of 16, 12, 8 or 4
-// images, y in FP32 (yf = 0) or as the BF16 hi/lo split (yf = 1).
+// images, y in FP32 (yf = 0) or as the BF16 hi/lo split (yf = 1); sweep_v3g_qh* holds the
+// instances that read the distance-unit table from global memory (batches of 8 or 4).
 #define MRA_SWEEP_V3_TABLE(QH)                                     \
   namespace mra {                                                  \
   SweepV3Fn sweep_v3_qh##QH(int bi, int yf) {                      \
@@ -430,6 +444,15 @@ __global__ void __launch_bounds__(kV3Threads, 1) k_sweep_v3(const SweepV3Args a)
       case 17: return k_sweep_v3<QH, 8, 1>;                        \
       case 8: return k_sweep_v3<QH, 4, 0>;                         \
       case 9: return k_sweep_v3<QH, 4, 1>;                         \
+      default: return nullptr;                                     \
+    }                                                              \
+  }                                                                \
+  SweepV3Fn sweep_v3g_qh##QH(int bi, int yf) {                     \
+    switch (bi * 2 + (yf ? 1 : 0)) {                               \
+      case 16: return k_sweep_v3<QH, 8, 0, true>;                  \
+      case 17: return k_sweep_v3<QH, 8, 1, true>;                  \
+      case 8: return k_sweep_v3<QH, 4, 0, true>;                   \
+      case 9: return k_sweep_v3<QH, 4, 1, true>;                   \
       default: return nullptr;                                     \
     }                                                              \
   }                                                                \

@@ -23,6 +23,11 @@
 // locates each image's peak rotation l* and how far from it the weights matter; pass 2
 // recomputes those values as differences S(l* +- d) - S(l*) from c rotated to the peak and
 // an FP64-built table of (cos t - 1, -sin t), whose terms vanish near the peak.
+// Windows of one unit chunk hand each warp a fixed stride of images.  Wider windows cost per
+// image in proportion to the spread of its posterior (pass 2 and the back transform run over
+// the distances within D of the peak), so their warps take images one at a time from a counter
+// in the control block once the first two (static) are done, and the last warp to finish
+// clears the counter for the next launch.
 // The CTA combines its warps' sums once at the end and writes FP64 partials.
 #pragma once
 #include "common.cuh"
@@ -109,6 +114,8 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR, IPW>::kThreads, 1) k_swee
   __syncthreads();
 
   const int gw = blockIdx.x * nwarps + warp, GW = gridDim.x * nwarps;
+  constexpr bool kDyn = LWC <= 0 && IPW == 1;  // images handed out one at a time
+  int held0 = gw, held1 = gw + GW;              // kDyn: the image in ring stage 0 / 1 (>= N: none)
   const uint32_t img_bytes = (uint32_t)M * 8u;
   unsigned char* const wring = ring + (size_t)warp * 2 * IPW * a.slot_bytes;
   uint64_t* mybar = bar + 2 * warp;
@@ -140,7 +147,7 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR, IPW>::kThreads, 1) k_swee
     issue(1, 1);
   }
 
-  for (int p = 0; warp < nwarps && gw + p * IPW * GW < a.N; ++p) {
+  for (int p = 0; warp < nwarps && (kDyn ? ((p & 1) ? held1 : held0) : gw + p * IPW * GW) < a.N; ++p) {
     const int st = p & 1;
     const uint32_t parity = (uint32_t)((p >> 1) & 1);
     const bool ok = mbar_wait_bounded(&mybar[st], parity);
@@ -148,7 +155,8 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR, IPW>::kThreads, 1) k_swee
       if (lane == 0) {
         atomicExch(&a.ctrl->status, (int)MRA_ETIMEOUT);
         mbar_wait_bounded(&mybar[st], parity);
-        if (gw + (p + 1) * IPW * GW < a.N) mbar_wait_bounded(&mybar[st ^ 1], (uint32_t)(((p + 1) >> 1) & 1));
+        if ((kDyn ? (st ? held0 : held1) : gw + (p + 1) * IPW * GW) < a.N)
+          mbar_wait_bounded(&mybar[st ^ 1], (uint32_t)(((p + 1) >> 1) & 1));
       }
       break;
     }
@@ -158,7 +166,7 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR, IPW>::kThreads, 1) k_swee
     int ph0[IPW], phstep[IPW], sjv[IPW];
 #pragma unroll
     for (int i = 0; i < IPW; ++i) {
-      img[i] = gw + (p * IPW + i) * GW;
+      img[i] = kDyn ? (st ? held1 : held0) : gw + (p * IPW + i) * GW;
       valid[i] = img[i] < a.N;
       y4[i] = reinterpret_cast<const float4*>(wring + (size_t)(st * IPW + i) * a.slot_bytes);
       int sj = 0;
@@ -674,9 +682,29 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR, IPW>::kThreads, 1) k_swee
     }
     // ring stage st may be refilled once every lane has finished reading it
     __syncwarp();
-    if (lane == 0) {
+    if constexpr (kDyn) {
+      int nxt = 0;
+      if (lane == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        nxt = 2 * GW + (int)atomicAdd(&a.ctrl->sched[0], 1u);
+        if (nxt < a.N) {
+          mbar_arrive_expect_tx(&mybar[st], img_bytes);
+          bulk_g2s(wring + (size_t)st * a.slot_bytes, a.y + (size_t)nxt * M, img_bytes, &mybar[st]);
+        }
+      }
+      nxt = __shfl_sync(0xffffffffu, nxt, 0);
+      if (st) held1 = nxt;
+      else held0 = nxt;
+    } else if (lane == 0) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       issue(p + 2, st);
+    }
+  }
+  if constexpr (kDyn) {  // the last warp out clears the counters (every fetch of this launch is done)
+    if (warp < nwarps && lane == 0 &&
+        atomicAdd(&a.ctrl->sched[1], 1u) == (unsigned)(gridDim.x * nwarps) - 1u) {
+      atomicExch(&a.ctrl->sched[0], 0u);
+      atomicExch(&a.ctrl->sched[1], 0u);
     }
   }
 

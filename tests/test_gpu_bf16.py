@@ -31,10 +31,13 @@ def test_split_kernel_is_bit_exact(gpu_lib):
     np.testing.assert_array_equal(host(out), want)
 
 
-@pytest.fixture(params=["cta", "chunk"])
+@pytest.fixture(params=["cta", "chunk", "cta-tdg"])
 def sweep(request, monkeypatch):
-    """Both sweeps that read the split format: the CTA batch sweep and the chunked two-read sweep."""
-    monkeypatch.setenv("MRA_SWEEP", request.param)
+    """Both sweeps that read the split format: the CTA batch sweep and the chunked two-read sweep
+    (cta-tdg: the batch sweep with its distance-unit table read from global memory)."""
+    monkeypatch.setenv("MRA_SWEEP", request.param.split("-")[0])
+    if request.param.endswith("-tdg"):
+        monkeypatch.setenv("MRA_SWEEP_TDG", "1")
     return request.param
 
 
@@ -71,6 +74,32 @@ def test_em_step_hl_config5_shapes(gpu_lib, sweep, N, L, window):
     full = O.em_step(synth.c64_round(inst.y), x0, lr, inst.L, inst.sigma2, Lw=Lw, l0=l0, shifts=sh)
     print(f"\nbf16 hi/lo, N={N}, Lw={Lw}: vs oracle on hi+lo x {ex:.2e} w {ew:.2e}; vs oracle on complex64 y "
           f"x {rel_err(host(xo), full.x):.2e} w {np.max(np.abs(host(w) - full.w)):.2e}")
+
+
+def test_em_step_hl_dense_window_table_in_global_memory(gpu_lib):
+    """The split format on the paper's dense window at |k| <= 32, Q = 24, L = 360 (721 rotations 0.05 grid
+    units apart, off-grid rotations): the batch sweep's distance-unit table does not fit in shared memory
+    next to its ring, so it reads the table from global memory."""
+    mra = gpu_lib
+    K, Q, L, N = 32, 24, 360, 300
+    inst = synth.make_instance(K, Q, N, L, snr=1 / 50, decay=400.0, seed=5400, offgrid=True)
+    y_hl = synth.bf16_merge(synth.bf16_split(inst.y), inst.y.shape)
+    Lw, l0, step = 2 * L + 1, -L, 36 / (2 * L)
+    x0 = O.align_mean(y_hl, inst.s, L)
+    lr = np.log(np.full(Lw, 1.0 / Lw))
+    d = mra.dims(N, K, Q, L, inst.sigma2)
+    ws = mra.workspace(mra.mra_em_workspace_bytes(d, Lw))
+    xi, lri = dev(x0), dev(lr)
+    xo, lro = torch.empty_like(xi), torch.empty_like(lri)
+    w = torch.empty((N, Lw), dtype=torch.float32, device="cuda")
+    ll = torch.empty(1, dtype=torch.float64, device="cuda")
+    mra.mra_em_step_hl(d, mra.em_params(Lw, l0=l0, step=step), _dev_hl(inst.y), dev(inst.s.astype(np.int32)),
+                       xi, lri, xo, lro, ll, None, w, ws)
+    torch.cuda.synchronize()
+    assert mra.mra_ws_status(ws) == 0
+    ref = O.em_step(y_hl, x0, lr, L, inst.sigma2, Lw=Lw, l0=l0, shifts=inst.s, step=step)
+    assert rel_err(host(xo), ref.x) <= TOL_X, rel_err(host(xo), ref.x)
+    assert np.max(np.abs(host(w) - ref.w)) <= TOL_W, np.max(np.abs(host(w) - ref.w))
 
 
 def test_em_run_hl_first_10k_images_of_config5(gpu_lib, sweep):

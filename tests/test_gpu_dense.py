@@ -45,9 +45,12 @@ def _compare(mra, inst, x, log_rho, Lw, l0, step, shifts=None, **kw):
     return xg, st
 
 
-@pytest.fixture(params=["cta", "warp", "chunk"])
+@pytest.fixture(params=["cta", "warp", "chunk", "cta-tdg"])
 def sweep(request, monkeypatch):
-    monkeypatch.setenv("MRA_SWEEP", request.param)
+    """cta-tdg: the batch sweep with its distance-unit table read from global memory."""
+    monkeypatch.setenv("MRA_SWEEP", request.param.split("-")[0])
+    if request.param.endswith("-tdg"):
+        monkeypatch.setenv("MRA_SWEEP_TDG", "1")
     return request.param
 
 
@@ -72,11 +75,13 @@ def test_dense_em_step_matches_oracle(gpu_lib, sweep, K, Q, N, L, Lw, l0, step):
     _compare(gpu_lib, inst, x0, lr, Lw, l0, step, shifts=inst.s)
 
 
-def test_dense_paper_example_window_full_workload_shape(gpu_lib):
+@pytest.mark.parametrize("kind", ["warp", "cta"])
+def test_dense_paper_example_window_full_workload_shape(gpu_lib, kind, monkeypatch):
     """The paper's example of the denser window at the Synch-EM workload's shape: the range
     [-pi BW/L, pi BW/L] with BW = 36 at spacing pi BW/L^2 (Lw = 2 L + 1 = 721 rotations 0.05 grid units
-    apart, |k| <= 32, Q = 24, L = 360).  Its unit twiddle table does not fit in shared memory next to the
-    image rings, so the warp sweep reads it from global memory."""
+    apart, |k| <= 32, Q = 24, L = 360).  Its unit tables do not fit in shared memory next to the image
+    rings, so the warp sweep and the batch sweep read them from global memory."""
+    monkeypatch.setenv("MRA_SWEEP", kind)
     K, Q, L = 32, 24, 360
     inst = synth.make_instance(K, Q, 300, L, snr=1 / 50, decay=400.0, seed=8150, offgrid=True)
     x0 = O.align_mean(synth.c64_round(inst.y), inst.s, inst.L)
@@ -115,6 +120,33 @@ def test_dense_em_run_trajectory(gpu_lib, sweep):
     x, lr = dev(x0), dev(lr0)
     traj = torch.empty((T, inst.K + 1, inst.Q), dtype=torch.complex128, device="cuda")
     assert mra.mra_em_run(d, prm, dev_y(y64), dev(inst.s.astype(np.int32)), x, lr, None, traj, ws) == T
+    xs, lrs = x0, lr0
+    for t in range(T):
+        st = O.em_step(y64, xs, lrs, inst.L, inst.sigma2, Lw=Lw, l0=l0, shifts=inst.s, step=step)
+        assert rel_err(host(traj[t]), st.x) <= TOL_X * (t + 1), (t, rel_err(host(traj[t]), st.x))
+        xs, lrs = st.x, st.log_rho
+    np.testing.assert_allclose(np.exp(host(lr)), np.exp(lrs), atol=1e-5 * T, rtol=0)
+
+
+@pytest.mark.parametrize("Lw,l0,step", [(201, -100, 0.4), (61, -30, 1.0)])
+def test_wide_window_warp_sweep_hands_out_images(gpu_lib, monkeypatch, Lw, l0, step):
+    """More images (7,000) than two per warp of the persistent grid (152 CTAs x 16 warps), so that the warp
+    sweep on a window wider than one unit chunk hands the rest out one at a time from its counter; three
+    EM iterations in one run (the counter must be clear again at every sweep) against the oracle."""
+    monkeypatch.setenv("MRA_SWEEP", "warp")
+    mra = gpu_lib
+    inst = synth.make_instance(8, 16, 7000, 120, snr=1 / 5, decay=50.0, seed=8450 + Lw, offgrid=step != 1.0)
+    y64 = synth.c64_round(inst.y)
+    T = 3
+    x0 = O.align_mean(y64, inst.s, inst.L)
+    lr0 = np.log(np.full(Lw, 1 / Lw))
+    d = mra.dims(inst.N, inst.K, inst.Q, inst.L, inst.sigma2)
+    prm = mra.em_params(Lw, l0=l0, max_iters=T, step=step)
+    ws = mra.workspace(mra.mra_em_workspace_bytes(d, Lw))
+    x, lr = dev(x0), dev(lr0)
+    traj = torch.empty((T, inst.K + 1, inst.Q), dtype=torch.complex128, device="cuda")
+    assert mra.mra_em_run(d, prm, dev_y(y64), dev(inst.s.astype(np.int32)), x, lr, None, traj, ws) == T
+    assert mra.mra_ws_status(ws) == 0
     xs, lrs = x0, lr0
     for t in range(T):
         st = O.em_step(y64, xs, lrs, inst.L, inst.sigma2, Lw=Lw, l0=l0, shifts=inst.s, step=step)

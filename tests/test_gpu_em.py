@@ -49,11 +49,14 @@ def compare(mra, inst, x, log_rho, Lw, l0=None, shifts=None, **kw):
     return xg, st
 
 
-@pytest.fixture(params=["cta", "warp", "chunk"])
+@pytest.fixture(params=["cta", "warp", "chunk", "cta-tdg"])
 def sweep(request, monkeypatch):
     """Every EM sweep: the CTA-cooperative batch sweep, the warp-per-image one and the
-    chunked two-read one (shapes a sweep cannot take fall back to the tile sweep)."""
-    monkeypatch.setenv("MRA_SWEEP", request.param)
+    chunked two-read one (shapes a sweep cannot take fall back to the tile sweep); cta-tdg is
+    the batch sweep with its distance-unit table read from global memory."""
+    monkeypatch.setenv("MRA_SWEEP", request.param.split("-")[0])
+    if request.param.endswith("-tdg"):
+        monkeypatch.setenv("MRA_SWEEP_TDG", "1")
     return request.param
 
 
