@@ -339,23 +339,34 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR, IPW>::kThreads, 1) k_swee
           dist[i] = peak_dist(bl, lo, hi);
         }
       } else if constexpr (IPW == 1) {
+        // wide windows: each lane owns whole units (u0 + lane, u0 + lane + 32) and sums over every row,
+        // with c_k broadcast from its quad (row k sits in quad k mod 8 as c[k / 8]) and coalesced
+        // twiddle rows, so no cross-lane reduction is needed per unit
         float* sb = sbuf0;
-        for (int u0 = 0; u0 < NUP; u0 += 4 * kUC) {  // pass 1 into the per-warp buffer
-          float A[1][kUC], Bv[1][kUC];
-          partials(u0, A, Bv);
-          float At[kUC], Bt[kUC];
+        for (int u0 = 0; u0 < NU; u0 += 64) {  // pass 1 into the per-warp buffer
+          const int ua = u0 + lane, ub = ua + 32;
+          const float2* ta = tus + min(ua, NUP - 1);
+          const float2* tb = tus + min(ub, NUP - 1);
+          float A0 = 0.f, B0 = 0.f, A1 = 0.f, B1 = 0.f;
 #pragma unroll
-          for (int t = 0; t < kUC; ++t) At[t] = quad_sum(A[0][t]), Bt[t] = quad_sum(Bv[0][t]);
-          if (r == 0) {
-#pragma unroll
-            for (int t = 0; t < kUC; ++t) {
-              const int u = u0 + j + 4 * t;
-              if (u < NU) {
-                const int2 ab = uab[u];
-                sb[ab.x] = fmaf(two_beta, At[t] - Bt[t], lrs[ab.x]);
-                if (ab.y >= 0) sb[ab.y] = fmaf(two_beta, At[t] + Bt[t], lrs[ab.y]);
-              }
+          for (int k = 0; k < 8 * MR; ++k) {
+            if (k < 8 * (MR - 1) || k < Kp1) {  // static for all row groups but the last: loads batch
+              const float cx = __shfl_sync(0xffffffffu, c[0][k >> 3].x, 4 * (k & 7));
+              const float cy = __shfl_sync(0xffffffffu, c[0][k >> 3].y, 4 * (k & 7));
+              const float2 va = ta[k * NUP], vb = tb[k * NUP];
+              A0 = fmaf(cx, va.x, A0); B0 = fmaf(cy, va.y, B0);
+              A1 = fmaf(cx, vb.x, A1); B1 = fmaf(cy, vb.y, B1);
             }
+          }
+          if (ua < NU) {
+            const int2 ab = uab[ua];
+            sb[ab.x] = fmaf(two_beta, A0 - B0, lrs[ab.x]);
+            if (ab.y >= 0) sb[ab.y] = fmaf(two_beta, A0 + B0, lrs[ab.y]);
+          }
+          if (ub < NU) {
+            const int2 ab = uab[ub];
+            sb[ab.x] = fmaf(two_beta, A1 - B1, lrs[ab.x]);
+            if (ab.y >= 0) sb[ab.y] = fmaf(two_beta, A1 + B1, lrs[ab.y]);
           }
         }
         __syncwarp();
@@ -440,6 +451,38 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR, IPW>::kThreads, 1) k_swee
             }
           }
           emit(j, Ad, Bd);
+        } else if constexpr (LWC <= 0) {
+          // wide windows: lanes own whole distances (d0 + lane, d0 + lane + 32), c' broadcast by row
+          // as in pass 1
+          auto emit_lane = [&](int d, float Ad, float Bd) {
+            if (d <= D) {
+              int la = p + d, lb = p - d;
+              if (wrap) {
+                if (la >= L) la -= L;
+                if (lb < 0) lb += L;
+              }
+              if (wrap || la < Lw) sb[la] = fmaf(two_beta, Ad - Bd, lrs[la] - lr_ref);
+              if (d > 0 && (wrap ? 2 * d != L : lb >= 0)) sb[lb] = fmaf(two_beta, Ad + Bd, lrs[lb] - lr_ref);
+            }
+          };
+          for (int d0 = 0; d0 <= D; d0 += 64) {
+            const int da = d0 + lane, db = da + 32;
+            const float2* ta = a.td + min(da, nd1);
+            const float2* tb = a.td + min(db, nd1);
+            float A0 = 0.f, B0 = 0.f, A1 = 0.f, B1 = 0.f;
+#pragma unroll
+            for (int k = 0; k < 8 * MR; ++k) {
+              if (k < 8 * (MR - 1) || k < Kp1) {
+                const float cx = __shfl_sync(0xffffffffu, cq[k >> 3].x, 4 * (k & 7));
+                const float cy = __shfl_sync(0xffffffffu, cq[k >> 3].y, 4 * (k & 7));
+                const float2 va = ta[k * a.nd], vb = tb[k * a.nd];
+                A0 = fmaf(cx, va.x, A0); B0 = fmaf(cy, va.y, B0);
+                A1 = fmaf(cx, vb.x, A1); B1 = fmaf(cy, vb.y, B1);
+              }
+            }
+            emit_lane(da, A0, B0);
+            emit_lane(db, A1, B1);
+          }
         } else {
           for (int d0 = 0; d0 <= D; d0 += 4 * kUC) {
             const int nt = min(kUC, (D - d0) / 4 + 1);  // slots t holding some d <= D
