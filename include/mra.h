@@ -153,8 +153,11 @@ MRA_API int mra_y_split_bf16(const float* y, int64_t count, void* y_hl_out, void
 
 /* mra_em_step / mra_em_run with y in the BF16 hi/lo split (other arguments as
  * there).  Products and sums stay FP32 as in the complex64 path; the cross-image
- * reductions are FP64.  MRA_EINVAL where the batch sweep cannot take the shape
- * (Q a multiple of 8 and (K+1) Q / 4 <= 512 are required). */
+ * reductions are FP64.  The batch sweep reads this format (the chunked sweep too,
+ * where the autotuner or MRA_SWEEP=chunk chooses it); a window whose distance table
+ * does not fit in shared memory next to the batch sweep's ring is read from global
+ * memory.  MRA_EINVAL where no such sweep can take the shape (Q a multiple of 8 and
+ * (K+1) Q / 4 <= 512 are required). */
 MRA_API int mra_em_step_hl(const mra_dims* dims, const mra_em_params* prm, const void* y_hl, const int32_t* shift,
                            const double* x_in, const double* log_rho_in, double* x_out, double* log_rho_out,
                            double* loglik_out, double* step_out, float* w_out, void* ws, size_t ws_bytes,
@@ -167,13 +170,15 @@ MRA_API int mra_em_run_hl(const mra_dims* dims, const mra_em_params* prm, const 
  * Neither has a counterpart in the paper, which treats one problem at a time. */
 
 /* Times every EM sweep that can take the problem (the warp-per-image sweep; the
- * batch sweep at 16, 12, 8 or 4 images per batch and 2 or 3 ring stages) for one
- * sweep over y from the state (x, log_rho), and caches the fastest for this
- * device and shape (K, Q, L, Lw, l0, y_format).  Later EM calls on that shape use
- * the cached choice unless the MRA_SWEEP* environment variables fix one.
+ * batch sweep at 16, 12, 8 or 4 images per batch and 2 or 3 ring stages; the
+ * chunked two-read sweep at 128, 64, 32 or 16 images per chunk and 1 or 2 CTAs per
+ * SM) for one sweep over y from the state (x, log_rho), and caches the fastest for
+ * this device and shape (K, Q, L, Lw, l0, step, y_format).  Later EM calls on that
+ * shape use the cached choice unless the MRA_SWEEP* environment variables fix one.
  * Synchronizes the stream.
  *   y_format   0: y complex64; 1: the BF16 hi/lo split of mra_y_split_bf16
- *   choice_out host int32[3] (kind 1 warp / 2 batch / 0 none applies, batch, stages), or NULL
+ *   choice_out host int32[3]: kind (1 warp, 2 batch, 3 chunked, 0 none applies),
+ *              images per batch or chunk, ring stages or CTAs per SM; or NULL
  * The workspace is the one of mra_em_workspace_bytes; its contents are clobbered. */
 MRA_API int mra_em_autotune(const mra_dims* dims, const mra_em_params* prm, const void* y, int32_t y_format,
                             const int32_t* shift, const double* x, const double* log_rho, int32_t* choice_out,

@@ -226,7 +226,8 @@ def mra_em_run_hl(d, prm, y_hl, shift, x_inout, log_rho_inout, stats_out=None, x
 
 
 def mra_em_autotune(d, prm, y, shift, x, log_rho, ws, y_format=0, stream=None):
-    """Time every applicable EM sweep on this problem and cache the fastest; returns (kind, batch, stages)."""
+    """Time every applicable EM sweep on this problem and cache the fastest; returns (kind, images, stages):
+    kind 1 warp, 2 batch, 3 chunked (0 none applies); images per batch or chunk; ring stages or CTAs per SM."""
     ch = (c_int32 * 3)()
     _check("mra_em_autotune", load().mra_em_autotune(ctypes.byref(d), ctypes.byref(prm), _p(y), int(y_format),
                                                      _p(shift), _p(x), _p(log_rho), ch, _p(ws), ws.numel(),
