@@ -530,6 +530,36 @@ def test_template_match_1d_against_signal_space_brute_force():
     np.testing.assert_array_equal(got, want)
 
 
+def test_1d_em_step_in_coefficient_form_equals_signal_space_em():
+    """One EM step of the 1-D model written in signal space (posterior over all L cyclic shifts with
+    exp(-||v_j - roll(x, l)||^2 / (2 sigma^2)), x_new = mean_j sum_l w_jl roll(v_j, -l), rho_new = mean_j w_j)
+    against the oracle's EM step on the coefficient form with sigma2 = 2 sigma^2 (whole grid, l0 = 0)."""
+    L, N, sigma = 15, 60, 0.9
+    inst = synth.make_instance_1d(L, N, sigma, seed=41)
+    x0 = np.random.default_rng(42).standard_normal(L)
+    rho = np.random.default_rng(43).random(L) + 0.3
+    rho /= rho.sum()
+    # signal space, written out
+    logw = np.empty((N, L))
+    for j in range(N):
+        for l in range(L):
+            logw[j, l] = np.log(rho[l]) - np.sum((inst.v[j] - np.roll(x0, l)) ** 2) / (2 * sigma ** 2)
+    w = np.exp(logw - logw.max(axis=1, keepdims=True))
+    w /= w.sum(axis=1, keepdims=True)
+    x_new = np.zeros(L)
+    for j in range(N):
+        for l in range(L):
+            x_new += w[j, l] * np.roll(inst.v[j], -l)
+    x_new /= N
+    rho_new = w.mean(axis=0)
+    # coefficient form through the oracle
+    st = O.em_step(synth.coeffs_1d(inst.v), synth.coeffs_1d(x0), np.log(rho), L, synth.sigma2_coeff(sigma),
+                   Lw=L, l0=0)
+    np.testing.assert_allclose(st.w, w, atol=1e-12)
+    np.testing.assert_allclose(synth.signal_1d(st.x, L), x_new, atol=1e-12)
+    np.testing.assert_allclose(np.exp(st.log_rho), rho_new, atol=1e-12)
+
+
 def test_tm_shift_pmf_two_point_closed_form():
     """L = 2: p[0] = P(A_0 > A_1) = Phi((R[0] - R[1]) / (sqrt 2 sigma_c)) for the independent model."""
     from scipy import stats
