@@ -208,6 +208,26 @@ def test_full_window_uniform_prior_is_standard_em():
 
 
 # --------------------------------------------------------------------------- equivariance
+@pytest.mark.parametrize("Lw,l0,step", [(5, -1, 1.0), (7, -6, 1.0), (6, -2, 0.4)])
+def test_opposite_rotation_sign_is_the_reflected_window(Lw, l0, step):
+    """The opposite rotation convention (v = a e^{+ik theta}) is the paper's one with the window reflected,
+    l -> -l: EM on the conjugated observations and signal, over the window -(l0 + Lw - 1) .. -l0 with the prior
+    read backwards, gives the weights and prior read backwards and the conjugated signal (non-symmetric
+    windows, on and off the grid)."""
+    inst = tiny(seed=13, N=5, L=9)
+    L, sigma2 = inst.L, inst.sigma2
+    x = synth.make_signal(inst.K, inst.Q, 4.0, np.random.default_rng(14))
+    rho = np.random.default_rng(15).random(Lw) + 0.2
+    rho /= rho.sum()
+    st = O.em_step(inst.y, x, np.log(rho), L, sigma2, Lw=Lw, l0=l0, step=step)
+    sr = O.em_step(np.conj(inst.y), np.conj(x), np.log(rho[::-1]), L, sigma2, Lw=Lw, l0=-(l0 + Lw - 1),
+                   step=step)
+    np.testing.assert_allclose(sr.w, st.w[:, ::-1], atol=1e-13)
+    np.testing.assert_allclose(sr.x, np.conj(st.x), atol=1e-13)
+    np.testing.assert_allclose(sr.log_rho, st.log_rho[::-1], atol=1e-12)
+    assert abs(sr.loglik - st.loglik) <= 1e-10 * abs(st.loglik)
+
+
 def test_em_equivariant_under_global_rotation():
     inst = synth.make_instance(K=6, Q=4, N=60, L=24, sigma2=soft(0.3, 6, 4), decay=20.0, seed=31)
     L, g = inst.L, 5
