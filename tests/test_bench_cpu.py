@@ -7,8 +7,6 @@ import socket
 import subprocess
 import sys
 
-import bench
-
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 KEYS = ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
@@ -21,7 +19,15 @@ def _json_lines(cmd, timeout=600):
     return [json.loads(s) for s in r.stdout.splitlines() if s.startswith("{")]
 
 
+def _bench():
+    # imported inside the tests: importing bench sets the BLAS thread-count defaults of the process
+    import bench
+
+    return bench
+
+
 def _check_line(d, n_gpus, steps, warmup):
+    bench = _bench()
     for k in KEYS:
         assert k in d, k
     assert d["impl"] == "reference"
@@ -62,6 +68,7 @@ def test_reference_arm_under_torchrun_two_ranks():
 
 
 def test_sweep_choice_follows_the_environment(monkeypatch):
+    bench = _bench()
     tuned = (1, 0, 0)
     monkeypatch.delenv("MRA_SWEEP", raising=False)
     assert bench._effective_choice(tuned) == tuned
