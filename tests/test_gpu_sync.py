@@ -2,8 +2,6 @@
 through the C ABI.  Integer outputs must match the oracle exactly except where
 the oracle itself certifies a near-tie (its margin below the FP32 resolution
 of the GPU's arithmetic), in which case either choice is accepted."""
-import math
-
 import numpy as np
 import pytest
 import torch
