@@ -100,12 +100,14 @@ typedef struct {
 MRA_API const char* mra_status_string(int status);
 
 /* Number of streaming multiprocessors and the persistent-grid size the EM
- * sweep uses on the current device (host outputs).  Useful for sizing. */
+ * sweep uses on the current device (host outputs).  Useful for sizing; a runtime
+ * query with no counterpart in the paper. */
 MRA_API int mra_device_info(int32_t* num_sms, int32_t* sweep_grid);
 
 /* ------------------------------------------------------------------ EM */
 
-/* Workspace bytes for mra_em_step, mra_em_run and mra_loglik_grad. */
+/* Workspace bytes for mra_em_step, mra_em_run and mra_loglik_grad (sizing of the
+ * caller-owned scratch; no counterpart in the paper). */
 MRA_API size_t mra_em_workspace_bytes(const mra_dims* dims, int32_t Lw);
 
 /* One iteration of Algorithm Synch-EM (E-step with Eq. weights_2d_em on the
@@ -151,8 +153,8 @@ MRA_API int mra_em_run(const mra_dims* dims, const mra_em_params* prm, const flo
  *   y_hl_out device [count / 2] 16-byte groups, 16-byte aligned */
 MRA_API int mra_y_split_bf16(const float* y, int64_t count, void* y_hl_out, void* stream);
 
-/* mra_em_step / mra_em_run with y in the BF16 hi/lo split (other arguments as
- * there).  Products and sums stay FP32 as in the complex64 path; the cross-image
+/* Algorithm Synch-EM as mra_em_step / mra_em_run, with y in the BF16 hi/lo split (other
+ * arguments as there).  Products and sums stay FP32 as in the complex64 path; the cross-image
  * reductions are FP64.  The batch sweep reads this format (the chunked sweep too,
  * where the autotuner or MRA_SWEEP=chunk chooses it); a window whose distance table
  * does not fit in shared memory next to the batch sweep's ring is read from global
@@ -169,8 +171,9 @@ MRA_API int mra_em_run_hl(const mra_dims* dims, const mra_em_params* prm, const 
 /* ------------------------------------------------------------------ autotuner and batched runs
  * Neither has a counterpart in the paper, which treats one problem at a time. */
 
-/* Times every EM sweep that can take the problem (the warp-per-image sweep; the
- * batch sweep at 16, 12, 8 or 4 images per batch and 2 or 3 ring stages; the
+/* (No counterpart in the paper.)  Times every EM sweep that can take the problem
+ * (the warp-per-image sweep; the batch sweep at 16, 12, 8 or 4 images per batch and
+ * 2 or 3 ring stages; the
  * chunked two-read sweep at 128, 64, 32 or 16 images per chunk and 1 or 2 CTAs per
  * SM) for one sweep over y from the state (x, log_rho), and caches the fastest for
  * this device and shape (K, Q, L, Lw, l0, step, y_format).  Later EM calls on that
@@ -198,7 +201,8 @@ typedef struct {
   double* stats_out;       /* [max_iters][2] (loglik, step) or NULL */
 } mra_instance;
 
-/* Workspace for mra_em_run_batched: the instances' EM workspaces, 256-byte aligned, in order. */
+/* Workspace for mra_em_run_batched: the instances' EM workspaces, 256-byte aligned, in order
+ * (sizing; no counterpart in the paper). */
 MRA_API size_t mra_em_batched_workspace_bytes(const mra_instance* inst, int32_t n);
 
 /* Algorithm Synch-EM's loop for n independent problems of uneven N, K and window
@@ -213,7 +217,8 @@ MRA_API size_t mra_em_batched_workspace_bytes(const mra_instance* inst, int32_t 
 MRA_API int mra_em_run_batched(const mra_instance* inst, int32_t n, int32_t tune, int32_t* iters_out,
                                float* exec_ms_out, void* ws, size_t ws_bytes, void* stream);
 
-/* Marginal log-likelihood over the window and its gradient (Fisher identity),
+/* Marginal log-likelihood over the window (Sec. 2.2, the likelihood of the observation model) and its
+ * gradient (Fisher identity),
  *   l(x, kappa, eta) = sum_j log sum_l rho_l (pi sigma2)^{-M} exp(-||x o e^{-i k theta_l} - y_j||^2 / sigma2),
  *   log rho_l = kappa cos(theta_l) + eta_l - log sum_win exp(kappa cos theta + eta),
  *   theta_l = 2 pi step (l0+l)/L (step as in mra_em_params; 0 is read as 1).
@@ -231,7 +236,7 @@ MRA_API int mra_loglik_grad(const mra_dims* dims, int32_t Lw, int32_t l0, double
 
 /* ------------------------------------------------------------------ synchronization */
 
-/* Workspace bytes for mra_sync and its parts. */
+/* Workspace bytes for mra_sync and its parts (sizing; no counterpart in the paper). */
 MRA_API size_t mra_sync_workspace_bytes(const mra_dims* dims, int32_t P);
 
 /* Relative rotations of the first P images, Eq. (relative_angle_2d_dist):
@@ -296,7 +301,8 @@ MRA_API size_t mra_fb_setup_workspace_bytes(int32_t n, int32_t K, int32_t Q);
 MRA_API int mra_fb_setup(int32_t n, int32_t K, int32_t Q, float* P_out, double* zeros_out, void* ws, size_t ws_bytes,
                          void* stream);
 
-/* Coefficients of N images: y_out [N][K+1][Q] complex float = images [N][n][n] float times P, one GEMM
+/* App. A, the Fourier-Bessel expansion of pixel images:
+ * coefficients of N images: y_out [N][K+1][Q] complex float = images [N][n][n] float times P, one GEMM
  * (cuBLAS; tf32 != 0 uses TF32 tensor cores, relative error ~1e-3 instead of ~1e-6).  y_out has the
  * layout every EM and synchronization entry point reads.  All pointers device, 16-byte aligned. */
 MRA_API int mra_fb_project(int32_t N, int32_t n, int32_t K, int32_t Q, const float* images, const float* P,
@@ -322,7 +328,8 @@ MRA_API int mra_spca_fit(const mra_dims* dims, const float* y, float* basis_out,
 MRA_API int mra_spca_project(const mra_dims* dims, const float* y, int32_t K2, int32_t Q2, const float* basis,
                              float* y_out, void* stream);
 
-/* Eigen-decomposition of a Hermitian n x n matrix (HOST pointers, column-major complex double, n <= 512):
+/* The eigenvectors of the steerable PCA step of App. A:
+ * eigen-decomposition of a Hermitian n x n matrix (HOST pointers, column-major complex double, n <= 512):
  * w [n] descending, V [n][n] eigenvectors as columns, each with its largest-magnitude entry real positive.
  * FP64 cyclic Jacobi on the real symmetric embedding.  Used by mra_spca_fit; no GPU needed. */
 MRA_API int mra_hermitian_eig(int32_t n, const double* A, double* w, double* V);
@@ -376,7 +383,7 @@ MRA_API int mra_em_step_noalloc(const mra_dims* dims, const mra_em_params* prm, 
                                 double* loglik_out, double* step_out, float* w_out, void* stream);
 
 /* Synchronize the stream and return the workspace's device status word
- * (MRA_OK or MRA_ETIMEOUT), then clear it. */
+ * (MRA_OK or MRA_ETIMEOUT), then clear it (failure detection; no counterpart in the paper). */
 MRA_API int mra_ws_status(void* ws, void* stream);
 
 /* Self-test of the device-side failure detection (no counterpart in the paper).
