@@ -142,8 +142,8 @@ MRA_API int mra_em_run(const mra_dims* dims, const mra_em_params* prm, const flo
                        double* x_inout, double* log_rho_inout, int32_t* iters_out, double* stats_out,
                        double* x_traj_out, void* ws, size_t ws_bytes, void* stream);
 
-/* y as a BF16 hi/lo split (a storage format for the streamed observations; the
- * paper's method is unchanged).  Each pair of complex values (re0, im0, re1, im1)
+/* y as a BF16 hi/lo split (a storage format for the streamed observations, no
+ * counterpart in the paper; the paper's method is unchanged).  Each pair of complex values (re0, im0, re1, im1)
  * of y occupies one 16-byte group: bf16 hi of the four values, then bf16 lo of
  * their residuals, hi = rn_bf16(v), lo = rn_bf16(v - hi); the kernels read
  * v = hi + lo, which FP32 holds exactly (relative error of the split <= 2^-16).

@@ -80,3 +80,17 @@ def test_oracle_not_imported_by_product():
         for f in fs:
             if f.endswith(".py"):
                 assert not pat.search(open(os.path.join(dp, f)).read()), f
+
+
+def test_every_entry_point_names_its_passage():
+    """Each declaration's comment cites the paper's passage it implements (Sec., Eq., App., Algorithm), or
+    states that it has no counterpart in the paper."""
+    src = open(os.path.join(ROOT, "include", "mra.h")).read()
+    missing = []
+    for m in re.finditer(r"MRA_API[^;]*?\b(mra_\w+)\s*\(", src):
+        cstart, cend = src.rfind("/*", 0, m.start()), src.rfind("*/", 0, m.start())
+        comment = " ".join(src[cstart:cend].replace("*", " ").split()) if 0 <= cstart < cend else ""
+        if not re.search(r"Sec\.|Eq\.|App\.|Algorithm|counterpart in the paper|not in the paper", comment):
+            missing.append(m.group(1))
+    assert not missing, missing
+
