@@ -377,10 +377,24 @@ MRA_API int mra_relerr(int32_t K, int32_t Q, const double* x_hat, const double* 
  *     stream capture.
  *   - All calls share the one array and it keeps the previous call's contents;
  *     the call initialises everything it reads.  Calls that overlap on the GPU
- *     (for example on two streams) race on the array: serialise them. */
+ *     (for example on two streams) race on the array: serialise them.
+ *   - The cached address belongs to the device's context at the first call;
+ *     calls after cudaDeviceReset (or any other teardown of that context) in
+ *     the same process are not supported.
+ *   - A bounded wait that runs out inside the step is recorded in the array's
+ *     status word, which only mra_em_step_noalloc_status reads; the next call
+ *     of this entry point resets it, so query it after each step whose outputs
+ *     must be trusted. */
 MRA_API int mra_em_step_noalloc(const mra_dims* dims, const mra_em_params* prm, const float* y, const int32_t* shift,
                                 const double* x_in, const double* log_rho_in, double* x_out, double* log_rho_out,
                                 double* loglik_out, double* step_out, float* w_out, void* stream);
+
+/* Status of the last mra_em_step_noalloc on the current device (no counterpart
+ * in the paper): synchronizes the stream, returns the fixed scratch's device
+ * status word (MRA_OK, or MRA_ETIMEOUT when a bounded wait ran out and the
+ * step's outputs are incomplete) and clears it.  MRA_ECUDA if the scratch's
+ * address cannot be looked up. */
+MRA_API int mra_em_step_noalloc_status(void* stream);
 
 /* Synchronize the stream and return the workspace's device status word
  * (MRA_OK or MRA_ETIMEOUT), then clear it (failure detection; no counterpart in the paper). */

@@ -2238,6 +2238,15 @@ MRA_API int mra_em_step_noalloc(const mra_dims* d, const mra_em_params* p, const
                      kNoAllocScratchBytes, stream);
 }
 
+// The status word of the fixed scratch: the control block sits at its start, as in every
+// EM workspace, so the same read-and-clear as mra_ws_status applies.
+MRA_API int mra_em_step_noalloc_status(void* stream) {
+  void* scratch = nullptr;
+  const int st = noalloc_scratch(&scratch);
+  if (st != MRA_OK) return st;
+  return mra_ws_status(scratch, stream);
+}
+
 // Self-test of the bounded waits: one thread waits on an mbarrier that nothing arrives on,
 // with a limit of limit_ns, and records MRA_ETIMEOUT when the wait gives up.
 __global__ void k_selftest_wait(unsigned long long limit_ns, int* status) {

@@ -89,6 +89,7 @@ _SIGS = {
     "mra_fit_prior": (c_int, [c_int32, c_int32, c_int32, c_double, c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
     "mra_relerr": (c_int, [c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
     "mra_ws_status": (c_int, [c_void_p, c_void_p]),
+    "mra_em_step_noalloc_status": (c_int, [c_void_p]),
     "mra_selftest_wait_timeout": (c_int, [c_int32, c_void_p, c_void_p]),
 }
 
@@ -368,6 +369,10 @@ def mra_relerr(K, Q, x_hat, x, err_out, stream=None):
 
 def mra_ws_status(ws, stream=None) -> int:
     return int(load().mra_ws_status(_p(ws), _stream(stream)))
+
+
+def mra_em_step_noalloc_status(stream=None) -> int:
+    return int(load().mra_em_step_noalloc_status(_stream(stream)))
 
 
 def mra_selftest_wait_timeout(limit_us, status_out, stream=None):

@@ -50,7 +50,41 @@ def test_noalloc_step_matches_workspace_step_twice(gpu_lib):
         assert np.max(np.abs(host(got[4]) - host(ref[4]))) <= TOL_W, call
         assert abs(got[2].item() - ref[2].item()) <= 1e-9 * abs(ref[2].item())
         assert abs(got[3].item() - ref[3].item()) <= 1e-9 * abs(ref[3].item()) + 1e-15
+        assert mra.mra_em_step_noalloc_status() == 0, call
         x, lr = ref[0], ref[1]
+
+
+def _compare_once(mra, inst, Lw, L):
+    d = mra.dims(inst.N, inst.K, inst.Q, L, inst.sigma2)
+    prm = mra.em_params(Lw)
+    y = dev_y(inst.y)
+    sh = dev(inst.s.astype(np.int32))
+    x = dev(inst.x)
+    lr = torch.full((Lw,), -np.log(Lw), dtype=torch.float64, device="cuda")
+    ws = mra.workspace(mra.mra_em_workspace_bytes(d, Lw))  # a fresh workspace for the reference step
+    ref = _outputs(d, Lw, inst.N, inst.K, inst.Q)
+    got = _outputs(d, Lw, inst.N, inst.K, inst.Q)
+    mra.mra_em_step(d, prm, y, sh, x, lr, *ref, ws=ws)
+    mra.mra_em_step_noalloc(d, prm, y, sh, x, lr, *got)
+    assert mra.mra_em_step_noalloc_status() == 0  # synchronizes; MRA_OK: no wait ran out
+    assert rel_err(host(got[0]), host(ref[0])) <= TOL_X
+    np.testing.assert_allclose(np.exp(host(got[1])), np.exp(host(ref[1])), atol=TOL_W, rtol=0)
+    assert np.max(np.abs(host(got[4]) - host(ref[4]))) <= TOL_W
+    assert abs(got[2].item() - ref[2].item()) <= 1e-9 * abs(ref[2].item())
+
+
+def test_noalloc_larger_then_smaller_problem(gpu_lib):
+    """A problem whose scratch fills most of the array, then a smaller one of other K, Q, L and
+    window: the second call must not see the first call's partial sums, tables or norms."""
+    mra = gpu_lib
+    big = synth.make_instance(40, 32, 3000, 720, 1 / 50, 50.0, seed=5002)
+    d_big = mra.dims(big.N, big.K, big.Q, big.L, big.sigma2)
+    nb = mra.mra_em_workspace_bytes(d_big, 72)
+    assert (6 << 20) <= nb <= (8 << 20), nb
+    _compare_once(mra, big, 72, big.L)
+    c = synth.config(1)
+    small = synth.make_instance(c["K"], c["Q"], 700, c["L"], c["snr"], c["decay"], seed=5003)
+    _compare_once(mra, small, c["Lw"], small.L)
 
 
 def test_noalloc_rejects_problems_beyond_its_scratch(gpu_lib):
