@@ -1076,6 +1076,47 @@ bool plan_v2(int Kp1, int Q, int L, int Lw, int nup, int max_smem, V2Plan* p) {
   return false;
 }
 
+// Shared-memory plan of the lean warp sweep (grid windows of at most 32 mirror units that
+// are not the whole circle): the warp sweep's ring and tables plus the swapped copy of x, and
+// one per-warp buffer serving c_k (pass 1) and the window's values (images off the fast path).
+bool plan_v5(int Kp1, int Q, int L, int Lw, int nu, int nup, bool dense, int max_smem, V2Plan* p, int* cbp_out,
+             int* off_xs_out) {
+  if (dense || Lw >= L || nu > 32 || Q % 8 != 0 || Q / 8 > 4) return false;
+  const int QV = Q / 8, MR = (Kp1 + 7) / 8;
+  if (MR > 7) return false;
+  const SweepV2Launch ln = QV == 1 ? sweep_v5_q1(MR, nup) : QV == 2 ? sweep_v5_q2(MR, nup)
+                         : QV == 3 ? sweep_v5_q3(MR, nup) : sweep_v5_q4(MR, nup);
+  if (!ln.fn) return false;
+  const int M = Kp1 * Q;
+  const int slot = al16(M * 8);
+  const int sp = (Lw + 3) & ~3;
+  const int cbp = std::max(8 * MR, (sp + 1) / 2 + 1) & ~1;  // float2: rows up to 8 MR, or Lw floats
+  const int maxw = ln.threads / 32;
+  for (int nw = maxw; nw * 2 >= maxw && nw >= 1; --nw) {
+    int o = al16(2 * maxw * 8);
+    p->off_ring = o; o += 2 * nw * slot;
+    p->off_x = o; o += al16(M * 8);
+    const int off_xs = o; o += al16(M * 8);
+    p->off_tu = o; o += al16(8 * MR * nup * 8);  // rows padded to 8 MR
+    p->off_tf = o; o += al16(L * 8);
+    p->off_lr = o; o += al16(Lw * 4);
+    p->off_units = o; o += al16(nup * 8);
+    p->off_s = o; o += al16(maxw * cbp * 8);
+    p->off_wl = o; o += al16(maxw * sp * 4);
+    if (o + 1024 <= max_smem) {
+      p->launch = ln;
+      p->nwarps = nw;
+      p->slot_bytes = slot;
+      p->sp = sp;
+      p->smem = o;
+      *cbp_out = cbp;
+      *off_xs_out = off_xs;
+      return true;
+    }
+  }
+  return false;
+}
+
 struct V3Plan {
   SweepV3Fn fn;
   int bi, ns, slot_bytes, cp, sp, dp, nd, wrap, r0, d1, phase0, fsplit, smem;
@@ -1228,7 +1269,7 @@ struct SweepSel {
   int kind, bi, ns;
 };
 
-// MRA_SWEEP=warp|cta, MRA_SWEEP_BI=16|12|8|4 and MRA_SWEEP_NS=2|3 fix the sweep (for
+// MRA_SWEEP=warp|cta|chunk|lean, MRA_SWEEP_BI=16|12|8|4 and MRA_SWEEP_NS=2|3 fix the sweep (for
 // comparisons and tuning runs); they take precedence over the autotuner's cache.
 // MRA_SWEEP_TDG=1 makes the batch sweep read its distance-unit table from global memory
 // even where the table fits in shared memory (to test that variant on small windows).
@@ -1238,6 +1279,7 @@ SweepSel env_sweep() {
   if (k && strcmp(k, "warp") == 0) e.kind = 1;
   if (k && strcmp(k, "cta") == 0) e.kind = 2;
   if (k && strcmp(k, "chunk") == 0) e.kind = 3;
+  if (k && strcmp(k, "lean") == 0) e.kind = 4;
   const char* b = getenv("MRA_SWEEP_BI");
   const char* n = getenv("MRA_SWEEP_NS");
   e.bi = b ? atoi(b) : 0;
@@ -1323,6 +1365,8 @@ struct EmCall {
   int reduce_blocks;
   int update_smem;
   bool v2;  // warp-per-image sweep (rows of Q a multiple of 8) instead of the tile sweep
+  bool v5;  // with v2: the lean warp sweep's kernel and plan
+  int v5_cbp, v5_off_xs;
   V2Plan v2p;
   SweepV2Args sa2;
   bool v3;  // CTA-cooperative sweep over image batches
@@ -1369,6 +1413,7 @@ int prepare(const mra_dims* d, int Lw, int l0, double step, const float* y, cons
     if (tune_lookup(tune_key(d, Lw, l0, step, yfmt), &tuned)) sel = tuned;
   }
   c->v4 = false;
+  c->v5 = false;
   if (yfmt) {  // the batch sweep reads the split format, and the chunked sweep when chosen
     c->v2 = false;
     if (sel.kind == 3) {
@@ -1385,6 +1430,7 @@ int prepare(const mra_dims* d, int Lw, int l0, double step, const float* y, cons
     // faster one there; wider windows (up to the whole circle) go to the batch sweep, unless
     // its distance-unit table would have to stay in global memory (the 721-rotation dense
     // window at |k| <= 32: 4.04 ms per sweep against 3.20 ms for the warp sweep).
+    c->v5 = false;
     c->v2 = sel.kind != 2 && plan_v2(Kp1, d->Q, d->L, Lw, nup, di.max_smem_optin, &c->v2p);
     c->v3 = allow_v3 && sel.kind != 1 && (!c->v2 || sel.kind == 2 || nup > kUnitChunk) &&
             plan_v3(Kp1, d->Q, d->L, Lw, l0, dense, 0, sel.bi, sel.ns, di.max_smem_optin, &c->v3p, env_tdg());
@@ -1399,7 +1445,20 @@ int prepare(const mra_dims* d, int Lw, int l0, double step, const float* y, cons
         c->lay.G = c->v4p.grid;
       }
     }
-    if (force && ((force->kind == 1 && !c->v2) || (force->kind == 2 && !c->v3) || (force->kind == 3 && !c->v4)))
+    // The lean warp sweep (EM calls only; align mode stays in the warp sweep) where it plans, when
+    // chosen or by default in place of the warp sweep.
+    c->v5 = false;
+    if (allow_v3 && (sel.kind == 4 || (sel.kind == 0 && !c->v3 && !c->v4))) {
+      V2Plan p5;
+      if (plan_v5(Kp1, d->Q, d->L, Lw, nu, nup, dense, di.max_smem_optin, &p5, &c->v5_cbp, &c->v5_off_xs)) {
+        c->v2p = p5;
+        c->v2 = c->v5 = true;
+        c->v3 = c->v4 = false;
+        c->lay.G = G;
+      }
+    }
+    if (force && ((force->kind == 1 && !c->v2) || (force->kind == 2 && !c->v3) || (force->kind == 3 && !c->v4) ||
+                  (force->kind == 4 && !c->v5)))
       return MRA_EINVAL;
   }
   if (c->v4) {
@@ -1456,6 +1515,8 @@ int prepare(const mra_dims* d, int Lw, int l0, double step, const float* y, cons
   v.nwarps = c->v2p.nwarps; v.slot_bytes = c->v2p.slot_bytes; v.sp = c->v2p.sp;
   v.off_ring = c->v2p.off_ring; v.off_x = c->v2p.off_x; v.off_tu = c->v2p.off_tu; v.off_tf = c->v2p.off_tf;
   v.off_lr = c->v2p.off_lr; v.off_units = c->v2p.off_units; v.off_s = c->v2p.off_s; v.off_wl = c->v2p.off_wl;
+  v.off_xs = c->v5 ? c->v5_off_xs : 0;
+  v.cbp = c->v5 ? c->v5_cbp : 0;
   v.two_beta = s.two_beta;
   v.align_only = 0;
   v.wrap = !dense && Lw == d->L ? 1 : 0;
@@ -1846,7 +1907,7 @@ namespace {
 constexpr int kBatchedImagesPerCta = 64;
 
 // Sweep candidates the autotuner times, in the order of the default preference.
-const SweepSel kTuneCandidates[] = {{1, 0, 0},  {2, 16, 2}, {2, 12, 2}, {2, 8, 3},  {2, 8, 2}, {2, 4, 3},
+const SweepSel kTuneCandidates[] = {{4, 0, 0},  {1, 0, 0},  {2, 16, 2}, {2, 12, 2}, {2, 8, 3},  {2, 8, 2}, {2, 4, 3},
                                     {2, 4, 2},  {3, 64, 2}, {3, 32, 2}, {3, 16, 2}, {3, 128, 1},
                                     {3, 64, 1}, {3, 32, 1}};
 
