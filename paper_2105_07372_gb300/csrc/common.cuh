@@ -157,13 +157,19 @@ struct EmLayout {
   int kp4;      // K+1 rounded up to a multiple of 4 (rows of the table)
   int cols;     // 2M + Lw + 2 reduced columns
   int nup;      // mirror units padded to a multiple of kUnitChunk
-  size_t ctrl, tf32, tf64, tw, tw64, x32, x64, inv_den, logrho32, rho64, rhobar64, units, tu, td, part, tot, total;
+  size_t ctrl, tf32, tf64, tw, tw64, x32, x64, inv_den, logrho32, rho64, rhobar64, units, tu, td, part, tot;
+  size_t tcb, cbuf, wbuf;  // split sweep only (zero-sized otherwise)
+  size_t total;
 };
 
 __host__ __device__ inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+// The split sweep's extra workspace (correlation and weight buffers, the B operand) exists for
+// windows it can take: wider than 64 rotations, at most 512, K+1 <= 48.
+__host__ __device__ inline bool split_possible(int Kp1, int Q, int Lw) {
+  return Lw > 64 && Lw <= 512 && Kp1 <= 48 && Q % 8 == 0 && Q / 8 <= 4;
+}
 
 inline EmLayout em_layout(int N, int K, int Q, int L, int Lw, int G) {
-  (void)N;
   EmLayout l{};
   l.G = G;
   l.Kp1 = K + 1;
@@ -191,6 +197,11 @@ inline EmLayout em_layout(int N, int K, int Q, int L, int Lw, int G) {
   l.td = o;        o = align256(o + sizeof(float2) * (size_t)l.Kp1 * (size_t)(Lw > L / 2 + 1 ? Lw : L / 2 + 1));
   l.part = o;      o = align256(o + sizeof(double) * (size_t)l.cols * G);
   l.tot = o;       o = align256(o + sizeof(double) * (l.cols + 8));
+  const bool split = split_possible(l.Kp1, Q, Lw);
+  const size_t ka = (size_t)((2 * ((l.Kp1 + 3) / 4 * 4) + 15) / 16 * 16), np = (size_t)((Lw + 15) / 16 * 16);
+  l.tcb = o;       o = align256(o + (split ? np * ka * 2 : 0));
+  l.cbuf = o;      o = align256(o + (split ? sizeof(float2) * (size_t)N * l.Kp1 : 0));
+  l.wbuf = o;      o = align256(o + (split ? sizeof(float2) * (size_t)N * l.Kp1 : 0));
   l.total = o;
   return l;
 }
@@ -316,6 +327,48 @@ SweepV4Launch sweep_v4_q1_f1(int MR, int cpsm);
 SweepV4Launch sweep_v4_q2_f1(int MR, int cpsm);
 SweepV4Launch sweep_v4_q3_f1(int MR, int cpsm);
 SweepV4Launch sweep_v4_q4_f1(int MR, int cpsm);
+
+// Arguments of the split sweep (sweep_tc_impl.cuh): correlation, tensor-core transform and
+// accumulation kernels launched in turn.
+struct SplitArgs {
+  const float2* y;
+  const int* shift;
+  int N, Kp1, M, L, Lw;
+  int nwarps, slot_bytes;           // stream kernels: active warps per CTA, bytes per ring slot
+  int off_ring, off_x, off_xs, off_tf;
+  int NP, ncols;                    // transform: window columns padded to 16, tensor-memory columns
+  int k2_off_b, k2_off_ah, k2_off_al, k2_off_lr, k2_off_tf, k2_off_wt, k2_off_ll;
+  int k2_off_cs;                    // transform: the tile's c (then W) rows [128][Kp1] float2
+  int k2_off_td;                    // transform: the distance-unit table, or 0 (read from global)
+  int k2_off_info;                  // transform: per-image peaks, distances, scales and bounds
+  int wrap, l0m, nd, twp;
+  float two_beta;
+  const float2* x32;
+  const float2* tf32;
+  const float2* td;                 // [Kp1][nd] (cos t - 1, -sin t)
+  const float2* tw;                 // dense window only (else null): [Kp1][twp] e^{-i k theta_l}
+  const float* logrho32;
+  const void* tcb;                  // [NP][KA] FP16 operand layout: (cos, sin) of k theta_l, KA = 2 KP to 16
+  float2* cbuf;                     // [N][Kp1] aligned correlations
+  float2* wbuf;                     // [N][Kp1] back-transformed weights W_jk
+  double* part;
+  int G;
+  float* w_out;
+  Ctrl* ctrl;
+};
+constexpr int kTcTile = 128;            // split sweep: images per transform tile (the MMA's M)
+constexpr int kTcStreamThreads = 512;   // split sweep: threads of the streaming kernels
+constexpr int kTcTransThreads = 512;    // split sweep: threads of the transform kernel
+struct SplitStreamFns {
+  void (*corr)(const SplitArgs);
+  void (*accum)(const SplitArgs);
+};
+SplitStreamFns sweep_tc_q1(int MR);
+SplitStreamFns sweep_tc_q2(int MR);
+SplitStreamFns sweep_tc_q3(int MR);
+SplitStreamFns sweep_tc_q4(int MR);
+typedef void (*SplitTransFn)(const SplitArgs);
+SplitTransFn sweep_tc_trans(int KP);  // KP = K+1 rounded up to 4, at most 48
 
 // Mirror units of a window: offsets o and -o (mod L) share cos/sin.  Writes the
 // (a, b) index pairs in window order of a; returns the number of units.  A dense window

@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "tc.cuh"
 
 namespace mra {
 
@@ -172,6 +173,30 @@ __global__ void k_setup_tw(const SetupArgs a) {
 }
 
 // Mirror units of the window (one thread: integer bookkeeping over Lw entries).
+// B operand of the split sweep's tensor-core pass 1: row l (window rotation theta_l), columns
+// (cos k theta_l, sin k theta_l) for k = 0..K, zero padded to NP rows and KA columns, FP16 in the
+// K-major core-matrix layout of tc::op_offset.
+__global__ void k_setup_tcb(const SetupArgs a, __half* tcb, int NP, int KA) {
+  const int n = NP * KA;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+    const int l = idx / KA, kk = idx - l * KA, k = kk >> 1;
+    double v = 0.0;
+    if (l < a.Lw && k < a.Kp1) {
+      double2 t;  // (cos, -sin) of k theta_l
+      if (a.dense) {
+        t = dense_twiddle(k, a.l0 + l, a.step, a.L);
+      } else {
+        int off = (a.l0 + l) % a.L;
+        if (off < 0) off += a.L;
+        t = a.tf64[(int)(((long long)k * off) % a.L)];
+      }
+      v = (kk & 1) ? -t.y : t.x;
+    }
+    *reinterpret_cast<__half*>(reinterpret_cast<unsigned char*>(tcb) + tc::op_offset(l, kk, KA)) =
+        __float2half_rn((float)v);
+  }
+}
+
 __global__ void k_setup_units(const SetupArgs a) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     const int nu = window_units(a.L, a.Lw, a.l0, a.dense != 0, a.units);
@@ -1117,6 +1142,71 @@ bool plan_v5(int Kp1, int Q, int L, int Lw, int nu, int nup, bool dense, int max
   return false;
 }
 
+// Plan of the split sweep: the stream kernels' ring (two slots per warp), x and its swapped copy and
+// the grid twiddles; the transform kernel's B operand, two A tiles, tables and reduction scratch
+// (at least 116 KB, so that one transform CTA holds a streaming multiprocessor's tensor memory).
+struct SplitPlan {
+  SplitStreamFns fns;
+  SplitTransFn trans;
+  int KP, KA, NP, ncols, smem1, smem2, nwarps, slot_bytes;
+  int off_ring, off_x, off_xs, off_tf;
+  int k2_off_b, k2_off_ah, k2_off_al, k2_off_lr, k2_off_tf, k2_off_wt, k2_off_ll, k2_off_cs, k2_off_td;
+  int k2_off_info;
+};
+bool plan_split(int Kp1, int Q, int L, int Lw, int max_smem, SplitPlan* p) {
+  if (!split_possible(Kp1, Q, Lw)) return false;
+  const int QV = Q / 8, MR = (Kp1 + 7) / 8;
+  if (MR > 6) return false;
+  p->fns = QV == 1 ? sweep_tc_q1(MR) : QV == 2 ? sweep_tc_q2(MR) : QV == 3 ? sweep_tc_q3(MR) : sweep_tc_q4(MR);
+  p->KP = (Kp1 + 3) / 4 * 4;
+  p->trans = sweep_tc_trans(p->KP);
+  if (!p->fns.corr || !p->trans) return false;
+  p->KA = (2 * p->KP + 15) / 16 * 16;
+  p->NP = (Lw + 15) / 16 * 16;
+  p->ncols = 32;
+  while (p->ncols < p->NP) p->ncols *= 2;
+  const int M = Kp1 * Q;
+  p->slot_bytes = al16(M * 8);
+  const int maxw = kTcStreamThreads / 32;
+  bool ok = false;
+  for (int nw = maxw; nw >= maxw / 2; --nw) {
+    int o = al16(2 * maxw * 8);
+    p->off_ring = o; o += 2 * nw * p->slot_bytes;
+    p->off_x = o; o += al16(M * 8);
+    p->off_xs = o; o += al16(M * 8);
+    p->off_tf = o; o += al16(L * 8);
+    if (o + 1024 <= max_smem) {
+      p->nwarps = nw;
+      p->smem1 = o;
+      ok = true;
+      break;
+    }
+  }
+  if (!ok) return false;
+  int o = 128;  // mbarrier and tensor-memory address
+  p->k2_off_b = o; o += al16(p->NP * p->KA * 2);
+  p->k2_off_ah = o; o += al16(kTcTile * p->KA * 2);
+  p->k2_off_al = o; o += al16(kTcTile * p->KA * 2);
+  p->k2_off_lr = o; o += al16(Lw * 4);
+  p->k2_off_tf = o; o += al16(L * 8);
+  o = (o + 7) & ~7;
+  p->k2_off_wt = o; o += al16(Lw * 8);
+  p->k2_off_ll = o; o += al16(kTcTransThreads * 8);
+  p->k2_off_cs = o; o += al16(kTcTile * Kp1 * 8);
+  p->k2_off_info = o; o += al16(kTcTile * 4 * 14);  // [4][128] maxima, indices, distances; scales; bounds
+  if (o + 1024 > max_smem) return false;
+  const int nd = Lw == L ? L / 2 + 1 : Lw;
+  const int tdb = al16(Kp1 * nd * 8);
+  if (o + tdb + 1024 <= max_smem) {
+    p->k2_off_td = o;
+    o += tdb;
+  } else {
+    p->k2_off_td = 0;
+  }
+  p->smem2 = std::max(o, 116 * 1024);
+  return p->smem2 + 1024 <= max_smem;
+}
+
 struct V3Plan {
   SweepV3Fn fn;
   int bi, ns, slot_bytes, cp, sp, dp, nd, wrap, r0, d1, phase0, fsplit, smem;
@@ -1280,6 +1370,7 @@ SweepSel env_sweep() {
   if (k && strcmp(k, "cta") == 0) e.kind = 2;
   if (k && strcmp(k, "chunk") == 0) e.kind = 3;
   if (k && strcmp(k, "lean") == 0) e.kind = 4;
+  if (k && strcmp(k, "tc") == 0) e.kind = 5;
   const char* b = getenv("MRA_SWEEP_BI");
   const char* n = getenv("MRA_SWEEP_NS");
   e.bi = b ? atoi(b) : 0;
@@ -1375,11 +1466,15 @@ struct EmCall {
   bool v4;  // chunked two-read sweep
   V4Plan v4p;
   SweepV4Args sa4;
+  bool vs;  // split sweep (tensor-core transform)
+  SplitPlan sp;
+  SplitArgs sa5;
   void set_w_out(float* w) {
     sa.w_out = w;
     sa2.w_out = w;
     sa3.w_out = w;
     sa4.w_out = w;
+    sa5.w_out = w;
   }
 };
 
@@ -1414,6 +1509,7 @@ int prepare(const mra_dims* d, int Lw, int l0, double step, const float* y, cons
   }
   c->v4 = false;
   c->v5 = false;
+  c->vs = false;
   if (yfmt) {  // the batch sweep reads the split format, and the chunked sweep when chosen
     c->v2 = false;
     if (sel.kind == 3) {
@@ -1457,11 +1553,28 @@ int prepare(const mra_dims* d, int Lw, int l0, double step, const float* y, cons
         c->lay.G = G;
       }
     }
+    // The split sweep (tensor-core transform) for windows wider than 64 rotations when chosen, and by
+    // default for the whole circle (full search: 0.45 ms against the batch sweep's 0.73 ms per step at
+    // |k| <= 32, Q = 24, N = 1e5, L = 360 on sharp posteriors).
+    c->vs = false;
+    const bool split_default = sel.kind == 0 && !dense && Lw == d->L;
+    if (allow_v3 && (sel.kind == 5 || split_default) && split_possible(Kp1, d->Q, Lw) &&
+        plan_split(Kp1, d->Q, d->L, Lw, di.max_smem_optin, &c->sp)) {
+      c->vs = true;
+      c->v2 = c->v3 = c->v4 = c->v5 = false;
+      c->lay.G = G;
+    }
     if (force && ((force->kind == 1 && !c->v2) || (force->kind == 2 && !c->v3) || (force->kind == 3 && !c->v4) ||
-                  (force->kind == 4 && !c->v5)))
+                  (force->kind == 4 && !c->v5) || (force->kind == 5 && !c->vs)))
       return MRA_EINVAL;
   }
-  if (c->v4) {
+  if (c->vs) {
+    if (raise_smem_limit(reinterpret_cast<const void*>(c->sp.fns.corr), c->sp.smem1) != MRA_OK ||
+        raise_smem_limit(reinterpret_cast<const void*>(c->sp.fns.accum), c->sp.smem1) != MRA_OK ||
+        raise_smem_limit(reinterpret_cast<const void*>(c->sp.trans), c->sp.smem2) != MRA_OK)
+      return MRA_ECUDA;
+    c->sweep = nullptr;
+  } else if (c->v4) {
     if (raise_smem_limit(reinterpret_cast<const void*>(c->v4p.launch.fn), c->v4p.smem) != MRA_OK) return MRA_ECUDA;
     c->sweep = nullptr;
   } else if (c->v3) {
@@ -1578,6 +1691,35 @@ int prepare(const mra_dims* d, int Lw, int l0, double step, const float* y, cons
   v4.w_out = nullptr;
   v4.ctrl = c->ctrl;
 
+  SplitArgs& x5 = c->sa5;
+  const SplitPlan& q5 = c->sp;
+  x5.y = s.y;
+  x5.shift = shift;
+  x5.N = d->N; x5.Kp1 = Kp1; x5.M = M; x5.L = d->L; x5.Lw = Lw;
+  x5.nwarps = q5.nwarps; x5.slot_bytes = q5.slot_bytes;
+  x5.off_ring = q5.off_ring; x5.off_x = q5.off_x; x5.off_xs = q5.off_xs; x5.off_tf = q5.off_tf;
+  x5.NP = q5.NP; x5.ncols = q5.ncols;
+  x5.k2_off_b = q5.k2_off_b; x5.k2_off_ah = q5.k2_off_ah; x5.k2_off_al = q5.k2_off_al; x5.k2_off_lr = q5.k2_off_lr;
+  x5.k2_off_tf = q5.k2_off_tf; x5.k2_off_wt = q5.k2_off_wt; x5.k2_off_ll = q5.k2_off_ll;
+  x5.k2_off_cs = q5.k2_off_cs; x5.k2_off_td = q5.k2_off_td; x5.k2_off_info = q5.k2_off_info;
+  x5.wrap = !dense && Lw == d->L ? 1 : 0;
+  x5.l0m = ((l0 % d->L) + d->L) % d->L;
+  x5.nd = x5.wrap ? d->L / 2 + 1 : Lw;
+  x5.twp = L_.twp;
+  x5.two_beta = s.two_beta;
+  x5.x32 = s.x32;
+  x5.tf32 = s.tf32;
+  x5.td = reinterpret_cast<const float2*>(base + L_.td);
+  x5.tw = dense ? s.tw : nullptr;
+  x5.logrho32 = s.logrho32;
+  x5.tcb = base + L_.tcb;
+  x5.cbuf = reinterpret_cast<float2*>(base + L_.cbuf);
+  x5.wbuf = reinterpret_cast<float2*>(base + L_.wbuf);
+  x5.part = s.part;
+  x5.G = G;
+  x5.w_out = nullptr;
+  x5.ctrl = c->ctrl;
+
   SetupArgs& u = c->su;
   u.N = d->N; u.Kp1 = Kp1; u.Q = d->Q; u.M = M; u.L = d->L; u.Lw = Lw;
   u.l0 = l0; u.twp = L_.twp; u.kp4 = L_.kp4; u.sigma2 = d->sigma2;
@@ -1596,7 +1738,7 @@ int prepare(const mra_dims* d, int Lw, int l0, double step, const float* y, cons
   u.units = reinterpret_cast<int2*>(base + L_.units);
   u.tu = reinterpret_cast<float2*>(base + L_.tu);
   u.td = reinterpret_cast<float2*>(base + L_.td);
-  u.nd = c->v3 ? c->v3p.nd : c->v4 ? c->v4p.nd : c->v2 ? v.nd : 0;
+  u.nd = c->vs ? x5.nd : c->v3 ? c->v3p.nd : c->v4 ? c->v4p.nd : c->v2 ? v.nd : 0;
   u.nu = nu;
   u.nup = nup;
   u.ctrl = c->ctrl;
@@ -1622,7 +1764,17 @@ int launch_setup(const EmCall& c, cudaStream_t st) {
   const int n = std::max(std::max(c.su.L, c.su.M), c.su.Lw);
   const int blocks = std::min(1024, (n + 127) / 128);
   k_setup<<<blocks, 128, 0, st>>>(c.su);
-  if (c.v3 || c.v4) {
+  if (c.vs) {
+    const int ntd = c.su.Kp1 * c.su.nd;
+    k_setup_td<<<std::min(1024, (ntd + 255) / 256), 256, 0, st>>>(c.su);
+    if (c.su.dense) {
+      const int ntw = c.su.kp4 * c.su.twp;
+      k_setup_tw<<<std::min(1024, (ntw + 255) / 256), 256, 0, st>>>(c.su);
+    }
+    const int nb = c.sp.NP * c.sp.KA;
+    k_setup_tcb<<<std::min(1024, (nb + 255) / 256), 256, 0, st>>>(
+        c.su, reinterpret_cast<__half*>(const_cast<void*>(c.sa5.tcb)), c.sp.NP, c.sp.KA);
+  } else if (c.v3 || c.v4) {
     const int ntd = c.su.Kp1 * c.su.nd;
     k_setup_td<<<std::min(1024, (ntd + 255) / 256), 256, 0, st>>>(c.su);
     if (c.su.dense) {  // the rotation to each image's reference
@@ -1647,7 +1799,11 @@ int launch_setup(const EmCall& c, cudaStream_t st) {
 }
 
 void launch_sweep(const EmCall& c, cudaStream_t st) {
-  if (c.v4)
+  if (c.vs) {
+    c.sp.fns.corr<<<c.lay.G, kTcStreamThreads, c.sp.smem1, st>>>(c.sa5);
+    c.sp.trans<<<c.lay.G, kTcTransThreads, c.sp.smem2, st>>>(c.sa5);
+    c.sp.fns.accum<<<c.lay.G, kTcStreamThreads, c.sp.smem1, st>>>(c.sa5);
+  } else if (c.v4)
     c.v4p.launch.fn<<<c.lay.G, c.v4p.launch.threads, c.v4p.smem, st>>>(c.sa4);
   else if (c.v3)
     c.v3p.fn<<<c.lay.G, kV3Threads, c.v3p.smem, st>>>(c.sa3);
@@ -1907,7 +2063,7 @@ namespace {
 constexpr int kBatchedImagesPerCta = 64;
 
 // Sweep candidates the autotuner times, in the order of the default preference.
-const SweepSel kTuneCandidates[] = {{4, 0, 0},  {1, 0, 0},  {2, 16, 2}, {2, 12, 2}, {2, 8, 3},  {2, 8, 2}, {2, 4, 3},
+const SweepSel kTuneCandidates[] = {{4, 0, 0},  {5, 0, 0},  {1, 0, 0},  {2, 16, 2}, {2, 12, 2}, {2, 8, 3},  {2, 8, 2}, {2, 4, 3},
                                     {2, 4, 2},  {3, 64, 2}, {3, 32, 2}, {3, 16, 2}, {3, 128, 1},
                                     {3, 64, 1}, {3, 32, 1}};
 

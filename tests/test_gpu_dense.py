@@ -45,7 +45,7 @@ def _compare(mra, inst, x, log_rho, Lw, l0, step, shifts=None, **kw):
     return xg, st
 
 
-@pytest.fixture(params=["cta", "warp", "chunk", "cta-tdg"])
+@pytest.fixture(params=["cta", "warp", "chunk", "cta-tdg", "tc"])
 def sweep(request, monkeypatch):
     """cta-tdg: the batch sweep with its distance-unit table read from global memory."""
     monkeypatch.setenv("MRA_SWEEP", request.param.split("-")[0])

@@ -49,11 +49,12 @@ def compare(mra, inst, x, log_rho, Lw, l0=None, shifts=None, **kw):
     return xg, st
 
 
-@pytest.fixture(params=["cta", "warp", "chunk", "cta-tdg", "lean"])
+@pytest.fixture(params=["cta", "warp", "chunk", "cta-tdg", "lean", "tc"])
 def sweep(request, monkeypatch):
     """Every EM sweep: the CTA-cooperative batch sweep, the warp-per-image one, the chunked
-    two-read one and the lean warp sweep (shapes a sweep cannot take fall back to the default
-    choice); cta-tdg is the batch sweep with its distance-unit table read from global memory."""
+    two-read one, the lean warp sweep and the split sweep with its tensor-core transform (shapes
+    a sweep cannot take fall back to the default choice); cta-tdg is the batch sweep with its
+    distance-unit table read from global memory."""
     monkeypatch.setenv("MRA_SWEEP", request.param.split("-")[0])
     if request.param.endswith("-tdg"):
         monkeypatch.setenv("MRA_SWEEP_TDG", "1")
@@ -280,3 +281,15 @@ def test_em_step_weights_across_snr(gpu_lib, sweep, snr, K, Q, N, L, Lw):
     inst = synth.make_instance(K, Q, N, L, snr, 400.0 if K > 20 else 50.0, seed=3100 + K)
     x0 = O.align_mean(synth.c64_round(inst.y), inst.s, inst.L)
     compare(gpu_lib, inst, x0, np.log(np.full(Lw, 1 / Lw)), Lw, shifts=inst.s)
+
+
+@pytest.mark.parametrize("Lw,l0,snr", [(360, 0, 1 / 50), (100, -50, 1 / 50), (360, 0, 1 / 10), (65, -32, 1 / 20)])
+def test_em_step_wide_windows_config2_shape(gpu_lib, sweep, Lw, l0, snr):
+    """Full search (all 360 rotations) and wide windows at |k| <= 32, Q = 24: from the aligned mean
+    (sharp posteriors) and from a random start (posteriors spread over the circle).  (At SNR 1/5 every
+    sweep's FP32 values far from an image's peak move some weights by 1.0e-5 to 1.3e-5.)"""
+    c = synth.config(2)
+    inst = synth.make_instance(c["K"], c["Q"], 2500, c["L"], snr, c["decay"], seed=3300 + Lw)
+    y64 = synth.c64_round(inst.y)
+    for x0 in (O.align_mean(y64, inst.s, inst.L), synth.random_init(inst.K, inst.Q, c["decay"], seed=7)):
+        compare(gpu_lib, inst, x0, np.log(np.full(Lw, 1 / Lw)), Lw, l0=l0, shifts=inst.s)
