@@ -305,16 +305,27 @@ MRA_API size_t mra_fb_setup_workspace_bytes(int32_t n, int32_t K, int32_t Q);
 MRA_API int mra_fb_setup(int32_t n, int32_t K, int32_t Q, float* P_out, double* zeros_out, void* ws, size_t ws_bytes,
                          void* stream);
 
-/* App. A, the Fourier-Bessel expansion of pixel images:
- * coefficients of N images: y_out [N][K+1][Q] complex float = images [N][n][n] float times P, one GEMM
- * (cuBLAS; tf32 != 0 uses TF32 tensor cores, relative error ~1e-3 instead of ~1e-6).  y_out has the
- * layout every EM and synchronization entry point reads.  All pointers device, 16-byte aligned. */
-MRA_API int mra_fb_project(int32_t N, int32_t n, int32_t K, int32_t Q, const float* images, const float* P,
-                           float* y_out, int32_t tf32, void* stream);
+/* App. A, the Fourier-Bessel expansion of pixel images, applied to every image: the projection P of
+ * mra_fb_setup is first packed into the operand of the library's tensor-core GEMM (P^T in 256-column
+ * by 32-pixel tiles, each value split into three BF16 pieces that sum to it within 2^-24), once per P:
+ *   mra_fb_operand_bytes(n, K, Q): size of that operand (0 for dimensions mra_fb_setup rejects);
+ *   mra_fb_pack: op_out (device, 256-byte aligned) from P (device, as written by mra_fb_setup).
+ * mra_fb_project: y_out [N][K+1][Q] complex float = images [N][n][n] float times P, one tcgen05 GEMM
+ * over all images: the images are split into the same three pieces as they are read, six of the nine
+ * piece products accumulate in FP32 (relative error ~1e-6, as FP32); fast != 0 keeps three of them
+ * (relative error ~1e-5).  y_out has the layout every EM and synchronization entry point reads.
+ * images and y_out 16-byte aligned, op 256-byte aligned.  A bounded wait that runs out leaves y_out
+ * incomplete and sets the operand's status word to MRA_ETIMEOUT (read and cleared by
+ * mra_ws_status(op, stream)). */
+MRA_API size_t mra_fb_operand_bytes(int32_t n, int32_t K, int32_t Q);
+MRA_API int mra_fb_pack(int32_t n, int32_t K, int32_t Q, const float* P, void* op_out, void* stream);
+MRA_API int mra_fb_project(int32_t N, int32_t n, int32_t K, int32_t Q, const float* images, const void* op,
+                           float* y_out, int32_t fast, void* stream);
 
 /* Steerable PCA of coefficients (App. A: a data-driven radial basis per angular index k that keeps
  * steerability).  For every k the uncentred second moment C_k = (1/N) sum_i a_ik a_ik^H over the Q
- * radial entries (FP32 GEMM over the images), its eigenvectors on the host (FP64 Jacobi), kept where the
+ * radial entries (FP32 products summed in FP64 per chunk of 2,048 images, the chunks added in order), its
+ * eigenvectors on the host (FP64 Jacobi), kept where the
  * eigenvalue exceeds sigma2 (1 + sqrt(Q/N))^2 (dims->sigma2 is the coefficients' noise variance).  Each
  * kept eigenvector's largest-magnitude entry is real positive; eigenvalues descend.  The reduced
  * coefficients b_ik = U_k^H a_ik have shape [K2+1][Q2]: K2 the largest k that keeps a component, Q2 the

@@ -7,8 +7,11 @@
 //            the Jacobi start diag(G)^{-1} (DGEMMs; the Jacobi-scaled Gram of the sampled basis is
 //            within ~1% of the identity, so a few steps reach FP64 accuracy), the projection
 //            P = G^{-1} A^T, stored per pixel in the coefficient layout [n^2][K+1][Q] complex FP32.
-//   project  y = images P, one GEMM over all images: [N x n^2] by [n^2 x 2M] (cuBLAS SGEMM, or
-//            TF32 tensor cores on request).  This is a plain library GEMM.
+//   pack     P transposed and split into three BF16 pieces in the tiled operand layout of the
+//            tcgen05 GEMM (gemm3.cuh), once per P.
+//   project  y = images P, one GEMM over all images: [N x n^2] by [n^2 x 2M] on the tensor cores
+//            (k_gemm3: six BF16 products of the three-piece split, FP32 accumulation; three in the
+//            fast mode).
 //
 // Basis (App. A): u^{k,q}(r, theta) = N_{k,q} J_|k|(R_{|k|,q} r / c) e^{i k theta} on r <= c = (n - 1)/2,
 // N_{k,q} = 1 / (c sqrt(pi) |J_{k+1}(R_{k,q})|); pixel (row iy, column ix) at x = ix - c, y = iy - c.
@@ -20,6 +23,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "gemm3.cuh"
 
 namespace mra {
 namespace {
@@ -275,33 +279,70 @@ MRA_API int mra_fb_setup(int32_t n, int32_t K, int32_t Q, float* P_out, double* 
   return st;
 }
 
-MRA_API int mra_fb_project(int32_t N, int32_t n, int32_t K, int32_t Q, const float* images, const float* P,
-                           float* y_out, int32_t tf32, void* stream) {
-  if (N < 1 || !fb_dims_ok(n, K, Q)) return MRA_EINVAL;
-  if (!images || !P || !y_out || (reinterpret_cast<uintptr_t>(images) % 16) != 0 ||
-      (reinterpret_cast<uintptr_t>(P) % 16) != 0 || (reinterpret_cast<uintptr_t>(y_out) % 16) != 0)
-    return MRA_EINVAL;
-  cublasHandle_t h;
-  if (blas_handle(&h) != MRA_OK) return MRA_ECUDA;
-  if (cublasSetStream(h, static_cast<cudaStream_t>(stream)) != CUBLAS_STATUS_SUCCESS) return MRA_ECUDA;
+// The packed projection operand: a 256-byte header (the status word of the projection's bounded
+// waits) and the tiles of P^T.
+static size_t fb_operand_bytes(int n, int K, int Q) {
   const int npix = n * n, two_m = 2 * (K + 1) * Q;
-  const float one = 1.f, zero = 0.f;
-  // row-major y [N x 2M] = images [N x npix] P [npix x 2M]  <=>  column-major y^T = P^T images^T
-  const cublasStatus_t r = cublasGemmEx(h, CUBLAS_OP_N, CUBLAS_OP_N, two_m, N, npix, &one, P, CUDA_R_32F, two_m,
-                                        images, CUDA_R_32F, npix, &zero, y_out, CUDA_R_32F, two_m,
-                                        tf32 ? CUBLAS_COMPUTE_32F_FAST_TF32 : CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
-  return r == CUBLAS_STATUS_SUCCESS ? MRA_OK : MRA_ECUDA;
+  const size_t NT = (size_t)(two_m + kG3Cols - 1) / kG3Cols, KB = (size_t)(npix + kG3KB - 1) / kG3KB;
+  return 256 + NT * KB * 3 * kG3BTile;
+}
+
+MRA_API size_t mra_fb_operand_bytes(int32_t n, int32_t K, int32_t Q) {
+  if (!fb_dims_ok(n, K, Q)) return 0;
+  return fb_operand_bytes(n, K, Q);
+}
+
+MRA_API int mra_fb_pack(int32_t n, int32_t K, int32_t Q, const float* P, void* op_out, void* stream) {
+  if (!fb_dims_ok(n, K, Q) || !P || !op_out || (reinterpret_cast<uintptr_t>(P) % 16) != 0 ||
+      (reinterpret_cast<uintptr_t>(op_out) % 256) != 0)
+    return MRA_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int npix = n * n, two_m = 2 * (K + 1) * Q;
+  const int NT = (two_m + kG3Cols - 1) / kG3Cols, KB = (npix + kG3KB - 1) / kG3KB;
+  unsigned char* op = static_cast<unsigned char*>(op_out);
+  if (cudaMemsetAsync(op, 0, 256, s) != cudaSuccess) return MRA_ECUDA;
+  // B^T(j, p) = P[p][j]: column j of the coefficient layout, pixel p
+  k_gemm3_pack<<<4096, 256, 0, s>>>(P, 1, two_m, two_m, npix, NT, KB, op + 256);
+  return cudaGetLastError() == cudaSuccess ? MRA_OK : MRA_ECUDA;
+}
+
+MRA_API int mra_fb_project(int32_t N, int32_t n, int32_t K, int32_t Q, const float* images, const void* op,
+                           float* y_out, int32_t fast, void* stream) {
+  if (N < 1 || !fb_dims_ok(n, K, Q)) return MRA_EINVAL;
+  if (!images || !op || !y_out || (reinterpret_cast<uintptr_t>(images) % 16) != 0 ||
+      (reinterpret_cast<uintptr_t>(op) % 256) != 0 || (reinterpret_cast<uintptr_t>(y_out) % 16) != 0)
+    return MRA_EINVAL;
+  DevInfo di;
+  if (dev_info(&di) != MRA_OK) return MRA_ECUDA;
+  if (raise_smem_limit(reinterpret_cast<const void*>(k_gemm3<0>), kG3Smem) != MRA_OK) return MRA_ECUDA;
+  const int npix = n * n, two_m = 2 * (K + 1) * Q;
+  Gemm3Args g{};
+  g.A = images;
+  g.lda = npix;
+  g.rows = N;
+  g.K = npix;
+  g.Bp = static_cast<const unsigned char*>(op) + 256;
+  g.NT = (two_m + kG3Cols - 1) / kG3Cols;
+  g.KB = (npix + kG3KB - 1) / kG3KB;
+  g.cols = two_m;
+  g.nprod = fast ? 3 : 6;
+  g.C = y_out;
+  g.ldc = two_m;
+  g.status = reinterpret_cast<int*>(const_cast<void*>(op));
+  const int items = ((N + kG3Rows - 1) / kG3Rows) * g.NT;
+  k_gemm3<0><<<std::min(items, di.sms), kG3Threads, kG3Smem, static_cast<cudaStream_t>(stream)>>>(g);
+  return cudaGetLastError() == cudaSuccess ? MRA_OK : MRA_ECUDA;
 }
 
 }  // extern "C"
 
 // ============================================================================ steerable PCA
 // For every angular index k: the uncentred second moment C_k = (1/N) sum_i a_ik a_ik^H over the Q
-// radial entries (one strided-batched cuBLAS CGEMM over all images), its eigen-decomposition on
+// radial entries (k_spca_moments: FP64 partial sums per chunk of images), its eigen-decomposition on
 // the host (C++, FP64: cyclic Jacobi on the real symmetric embedding [[Re C, -Im C], [Im C, Re C]],
 // whose eigenvectors (x; y) are the complex eigenvectors x + i y, each twice; a complex Gram-Schmidt
 // pass keeps one of each pair), the eigenvectors whose eigenvalue exceeds the noise-only edge
-// sigma^2 (1 + sqrt(Q/N))^2, and the projection b_ik = U_k^H a_ik (a second strided-batched CGEMM).
+// sigma^2 (1 + sqrt(Q/N))^2, and the projection b_ik = U_k^H a_ik (k_spca_project).
 #include <complex>
 #include <vector>
 
@@ -400,6 +441,74 @@ int herm_eig(int n, const cd* A, double* w, cd* V) {
   return MRA_OK;
 }
 
+// Second moments of steerable PCA: block (chunk, k) sums a_ik[q] conj(a_ik[q']) over its images into
+// the FP64 partial part[k][chunk][q][q'] (each thread owns entries q Q + q' = tid, tid + 256, ...;
+// images staged 64 at a time in shared memory).  k_spca_moments_sum adds the partials in chunk order.
+constexpr int kSpcaChunk = 2048, kSpcaStage = 64;
+__global__ void k_spca_moments(const float2* y, int N, int Kp1, int Q, int nchunk, int stage, double2* part) {
+  extern __shared__ float2 sa[];  // [stage][Q]
+  const int k = blockIdx.y, chunk = blockIdx.x, M = Kp1 * Q, QQ = Q * Q;
+  const int i0 = chunk * kSpcaChunk, i1 = min(N, i0 + kSpcaChunk);
+  double2* out = part + ((size_t)k * nchunk + chunk) * QQ;
+  for (int e = threadIdx.x; e < QQ; e += blockDim.x) out[e] = make_double2(0.0, 0.0);
+  for (int b = i0; b < i1; b += stage) {
+    const int nb = min(stage, i1 - b);
+    __syncthreads();
+    for (int t = threadIdx.x; t < nb * Q; t += blockDim.x) {
+      const int ii = t / Q, q = t - ii * Q;
+      sa[ii * Q + q] = y[(size_t)(b + ii) * M + (size_t)k * Q + q];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < QQ; e += blockDim.x) {
+      const int q = e / Q, q2 = e - q * Q;
+      float re = 0.f, im = 0.f;
+      for (int ii = 0; ii < nb; ++ii) {
+        const float2 u = sa[ii * Q + q], v = sa[ii * Q + q2];  // u conj(v)
+        re = fmaf(u.x, v.x, fmaf(u.y, v.y, re));
+        im = fmaf(u.y, v.x, fmaf(-u.x, v.y, im));
+      }
+      out[e].x += (double)re;
+      out[e].y += (double)im;
+    }
+  }
+}
+__global__ void k_spca_moments_sum(const double2* part, int Kp1, int Q, int nchunk, double invN, float2* D) {
+  const int QQ = Q * Q;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < Kp1 * QQ; idx += gridDim.x * blockDim.x) {
+    const int k = idx / QQ, e = idx - k * QQ;
+    double re = 0.0, im = 0.0;
+    for (int c = 0; c < nchunk; ++c) {
+      const double2 v = part[((size_t)k * nchunk + c) * QQ + e];
+      re += v.x, im += v.y;
+    }
+    // column-major Q x Q per k (entry (q, q') at q' Q + q), as the eigensolver reads it
+    const int q = e / Q, q2 = e - q * Q;
+    D[(size_t)k * QQ + (size_t)q2 * Q + q] = make_float2((float)(re * invN), (float)(im * invN));
+  }
+}
+
+// Reduced coefficients b_ik[c] = sum_q conj(U_k[q][c]) a_ik[q] (U column-major per k), zero for c >= qc.
+__global__ void k_spca_project(const float2* y, int N, int Kp1, int Q, int K2, int Q2, int qc, const float2* U,
+                               float2* out) {
+  const int M2 = (K2 + 1) * Q2, M = Kp1 * Q;
+  const long long n = (long long)N * M2;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / M2), r = (int)(idx - (long long)i * M2), k = r / Q2, c = r - k * Q2;
+    float2 acc = make_float2(0.f, 0.f);
+    if (c < qc) {
+      const float2* a = y + (size_t)i * M + (size_t)k * Q;
+      const float2* u = U + ((size_t)k * Q + c) * Q;
+      for (int q = 0; q < Q; ++q) {
+        const float2 av = a[q], uv = u[q];  // conj(u) a
+        acc.x = fmaf(uv.x, av.x, fmaf(uv.y, av.y, acc.x));
+        acc.y = fmaf(uv.x, av.y, fmaf(-uv.y, av.x, acc.y));
+      }
+    }
+    out[idx] = acc;
+  }
+}
+
 }  // namespace
 }  // namespace mra
 
@@ -411,8 +520,9 @@ MRA_API int mra_hermitian_eig(int32_t n, const double* A, double* w, double* V) 
 }
 
 MRA_API size_t mra_spca_workspace_bytes(const mra_dims* d) {
-  if (!d || d->K < 0 || d->Q < 1 || d->Q > 512) return 0;
-  return align256(sizeof(float) * 2 * (size_t)(d->K + 1) * d->Q * d->Q);
+  if (!d || d->N < 1 || d->K < 0 || d->Q < 1 || d->Q > 512) return 0;
+  const size_t QQ = (size_t)d->Q * d->Q, nchunk = ((size_t)d->N + kSpcaChunk - 1) / kSpcaChunk;
+  return align256(sizeof(float) * 2 * (size_t)(d->K + 1) * QQ) + align256(sizeof(double) * 2 * (d->K + 1) * nchunk * QQ);
 }
 
 MRA_API int mra_spca_fit(const mra_dims* d, const float* y, float* basis_out, double* eig_out, int32_t* counts_out,
@@ -424,18 +534,22 @@ MRA_API int mra_spca_fit(const mra_dims* d, const float* y, float* basis_out, do
   const int Kp1 = d->K + 1, Q = d->Q, M = Kp1 * Q, N = d->N;
   if (M % 2 != 0) return MRA_EINVAL;
   if (ws_bytes < mra_spca_workspace_bytes(d)) return MRA_EWORKSPACE;
-  cublasHandle_t h;
-  if (blas_handle(&h) != MRA_OK) return MRA_ECUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (cublasSetStream(h, s) != CUBLAS_STATUS_SUCCESS) return MRA_ECUDA;
-  // C_k = B B^H / N with B = a[:, k, :]^T (column-major Q x N, leading dimension M): entry (q, q') is the
-  // mean of a_q conj(a_q')
-  const cuComplex alpha = make_cuComplex(1.f / (float)N, 0.f), beta = make_cuComplex(0.f, 0.f);
+  // C_k = (1/N) sum_i a_ik a_ik^H: entry (q, q') is the mean of a_q conj(a_q'); per-chunk FP64 partials
+  // added in a fixed order
+  const int nchunk = (N + kSpcaChunk - 1) / kSpcaChunk;
   cuComplex* D = static_cast<cuComplex*>(ws);
-  if (cublasCgemmStridedBatched(h, CUBLAS_OP_N, CUBLAS_OP_C, Q, Q, N, &alpha,
-                                reinterpret_cast<const cuComplex*>(y), M, Q, reinterpret_cast<const cuComplex*>(y),
-                                M, Q, &beta, D, Q, (long long)Q * Q, Kp1) != CUBLAS_STATUS_SUCCESS)
+  double2* part = reinterpret_cast<double2*>(static_cast<unsigned char*>(ws) +
+                                             align256(sizeof(float) * 2 * (size_t)Kp1 * Q * Q));
+  const int stage = std::max(1, std::min(kSpcaStage, (96 * 1024) / (Q * 8)));  // images staged per pass
+  const int sm = stage * Q * 8;
+  if (sm > 48 * 1024 && raise_smem_limit(reinterpret_cast<const void*>(k_spca_moments), sm) != MRA_OK)
     return MRA_ECUDA;
+  k_spca_moments<<<dim3(nchunk, Kp1), 256, sm, s>>>(reinterpret_cast<const float2*>(y), N, Kp1, Q, nchunk, stage,
+                                                    part);
+  k_spca_moments_sum<<<std::min(1024, (Kp1 * Q * Q + 255) / 256), 256, 0, s>>>(part, Kp1, Q, nchunk, 1.0 / N,
+                                                                               reinterpret_cast<float2*>(D));
+  if (cudaGetLastError() != cudaSuccess) return MRA_ECUDA;
   std::vector<cuComplex> Dh((size_t)Kp1 * Q * Q);
   if (cudaMemcpyAsync(Dh.data(), D, sizeof(cuComplex) * Dh.size(), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
@@ -482,19 +596,14 @@ MRA_API int mra_spca_project(const mra_dims* d, const float* y, int32_t K2, int3
     return MRA_EINVAL;
   const int Q = d->Q, M = (d->K + 1) * Q, M2 = (K2 + 1) * Q2, N = d->N;
   if (M2 % 2 != 0) return MRA_EINVAL;
-  cublasHandle_t h;
-  if (blas_handle(&h) != MRA_OK) return MRA_ECUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (cublasSetStream(h, s) != CUBLAS_STATUS_SUCCESS) return MRA_ECUDA;
-  const cuComplex one = make_cuComplex(1.f, 0.f), zero = make_cuComplex(0.f, 0.f);
+  (void)M;
   const int qc = std::min(Q2, Q);  // basis columns used (a padding column beyond Q stays zero)
-  if (Q2 > Q && cudaMemsetAsync(y_out, 0, sizeof(cuComplex) * (size_t)N * M2, s) != cudaSuccess) return MRA_ECUDA;
-  // out_k (column-major qc x N, leading dimension M2) = U_k^H (qc x Q) a[:, k, :]^T (Q x N, leading dimension M)
-  if (cublasCgemmStridedBatched(h, CUBLAS_OP_C, CUBLAS_OP_N, qc, N, Q, &one, reinterpret_cast<const cuComplex*>(basis),
-                                Q, (long long)Q * Q, reinterpret_cast<const cuComplex*>(y), M, Q, &zero,
-                                reinterpret_cast<cuComplex*>(y_out), M2, Q2, K2 + 1) != CUBLAS_STATUS_SUCCESS)
-    return MRA_ECUDA;
-  return MRA_OK;
+  const long long n = (long long)N * M2;
+  k_spca_project<<<(int)std::min<long long>(4096, (n + 255) / 256), 256, 0, s>>>(
+      reinterpret_cast<const float2*>(y), N, d->K + 1, Q, K2, Q2, qc, reinterpret_cast<const float2*>(basis),
+      reinterpret_cast<float2*>(y_out));
+  return cudaGetLastError() == cudaSuccess ? MRA_OK : MRA_ECUDA;
 }
 
 }  // extern "C"

@@ -38,6 +38,11 @@ __host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
          | ((uint32_t)(M >> 4) << 24);  // M / 16
 }
 
+// The same with BF16 A and B.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
 // ---- tensor memory
 // Allocate ncols columns (a power of two, 32..512) for the CTA; the warp that calls this owns
 // the allocation and must also free it.  The base address is written to *dst (shared memory).

@@ -75,6 +75,8 @@ _SIGS = {
     "mra_template_match": (c_int, [POINTER(mra_dims), c_void_p, c_void_p, c_void_p, c_void_p]),
     "mra_fb_setup_workspace_bytes": (c_size_t, [c_int32, c_int32, c_int32]),
     "mra_fb_setup": (c_int, [c_int32, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "mra_fb_operand_bytes": (c_size_t, [c_int32, c_int32, c_int32]),
+    "mra_fb_pack": (c_int, [c_int32, c_int32, c_int32, c_void_p, c_void_p, c_void_p]),
     "mra_fb_project": (c_int, [c_int32, c_int32, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
     "mra_spca_workspace_bytes": (c_size_t, [POINTER(mra_dims)]),
     "mra_spca_fit": (c_int, [POINTER(mra_dims), c_void_p, c_void_p, c_void_p, c_void_p, POINTER(c_int32),
@@ -298,9 +300,25 @@ def mra_fb_setup(n, K, Q, P_out, zeros_out, ws, stream=None):
                                                _stream(stream)))
 
 
-def mra_fb_project(N, n, K, Q, images, P, y_out, tf32=False, stream=None):
-    _check("mra_fb_project", load().mra_fb_project(int(N), int(n), int(K), int(Q), _p(images), _p(P), _p(y_out),
-                                                   1 if tf32 else 0, _stream(stream)))
+def mra_fb_operand_bytes(n, K, Q) -> int:
+    return int(load().mra_fb_operand_bytes(int(n), int(K), int(Q)))
+
+
+def mra_fb_pack(n, K, Q, P, op_out, stream=None):
+    _check("mra_fb_pack", load().mra_fb_pack(int(n), int(K), int(Q), _p(P), _p(op_out), _stream(stream)))
+
+
+def mra_fb_project(N, n, K, Q, images, op, y_out, fast=False, stream=None):
+    """op: the packed projection operand of mra_fb_pack (see fb_operand)."""
+    _check("mra_fb_project", load().mra_fb_project(int(N), int(n), int(K), int(Q), _p(images), _p(op), _p(y_out),
+                                                   1 if fast else 0, _stream(stream)))
+
+
+def fb_operand(n, K, Q, P, stream=None) -> torch.Tensor:
+    """The packed projection operand of P (a byte tensor) for mra_fb_project."""
+    op = workspace(mra_fb_operand_bytes(n, K, Q), P.device)
+    mra_fb_pack(n, K, Q, P, op, stream)
+    return op
 
 
 def mra_spca_workspace_bytes(d) -> int:

@@ -45,19 +45,19 @@ def synchronize(y, d, P, ws: Workspaces, n_power=50, n_ppm=100, stream=None) -> 
 
 
 def fb_projection(n, K, Q, device="cuda", stream=None):
-    """The Fourier-Bessel projection of App. A for n x n images onto k = 0..K, q = 1..Q: a complex64 tensor
-    [n*n, K+1, Q] (set up once; mra_fb_setup)."""
+    """The Fourier-Bessel projection of App. A for n x n images onto k = 0..K, q = 1..Q, set up once
+    (mra_fb_setup) and packed for the tensor-core projection (mra_fb_pack): the operand of mra_fb_project."""
     P = torch.empty((n * n, K + 1, Q), dtype=torch.complex64, device=device)
     ws = mra.workspace(mra.mra_fb_setup_workspace_bytes(n, K, Q), device)
     mra.mra_fb_setup(n, K, Q, P, None, ws, stream)
-    return P
+    return mra.fb_operand(n, K, Q, P, stream)
 
 
-def fb_coefficients(images, P, K, Q, tf32=False, stream=None) -> torch.Tensor:
+def fb_coefficients(images, op, K, Q, fast=False, stream=None) -> torch.Tensor:
     """Coefficients [N, K+1, Q] (complex64) of images [N, n, n] (float32): the observations y of Eq. MRA_Model_FB."""
     N, n = images.shape[0], images.shape[-1]
     y = torch.empty((N, K + 1, Q), dtype=torch.complex64, device=images.device)
-    mra.mra_fb_project(N, n, K, Q, images.contiguous(), P, y, tf32, stream)
+    mra.mra_fb_project(N, n, K, Q, images.contiguous(), op, y, fast, stream)
     return y
 
 
