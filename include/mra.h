@@ -258,7 +258,11 @@ MRA_API int mra_sync_ppm(int32_t L, int32_t P, const int32_t* rel, int32_t n_pow
                          void* stream);
 
 /* Matching step of Algorithm Synchronize and Match: image i takes phi[n*],
- * n* = argmin_{n < P, n != i} ||y_i - y_n||^2 (smallest n on ties).
+ * n* = argmin_{n < P, n != i} ||y_i - y_n||^2 (smallest n on ties), scored as
+ * ||y_n||^2 - 2 <y_i, y_n>.  For P <= 256 the inner products are one tcgen05 GEMM of all images with
+ * the P references (each FP32 value split into three BF16 pieces, six piece products, FP32
+ * accumulation) with the arg-min fused into its epilogue; a bounded wait that runs out sets the sync
+ * workspace's status word (mra_ws_status(ws)) to MRA_ETIMEOUT.  Larger P use an FP32 CUDA-core tile kernel.
  *   phi [P] int32 in, shift_out [N] int32. */
 MRA_API int mra_sync_match(const mra_dims* dims, const float* y, int32_t P, const int32_t* phi, int32_t* shift_out,
                            void* ws, size_t ws_bytes, void* stream);

@@ -302,7 +302,7 @@ MRA_API int mra_fb_pack(int32_t n, int32_t K, int32_t Q, const float* P, void* o
   unsigned char* op = static_cast<unsigned char*>(op_out);
   if (cudaMemsetAsync(op, 0, 256, s) != cudaSuccess) return MRA_ECUDA;
   // B^T(j, p) = P[p][j]: column j of the coefficient layout, pixel p
-  k_gemm3_pack<<<4096, 256, 0, s>>>(P, 1, two_m, two_m, npix, NT, KB, op + 256);
+  k_gemm3_pack<<<4096, 256, 0, s>>>(P, 1, two_m, two_m, npix, NT, KB, kG3Cols, op + 256);
   return cudaGetLastError() == cudaSuccess ? MRA_OK : MRA_ECUDA;
 }
 
@@ -326,6 +326,7 @@ MRA_API int mra_fb_project(int32_t N, int32_t n, int32_t K, int32_t Q, const flo
   g.KB = (npix + kG3KB - 1) / kG3KB;
   g.cols = two_m;
   g.nprod = fast ? 3 : 6;
+  g.brows = kG3Cols;
   g.C = y_out;
   g.ldc = two_m;
   g.status = reinterpret_cast<int*>(const_cast<void*>(op));

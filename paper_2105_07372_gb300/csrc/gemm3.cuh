@@ -9,8 +9,8 @@
 //      pieces of B^T's [256][32] block in the K-major core-matrix layout of tc::op_offset,
 //      contiguous (48 KB), so that one bulk copy fills a stage
 //
-// Roles per CTA (320 threads): warps 0-3 produce A, warp 4 copies B, warp 5 issues the MMAs, warps
-// 6-9 run the epilogue (tile row 32 (w % 4) + lane = tensor-memory lane).  Stages are released by
+// Roles per CTA (448 threads): warps 0-7 produce A, warp 8 copies B, warp 9 issues the MMAs, warps
+// 10-13 run the epilogue (tile row 32 (w % 4) + lane = tensor-memory lane).  Stages are released by
 // tcgen05.commit; every wait is bounded and reports MRA_ETIMEOUT through the status word.
 // Output tiles are taken in groups that cover every column tile of consecutive row tiles, so
 // that CTAs working at the same time share A rows and B tiles through L2.
@@ -21,7 +21,7 @@
 
 namespace mra {
 
-constexpr int kG3Rows = 128, kG3Cols = 256, kG3KB = 32, kG3Stages = 3, kG3Threads = 320;
+constexpr int kG3Rows = 128, kG3Cols = 256, kG3KB = 32, kG3Stages = 3, kG3Threads = 448;
 constexpr int kG3ATile = kG3Rows * kG3KB * 2;  // bytes of one A piece per stage
 constexpr int kG3BTile = kG3Cols * kG3KB * 2;  // bytes of one B piece per stage
 constexpr int kG3Stage = 3 * kG3ATile + 3 * kG3BTile;
@@ -31,8 +31,9 @@ struct Gemm3Args {
   const float* A;
   long long lda;
   int rows, K;
-  const void* Bp;  // packed B: [NT][KB][3][256 x 32 BF16]
+  const void* Bp;  // packed B: [NT][KB][3][brows x 32 BF16]
   int NT, KB, cols;
+  int brows;       // rows of a packed B tile (a multiple of 16, <= 256; the MMAs' N)
   int nprod;       // 6 (accurate) or 3 (fast)
   float* C;        // store epilogue: C [rows][cols], row stride ldc
   long long ldc;
@@ -50,26 +51,28 @@ __device__ __forceinline__ void split3(float v, __nv_bfloat16& h, __nv_bfloat16&
   l = __float2bfloat16_rn(r1 - __bfloat162float(m));
 }
 
-// Pack B^T: element (j, k) of the [cols][K] matrix read as Bt(j, k) = src[j * sj + k * sk].
-__global__ void k_gemm3_pack(const float* src, long long sj, long long sk, int cols, int K, int NT, int KB,
-                             unsigned char* out) {
-  const long long n = (long long)NT * kG3Cols * KB * kG3KB;
+// Pack B^T: element (j, k) of the [cols][K] matrix read as Bt(j, k) = src[j * sj + k * sk], into tiles of
+// brows columns (the last one zero padded).
+static __global__ void k_gemm3_pack(const float* src, long long sj, long long sk, int cols, int K, int NT, int KB,
+                                    int brows, unsigned char* out) {
+  const long long n = (long long)NT * brows * KB * kG3KB;
+  const int ptile = brows * kG3KB * 2;  // bytes of one piece of a tile
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
        idx += (long long)gridDim.x * blockDim.x) {
     // idx runs over (k, j) with j fastest: consecutive threads read consecutive columns
-    const long long kk = idx / (NT * kG3Cols);
-    const int jj = (int)(idx - kk * (NT * kG3Cols));
+    const long long kk = idx / (NT * brows);
+    const int jj = (int)(idx - kk * (NT * brows));
     const int k = (int)kk;
     float v = 0.f;
     if (jj < cols && k < K) v = src[jj * sj + k * sk];
     __nv_bfloat16 h, m, l;
     split3(v, h, m, l);
-    const int nt = jj / kG3Cols, r = jj % kG3Cols, kb = k / kG3KB, c = k % kG3KB;
-    unsigned char* chunk = out + ((size_t)nt * KB + kb) * (3 * kG3BTile);
+    const int nt = jj / brows, r = jj % brows, kb = k / kG3KB, c = k % kG3KB;
+    unsigned char* chunk = out + ((size_t)nt * KB + kb) * (3 * ptile);
     const int off = tc::op_offset(r, c, kG3KB);
     *reinterpret_cast<__nv_bfloat16*>(chunk + off) = h;
-    *reinterpret_cast<__nv_bfloat16*>(chunk + kG3BTile + off) = m;
-    *reinterpret_cast<__nv_bfloat16*>(chunk + 2 * kG3BTile + off) = l;
+    *reinterpret_cast<__nv_bfloat16*>(chunk + ptile + off) = m;
+    *reinterpret_cast<__nv_bfloat16*>(chunk + 2 * ptile + off) = l;
   }
 }
 
@@ -83,7 +86,7 @@ template <int EPI>
 __global__ void __launch_bounds__(kG3Threads, 1) k_gemm3(const Gemm3Args a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  uint64_t* full_a = reinterpret_cast<uint64_t*>(smem);        // [stages], 128 producer arrivals
+  uint64_t* full_a = reinterpret_cast<uint64_t*>(smem);        // [stages], 256 producer arrivals
   uint64_t* full_b = full_a + kG3Stages;                       // [stages], bulk-copy bytes
   uint64_t* empty = full_b + kG3Stages;                        // [stages], MMA commit
   uint64_t* acc_full = empty + kG3Stages;                      // [2] MMA commit after a segment
@@ -92,7 +95,7 @@ __global__ void __launch_bounds__(kG3Threads, 1) k_gemm3(const Gemm3Args a) {
   unsigned char* stages = smem + 1024;
   if (tid == 0) {
     for (int s = 0; s < kG3Stages; ++s) {
-      mbar_init(&full_a[s], kG3Rows);
+      mbar_init(&full_a[s], 2 * kG3Rows);
       mbar_init(&full_b[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -126,24 +129,30 @@ __global__ void __launch_bounds__(kG3Threads, 1) k_gemm3(const Gemm3Args a) {
     }
     return true;
   };
-  if (warp < 4) {
-    // ---- A producers: lane l of warp w holds rows 32 w + 8 i + l / 4 (i = 0..3), columns 8 (l % 4) .. + 7
+  if (warp < 8) {
+    // ---- A producers: lane l of warp w holds rows 16 w + 8 i + l / 4 (i = 0, 1), columns 8 (l % 4) .. + 7
     // of a k block; the next block's values are loaded (into registers) before this one is converted
     const int c0 = 8 * (lane & 3);
-    auto load_blk = [&](int row0, int kb, float (&v)[4][8]) {
+    const bool vec = (a.lda % 4) == 0 && (reinterpret_cast<uintptr_t>(a.A) % 16) == 0;
+    auto load_blk = [&](int row0, int kb, float (&v)[2][8]) {
       const int k0 = kb * kG3KB + c0;
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int gr = row0 + 32 * warp + 8 * i + (lane >> 2);
+      for (int i = 0; i < 2; ++i) {
+        const int gr = row0 + 16 * warp + 8 * i + (lane >> 2);
         const float* src = a.A + (long long)gr * a.lda + k0;
+        if (vec && gr < a.rows && k0 + 8 <= a.K) {
+          const float4 u = __ldg(reinterpret_cast<const float4*>(src)), w = __ldg(reinterpret_cast<const float4*>(src) + 1);
+          v[i][0] = u.x, v[i][1] = u.y, v[i][2] = u.z, v[i][3] = u.w, v[i][4] = w.x, v[i][5] = w.y, v[i][6] = w.z, v[i][7] = w.w;
+        } else {
 #pragma unroll
-        for (int e = 0; e < 8; ++e) v[i][e] = (gr < a.rows && k0 + e < a.K) ? __ldg(src + e) : 0.f;
+          for (int e = 0; e < 8; ++e) v[i][e] = (gr < a.rows && k0 + e < a.K) ? __ldg(src + e) : 0.f;
+        }
       }
     };
     int kiter = 0;
     for (int it = blockIdx.x; it < items && !failed; it += gridDim.x) {
       const int row0 = (it / a.NT) * kG3Rows;
-      float cur[4][8], nxt[4][8];
+      float cur[2][8], nxt[2][8];
       load_blk(row0, 0, cur);
       for (int kb = 0; kb < a.KB; ++kb, ++kiter) {
         if (kb + 1 < a.KB) load_blk(row0, kb + 1, nxt);
@@ -151,8 +160,8 @@ __global__ void __launch_bounds__(kG3Threads, 1) k_gemm3(const Gemm3Args a) {
         if (!wait(&empty[s], (uint32_t)(((kiter / kG3Stages) & 1) ^ 1))) break;
         unsigned char* st = stages + (size_t)s * kG3Stage;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int r = 32 * warp + 8 * i + (lane >> 2);
+        for (int i = 0; i < 2; ++i) {
+          const int r = 16 * warp + 8 * i + (lane >> 2);
           __align__(16) __nv_bfloat16 ph[8], pm[8], pl[8];
 #pragma unroll
           for (int e = 0; e < 8; ++e) split3(cur[i][e], ph[e], pm[e], pl[e]);
@@ -164,25 +173,26 @@ __global__ void __launch_bounds__(kG3Threads, 1) k_gemm3(const Gemm3Args a) {
         tc::fence_proxy_async();
         mbar_arrive(&full_a[s]);
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < 2; ++i)
 #pragma unroll
           for (int e = 0; e < 8; ++e) cur[i][e] = nxt[i][e];
       }
     }
-  } else if (warp == 4) {
+  } else if (warp == 8) {
     // ---- B producer: one bulk copy of the three pieces per stage
     if (lane == 0) {
       int kiter = 0;
       for (int it = blockIdx.x; it < items && !failed; it += gridDim.x) {
         const int nt = it % a.NT;
-        const unsigned char* src = static_cast<const unsigned char*>(a.Bp) + (size_t)nt * a.KB * (3 * kG3BTile);
+        const uint32_t ptile = (uint32_t)a.brows * kG3KB * 2;
+        const unsigned char* src = static_cast<const unsigned char*>(a.Bp) + (size_t)nt * a.KB * (3 * ptile);
         for (int kb = 0; kb < a.KB; ++kb, ++kiter) {
           const int s = kiter % kG3Stages;
           if (!wait(&empty[s], (uint32_t)(((kiter / kG3Stages) & 1) ^ 1))) break;
           unsigned char* st = stages + (size_t)s * kG3Stage + 3 * kG3ATile;
-          const uint32_t bytes = (a.nprod > 3 ? 3 : 2) * kG3BTile;  // the fast mode reads no l piece
+          const uint32_t bytes = (a.nprod > 3 ? 3 : 2) * ptile;  // the fast mode reads no l piece
           mbar_arrive_expect_tx(&full_b[s], bytes);
-          bulk_g2s(st, src + (size_t)kb * (3 * kG3BTile), bytes, &full_b[s]);
+          bulk_g2s(st, src + (size_t)kb * (3 * ptile), bytes, &full_b[s]);
         }
       }
       if (failed) {  // copies this warp issued land before the CTA exits (each wait bounded)
@@ -190,10 +200,11 @@ __global__ void __launch_bounds__(kG3Threads, 1) k_gemm3(const Gemm3Args a) {
           mbar_wait_bounded(&full_b[u % kG3Stages], (uint32_t)((u / kG3Stages) & 1));
       }
     }
-  } else if (warp == 5) {
+  } else if (warp == 9) {
     // ---- MMA issuer: accumulator sc & 1 for the sc-th segment of this CTA
     if (lane == 0) {
-      const uint32_t idesc = tc::idesc_bf16(kG3Rows, kG3Cols);
+      const uint32_t idesc = tc::idesc_bf16(kG3Rows, a.brows);
+      const uint32_t ptile = (uint32_t)a.brows * kG3KB * 2;
       constexpr uint32_t SBO = (kG3KB / 8) * 128;
       int kiter = 0, sc = 0;
       for (int it = blockIdx.x; it < items && !failed; it += gridDim.x) {
@@ -215,8 +226,8 @@ __global__ void __launch_bounds__(kG3Threads, 1) k_gemm3(const Gemm3Args a) {
               const uint32_t ko = ks * 256;
               const uint64_t ah = tc::smem_desc(sa + ko, 128, SBO), am = tc::smem_desc(sa + kG3ATile + ko, 128, SBO),
                              al = tc::smem_desc(sa + 2 * kG3ATile + ko, 128, SBO);
-              const uint64_t bh = tc::smem_desc(sb + ko, 128, SBO), bm = tc::smem_desc(sb + kG3BTile + ko, 128, SBO),
-                             bl = tc::smem_desc(sb + 2 * kG3BTile + ko, 128, SBO);
+              const uint64_t bh = tc::smem_desc(sb + ko, 128, SBO), bm = tc::smem_desc(sb + ptile + ko, 128, SBO),
+                             bl = tc::smem_desc(sb + 2 * ptile + ko, 128, SBO);
               const uint32_t first = (kb == g * seg && ks == 0) ? 0u : 1u;
               tc::mma_f16(dacc, ah, bh, idesc, first);
               tc::mma_f16(dacc, ah, bm, idesc, 1u);
@@ -235,7 +246,7 @@ __global__ void __launch_bounds__(kG3Threads, 1) k_gemm3(const Gemm3Args a) {
       }
     }
   } else {
-    // ---- epilogue warps 6..9: tile row = 32 (warp % 4) + lane = tensor-memory lane
+    // ---- epilogue warps 10..13: tile row = 32 (warp % 4) + lane = tensor-memory lane
     const int qtr = warp & 3, row = 32 * qtr + lane;
     int sc = 0;
     for (int it = blockIdx.x; it < items && !failed; it += gridDim.x) {
@@ -249,8 +260,8 @@ __global__ void __launch_bounds__(kG3Threads, 1) k_gemm3(const Gemm3Args a) {
         tc::fence_after_sync();
         const uint32_t trow = tbase + ((uint32_t)(qtr * 32) << 16) + (uint32_t)(b * kG3Cols);
         if (EPI == 0) {
-          const int col0 = nt * kG3Cols;
-          for (int c = 0; c < kG3Cols; c += 16) {
+          const int col0 = nt * a.brows;
+          for (int c = 0; c < a.brows; c += 16) {
             float v[16];
             tc::tmem_ld16(trow + (uint32_t)c, v);
             if (gr < a.rows) {
@@ -272,7 +283,7 @@ __global__ void __launch_bounds__(kG3Threads, 1) k_gemm3(const Gemm3Args a) {
             }
           }
         } else {
-          for (int c = 0; c < kG3Cols; c += 16) {
+          for (int c = 0; c < a.brows; c += 16) {
             float v[16];
             tc::tmem_ld16(trow + (uint32_t)c, v);
 #pragma unroll

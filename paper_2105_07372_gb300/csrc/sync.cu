@@ -14,6 +14,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "gemm3.cuh"
 
 namespace mra {
 namespace {
@@ -621,15 +622,24 @@ int check_sync_dims(const mra_dims* d, int P) {
   return MRA_OK;
 }
 
+// Sync workspace: a status word (the bounded waits of the tensor-core match), the relative rotations,
+// the synchronized rotations, the references' norms and, for P <= 256, the references packed as the
+// tensor-core GEMM's B operand (coordinates as K).
 struct SyncLayout {
-  size_t rel, phi, nrm, total;
+  size_t status, rel, phi, nrm, bpack, total;
+  int KB, brows;  // K blocks of the packed references, and their rows (P rounded up to 16)
 };
-SyncLayout sync_layout(int P) {
+bool match_on_tc(int P) { return P <= kG3Cols; }
+SyncLayout sync_layout(int P, int D) {
   SyncLayout s;
   size_t o = 0;
+  s.status = o; o = 256;
   s.rel = o; o = align256(o + sizeof(int) * (size_t)P * P);
   s.phi = o; o = align256(o + sizeof(int) * (size_t)P);
   s.nrm = o; o = align256(o + sizeof(float) * (size_t)P);
+  s.KB = (D + kG3KB - 1) / kG3KB;
+  s.brows = (P + 15) / 16 * 16;
+  s.bpack = o; o = align256(o + (match_on_tc(P) ? (size_t)s.KB * 3 * s.brows * kG3KB * 2 : 0));
   s.total = o;
   return s;
 }
@@ -643,7 +653,7 @@ extern "C" {
 
 MRA_API size_t mra_sync_workspace_bytes(const mra_dims* d, int32_t P) {
   if (check_sync_dims(d, P) != MRA_OK) return 0;
-  return sync_layout(P).total;
+  return sync_layout(P, 2 * (d->K + 1) * d->Q).total;
 }
 
 MRA_API int mra_sync_pairwise(const mra_dims* d, const float* y, int32_t P, int32_t* rel_out, void* stream) {
@@ -700,20 +710,46 @@ MRA_API int mra_sync_match(const mra_dims* d, const float* y, int32_t P, const i
   if (check_sync_dims(d, P) != MRA_OK || !ok_ptr(y, 16) || !ok_ptr(phi, 4) || !ok_ptr(shift_out, 4) ||
       !ok_ptr(ws, 256))
     return MRA_EINVAL;
-  const SyncLayout sl = sync_layout(P);
+  const int D = 2 * (d->K + 1) * d->Q;
+  const SyncLayout sl = sync_layout(P, D);
   if (ws_bytes < sl.total) return MRA_EWORKSPACE;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  float* nrm = reinterpret_cast<float*>(static_cast<unsigned char*>(ws) + sl.nrm);
-  const int D = 2 * (d->K + 1) * d->Q;
+  unsigned char* base = static_cast<unsigned char*>(ws);
+  float* nrm = reinterpret_cast<float*>(base + sl.nrm);
   k_refnorm<<<(P + 7) / 8, 256, 0, s>>>(y, D, P, nrm);
-  k_match<<<(d->N + kMT - 1) / kMT, 256, 0, s>>>(y, d->N, D, P, nrm, phi, shift_out);
+  if (match_on_tc(P)) {
+    // score_in = ||y_n||^2 - 2 <y_i, y_n> from the tensor-core GEMM of the images with the P references
+    DevInfo di;
+    if (dev_info(&di) != MRA_OK) return MRA_ECUDA;
+    if (raise_smem_limit(reinterpret_cast<const void*>(k_gemm3<1>), kG3Smem) != MRA_OK) return MRA_ECUDA;
+    k_gemm3_pack<<<1024, 256, 0, s>>>(y, D, 1, P, D, 1, sl.KB, sl.brows, base + sl.bpack);
+    Gemm3Args g{};
+    g.A = y;
+    g.lda = D;
+    g.rows = d->N;
+    g.K = D;
+    g.Bp = base + sl.bpack;
+    g.NT = 1;
+    g.KB = sl.KB;
+    g.cols = P;
+    g.nprod = 6;
+    g.brows = sl.brows;
+    g.rn = nrm;
+    g.phi = phi;
+    g.out = shift_out;
+    g.status = reinterpret_cast<int*>(base + sl.status);
+    const int items = (d->N + kG3Rows - 1) / kG3Rows;
+    k_gemm3<1><<<std::min(items, di.sms), kG3Threads, kG3Smem, s>>>(g);
+  } else {
+    k_match<<<(d->N + kMT - 1) / kMT, 256, 0, s>>>(y, d->N, D, P, nrm, phi, shift_out);
+  }
   return cudaGetLastError() == cudaSuccess ? MRA_OK : MRA_ECUDA;
 }
 
 MRA_API int mra_sync(const mra_dims* d, const float* y, int32_t P, int32_t n_power, int32_t n_ppm, int32_t* shift_out,
                      void* ws, size_t ws_bytes, void* stream) {
   if (check_sync_dims(d, P) != MRA_OK || !ok_ptr(ws, 256)) return MRA_EINVAL;
-  const SyncLayout sl = sync_layout(P);
+  const SyncLayout sl = sync_layout(P, 2 * (d->K + 1) * d->Q);
   if (ws_bytes < sl.total) return MRA_EWORKSPACE;
   unsigned char* base = static_cast<unsigned char*>(ws);
   int* rel = reinterpret_cast<int*>(base + sl.rel);
