@@ -486,7 +486,7 @@ def main():
     alu_peak = fp32_alu_peak_tflops()
     traffic = traffic_for()
     kernel = {1: "k_sweep_v2", 2: "k_sweep_v3", 3: "k_sweep_v4", 4: "k_sweep_v5",
-              5: "k_tc_corr+k_tc_trans+k_tc_accum"}.get(tuned[0], "k_em_sweep")
+              5: "k_tc_corr+k_tc_trans+k_tc_accum", 6: "k_sweep_v6"}.get(tuned[0], "k_em_sweep")
     hbm_side = {"achieved": bytes_per_sweep / avg_sweep_s / 1e9, "peak": peak, "unit": "GB/s"}
     alu_side = {"achieved": flops_per_sweep / avg_sweep_s / 1e12, "peak": alu_peak, "unit": "TFLOP/s"}
     hbm_bound = bytes_per_sweep / (peak * 1e9) >= flops_per_sweep / (alu_peak * 1e12)
@@ -656,7 +656,7 @@ def _timed_steps(step, args, clk):
 
 def _effective_choice(tuned):
     """The sweep the timed steps use: MRA_SWEEP (with MRA_SWEEP_BI / _NS) overrides the autotuner's choice."""
-    kind = {"warp": 1, "cta": 2, "chunk": 3, "lean": 4, "tc": 5}.get(os.environ.get("MRA_SWEEP", ""))
+    kind = {"warp": 1, "cta": 2, "chunk": 3, "lean": 4, "tc": 5, "pair": 6}.get(os.environ.get("MRA_SWEEP", ""))
     if kind is None:
         return tuned
     return [kind, int(os.environ.get("MRA_SWEEP_BI", 0) or 0), int(os.environ.get("MRA_SWEEP_NS", 0) or 0)]

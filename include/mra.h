@@ -172,8 +172,8 @@ MRA_API int mra_em_run_hl(const mra_dims* dims, const mra_em_params* prm, const 
  * Neither has a counterpart in the paper, which treats one problem at a time. */
 
 /* (No counterpart in the paper.)  Times every EM sweep that can take the problem
- * (the lean warp sweep for grid windows of at most 32 mirror units that are not the whole
- * circle; the split sweep with its tcgen05 window transform for windows of 65 to 512 rotations
+ * (the paired-warp sweep, two warps per image, and the lean warp sweep for grid windows of at
+ * most 32 mirror units that are not the whole circle; the split sweep with its tcgen05 window transform for windows of 65 to 512 rotations
  * and K+1 <= 48 (the default on the whole circle); the warp-per-image sweep; the batch sweep at
  * 16, 12, 8 or 4 images per batch and
  * 2 or 3 ring stages; the
@@ -183,8 +183,8 @@ MRA_API int mra_em_run_hl(const mra_dims* dims, const mra_em_params* prm, const 
  * shape use the cached choice unless the MRA_SWEEP* environment variables fix one.
  * Synchronizes the stream.
  *   y_format   0: y complex64; 1: the BF16 hi/lo split of mra_y_split_bf16
- *   choice_out host int32[3]: kind (1 warp, 2 batch, 3 chunked, 4 lean warp, 5 split, 0 none
- *              applies),
+ *   choice_out host int32[3]: kind (1 warp, 2 batch, 3 chunked, 4 lean warp, 5 split,
+ *              6 paired warps, 0 none applies),
  *              images per batch or chunk, ring stages or CTAs per SM; or NULL
  * The workspace is the one of mra_em_workspace_bytes; its contents are clobbered. */
 MRA_API int mra_em_autotune(const mra_dims* dims, const mra_em_params* prm, const void* y, int32_t y_format,

@@ -256,6 +256,42 @@ SweepV2Launch sweep_v5_q2(int MR, int nup);
 SweepV2Launch sweep_v5_q3(int MR, int nup);
 SweepV2Launch sweep_v5_q4(int MR, int nup);
 
+// Arguments of the paired-warp sweep (sweep6_impl.cuh): grid windows of at most 32 mirror units,
+// two warps per image, the tables of the warp sweep (units, tu, td).
+struct SweepV6Args {
+  const float2* y;
+  const int* shift;
+  int N, K, M, L, Lw, NU;
+  int ns;          // ring slots per warp pair
+  int slot_bytes;  // bytes per ring slot
+  int sp;          // pitch (floats) of the per-warp window buffers
+  int off_bar, off_ring, off_tab, off_tf, off_lr, off_units, off_cb, off_xp, off_xq, off_pv, off_sb, off_wl;
+  float two_beta;
+  int l0m;         // l0 mod L
+  int nd;          // distance units in td (Lw)
+  int nup;         // pitch of tu
+  const float2* x32;
+  const float2* tu;    // [Kp1][nup] e^{-i k theta} of each mirror unit's first offset
+  const int2* units;   // [nup] window indices (a, b), b = -1 for a unit without mirror
+  const float2* td;    // [Kp1][nd] (cos t - 1, -sin t), t = 2 pi k d / L
+  const float2* tf32;
+  const float* logrho32;
+  double* part;
+  int G;
+  float* w_out;
+  Ctrl* ctrl;
+};
+struct SweepV6Launch {
+  void (*fn)(const SweepV6Args);
+  int threads;
+};
+// QV = float4 per lane per row (Q / 8); MR = rows per quad and warp (K <= 16 MR); instances with
+// MR x QV <= 6.
+SweepV6Launch sweep_v6_q1(int MR);
+SweepV6Launch sweep_v6_q2(int MR);
+SweepV6Launch sweep_v6_q3(int MR);
+SweepV6Launch sweep_v6_q4(int MR);
+
 // Arguments of the CTA-cooperative sweep (sweep3_impl.cuh), launched with kV3Threads threads.
 constexpr int kV3Threads = 512;
 struct SweepV3Args {

@@ -1142,6 +1142,53 @@ bool plan_v5(int Kp1, int Q, int L, int Lw, int nu, int nup, bool dense, int max
   return false;
 }
 
+// Shared-memory plan of the paired-warp sweep (grid windows of at most 32 mirror units that are
+// not the whole circle, K <= 16 MR with MR x QV <= 6): per pair a ring of three image slots
+// (two where three do not fit), the unit table in row pairs, the grid twiddles and the small
+// per-warp and per-pair exchange buffers.
+struct V6Plan {
+  SweepV6Launch launch;
+  int ns, slot_bytes, sp, smem;
+  int off_bar, off_ring, off_tab, off_tf, off_lr, off_units, off_cb, off_xp, off_xq, off_pv, off_sb, off_wl;
+};
+bool plan_v6(int Kp1, int Q, int L, int Lw, int nu, bool dense, int max_smem, V6Plan* p) {
+  const int K = Kp1 - 1;
+  if (dense || Lw >= L || nu > 32 || K < 1 || L > 100000 || Q % 8 != 0 || Q / 8 > 4) return false;
+  const int QV = Q / 8, MR = (K + 15) / 16;
+  if (MR * QV > 6) return false;
+  const SweepV6Launch ln = QV == 1 ? sweep_v6_q1(MR) : QV == 2 ? sweep_v6_q2(MR)
+                         : QV == 3 ? sweep_v6_q3(MR) : sweep_v6_q4(MR);
+  if (!ln.fn) return false;
+  const int NW = ln.threads / 32, NP = NW / 2;
+  const int M = Kp1 * Q;
+  const int slot = al16(M * 8);
+  const int sp = (Lw + 3) & ~3;
+  for (int ns = 3; ns >= 2; --ns) {
+    int o = 0;
+    p->off_bar = o; o += al16(NP * ns * 8);
+    p->off_ring = o; o += NP * ns * slot;
+    p->off_tab = o; o += 8 * MR * 32 * 16;
+    p->off_tf = o; o += al16(L * 8);
+    p->off_lr = o; o += al16(Lw * 4);
+    p->off_units = o; o += 32 * 8;
+    p->off_cb = o; o += NW * 8 * MR * 8;
+    p->off_xp = o; o += NP * 64 * 8;
+    p->off_xq = o; o += NP * 8 * 8;
+    p->off_pv = o; o += al16(NP * 2 * sp * 4);
+    p->off_sb = o; o += al16(NW * sp * 4);
+    p->off_wl = o; o += al16(NP * sp * 4);
+    if (o + 1024 <= max_smem) {
+      p->launch = ln;
+      p->ns = ns;
+      p->slot_bytes = slot;
+      p->sp = sp;
+      p->smem = o;
+      return true;
+    }
+  }
+  return false;
+}
+
 // Plan of the split sweep: the stream kernels' ring (two slots per warp), x and its swapped copy and
 // the grid twiddles; the transform kernel's B operand, two A tiles, tables and reduction scratch
 // (at least 116 KB, so that one transform CTA holds a streaming multiprocessor's tensor memory).
@@ -1354,12 +1401,13 @@ bool plan_v4(int Kp1, int Q, int L, int Lw, int l0, bool dense, int yf, int want
 
 // Which EM sweep a call uses.  kind: 0 = automatic, 1 = warp per image, 2 = batch
 // (CTA-cooperative) with batch bi and ring stages ns (0 = the first that fits),
-// 3 = chunked two-read with bi images per chunk and ns CTAs per SM (0 = first that fits).
+// 3 = chunked two-read with bi images per chunk and ns CTAs per SM (0 = first that fits),
+// 4 = lean warp per image, 5 = split (tensor-core transform), 6 = paired warps per image.
 struct SweepSel {
   int kind, bi, ns;
 };
 
-// MRA_SWEEP=warp|cta|chunk|lean, MRA_SWEEP_BI=16|12|8|4 and MRA_SWEEP_NS=2|3 fix the sweep (for
+// MRA_SWEEP=warp|cta|chunk|lean|tc|pair, MRA_SWEEP_BI=16|12|8|4 and MRA_SWEEP_NS=2|3 fix the sweep (for
 // comparisons and tuning runs); they take precedence over the autotuner's cache.
 // MRA_SWEEP_TDG=1 makes the batch sweep read its distance-unit table from global memory
 // even where the table fits in shared memory (to test that variant on small windows).
@@ -1371,6 +1419,7 @@ SweepSel env_sweep() {
   if (k && strcmp(k, "chunk") == 0) e.kind = 3;
   if (k && strcmp(k, "lean") == 0) e.kind = 4;
   if (k && strcmp(k, "tc") == 0) e.kind = 5;
+  if (k && strcmp(k, "pair") == 0) e.kind = 6;
   const char* b = getenv("MRA_SWEEP_BI");
   const char* n = getenv("MRA_SWEEP_NS");
   e.bi = b ? atoi(b) : 0;
@@ -1458,6 +1507,9 @@ struct EmCall {
   bool v2;  // warp-per-image sweep (rows of Q a multiple of 8) instead of the tile sweep
   bool v5;  // with v2: the lean warp sweep's kernel and plan
   int v5_cbp, v5_off_xs;
+  bool v6;  // with v2 (whose tables it reads): the paired-warp sweep
+  V6Plan v6p;
+  SweepV6Args sa6;
   V2Plan v2p;
   SweepV2Args sa2;
   bool v3;  // CTA-cooperative sweep over image batches
@@ -1472,6 +1524,7 @@ struct EmCall {
   void set_w_out(float* w) {
     sa.w_out = w;
     sa2.w_out = w;
+    sa6.w_out = w;
     sa3.w_out = w;
     sa4.w_out = w;
     sa5.w_out = w;
@@ -1509,6 +1562,7 @@ int prepare(const mra_dims* d, int Lw, int l0, double step, const float* y, cons
   }
   c->v4 = false;
   c->v5 = false;
+  c->v6 = false;
   c->vs = false;
   if (yfmt) {  // the batch sweep reads the split format, and the chunked sweep when chosen
     c->v2 = false;
@@ -1553,6 +1607,15 @@ int prepare(const mra_dims* d, int Lw, int l0, double step, const float* y, cons
         c->lay.G = G;
       }
     }
+    // The paired-warp sweep (EM calls only) where it plans, when chosen (it ties the lean sweep at the
+    // benchmark's shape: 0.225 ms per sweep).
+    c->v6 = false;
+    if (allow_v3 && sel.kind == 6 &&
+        plan_v6(Kp1, d->Q, d->L, Lw, nu, dense, di.max_smem_optin, &c->v6p)) {
+      c->v2 = c->v6 = true;  // v2: the warp sweep's tables
+      c->v3 = c->v4 = c->v5 = false;
+      c->lay.G = G;
+    }
     // The split sweep (tensor-core transform) for windows wider than 64 rotations when chosen, and by
     // default for the whole circle (full search: 0.45 ms against the batch sweep's 0.73 ms per step at
     // |k| <= 32, Q = 24, N = 1e5, L = 360 on sharp posteriors).
@@ -1561,11 +1624,11 @@ int prepare(const mra_dims* d, int Lw, int l0, double step, const float* y, cons
     if (allow_v3 && (sel.kind == 5 || split_default) && split_possible(Kp1, d->Q, Lw) &&
         plan_split(Kp1, d->Q, d->L, Lw, di.max_smem_optin, &c->sp)) {
       c->vs = true;
-      c->v2 = c->v3 = c->v4 = c->v5 = false;
+      c->v2 = c->v3 = c->v4 = c->v5 = c->v6 = false;
       c->lay.G = G;
     }
     if (force && ((force->kind == 1 && !c->v2) || (force->kind == 2 && !c->v3) || (force->kind == 3 && !c->v4) ||
-                  (force->kind == 4 && !c->v5) || (force->kind == 5 && !c->vs)))
+                  (force->kind == 4 && !c->v5) || (force->kind == 5 && !c->vs) || (force->kind == 6 && !c->v6)))
       return MRA_EINVAL;
   }
   if (c->vs) {
@@ -1579,6 +1642,10 @@ int prepare(const mra_dims* d, int Lw, int l0, double step, const float* y, cons
     c->sweep = nullptr;
   } else if (c->v3) {
     if (raise_smem_limit(reinterpret_cast<const void*>(c->v3p.fn), c->v3p.smem) != MRA_OK)
+      return MRA_ECUDA;
+    c->sweep = nullptr;
+  } else if (c->v6) {
+    if (raise_smem_limit(reinterpret_cast<const void*>(c->v6p.launch.fn), c->v6p.smem) != MRA_OK)
       return MRA_ECUDA;
     c->sweep = nullptr;
   } else if (c->v2) {
@@ -1647,6 +1714,30 @@ int prepare(const mra_dims* d, int Lw, int l0, double step, const float* y, cons
   v.G = G;
   v.w_out = nullptr;
   v.ctrl = c->ctrl;
+
+  SweepV6Args& v6 = c->sa6;
+  const V6Plan& q6 = c->v6p;
+  v6.y = s.y;
+  v6.shift = shift;
+  v6.N = d->N; v6.K = d->K; v6.M = M; v6.L = d->L; v6.Lw = Lw; v6.NU = nu;
+  v6.ns = q6.ns; v6.slot_bytes = q6.slot_bytes; v6.sp = q6.sp;
+  v6.off_bar = q6.off_bar; v6.off_ring = q6.off_ring; v6.off_tab = q6.off_tab; v6.off_tf = q6.off_tf;
+  v6.off_lr = q6.off_lr; v6.off_units = q6.off_units; v6.off_cb = q6.off_cb; v6.off_xp = q6.off_xp;
+  v6.off_xq = q6.off_xq; v6.off_pv = q6.off_pv; v6.off_sb = q6.off_sb; v6.off_wl = q6.off_wl;
+  v6.two_beta = s.two_beta;
+  v6.l0m = v.l0m;
+  v6.nd = v.nd;
+  v6.nup = nup;
+  v6.x32 = s.x32;
+  v6.tu = v.tu;
+  v6.units = v.units;
+  v6.td = v.td;
+  v6.tf32 = s.tf32;
+  v6.logrho32 = s.logrho32;
+  v6.part = s.part;
+  v6.G = G;
+  v6.w_out = nullptr;
+  v6.ctrl = c->ctrl;
 
   SweepV3Args& w = c->sa3;
   const V3Plan& q3 = c->v3p;
@@ -1807,6 +1898,8 @@ void launch_sweep(const EmCall& c, cudaStream_t st) {
     c.v4p.launch.fn<<<c.lay.G, c.v4p.launch.threads, c.v4p.smem, st>>>(c.sa4);
   else if (c.v3)
     c.v3p.fn<<<c.lay.G, kV3Threads, c.v3p.smem, st>>>(c.sa3);
+  else if (c.v6)
+    c.v6p.launch.fn<<<c.lay.G, c.v6p.launch.threads, c.v6p.smem, st>>>(c.sa6);
   else if (c.v2)
     c.v2p.launch.fn<<<c.lay.G, c.v2p.launch.threads, c.v2p.smem, st>>>(c.sa2);
   else
@@ -2063,7 +2156,7 @@ namespace {
 constexpr int kBatchedImagesPerCta = 64;
 
 // Sweep candidates the autotuner times, in the order of the default preference.
-const SweepSel kTuneCandidates[] = {{4, 0, 0},  {5, 0, 0},  {1, 0, 0},  {2, 16, 2}, {2, 12, 2}, {2, 8, 3},  {2, 8, 2}, {2, 4, 3},
+const SweepSel kTuneCandidates[] = {{6, 0, 0},  {4, 0, 0},  {5, 0, 0},  {1, 0, 0},  {2, 16, 2}, {2, 12, 2}, {2, 8, 3},  {2, 8, 2}, {2, 4, 3},
                                     {2, 4, 2},  {3, 64, 2}, {3, 32, 2}, {3, 16, 2}, {3, 128, 1},
                                     {3, 64, 1}, {3, 32, 1}};
 
@@ -2238,7 +2331,8 @@ MRA_API int mra_em_run_batched(const mra_instance* inst, int32_t n, int32_t tune
     if (c.v2 || c.v3 || c.v4) {
       const int cap = std::max(1, (a.dims.N + kBatchedImagesPerCta - 1) / kBatchedImagesPerCta);
       if (cap < c.lay.G) c.lay.G = cap;
-      c.sa2.G = c.lay.G;  // the warp sweep's partial-sum stride is its launch grid
+      c.sa2.G = c.lay.G;  // the warp sweeps' partial-sum stride is their launch grid
+      c.sa6.G = c.lay.G;
     }
     c.su.x_in = reinterpret_cast<const double2*>(a.x_inout);
     c.su.log_rho_in = a.log_rho_inout;
