@@ -127,3 +127,41 @@ def test_em_run_hl_first_10k_images_of_config5(gpu_lib, sweep):
         xs, lro = st.x, st.log_rho
     print(f"\nbf16 hi/lo, first 10k images, {T} iterations: x error {rel_err(host(x), xs):.2e}; "
           f"x vs truth {O.relerr(host(x), inst.x):.3e}")
+
+
+def test_hl_error_against_unsplit_y_first_10k_config5(gpu_lib):
+    """The error of the storage format itself, on the first 10,000 images of the largest workload
+    (|k| <= 48, Q = 32, L = 720, window 72): EM on the BF16 hi/lo split against the FP64 oracle on the
+    complex64 observations (not on hi + lo), two iterations from the aligned mean.  The split keeps
+    each real value to within 2^-16 of itself, so every result moves by that order: the bounds below
+    are the per-value error times the data's own scale (the mean image norm over ||x|| for x, the
+    mean squared image norm times 2 beta per image for the log-likelihood), with a factor of 4."""
+    mra = gpu_lib
+    c = synth.config(5)
+    inst = synth.make_instance(c["K"], c["Q"], 10_000, c["L"], c["snr"], c["decay"], seed=5001)
+    y64 = synth.c64_round(inst.y)
+    Lw = c["Lw"]
+    x0 = O.align_mean(y64, inst.s, inst.L)
+    lr = np.log(np.full(Lw, 1.0 / Lw))
+    T = 2
+    d = mra.dims(inst.N, inst.K, inst.Q, inst.L, inst.sigma2)
+    prm = mra.em_params(Lw, max_iters=T)
+    ws = mra.workspace(mra.mra_em_workspace_bytes(d, Lw))
+    x, lrd = dev(x0), dev(lr)
+    traj = torch.empty((T, inst.K + 1, inst.Q), dtype=torch.complex128, device="cuda")
+    stats = torch.empty((T, 2), dtype=torch.float64, device="cuda")
+    assert mra.mra_em_run_hl(d, prm, _dev_hl(inst.y), dev(inst.s.astype(np.int32)), x, lrd, stats, traj, ws) == T
+    eps = 2.0 ** -16
+    ynorm = np.linalg.norm(y64.reshape(inst.N, -1), axis=1)
+    xs, lro = x0, lr
+    for t in range(T):
+        st = O.em_step(y64, xs, lro, inst.L, inst.sigma2, Lw=Lw, shifts=inst.s)
+        ex = rel_err(host(traj[t]), st.x)
+        el = abs(float(host(stats)[t, 0]) - st.loglik)
+        bx = 4 * eps * ynorm.mean() / np.linalg.norm(st.x)
+        bl = 4 * eps * (2 / inst.sigma2) * float((ynorm ** 2).sum())
+        print(f"\nbf16 hi/lo vs FP64 oracle on complex64 y, iteration {t + 1}: x rel err {ex:.2e} (bound {bx:.1e}); "
+              f"loglik abs err {el:.3e} of |loglik| {abs(st.loglik):.4e} (rel {el / abs(st.loglik):.2e}, bound {bl:.1e})")
+        assert ex <= bx, (t, ex, bx)
+        assert el <= bl, (t, el, bl)
+        xs, lro = st.x, st.log_rho
