@@ -370,14 +370,15 @@ def main():
     ap.add_argument("--impl", default="gpu")
     ap.add_argument("--no-ttc", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--config", default=str(CFG), choices=("2", "4", "5", "dense", "tm", "fb"),
-                    help="2: Synch-EM at N=1e5 (default); 4: 64 uneven instances in one graph launch; "
+    ap.add_argument("--config", default=str(CFG), choices=("1", "2", "4", "5", "dense", "tm", "fb"),
+                    help="2: Synch-EM at N=1e5 (default); 1: the small Synch-EM workload (N=500, |k|<=10, Q=8, "
+                         "L=72, window 24, SNR 1/10, 20 iterations); 4: 64 uneven instances in one graph launch; "
                          "5: N=1e6 with y in the BF16 hi/lo split; dense: the workload of 2 with the "
                          "denser-resolution window (2L+1 rotations over BW = 36) on off-grid rotations; tm: "
                          "template matching of the images of 2 against the first one; fb: the Fourier-Bessel "
                          "front end on 10,000 images of 129 x 129 pixels")
     args = ap.parse_args()
-    c = dense_config() if args.config == "dense" else synth.config(CFG)
+    c = dense_config() if args.config == "dense" else synth.config(1 if args.config == "1" else CFG)
     if args.impl == "reference":
         return run_reference(args, c)
     if args.config == "4":
@@ -722,10 +723,13 @@ def bench_batched(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"{len(specs)} independent MRA instances, N~U[1000,50000] (sum "
                                    f"{sum(s['N'] for s in specs)}), K~U{{8..40}}, Q=16, L=360, Lw~U{{12..72}}, "
-                                   "SNR log-U[1/100,1/5], 30 EM iterations each, one graph launch",
+                                   "SNR log-U[1/100,1/5], 30 EM iterations each, one graph launch "
+                                   + ("(per-instance launches)" if os.environ.get("MRA_BATCHED") == "graph"
+                                      else "(one persistent kernel for all iterations)"),
                        "parallelism": "single", "l2": "inputs larger than L2"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": None, "peak_source": f"{peak_kind} hbm_gbs", "kernel": "whole batched graph",
+                         "traffic": None, "peak_source": f"{peak_kind} hbm_gbs", "kernel": ("whole batched graph" if os.environ.get("MRA_BATCHED") == "graph"
+                                                  else "k_em_batched (persistent, in the batched graph)"),
                          "algorithmic_bytes_per_launch": ybytes, "avg_launch_ms": launch_ms},
             "autotune_s": t_tune, "graph_launch_ms": launch_ms, "clocks": clk.summary(),
             "gpu_launches": sum(4 + 3 * sp["iters"] + 1 for sp in specs) * args.steps}

@@ -205,13 +205,21 @@ typedef struct {
   double* stats_out;       /* [max_iters][2] (loglik, step) or NULL */
 } mra_instance;
 
-/* Workspace for mra_em_run_batched: the instances' EM workspaces, 256-byte aligned, in order
- * (sizing; no counterpart in the paper). */
+/* Workspace for mra_em_run_batched: the instances' EM workspaces, 256-byte aligned, in order,
+ * then the persistent kernel's instance table and counters (sizing; no counterpart in the paper). */
 MRA_API size_t mra_em_batched_workspace_bytes(const mra_instance* inst, int32_t n);
 
 /* Algorithm Synch-EM's loop for n independent problems of uneven N, K and window
- * in ONE graph launch: each instance's setup, iterations and export are captured as
- * a branch of a single CUDA graph, which is launched once and synchronized.
+ * in ONE graph launch.  Where every instance has rows of 16 coefficients, complex64 y and a window
+ * the lean warp sweep (or the warp sweep's any-window instance) takes, the graph holds the
+ * instances' setups, ONE persistent cooperative kernel for all their iterations, and the exports:
+ * one CTA per SM takes (instance, CTA slot) sweep items from a queue, then the instances'
+ * reductions and updates, with a bounded grid barrier between the phases (a wait that runs out
+ * ends the run with MRA_ETIMEOUT); each instance runs the arithmetic of its own launches of the same
+ * sweep.
+ * Otherwise (or with the environment variable MRA_BATCHED=graph) each instance's setup,
+ * iterations and export are captured as a branch of the graph.  The graph is launched once and
+ * synchronized.
  *   tune        1: run mra_em_autotune first for every shape not yet in the cache
  *   iters_out   host int32[n] iterations performed per instance, or NULL
  *   exec_ms_out host float: device time of the graph launch (CUDA events), or NULL
@@ -427,6 +435,16 @@ MRA_API int mra_ws_status(void* ws, void* stream);
  *   limit_us   1 .. 2,000,000
  *   status_out device int32[1], written by the kernel */
 MRA_API int mra_selftest_wait_timeout(int32_t limit_us, int32_t* status_out, void* stream);
+
+/* Self-test of the grid barrier that separates the iterations of a persistent batched run (no
+ * counterpart in the paper).  One CTA per SM is launched cooperatively and meets at one grid
+ * barrier that CTA 0 never reaches; every waiting CTA gives up after limit_us microseconds (the
+ * batched run's limit is 2 s) and writes MRA_ETIMEOUT to scratch[2].  The waits end by themselves:
+ * no fault, the context stays usable.
+ *   limit_us   1 .. 2,000,000
+ *   scratch    device int32[4], 16-byte aligned: cleared by the call, then the barrier's two words
+ *              and the status (MRA_OK or MRA_ETIMEOUT) */
+MRA_API int mra_selftest_grid_barrier(int32_t limit_us, int32_t* scratch, void* stream);
 
 #ifdef __cplusplus
 }

@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmra.so")
 # one translation unit per sweep family and row width, so that they compile in parallel
-SOURCES = (["em.cu", "sync.cu", "fb.cu"] + [f"sweep_v{v}_q{q}.cu" for v in (2, 3, 5, 6) for q in (1, 2, 3, 4)]
+SOURCES = (["em.cu", "sync.cu", "fb.cu", "batched.cu"] + [f"sweep_v{v}_q{q}.cu" for v in (2, 3, 5, 6) for q in (1, 2, 3, 4)]
            + [f"sweep_v4_q{q}_f{f}.cu" for q in (1, 2, 3, 4) for f in (0, 1)]
            + [f"sweep_tc_q{q}.cu" for q in (1, 2, 3, 4)] + ["sweep_tc_k2.cu"])
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -28,6 +28,7 @@
 #include <mutex>
 #include <vector>
 
+#include "batched.cuh"
 #include "common.cuh"
 #include "tc.cuh"
 
@@ -623,221 +624,20 @@ __global__ void __launch_bounds__(kSweepThreads, 1) k_em_sweep(const SweepArgs a
   }
 }
 
+}  // namespace mra
+
+#include "update_impl.cuh"
+
+namespace mra {
+
+__global__ void __launch_bounds__(kUpdateThreads, 1) k_update(const UpdateArgs a) { update_body(a); }
+
 // tot[col] = sum_g part[col][g] in FP64, one warp per column, fixed summation order.
 __global__ void k_reduce_cols(const double* part, int G, int cols, double* tot, const Ctrl* ctrl) {
   if (ctrl && ctrl->done) return;
   const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
   if (col >= cols) return;
-  const double* p = part + (size_t)col * G;
-  double s = 0.0;
-  for (int g = lane; g < G; g += 32) s += p[g];
-  s = warp_sum_d(s);
-  if (lane == 0) tot[col] = s;
-}
-
-struct UpdateArgs {
-  int N, Kp1, Q, M, L, Lw;
-  double sigma2, beta, gamma, tol;
-  double ll_const;  // N M log(pi sigma2), computed on the host (an FP64 log is slow on the device)
-  int update_rho, max_iters;
-  const double* tot;  // [cols + 8]; tot[cols] keeps sum_j ||y_j||^2 from the first iteration
-  int cols;
-  double2* x64;
-  float2* x32;
-  const double* inv_den;
-  double* rho64;
-  float* logrho32;
-  const double* rhobar64;
-  const double2* tf64;
-  const float2* tf32;
-  Ctrl* ctrl;
-  double* stats;    // [T][2] or null
-  double2* x_traj;  // [T][M] or null
-  double2* x_out;
-  double* log_rho_out;
-  double* loglik_out;
-  double* step_out;
-};
-
-// Block-wide FP64 sum, fixed order; red needs 33 slots.
-__device__ __forceinline__ double block_sum_d(double v, double* red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  v = warp_sum_d(v);
-  __syncthreads();
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  if (warp == 0) {
-    const int nw = (blockDim.x + 31) >> 5;
-    double t = lane < nw ? red[lane] : 0.0;
-    t = warp_sum_d(t);
-    if (lane == 0) red[32] = t;
-  }
-  __syncthreads();
-  return red[32];
-}
-
-// Shared memory of k_update: xn [M] double2, t64 [L] double2, t32 [L] float2, d32 [Kp1] float2,
-// sc [L] float, then xf [M] float4 (a_{t+1}, a_t in FP32) at a 16-byte boundary.
-__host__ __device__ inline int update_xf_offset(int M, int L, int Kp1) {
-  return (16 * M + 28 * L + 8 * Kp1 + 15) & ~15;
-}
-
-__device__ __forceinline__ float block_sum_f(float v, float* red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  v = warp_sum(v);
-  __syncthreads();
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  if (warp == 0) {
-    const int nw = (blockDim.x + 31) >> 5;
-    float t = lane < nw ? red[lane] : 0.f;
-    t = warp_sum(t);
-    if (lane == 0) red[32] = t;
-  }
-  __syncthreads();
-  return red[32];
-}
-
-// One CTA: a_{t+1}, rho_{t+1}, log-likelihood at a_t, step; state update.  FP64 arithmetic is
-// slow on this part (one FP64 warp instruction holds the SM's FP64 pipe for many cycles), so
-// FP64 is kept to the state a_{t+1} = num / (N + sigma^2 Gamma^-1) and the final likelihood
-// sum; norms, rho and the step run in FP32 (the step as a direct sum of squares, which has no
-// cancellation, to relative accuracy ~1e-6).
-constexpr int kUpdateThreads = 512;
-
-__global__ void __launch_bounds__(kUpdateThreads, 1) k_update(const UpdateArgs a) {
-  extern __shared__ __align__(16) unsigned char usmem[];
-  if (a.ctrl->done) return;
-  double2* xn = reinterpret_cast<double2*>(usmem);            // [M]
-  double2* t64 = xn + a.M;                                      // [L]  (unused: kept for layout)
-  float2* t32 = reinterpret_cast<float2*>(t64 + a.L);          // [L]
-  float2* d32 = t32 + a.L;                                      // [Kp1]
-  float* sc = reinterpret_cast<float*>(d32 + a.Kp1);           // [L]
-  float4* xf = reinterpret_cast<float4*>(usmem + update_xf_offset(a.M, a.L, a.Kp1));  // [M]
-  __shared__ float fred[33];
-  __shared__ double ysq_total;
-  __shared__ int ncand;
-  __shared__ int cand[16];
-  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-  const int iter = a.ctrl->iter;
-  if (tid == 0) ncand = 0;
-  for (int l = tid; l < a.L; l += nt) t32[l] = a.tf32[l];
-
-  float nx_old = 0.f;
-  for (int e = tid; e < a.M; e += nt) {
-    const double2 xo = a.x64[e];
-    const double id = a.inv_den[e];
-    const double2 v = make_double2(a.tot[2 * e] * id, a.tot[2 * e + 1] * id);
-    xn[e] = v;
-    xf[e] = make_float4((float)v.x, (float)v.y, (float)xo.x, (float)xo.y);
-    nx_old = fmaf((float)xo.x, (float)xo.x, fmaf((float)xo.y, (float)xo.y, nx_old));
-  }
-  nx_old = block_sum_f(nx_old, fred);
-  if (tid == 0) {
-    double* keep = const_cast<double*>(a.tot) + a.cols;
-    if (iter == 0) keep[0] = a.tot[2 * a.M + a.Lw + 1];
-    ysq_total = keep[0];
-  }
-  // d_k = sum_q conj(a_{t+1,kq}) a_{t,kq} (FP32, ranks the rotations), one warp per row
-  for (int k = warp; k < a.Kp1; k += nw) {
-    float dr = 0.f, di = 0.f;
-    for (int q = lane; q < a.Q; q += 32) {
-      const float4 v = xf[k * a.Q + q];
-      dr = fmaf(v.x, v.z, fmaf(v.y, v.w, dr));
-      di = fmaf(v.x, v.w, fmaf(-v.y, v.z, di));
-    }
-    dr = warp_sum(dr);
-    di = warp_sum(di);
-    if (lane == 0) d32[k] = make_float2(dr, di);
-  }
-  __syncthreads();
-
-  // rho update (one warp: the window is short)
-  if (warp == 0) {
-    if (a.update_rho) {
-      float v = 0.f;
-      for (int l = lane; l < a.Lw; l += 32) v += (float)(a.tot[2 * a.M + l] + a.gamma * a.rhobar64[l]);
-      const float inv = 1.f / warp_sum(v);
-      for (int l = lane; l < a.Lw; l += 32) {
-        const float r = (float)(a.tot[2 * a.M + l] + a.gamma * a.rhobar64[l]) * inv;
-        a.rho64[l] = (double)r;
-        a.logrho32[l] = logf(r);  // -inf for an empty bin
-        if (a.log_rho_out) a.log_rho_out[l] = (double)logf(r);
-      }
-    } else if (a.log_rho_out) {
-      for (int l = lane; l < a.Lw; l += 32) a.log_rho_out[l] = (double)logf((float)a.rho64[l]);
-    }
-  }
-
-  // step: rank the L rotations in FP32
-  float dmag = 0.f;
-  for (int k = 0; k < a.Kp1; ++k) dmag += fabsf(d32[k].x) + fabsf(d32[k].y);
-  float best = -INFINITY;
-  for (int l = tid; l < a.L; l += nt) {
-    float sv = 0.f;
-    int m = 0;
-    for (int k = 0; k < a.Kp1; ++k) {
-      const float2 t = t32[m], dv = d32[k];
-      sv = fmaf(dv.x, t.x, fmaf(-dv.y, t.y, sv));
-      m += l;
-      if (m >= a.L) m -= a.L;
-    }
-    sc[l] = sv;
-    best = fmaxf(best, sv);
-  }
-  best = warp_max(best);
-  if (lane == 0) fred[warp] = best;
-  __syncthreads();
-  float gbest = -INFINITY;
-  for (int w = 0; w < nw; ++w) gbest = fmaxf(gbest, fred[w]);
-  const float thr = gbest - (1e-5f * dmag + 1e-30f);
-  for (int l = tid; l < a.L; l += nt) {
-    if (sc[l] >= thr) {
-      const int slot = atomicAdd(&ncand, 1);
-      if (slot < 16) cand[slot] = l;
-    }
-  }
-  __syncthreads();
-  const int nc = min(ncand, 16);
-  // ||a_{t+1} - e^{-2 pi i k l / L} a_t||^2 of the candidates, summed directly in FP32
-  float step = INFINITY;
-  for (int ci = 0; ci < nc; ++ci) {
-    const int l = cand[ci];
-    float part = 0.f;
-    for (int e = tid; e < a.M; e += nt) {
-      const int k = e / a.Q;
-      const float2 t = t32[(int)(((long long)k * l) % a.L)];
-      const float4 v = xf[e];
-      const float dr = v.x - (v.z * t.x - v.w * t.y);
-      const float di = v.y - (v.z * t.y + v.w * t.x);
-      part = fmaf(dr, dr, fmaf(di, di, part));
-    }
-    step = fminf(step, block_sum_f(part, fred));
-  }
-  step = fmaxf(step, 0.f);
-
-  // state
-  for (int e = tid; e < a.M; e += nt) {
-    const double2 v = xn[e];
-    a.x64[e] = v;
-    a.x32[e] = make_float2((float)v.x, (float)v.y);
-    if (a.x_traj) a.x_traj[(size_t)iter * a.M + e] = v;
-    if (a.x_out) a.x_out[e] = v;
-  }
-  if (tid == 0) {
-    const double ll =
-        a.tot[2 * a.M + a.Lw] - a.beta * ysq_total - (double)a.N * a.beta * (double)nx_old - a.ll_const;
-    if (a.stats) {
-      a.stats[2 * iter] = ll;
-      a.stats[2 * iter + 1] = (double)step;
-    }
-    if (a.loglik_out) *a.loglik_out = ll;
-    if (a.step_out) *a.step_out = (double)step;
-    const int nit = iter + 1;
-    a.ctrl->iter = nit;
-    if ((a.tol > 0.0 && (double)step < a.tol) || nit >= a.max_iters) a.ctrl->done = 1;
-  }
+  reduce_cols_warp(part, G, col, tot);
 }
 
 // em_run epilogue: final state out.
@@ -1057,6 +857,7 @@ bool plan_sweep(int Kp1, int Q, int L, int Lw, int max_smem, SweepPlan* p) {
 struct V2Plan {
   SweepV2Launch launch;
   int nwarps, slot_bytes, sp, smem;
+  int lwc;  // the warp sweep's window mode (see sweep_impl.cuh); 0 for the lean sweep
   int off_ring, off_x, off_tu, off_tf, off_lr, off_units, off_s, off_wl;
 };
 
@@ -1094,6 +895,7 @@ bool plan_v2(int Kp1, int Q, int L, int Lw, int nup, int max_smem, V2Plan* p) {
         p->slot_bytes = slot;
         p->sp = sp;
         p->smem = o;
+        p->lwc = lwc;
         return true;
       }
     }
@@ -1134,6 +936,7 @@ bool plan_v5(int Kp1, int Q, int L, int Lw, int nu, int nup, bool dense, int max
       p->slot_bytes = slot;
       p->sp = sp;
       p->smem = o;
+      p->lwc = 0;
       *cbp_out = cbp;
       *off_xs_out = off_xs;
       return true;
@@ -1535,8 +1338,10 @@ struct EmCall {
 // force: a fixed sweep (the autotuner's candidates); otherwise the environment, then the
 // autotuner's cache, then the default rule below.
 // step: spacing of the window's rotations in grid units (1 = the grid, see window_ok).
+// smem_cap > 0: plan the sweeps for at most that much dynamic shared memory per CTA.
 int prepare(const mra_dims* d, int Lw, int l0, double step, const float* y, const int32_t* shift, void* ws,
-            size_t ws_bytes, EmCall* c, bool allow_v3 = true, int yfmt = 0, const SweepSel* force = nullptr) {
+            size_t ws_bytes, EmCall* c, bool allow_v3 = true, int yfmt = 0, const SweepSel* force = nullptr,
+            int smem_cap = 0) {
   int st = check_dims(d);
   if (st != MRA_OK) return st;
   if (!window_ok(d->L, Lw, l0, step)) return MRA_EINVAL;
@@ -1545,6 +1350,7 @@ int prepare(const mra_dims* d, int Lw, int l0, double step, const float* y, cons
   if (shift && !ptr_ok(shift, 4)) return MRA_EINVAL;
   DevInfo di;
   if ((st = dev_info(&di)) != MRA_OK) return st;
+  if (smem_cap > 0) di.max_smem_optin = std::min(di.max_smem_optin, smem_cap);
   const int G = di.sms;
   // partial sums have room for kMaxCtasPerSm CTAs per SM; lay.G is the launch grid
   c->lay = em_layout(d->N, d->K, d->Q, d->L, Lw, G * kMaxCtasPerSm);
@@ -2208,6 +2014,14 @@ int autotune_impl(const mra_dims* d, const mra_em_params* p, const float* y, int
   return MRA_OK;
 }
 
+// Bytes after the instances' workspaces in a batched workspace: the persistent kernel's instance
+// table, its item counters and its grid barrier.
+size_t batched_extra_bytes(int n, int tmax) {
+  return align256(sizeof(BatchedInst) * (size_t)n) + align256(sizeof(unsigned) * (2 * (size_t)tmax + 2));
+}
+constexpr int kNotPersistent = 1;  // run_batched_persistent: some instance has no persistent body
+constexpr size_t kBatchedTileBytes = (size_t)1 << 20;  // default y bytes per persistent sweep item
+
 // Instantiated graphs of batched runs, keyed by the exact instance list, workspace and
 // device: a repeated call with the same list launches the same graph again.
 struct BatchedGraph {
@@ -2216,6 +2030,7 @@ struct BatchedGraph {
   std::vector<Ctrl*> ctrl;
 };
 std::mutex g_graph_mu;
+std::map<std::vector<unsigned char>, size_t> g_tiles;  // persistent batched runs: the tuned tile
 std::vector<BatchedGraph> g_graphs;  // most recent last
 constexpr size_t kGraphCache = 4;
 
@@ -2232,6 +2047,213 @@ std::vector<unsigned char> batched_key(const mra_instance* inst, int n, const vo
   o += sizeof(ws_bytes);
   memcpy(o, &dev, sizeof(dev));
   return k;
+}
+
+// The persistent path of mra_em_run_batched: every instance runs the lean warp sweep (or, for windows
+// it cannot take, the warp sweep's any-window instance) as items of one cooperative kernel.
+// Returns kNotPersistent if some instance has no body in that kernel.
+int run_batched_persistent(const mra_instance* inst, int n, int tune, int32_t* iters_out, float* exec_ms_out,
+                           unsigned char* base, const std::vector<size_t>& off, cudaStream_t s,
+                           std::vector<unsigned char> key) {
+  key.push_back(1);  // the persistent kernel's graph and tile, not the per-instance graph
+  DevInfo di;
+  int rc = dev_info(&di);
+  if (rc != MRA_OK) return rc;
+  const int cap = di.max_smem_optin - batched_static_smem() - 256;
+  int tmax = 0;
+  for (int i = 0; i < n; ++i) {
+    if (inst[i].y_format != 0) return kNotPersistent;
+    tmax = std::max(tmax, inst[i].prm.max_iters);
+  }
+  std::vector<EmCall> calls(n);
+  std::vector<BatchedInst> hb(n);
+  std::vector<int> gmax(n);
+  int smem = 0;
+  for (int i = 0; i < n; ++i) {
+    const mra_instance& a = inst[i];
+    EmCall& c = calls[i];
+    const SweepSel lean{4, 0, 0}, warp{1, 0, 0};
+    const float* y = static_cast<const float*>(a.y);
+    rc = prepare(&a.dims, a.prm.Lw, a.prm.l0, param_step(&a.prm), y, a.shift, base + off[i], off[i + 1] - off[i], &c,
+                 true, 0, &lean, cap);
+    if (rc == MRA_EINVAL)
+      rc = prepare(&a.dims, a.prm.Lw, a.prm.l0, param_step(&a.prm), y, a.shift, base + off[i], off[i + 1] - off[i],
+                   &c, true, 0, &warp, cap);
+    if (rc == MRA_EINVAL) return kNotPersistent;
+    if (rc != MRA_OK) return rc;
+    const int body = batched_body_id(a.dims.Q, c.v5, (a.dims.K + 1 + 7) / 8, c.sa2.NUP, c.v2p.lwc);
+    if (body < 0) return kNotPersistent;
+    gmax[i] = c.lay.G;
+    c.su.x_in = reinterpret_cast<const double2*>(a.x_inout);
+    c.su.log_rho_in = a.log_rho_inout;
+    c.su.log_rho_bar = a.prm.gamma > 0.0 ? a.prm.log_rho_bar : nullptr;
+    c.su.gamma_a_inv = a.prm.gamma_a_inv;
+    c.ua.gamma = a.prm.gamma;
+    c.ua.tol = a.prm.tol;
+    c.ua.update_rho = a.prm.update_rho ? 1 : 0;
+    c.ua.max_iters = a.prm.max_iters;
+    c.ua.stats = a.stats_out;
+    BatchedInst& bi = hb[i];
+    bi.ua = c.ua;
+    bi.body = body;
+    bi.cols = c.lay.cols;
+    bi.part = c.sa.part;
+    bi.tot = c.tot;
+    bi.ctrl = c.ctrl;
+    smem = std::max(smem, std::max(c.v2p.smem, c.update_smem));
+  }
+  BatchedInst* dinst = reinterpret_cast<BatchedInst*>(base + off[n]);
+  unsigned* counters = reinterpret_cast<unsigned*>(base + off[n] + align256(sizeof(BatchedInst) * (size_t)n));
+  const size_t cnt_bytes = sizeof(unsigned) * (2 * (size_t)tmax + 2);
+  // Tile: about `tile_bytes` of y per sweep item, so that items of instances with long and short rows
+  // take similar times and the CTAs reach each grid barrier together.
+  int items = 0;
+  auto assign = [&](size_t tile_bytes) -> int {
+    items = 0;
+    for (int i = 0; i < n; ++i) {
+      const size_t img = (size_t)calls[i].lay.M * 8;
+      const size_t want = ((size_t)inst[i].dims.N * img + tile_bytes - 1) / tile_bytes;
+      const int slots = (int)std::max<size_t>(1, std::min<size_t>((size_t)gmax[i], want));
+      calls[i].lay.G = slots;
+      calls[i].sa2.G = slots;
+      hb[i].sa = calls[i].sa2;
+      hb[i].slots = slots;
+      hb[i].first_item = items;
+      items += slots;
+    }
+    if (cudaMemcpyAsync(dinst, hb.data(), sizeof(BatchedInst) * (size_t)n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return MRA_ECUDA;
+    return MRA_OK;
+  };
+  size_t tile_bytes = kBatchedTileBytes;
+  if (const char* e = getenv("MRA_BATCHED_TILE_KB")) tile_bytes = (size_t)std::max(16, atoi(e)) * 1024;
+  bool have_tile = false;
+  {
+    std::lock_guard<std::mutex> g(g_graph_mu);
+    auto it = g_tiles.find(key);
+    if (it != g_tiles.end()) tile_bytes = it->second, have_tile = true;
+  }
+  BatchedArgs ba;
+  ba.inst = dinst;
+  ba.n = n;
+  ba.items = items;
+  ba.iters = tmax;
+  ba.counters = counters;
+  ba.barrier = counters + 2 * tmax;
+  ba.status = &calls[0].ctrl->status;  // a grid barrier that gives up reports through the first instance
+  ba.limit_ns = kWaitLimitNs;
+  // the run: counters cleared, setups, the persistent kernel (all iterations, or one for tuning), exports
+  auto record = [&](cudaStream_t st, bool tuning = false) -> int {
+    if (cudaMemsetAsync(counters, 0, cnt_bytes, st) != cudaSuccess) return MRA_ECUDA;
+    for (int i = 0; i < n; ++i) {
+      const int r = launch_setup(calls[i], st);
+      if (r != MRA_OK) return r;
+    }
+    BatchedArgs b2 = ba;
+    b2.items = items;
+    if (tuning) b2.iters = 1;
+    const int r = launch_em_batched(b2, di.sms, smem, st);
+    if (r != MRA_OK) return r;
+    if (tuning) return cudaGetLastError() == cudaSuccess ? MRA_OK : MRA_ECUDA;
+    for (int i = 0; i < n; ++i) {
+      const int Lw = inst[i].prm.Lw, M = calls[i].lay.M;
+      k_export<<<std::max(1, (std::max(M, Lw) + 255) / 256), 256, 0, st>>>(
+          M, Lw, calls[i].su.x64, calls[i].su.rho64, reinterpret_cast<double2*>(inst[i].x_inout), inst[i].log_rho_inout);
+    }
+    return cudaGetLastError() == cudaSuccess ? MRA_OK : MRA_ECUDA;
+  };
+  std::vector<Ctrl*> ctrl(n);
+  for (int i = 0; i < n; ++i) ctrl[i] = calls[i].ctrl;
+  auto finish = [&](cudaEvent_t t0, cudaEvent_t t1) -> int {
+    int r = MRA_OK;
+    if (cudaEventSynchronize(t1) != cudaSuccess) r = MRA_ECUDA;
+    if (r == MRA_OK && exec_ms_out && cudaEventElapsedTime(exec_ms_out, t0, t1) != cudaSuccess) r = MRA_ECUDA;
+    for (int i = 0; i < n && r == MRA_OK; ++i) {
+      Ctrl h{};
+      if (cudaMemcpy(&h, ctrl[i], 16, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        r = MRA_ECUDA;
+        break;
+      }
+      if (iters_out) iters_out[i] = h.iter;
+      if (h.status != MRA_OK) r = h.status;
+    }
+    return r;
+  };
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  if (cudaEventCreate(&t0) != cudaSuccess || cudaEventCreate(&t1) != cudaSuccess) rc = MRA_ECUDA;
+  // the autotuner's part: one iteration of the persistent kernel per tile candidate (no export, so the
+  // instances' x and log rho are not touched), the fastest kept for this instance list
+  if (rc == MRA_OK && tune && !have_tile && !getenv("MRA_BATCHED_TILE_KB")) {
+    float best = -1.f;
+    for (const size_t cand : {(size_t)512 << 10, (size_t)1 << 20, (size_t)2 << 20, (size_t)4 << 20}) {
+      if ((rc = assign(cand)) != MRA_OK) break;
+      float ms = 0.f;
+      for (int rep = 0; rep < 2 && rc == MRA_OK; ++rep) {
+        if (cudaEventRecord(t0, s) != cudaSuccess) rc = MRA_ECUDA;
+        if (rc == MRA_OK) rc = record(s, true);
+        if (rc == MRA_OK && (cudaEventRecord(t1, s) != cudaSuccess || cudaEventSynchronize(t1) != cudaSuccess ||
+                             cudaEventElapsedTime(&ms, t0, t1) != cudaSuccess))
+          rc = MRA_ECUDA;
+      }
+      if (rc == MRA_OK && (best < 0.f || ms < best)) best = ms, tile_bytes = cand;
+    }
+    for (int i = 0; i < n && rc == MRA_OK; ++i) {  // a timed-out tuning run must not pass silently
+      Ctrl h{};
+      if (cudaMemcpy(&h, calls[i].ctrl, 16, cudaMemcpyDeviceToHost) != cudaSuccess) rc = MRA_ECUDA;
+      else if (h.status != MRA_OK) rc = h.status;
+    }
+    if (rc == MRA_OK) {
+      std::lock_guard<std::mutex> g(g_graph_mu);
+      g_tiles[key] = tile_bytes;
+    }
+  }
+  if (rc == MRA_OK) rc = assign(tile_bytes);
+  cudaGraphExec_t cached = nullptr;
+  {
+    std::lock_guard<std::mutex> g(g_graph_mu);
+    for (auto& e : g_graphs)
+      if (e.key == key) cached = e.exec;
+  }
+  if (rc == MRA_OK && !cached) {  // capture the run as a graph (or, if capture fails, launch it directly)
+    cudaStream_t capst = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool captured = false;
+    if (cudaStreamCreateWithFlags(&capst, cudaStreamNonBlocking) == cudaSuccess &&
+        cudaStreamBeginCapture(capst, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      const int r = record(capst);
+      const bool ended = cudaStreamEndCapture(capst, &graph) == cudaSuccess;
+      captured = r == MRA_OK && ended && graph && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+    }
+    cudaGetLastError();  // a failed capture leaves an error behind; the direct launch below decides
+    if (graph) cudaGraphDestroy(graph);
+    if (capst) cudaStreamDestroy(capst);
+    if (captured) {
+      std::lock_guard<std::mutex> g(g_graph_mu);
+      if (g_graphs.size() >= kGraphCache) {
+        cudaGraphExecDestroy(g_graphs.front().exec);
+        g_graphs.erase(g_graphs.begin());
+      }
+      g_graphs.push_back(BatchedGraph{key, exec, ctrl});
+      cached = exec;
+    } else {
+      if (exec) cudaGraphExecDestroy(exec);
+      if (cudaEventRecord(t0, s) != cudaSuccess) rc = MRA_ECUDA;
+      if (rc == MRA_OK) rc = record(s);
+      if (rc == MRA_OK && cudaEventRecord(t1, s) != cudaSuccess) rc = MRA_ECUDA;
+      if (rc == MRA_OK) rc = finish(t0, t1);
+    }
+  }
+  if (rc == MRA_OK && cached) {
+    if (cudaEventRecord(t0, s) != cudaSuccess || cudaGraphLaunch(cached, s) != cudaSuccess ||
+        cudaEventRecord(t1, s) != cudaSuccess)
+      rc = MRA_ECUDA;
+    if (rc == MRA_OK) rc = finish(t0, t1);
+  }
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  return rc;
 }
 
 }  // namespace
@@ -2260,8 +2282,12 @@ MRA_API int mra_em_autotune(const mra_dims* d, const mra_em_params* p, const voi
 MRA_API size_t mra_em_batched_workspace_bytes(const mra_instance* inst, int32_t n) {
   if (!inst || n < 1) return 0;
   size_t total = 0;
-  for (int i = 0; i < n; ++i) total += align256(mra_em_workspace_bytes(&inst[i].dims, std::max(inst[i].prm.Lw, 1)));
-  return total;
+  int tmax = 0;
+  for (int i = 0; i < n; ++i) {
+    total += align256(mra_em_workspace_bytes(&inst[i].dims, std::max(inst[i].prm.Lw, 1)));
+    tmax = std::max(tmax, inst[i].prm.max_iters);
+  }
+  return total + batched_extra_bytes(n, tmax);
 }
 
 MRA_API int mra_em_run_batched(const mra_instance* inst, int32_t n, int32_t tune, int32_t* iters_out,
@@ -2317,6 +2343,15 @@ MRA_API int mra_em_run_batched(const mra_instance* inst, int32_t n, int32_t tune
       const int st = autotune_impl(&a.dims, &a.prm, static_cast<const float*>(a.y), a.y_format, a.shift, a.x_inout,
                                    a.log_rho_inout, base + off[i], off[i + 1] - off[i], s, nullptr);
       if (st != MRA_OK) return st;
+    }
+  }
+  // one persistent kernel for all instances where every instance has a sweep body in it (the
+  // default); MRA_BATCHED=graph keeps the graph of per-instance launches below
+  {
+    const char* bm = getenv("MRA_BATCHED");
+    if (!(bm && strcmp(bm, "graph") == 0)) {
+      const int rc = run_batched_persistent(inst, n, tune, iters_out, exec_ms_out, base, off, s, key);
+      if (rc != kNotPersistent) return rc;
     }
   }
   std::vector<EmCall> calls(n);
@@ -2575,6 +2610,17 @@ MRA_API int mra_selftest_wait_timeout(int32_t limit_us, int32_t* status_out, voi
   k_selftest_wait<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>((unsigned long long)limit_us * 1000ull,
                                                                   reinterpret_cast<int*>(status_out));
   return cudaGetLastError() == cudaSuccess ? MRA_OK : MRA_ECUDA;
+}
+
+MRA_API int mra_selftest_grid_barrier(int32_t limit_us, int32_t* scratch, void* stream) {
+  if (limit_us < 1 || limit_us > 2000000 || !ptr_ok(scratch, 16)) return MRA_EINVAL;
+  DevInfo di;
+  int st = dev_info(&di);
+  if (st != MRA_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  MRA_CUDA_TRY(cudaMemsetAsync(scratch, 0, 4 * sizeof(int32_t), s));
+  return launch_selftest_grid_barrier(di.sms, reinterpret_cast<unsigned*>(scratch), reinterpret_cast<int*>(scratch) + 2,
+                                      (unsigned long long)limit_us * 1000ull, s);
 }
 
 MRA_API int mra_ws_status(void* ws, void* stream) {

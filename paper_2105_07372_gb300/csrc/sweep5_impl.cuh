@@ -48,14 +48,18 @@ __device__ __forceinline__ int mod_l(int a, int L, float invL) {
 }
 
 // NUPC: the unit table's pitch (mirror units padded to 20 or 40), fixed at compile time.
+// A device function of (arguments, CTA index, grid size), as the warp sweep: the batched persistent
+// kernel runs it for one instance's CTA slot; k_sweep_v5 launches it directly.
 template <int QV, int MR, int NUPC>
-__global__ void __launch_bounds__(SweepV5Shape<QV, MR>::kThreads, 1) k_sweep_v5(const SweepV2Args a) {
+__device__ __forceinline__ void sweep_v5_body(const SweepV2Args& a, const int cta_, const int grid_) {
   extern __shared__ __align__(128) unsigned char smem[];
   constexpr int NT = SweepV5Shape<QV, MR>::kThreads;
   constexpr int row4 = QV * 4;  // float4 per row
   constexpr unsigned FULL = 0xffffffffu;
-  if (a.ctrl->done) return;
-  const bool want_ysq = (a.ctrl->iter == 0);
+  // the state (x, log rho, control words) may come from another CTA of a persistent launch: read
+  // it through L2
+  if (__ldcg(&a.ctrl->done)) return;
+  const bool want_ysq = (__ldcg(&a.ctrl->iter) == 0);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nwarps = a.nwarps;
   const int r = lane >> 2, j = lane & 3;
@@ -83,7 +87,7 @@ __global__ void __launch_bounds__(SweepV5Shape<QV, MR>::kThreads, 1) k_sweep_v5(
     float4* xw4w = reinterpret_cast<float4*>(smem + a.off_xs);
     const float4* xg = reinterpret_cast<const float4*>(a.x32);
     for (int i = tid; i < M / 2; i += NT) {
-      const float4 v = xg[i];
+      const float4 v = __ldcg(xg + i);
       x4w[i] = v;
       xw4w[i] = make_float4(v.y, -v.x, v.w, -v.z);
     }
@@ -92,7 +96,7 @@ __global__ void __launch_bounds__(SweepV5Shape<QV, MR>::kThreads, 1) k_sweep_v5(
     float2* tfw = reinterpret_cast<float2*>(smem + a.off_tf);
     for (int i = tid; i < L; i += NT) tfw[i] = a.tf32[i];
     float* lrw = reinterpret_cast<float*>(smem + a.off_lr);
-    for (int i = tid; i < Lw; i += NT) lrw[i] = a.logrho32[i];
+    for (int i = tid; i < Lw; i += NT) lrw[i] = __ldcg(a.logrho32 + i);
     int2* uw = reinterpret_cast<int2*>(smem + a.off_units);
     for (int i = tid; i < NUP; i += NT) uw[i] = a.units[i];
     float* wl0 = reinterpret_cast<float*>(smem + a.off_wl);
@@ -123,7 +127,7 @@ __global__ void __launch_bounds__(SweepV5Shape<QV, MR>::kThreads, 1) k_sweep_v5(
     tdr[m] = (k < Kp1 && j < a.nd) ? a.td[k * a.nd + j] : make_float2(0.f, 0.f);
   }
 
-  const int gw = blockIdx.x * nwarps + warp, GW = gridDim.x * nwarps;
+  const int gw = cta_ * nwarps + warp, GW = grid_ * nwarps;
   const uint32_t img_bytes = (uint32_t)M * 8u;
   unsigned char* const wring = ring + (size_t)warp * 2 * a.slot_bytes;
   uint64_t* mybar = bar + 2 * warp;
@@ -470,6 +474,7 @@ __global__ void __launch_bounds__(SweepV5Shape<QV, MR>::kThreads, 1) k_sweep_v5(
 
   // ---- CTA combination: per-warp FP32 sums through the (now idle) ring, then FP64 partials
   __syncthreads();
+  if (tid < 2 * nwarps) mbar_inval(&bar[tid]);  // the CTA may run another sweep on this memory next
   float4* red4 = reinterpret_cast<float4*>(ring);  // [NT/32][M/2]
   const int half = M / 2;
 #pragma unroll
@@ -481,7 +486,7 @@ __global__ void __launch_bounds__(SweepV5Shape<QV, MR>::kThreads, 1) k_sweep_v5(
     }
   }
   __syncthreads();
-  const int G = a.G, cta = blockIdx.x;
+  const int G = a.G, cta = cta_;
   const float* redf = reinterpret_cast<const float*>(ring);
   for (int col = tid; col < 2 * M; col += NT) {
     float sum = 0.f;
@@ -503,6 +508,11 @@ __global__ void __launch_bounds__(SweepV5Shape<QV, MR>::kThreads, 1) k_sweep_v5(
     a.part[(size_t)(2 * M + Lw) * G + cta] = t0;
     a.part[(size_t)(2 * M + Lw + 1) * G + cta] = t1;
   }
+}
+
+template <int QV, int MR, int NUPC>
+__global__ void __launch_bounds__(SweepV5Shape<QV, MR>::kThreads, 1) k_sweep_v5(const SweepV2Args a) {
+  sweep_v5_body<QV, MR, NUPC>(a, blockIdx.x, gridDim.x);
 }
 
 }  // namespace mra

@@ -54,12 +54,17 @@ __device__ __forceinline__ int mod_small(int a, int L, float invL) {
 // from global memory (windows whose table does not fit in shared memory next to the rings).
 // The fixed counts let the per-image loops over the window and its units unroll (the unit
 // table is then 4 kUC wide).
+//
+// The sweep is a device function of (arguments, CTA index, grid size), so that the batched
+// persistent kernel can run it for one instance's CTA slot; k_sweep_v2 launches it directly.
 template <int QV, int MR, int IPW, int LWC>
-__global__ void __launch_bounds__(SweepV2Shape<QV, MR, IPW>::kThreads, 1) k_sweep_v2(const SweepV2Args a) {
+__device__ __forceinline__ void sweep_v2_body(const SweepV2Args& a, const int cta_, const int grid_) {
   extern __shared__ __align__(128) unsigned char smem[];
   constexpr int NT = SweepV2Shape<QV, MR, IPW>::kThreads;
-  if (a.ctrl->done) return;
-  const bool want_ysq = (a.ctrl->iter == 0);
+  // the state (x, log rho, control words) may come from another CTA of a persistent launch: read
+  // it through L2
+  if (__ldcg(&a.ctrl->done)) return;
+  const bool want_ysq = (__ldcg(&a.ctrl->iter) == 0);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nwarps = a.nwarps;  // <= NT/32 (warps beyond it only join the final combination)
   const int r = lane >> 2, j = lane & 3;
@@ -95,7 +100,7 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR, IPW>::kThreads, 1) k_swee
   {
     float4* x4w = reinterpret_cast<float4*>(smem + a.off_x);
     const float4* xg = reinterpret_cast<const float4*>(a.x32);
-    for (int i = tid; i < M / 2; i += NT) x4w[i] = xg[i];
+    for (int i = tid; i < M / 2; i += NT) x4w[i] = __ldcg(xg + i);
     if constexpr (LWC >= 0) {
       float2* tuw = reinterpret_cast<float2*>(smem + a.off_tu);
       for (int i = tid; i < Kp1 * NUP; i += NT) tuw[i] = a.tu[i];
@@ -103,7 +108,7 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR, IPW>::kThreads, 1) k_swee
     float2* tfw = reinterpret_cast<float2*>(smem + a.off_tf);
     for (int i = tid; i < L; i += NT) tfw[i] = a.tf32[i];
     float* lrw = reinterpret_cast<float*>(smem + a.off_lr);
-    for (int i = tid; i < Lw; i += NT) lrw[i] = a.logrho32[i];
+    for (int i = tid; i < Lw; i += NT) lrw[i] = __ldcg(a.logrho32 + i);
     int2* uw = reinterpret_cast<int2*>(smem + a.off_units);
     for (int i = tid; i < NUP; i += NT) uw[i] = a.units[i];
     float* wl0 = reinterpret_cast<float*>(smem + a.off_wl);
@@ -113,7 +118,7 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR, IPW>::kThreads, 1) k_swee
   }
   __syncthreads();
 
-  const int gw = blockIdx.x * nwarps + warp, GW = gridDim.x * nwarps;
+  const int gw = cta_ * nwarps + warp, GW = grid_ * nwarps;
   constexpr bool kDyn = LWC <= 0 && IPW == 1;  // images handed out one at a time
   int held0 = gw, held1 = gw + GW;              // kDyn: the image in ring stage 0 / 1 (>= N: none)
   const uint32_t img_bytes = (uint32_t)M * 8u;
@@ -745,7 +750,7 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR, IPW>::kThreads, 1) k_swee
   }
   if constexpr (kDyn) {  // the last warp out clears the counters (every fetch of this launch is done)
     if (warp < nwarps && lane == 0 &&
-        atomicAdd(&a.ctrl->sched[1], 1u) == (unsigned)(gridDim.x * nwarps) - 1u) {
+        atomicAdd(&a.ctrl->sched[1], 1u) == (unsigned)(grid_ * nwarps) - 1u) {
       atomicExch(&a.ctrl->sched[0], 0u);
       atomicExch(&a.ctrl->sched[1], 0u);
     }
@@ -753,6 +758,7 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR, IPW>::kThreads, 1) k_swee
 
   // ---- CTA combination: per-warp FP32 sums through the (now idle) ring, then FP64 partials
   __syncthreads();
+  if (tid < 2 * nwarps) mbar_inval(&bar[tid]);  // the CTA may run another sweep on this memory next
   float4* red4 = reinterpret_cast<float4*>(ring);  // [NT/32][M/2]
   const int half = M / 2;
 #pragma unroll
@@ -764,7 +770,7 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR, IPW>::kThreads, 1) k_swee
     }
   }
   __syncthreads();
-  const int G = a.G, cta = blockIdx.x;
+  const int G = a.G, cta = cta_;
   const float* redf = reinterpret_cast<const float*>(ring);
   for (int col = tid; col < 2 * M; col += NT) {
     float sum = 0.f;
@@ -786,6 +792,11 @@ __global__ void __launch_bounds__(SweepV2Shape<QV, MR, IPW>::kThreads, 1) k_swee
     a.part[(size_t)(2 * M + Lw) * G + cta] = t0;
     a.part[(size_t)(2 * M + Lw + 1) * G + cta] = t1;
   }
+}
+
+template <int QV, int MR, int IPW, int LWC>
+__global__ void __launch_bounds__(SweepV2Shape<QV, MR, IPW>::kThreads, 1) k_sweep_v2(const SweepV2Args a) {
+  sweep_v2_body<QV, MR, IPW, LWC>(a, blockIdx.x, gridDim.x);
 }
 
 }  // namespace mra

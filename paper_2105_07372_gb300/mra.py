@@ -93,6 +93,7 @@ _SIGS = {
     "mra_ws_status": (c_int, [c_void_p, c_void_p]),
     "mra_em_step_noalloc_status": (c_int, [c_void_p]),
     "mra_selftest_wait_timeout": (c_int, [c_int32, c_void_p, c_void_p]),
+    "mra_selftest_grid_barrier": (c_int, [c_int32, c_void_p, c_void_p]),
 }
 
 
@@ -396,4 +397,10 @@ def mra_em_step_noalloc_status(stream=None) -> int:
 def mra_selftest_wait_timeout(limit_us, status_out, stream=None):
     """Run the bounded-wait self-test; status_out (device int32[1]) receives MRA_ETIMEOUT (-4) or MRA_OK."""
     _check("mra_selftest_wait_timeout", load().mra_selftest_wait_timeout(int(limit_us), _p(status_out),
+                                                                         _stream(stream)))
+
+
+def mra_selftest_grid_barrier(limit_us, scratch, stream=None):
+    """Run the grid-barrier self-test; scratch (device int32[4]) receives the status in scratch[2]."""
+    _check("mra_selftest_grid_barrier", load().mra_selftest_grid_barrier(int(limit_us), _p(scratch),
                                                                          _stream(stream)))

@@ -122,3 +122,87 @@ def test_batched_workload_list_small_n(gpu_lib):
         ws1 = mra.workspace(mra.mra_em_workspace_bytes(d, Lw))
         mra.mra_em_run(d, prm, it["y"], it["shift"], x1, lr1, None, None, ws1)
         assert rel_err(host(it["x"]), host(x1)) <= TOL_SAME
+
+
+# rows of 16 coefficients only: the persistent kernel takes every instance (the lean sweep for windows
+# of up to 32 mirror units, the warp sweep's any-window instance for the whole circle and wider windows)
+SHAPES16 = [
+    dict(K=12, N=1300, L=90, Lw=13, shifts=True, tol=0.0),
+    dict(K=20, N=700, L=120, Lw=45, shifts=True, tol=0.0),
+    dict(K=30, N=150, L=72, Lw=72, shifts=False, tol=0.0),
+    dict(K=40, N=2100, L=360, Lw=60, shifts=True, tol=0.0),
+    dict(K=8, N=90, L=40, Lw=9, shifts=True, tol=0.0),
+    dict(K=10, N=500, L=60, Lw=15, shifts=True, tol=1e3),  # stops after its first iteration
+    dict(K=16, N=3000, L=180, Lw=70, shifts=True, tol=0.0),
+]
+
+
+def test_persistent_batched_run_matches_graph_and_oracle(gpu_lib, monkeypatch):
+    """The persistent kernel (default for these shapes) against the graph of per-instance launches
+    (MRA_BATCHED=graph) from the same start, and against the FP64 oracle's trajectory; one instance
+    stops by its tolerance after one iteration while the others go on."""
+    mra = gpu_lib
+    T = 3
+
+    def run(graph):
+        if graph:
+            monkeypatch.setenv("MRA_BATCHED", "graph")
+        else:
+            monkeypatch.delenv("MRA_BATCHED", raising=False)
+        probs, items = [], []
+        for i, sh in enumerate(SHAPES16):
+            p = _problem(mra, dict(sh, Q=16), 100 + i, T)
+            p["prm"] = mra.em_params(p["Lw"], l0=p["l0"], max_iters=T, tol=sh["tol"])
+            probs.append(p)
+            items.append(dict(d=p["d"], prm=p["prm"], y=dev_y(p["y64"]), x=dev(p["x0"]), log_rho=dev(p["lr"]),
+                              shift=dev(p["s"].astype(np.int32)) if p["s"] is not None else None,
+                              stats=torch.full((T, 2), np.nan, dtype=torch.float64, device="cuda")))
+        arr = mra.instances(items)
+        ws = mra.workspace(mra.mra_em_batched_workspace_bytes(arr))
+        iters, ms = mra.mra_em_run_batched(arr, ws, tune=False)
+        return probs, items, iters, ms
+
+    probs, pers, it_p, ms_p = run(False)
+    _, graph, it_g, _ = run(True)
+    want = [1 if sh["tol"] > 0 else T for sh in SHAPES16]
+    assert it_p == want and it_g == want and ms_p > 0
+    for p, a, b, n in zip(probs, pers, graph, want):
+        assert rel_err(host(a["x"]), host(b["x"])) <= TOL_SAME
+        np.testing.assert_allclose(np.exp(host(a["log_rho"])), np.exp(host(b["log_rho"])), rtol=0, atol=TOL_SAME)
+        np.testing.assert_allclose(host(a["stats"])[:n, 0], host(b["stats"])[:n, 0], rtol=TOL_SAME)
+        xs, lrs = p["x0"], p["lr"]
+        for t in range(n):
+            st = O.em_step(p["y64"], xs, lrs, p["inst"].L, p["inst"].sigma2, Lw=p["Lw"], l0=p["l0"], shifts=p["s"])
+            assert abs(host(a["stats"])[t, 0] - st.loglik) <= 1e-6 * abs(st.loglik) + 1e-3, (t, st.loglik)
+            xs, lrs = st.x, st.log_rho
+        assert rel_err(host(a["x"]), xs) <= TOL_X * n, rel_err(host(a["x"]), xs)
+
+
+def test_persistent_batched_run_repeats_from_its_graph(gpu_lib):
+    """A second call with the same instance list (same tensors, reset to the same start) launches the
+    cached graph of the persistent kernel and gives the same results: bit for bit where the lean warp
+    sweep runs (fixed image order), to TOL_SAME where the warp sweep's any-window instance hands the
+    images out to its warps as they become free (the whole circle here: FP32 sums in varying order)."""
+    mra = gpu_lib
+    T = 2
+    probs, items = [], []
+    for i, sh in enumerate(SHAPES16[:4]):
+        p = _problem(mra, dict(sh, Q=16), 200 + i, T)
+        probs.append(p)
+        items.append(dict(d=p["d"], prm=p["prm"], y=dev_y(p["y64"]), x=dev(p["x0"]), log_rho=dev(p["lr"]),
+                          shift=dev(p["s"].astype(np.int32)) if p["s"] is not None else None))
+    arr = mra.instances(items)
+    ws = mra.workspace(mra.mra_em_batched_workspace_bytes(arr))
+    outs = []
+    for rep in range(2):
+        for p, it in zip(probs, items):
+            it["x"].copy_(dev(p["x0"]))
+            it["log_rho"].copy_(dev(p["lr"]))
+        iters, _ = mra.mra_em_run_batched(arr, ws, tune=False)
+        assert iters == [T] * 4
+        outs.append([host(it["x"]).copy() for it in items])
+    for sh, a, b in zip(SHAPES16[:4], *outs):
+        if sh["Lw"] < sh["L"] and sh["Lw"] <= 60:
+            np.testing.assert_array_equal(a, b)
+        else:
+            assert rel_err(a, b) <= TOL_SAME
