@@ -443,8 +443,8 @@ def main():
             sweep_times.extend(list(sweep_ms)[:n])
         return n
 
-    # kernels of ours per step: sync 4, prior hist 5, fit 1, align 4, em_run 2 + 3 T + 1
-    launches_per_step = 4 + 5 + 1 + 4 + 2 + 3 * T + 1
+    # kernels of ours per step: sync 4, prior hist 5, fit 1, align 4, em_run 2 + 2 T + 1 (sweep and finalize)
+    launches_per_step = 4 + 5 + 1 + 4 + 2 + 2 * T + 1
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         step(False)
@@ -732,7 +732,8 @@ def bench_batched(args):
                                                   else "k_em_batched (persistent, in the batched graph)"),
                          "algorithmic_bytes_per_launch": ybytes, "avg_launch_ms": launch_ms},
             "autotune_s": t_tune, "graph_launch_ms": launch_ms, "clocks": clk.summary(),
-            "gpu_launches": sum(4 + 3 * sp["iters"] + 1 for sp in specs) * args.steps}
+            "gpu_launches": (sum(4 + 2 * sp["iters"] + 1 for sp in specs) if os.environ.get("MRA_BATCHED") == "graph"
+                             else sum(4 + 1 for sp in specs) + 1) * args.steps}
     print(json.dumps(line), flush=True)
 
 
@@ -795,7 +796,7 @@ def bench_bf16(args):
                          "sweep_choice": {"kind": tuned[0], "batch": tuned[1], "stages_or_ctas": tuned[2]},
                          "algorithmic_bytes_per_launch": ybytes,
                          "avg_launch_ms": sw * 1e3},
-            "clocks": clk.summary(), "gpu_launches": (2 + 3 * T + 1) * args.steps}
+            "clocks": clk.summary(), "gpu_launches": (2 + 2 * T + 1) * args.steps}
     print(json.dumps(line), flush=True)
 
 

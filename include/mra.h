@@ -173,7 +173,7 @@ MRA_API int mra_em_run_hl(const mra_dims* dims, const mra_em_params* prm, const 
 
 /* (No counterpart in the paper.)  Times every EM sweep that can take the problem
  * (the paired-warp sweep, two warps per image, and the lean warp sweep for grid windows of at
- * most 32 mirror units that are not the whole circle; the split sweep with its tcgen05 window transform for windows of 65 to 512 rotations
+ * most 32 mirror units that are not the whole circle; the split sweep with its tcgen05 window transform for windows of 65 to 1024 rotations
  * and K+1 <= 48 (the default on the whole circle); the warp-per-image sweep; the batch sweep at
  * 16, 12, 8 or 4 images per batch and
  * 2 or 3 ring stages; the

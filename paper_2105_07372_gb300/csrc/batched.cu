@@ -8,7 +8,7 @@
 //             images of slot g) exactly as a launch of that sweep with grid slots_i would, and
 //             leaves the slot's FP64 partials in the instance's workspace
 //   finalize  items = instances: the column reduction in the fixed order of k_reduce_cols and the
-//             update of k_update (a_{t+1}, rho_{t+1}, log-likelihood, step, stopping rule)
+//             update of k_finalize (a_{t+1}, rho_{t+1}, log-likelihood, step, stopping rule)
 // so the arithmetic is that of the instance's own launches of the same sweep with grid slots_i (bit
 // for bit where the lean sweep runs; the any-window warp sweep hands images out to its warps as they
 // become free, so its FP32 sums vary in order from run to run).  Instances that have

@@ -150,7 +150,8 @@ struct Ctrl {
   int done;    // em_run: converged flag, makes the remaining kernels of a graph return at entry
   int iter;    // em_run: iterations performed
   unsigned sched[2];  // wide-window warp sweep: next image and finished warps (zero between launches)
-  int pad[59];
+  unsigned fin;       // finalize: CTAs done with their columns (zero between launches)
+  int pad[58];
 };
 
 __host__ __device__ inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
@@ -171,9 +172,10 @@ struct EmLayout {
 
 __host__ __device__ inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 // The split sweep's extra workspace (correlation and weight buffers, the B operand) exists for
-// windows it can take: wider than 64 rotations, at most 512, K+1 <= 48.
+// windows it can take: wider than 64 rotations, at most 1024 (two passes of 512 tensor-memory
+// columns beyond 512), K+1 <= 48.
 __host__ __device__ inline bool split_possible(int Kp1, int Q, int Lw) {
-  return Lw > 64 && Lw <= 512 && Kp1 <= 48 && Q % 8 == 0 && Q / 8 <= 4;
+  return Lw > 64 && Lw <= 1024 && Kp1 <= 48 && Q % 8 == 0 && Q / 8 <= 4;
 }
 
 inline EmLayout em_layout(int N, int K, int Q, int L, int Lw, int G) {
@@ -382,7 +384,8 @@ struct SplitArgs {
   int NP, ncols;                    // transform: window columns padded to 16, tensor-memory columns
   int k2_off_b, k2_off_ah, k2_off_al, k2_off_lr, k2_off_tf, k2_off_wt, k2_off_ll;
   int k2_off_cs;                    // transform: the tile's c (then W) rows [128][Kp1] float2
-  int k2_off_td;                    // transform: the distance-unit table, or 0 (read from global)
+  int k2_off_td;                    // transform: the distance-unit table's first k2_ndp distances, or 0
+  int k2_ndp;                       // distances of the table in shared memory (the rest read from global)
   int k2_off_info;                  // transform: per-image peaks, distances, scales and bounds
   int wrap, l0m, nd, twp;
   float two_beta;

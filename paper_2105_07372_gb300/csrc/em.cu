@@ -142,6 +142,7 @@ __global__ void k_setup(const SetupArgs a) {
     a.ctrl->iter = 0;
     a.ctrl->sched[0] = 0;
     a.ctrl->sched[1] = 0;
+    a.ctrl->fin = 0;
   }
 }
 
@@ -630,7 +631,28 @@ __global__ void __launch_bounds__(kSweepThreads, 1) k_em_sweep(const SweepArgs a
 
 namespace mra {
 
-__global__ void __launch_bounds__(kUpdateThreads, 1) k_update(const UpdateArgs a) { update_body(a); }
+// One EM finalize in one launch: every CTA reduces its share of the columns (a warp per column, the
+// fixed order of k_reduce_cols, so the totals are bit for bit the same), and the last CTA to finish
+// (a ticket in the control block, taken after a fence) runs the update on the totals, which it reads
+// through L2, and clears the ticket for the next launch.
+__global__ void __launch_bounds__(kUpdateThreads, 1) k_finalize(const UpdateArgs a, const double* part, int G,
+                                                                int cols) {
+  if (__ldcg(&a.ctrl->done)) return;
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int col = blockIdx.x * nw + warp; col < cols; col += gridDim.x * nw)
+    reduce_cols_warp(part, G, col, const_cast<double*>(a.tot));
+  __shared__ int last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(&a.ctrl->fin, 1u) == gridDim.x - 1u;
+    if (last) __threadfence();
+  }
+  __syncthreads();
+  if (!last) return;
+  update_body(a);
+  if (threadIdx.x == 0) atomicExch(&a.ctrl->fin, 0u);
+}
 
 // tot[col] = sum_g part[col][g] in FP64, one warp per column, fixed summation order.
 __global__ void k_reduce_cols(const double* part, int G, int cols, double* tot, const Ctrl* ctrl) {
@@ -1002,6 +1024,7 @@ struct SplitPlan {
   int off_ring, off_x, off_xs, off_tf;
   int k2_off_b, k2_off_ah, k2_off_al, k2_off_lr, k2_off_tf, k2_off_wt, k2_off_ll, k2_off_cs, k2_off_td;
   int k2_off_info;
+  int k2_ndp;
 };
 bool plan_split(int Kp1, int Q, int L, int Lw, int max_smem, SplitPlan* p) {
   if (!split_possible(Kp1, Q, Lw)) return false;
@@ -1013,8 +1036,8 @@ bool plan_split(int Kp1, int Q, int L, int Lw, int max_smem, SplitPlan* p) {
   if (!p->fns.corr || !p->trans) return false;
   p->KA = (2 * p->KP + 15) / 16 * 16;
   p->NP = (Lw + 15) / 16 * 16;
-  p->ncols = 32;
-  while (p->ncols < p->NP) p->ncols *= 2;
+  p->ncols = 32;  // tensor-memory columns: the window's, at most 512 (wider windows take two passes)
+  while (p->ncols < p->NP && p->ncols < 512) p->ncols *= 2;
   const int M = Kp1 * Q;
   p->slot_bytes = al16(M * 8);
   const int maxw = kTcStreamThreads / 32;
@@ -1045,13 +1068,18 @@ bool plan_split(int Kp1, int Q, int L, int Lw, int max_smem, SplitPlan* p) {
   p->k2_off_cs = o; o += al16(kTcTile * Kp1 * 8);
   p->k2_off_info = o; o += al16(kTcTile * 4 * 14);  // [4][128] maxima, indices, distances; scales; bounds
   if (o + 1024 > max_smem) return false;
+  // the distance-unit table in shared memory: whole, or its first distances (multiples of 16; those
+  // near each image's peak, where pass 2 works) with the rest read from global memory
   const int nd = Lw == L ? L / 2 + 1 : Lw;
-  const int tdb = al16(Kp1 * nd * 8);
-  if (o + tdb + 1024 <= max_smem) {
+  int ndp = std::min(nd, std::max(0, (max_smem - 1024 - o) & ~15) / (Kp1 * 8));
+  if (ndp < nd) ndp = ndp / 16 * 16;
+  if (ndp >= 16) {
     p->k2_off_td = o;
-    o += tdb;
+    p->k2_ndp = ndp;
+    o += al16(Kp1 * ndp * 8);
   } else {
     p->k2_off_td = 0;
+    p->k2_ndp = 0;
   }
   p->smem2 = std::max(o, 116 * 1024);
   return p->smem2 + 1024 <= max_smem;
@@ -1306,6 +1334,7 @@ struct EmCall {
   Ctrl* ctrl;
   double* tot;
   int reduce_blocks;
+  int fin_blocks;  // CTAs of k_finalize
   int update_smem;
   bool v2;  // warp-per-image sweep (rows of Q a multiple of 8) instead of the tile sweep
   bool v5;  // with v2: the lean warp sweep's kernel and plan
@@ -1426,7 +1455,7 @@ int prepare(const mra_dims* d, int Lw, int l0, double step, const float* y, cons
     // default for the whole circle (full search: 0.45 ms against the batch sweep's 0.73 ms per step at
     // |k| <= 32, Q = 24, N = 1e5, L = 360 on sharp posteriors).
     c->vs = false;
-    const bool split_default = sel.kind == 0 && !dense && Lw == d->L;
+    const bool split_default = sel.kind == 0 && !dense && Lw == d->L && Lw <= 512;
     if (allow_v3 && (sel.kind == 5 || split_default) && split_possible(Kp1, d->Q, Lw) &&
         plan_split(Kp1, d->Q, d->L, Lw, di.max_smem_optin, &c->sp)) {
       c->vs = true;
@@ -1599,6 +1628,7 @@ int prepare(const mra_dims* d, int Lw, int l0, double step, const float* y, cons
   x5.k2_off_b = q5.k2_off_b; x5.k2_off_ah = q5.k2_off_ah; x5.k2_off_al = q5.k2_off_al; x5.k2_off_lr = q5.k2_off_lr;
   x5.k2_off_tf = q5.k2_off_tf; x5.k2_off_wt = q5.k2_off_wt; x5.k2_off_ll = q5.k2_off_ll;
   x5.k2_off_cs = q5.k2_off_cs; x5.k2_off_td = q5.k2_off_td; x5.k2_off_info = q5.k2_off_info;
+  x5.k2_ndp = q5.k2_ndp;
   x5.wrap = !dense && Lw == d->L ? 1 : 0;
   x5.l0m = ((l0 % d->L) + d->L) % d->L;
   x5.nd = x5.wrap ? d->L / 2 + 1 : Lw;
@@ -1651,9 +1681,11 @@ int prepare(const mra_dims* d, int Lw, int l0, double step, const float* y, cons
   up.stats = nullptr; up.x_traj = nullptr; up.x_out = nullptr; up.log_rho_out = nullptr;
   up.loglik_out = nullptr; up.step_out = nullptr;
   c->update_smem = update_xf_offset(M, d->L, Kp1) + 16 * M;
-  if (c->update_smem > 48 * 1024 && raise_smem_limit(reinterpret_cast<const void*>(k_update), c->update_smem) != MRA_OK)
+  if (c->update_smem > 48 * 1024 && raise_smem_limit(reinterpret_cast<const void*>(k_finalize), c->update_smem) != MRA_OK)
     return MRA_ECUDA;
   c->reduce_blocks = (L_.cols + 7) / 8;
+  // about one column per warp, in one wave (the finalize's CTAs hold the update's shared memory)
+  c->fin_blocks = std::max(1, std::min(G, (L_.cols + 15) / 16));
   return MRA_OK;
 }
 
@@ -1717,8 +1749,7 @@ int launch_iteration(const EmCall& c, cudaStream_t st, cudaEvent_t ev0 = nullptr
   if (ev0 && cudaEventRecordWithFlags(ev0, st, cudaEventRecordExternal) != cudaSuccess) return MRA_ECUDA;
   launch_sweep(c, st);
   if (ev1 && cudaEventRecordWithFlags(ev1, st, cudaEventRecordExternal) != cudaSuccess) return MRA_ECUDA;
-  k_reduce_cols<<<c.reduce_blocks, 256, 0, st>>>(c.sa.part, c.lay.G, c.lay.cols, c.tot, c.ctrl);
-  k_update<<<1, kUpdateThreads, c.update_smem, st>>>(c.ua);
+  k_finalize<<<c.fin_blocks, kUpdateThreads, c.update_smem, st>>>(c.ua, c.sa.part, c.lay.G, c.lay.cols);
   return cudaGetLastError() == cudaSuccess ? MRA_OK : MRA_ECUDA;
 }
 

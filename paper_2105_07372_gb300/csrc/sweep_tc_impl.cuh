@@ -7,7 +7,9 @@
 //                 pass 1  S_jl = Re sum_k c_jk e^{-i k theta_l} for every window rotation as one
 //                         tcgen05 MMA per 16 columns of K: A = [c.re, c.im] rows in FP16 (hi + lo
 //                         split after a per-image power-of-two scale), B = [cos, sin] of the window
-//                         rotations in FP16, FP32 accumulation in tensor memory.  Each thread reads its
+//                         rotations in FP16, FP32 accumulation in tensor memory (windows of more than
+//                         512 rotations in passes of 512 columns, the earlier ones computed again for
+//                         the cut).  Each thread reads its
 //                         row, finds the peak l* and the distance D beyond which every log-weight is
 //                         more than 40 below it, widened by twice a bound on pass 1's rounding
 //                         (FP16 twiddles: 2^-12 per entry, times sum_k |c.re| + |c.im|)
@@ -201,14 +203,18 @@ __global__ void __launch_bounds__(kTcTransThreads, 1) k_tc_trans(const SplitArgs
     for (int i = tid; i < NP * KA / 8; i += NT) bw[i] = bg[i];
     for (int i = tid; i < Lw; i += NT) lrs[i] = a.logrho32[i], wts[i] = 0ull;
     for (int i = tid; i < L; i += NT) tfs[i] = a.tf32[i];
-    if (tds)
-      for (int i = tid; i < Kp1 * a.nd; i += NT) tds[i] = a.td[i];
+    if (tds)  // the first k2_ndp distances of every row (the ones near each image's peak)
+      for (int i = tid; i < Kp1 * a.k2_ndp; i += NT) {
+        const int k = i / a.k2_ndp;
+        tds[i] = a.td[k * a.nd + (i - k * a.k2_ndp)];
+      }
     if (tid == 0) {
       mbar_init(bar, 1);
       fence_barrier_init();
     }
   }
-  const float2* td = tds ? tds : a.td;
+  const int ndp = tds ? a.k2_ndp : 0;
+  auto tdat = [&](int k, int d) -> float2 { return d < ndp ? tds[k * ndp + d] : a.td[k * a.nd + d]; };
   if (warp == 0) {
     tc::tmem_alloc(tbase_s, (uint32_t)a.ncols);
     tc::tmem_relinquish();
@@ -219,8 +225,6 @@ __global__ void __launch_bounds__(kTcTransThreads, 1) k_tc_trans(const SplitArgs
   const uint32_t tbase = *tbase_s;
   const int qtr = warp & 3, cblk = warp >> 2;
   const uint32_t trow = tbase + ((uint32_t)(qtr * 32) << 16);  // this warp's lanes
-  const int NQ = ((NP + 3) / 4 + 15) / 16 * 16;                // columns per block
-  const int c_lo = cblk * NQ, c_hi = min(NP, c_lo + NQ);
   const uint32_t ah_addr = smem_addr(Ah), al_addr = smem_addr(Al), b_addr = smem_addr(Bs);
   const int nd1 = a.nd - 1;
   // pass 2: quad per image
@@ -271,54 +275,83 @@ __global__ void __launch_bounds__(kTcTransThreads, 1) k_tc_trans(const SplitArgs
     }
     tc::fence_before_sync();
     __syncthreads();
-    // ---- pass 1 on the tensor cores: D[128][NP] = (A_hi + A_lo) B^T
-    if (tid == 0) {
-      tc::fence_after_sync();
-      for (int n0 = 0; n0 < NP; n0 += 256) {
-        const int nc = NP - n0 < 256 ? NP - n0 : 256;
-        const uint32_t idesc = tc::idesc_f16(kTcTile, nc);
-#pragma unroll
-        for (int ks = 0; ks < KA / 16; ++ks) {
-          const uint64_t bd = tc::smem_desc(b_addr + (uint32_t)((n0 / 8) * SBO + ks * 256), 128, SBO);
-          tc::mma_f16(tbase + (uint32_t)n0, tc::smem_desc(ah_addr + ks * 256, 128, SBO), bd, idesc, ks > 0 ? 1u : 0u);
-          tc::mma_f16(tbase + (uint32_t)n0, tc::smem_desc(al_addr + ks * 256, 128, SBO), bd, idesc, 1u);
-        }
-      }
-      tc::mma_commit(bar);
-    }
-    const bool ok = mbar_wait_bounded(bar, phase);
-    phase ^= 1u;
-    if (!__syncthreads_and(ok)) {
+    // ---- pass 1 on the tensor cores: D[128][NP] = (A_hi + A_lo) B^T, in passes of at most 512 window
+    // columns (the tensor memory of one CTA); a second pass's columns reuse the same tensor memory
+    auto run_mma = [&](int base) -> bool {  // the caller has fenced and synchronised the previous reads
       if (tid == 0) {
-        atomicExch(&a.ctrl->status, (int)MRA_ETIMEOUT);
-        mbar_wait_bounded(bar, phase ^ 1u);  // let the MMAs in flight finish before the memory is freed
+        tc::fence_after_sync();
+        const int hi = min(NP, base + 512);
+        for (int n0 = base; n0 < hi; n0 += 256) {
+          const int nc = hi - n0 < 256 ? hi - n0 : 256;
+          const uint32_t idesc = tc::idesc_f16(kTcTile, nc);
+#pragma unroll
+          for (int ks = 0; ks < KA / 16; ++ks) {
+            const uint64_t bd = tc::smem_desc(b_addr + (uint32_t)((n0 / 8) * SBO + ks * 256), 128, SBO);
+            tc::mma_f16(tbase + (uint32_t)(n0 - base), tc::smem_desc(ah_addr + ks * 256, 128, SBO), bd, idesc,
+                        ks > 0 ? 1u : 0u);
+            tc::mma_f16(tbase + (uint32_t)(n0 - base), tc::smem_desc(al_addr + ks * 256, 128, SBO), bd, idesc, 1u);
+          }
+        }
+        tc::mma_commit(bar);
       }
-      break;
-    }
-    tc::fence_after_sync();
-    // ---- the peak: each warp over its column block of its 32 lanes (images 32 qtr + lane)
+      const bool ok = mbar_wait_bounded(bar, phase);
+      phase ^= 1u;
+      if (!__syncthreads_and(ok)) {
+        if (tid == 0) {
+          atomicExch(&a.ctrl->status, (int)MRA_ETIMEOUT);
+          mbar_wait_bounded(bar, phase ^ 1u);  // let the MMAs in flight finish before the memory is freed
+        }
+        return false;
+      }
+      tc::fence_after_sync();
+      return true;
+    };
+    // this warp's column block of a pass: 4 blocks of 16-column groups over the pass's columns
+    auto block = [&](int base, int& lo, int& hi) {
+      const int pc = min(512, NP - base), nq = ((pc + 3) / 4 + 15) / 16 * 16;
+      lo = base + cblk * nq;
+      hi = min(base + pc, lo + nq);
+    };
+    const int npass = (NP + 511) / 512;
+    bool failed = false;
+    // ---- the peak: each warp over its column blocks of its 32 lanes (images 32 qtr + lane)
     {
       const int row = qtr * 32 + lane;
       const float kap = two_beta / iscale[row];
       float best = -INFINITY;
       int bl = 0x7fffffff;
-      for (int c0 = c_lo; c0 < c_hi; c0 += 16) {
-        float v[16];
-        tc::tmem_ld16(trow + (uint32_t)c0, v);
+      for (int ps = 0; ps < npass; ++ps) {
+        if (ps > 0) {
+          tc::fence_before_sync();
+          __syncthreads();
+        }
+        if (!run_mma(512 * ps)) {
+          failed = true;
+          break;
+        }
+        int lo, hi;
+        block(512 * ps, lo, hi);
+        for (int c0 = lo; c0 < hi; c0 += 16) {
+          float v[16];
+          tc::tmem_ld16(trow + (uint32_t)(c0 - 512 * ps), v);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int l = c0 + i;
-          if (l < Lw) {
-            const float sv = fmaf(kap, v[i], lrs[l]);
-            if (sv > best) best = sv, bl = l;
+          for (int i = 0; i < 16; ++i) {
+            const int l = c0 + i;
+            if (l < Lw) {
+              const float sv = fmaf(kap, v[i], lrs[l]);
+              if (sv > best) best = sv, bl = l;
+            }
           }
         }
       }
-      ibest[cblk * kTcTile + row] = best;
-      ibl[cblk * kTcTile + row] = bl;
+      if (!failed) {
+        ibest[cblk * kTcTile + row] = best;
+        ibl[cblk * kTcTile + row] = bl;
+      }
     }
+    if (failed) break;
     __syncthreads();
-    if (tid < kTcTile) {  // combine the blocks in column order (the first maximum wins)
+    if (tid < kTcTile) {  // combine the blocks in order (the first maximum wins)
       float best = ibest[tid];
       int bl = ibl[tid];
       for (int b = 1; b < 4; ++b)
@@ -328,30 +361,47 @@ __global__ void __launch_bounds__(kTcTransThreads, 1) k_tc_trans(const SplitArgs
       ibl[tid] = bl;
     }
     __syncthreads();
-    // ---- the distance D beyond which every value is more than 40 (plus twice the bound) below the peak
+    // ---- the distance D beyond which every value is more than 40 (plus twice the bound) below the peak;
+    // the last pass is still in tensor memory, earlier passes are computed again
     {
       const int row = qtr * 32 + lane;
       const float kap = two_beta / iscale[row];
       const float thr = ibest[row] - 40.f - 2.f * ibound[row];
       const int bl = ibl[row];
       int D = 0;
-      for (int c0 = c_lo; c0 < c_hi; c0 += 16) {
-        float v[16];
-        tc::tmem_ld16(trow + (uint32_t)c0, v);
+      for (int k = 0; k < npass; ++k) {
+        const int ps = npass - 1 - k;
+        if (k > 0) {
+          tc::fence_before_sync();
+          __syncthreads();
+          if (!run_mma(512 * ps)) {
+            failed = true;
+            break;
+          }
+        }
+        int lo, hi;
+        block(512 * ps, lo, hi);
+        for (int c0 = lo; c0 < hi; c0 += 16) {
+          float v[16];
+          tc::tmem_ld16(trow + (uint32_t)(c0 - 512 * ps), v);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int l = c0 + i;
-          if (l < Lw && fmaf(kap, v[i], lrs[l]) >= thr) {
-            int dd = l > bl ? l - bl : bl - l;
-            if (wrap && L - dd < dd) dd = L - dd;
-            D = max(D, dd);
+          for (int i = 0; i < 16; ++i) {
+            const int l = c0 + i;
+            if (l < Lw && fmaf(kap, v[i], lrs[l]) >= thr) {
+              int dd = l > bl ? l - bl : bl - l;
+              if (wrap && L - dd < dd) dd = L - dd;
+              D = max(D, dd);
+            }
           }
         }
       }
-      tc::fence_before_sync();  // tensor memory is rewritten by the next tile's MMAs after a barrier
-      __syncthreads();          // every block has read ibest/ibl
-      iD[cblk * kTcTile + row] = D;
+      if (!failed) {
+        tc::fence_before_sync();  // tensor memory is rewritten by the next tile's MMAs after a barrier
+        __syncthreads();          // every block has read ibest/ibl
+        iD[cblk * kTcTile + row] = D;
+      }
     }
+    if (failed) break;
     __syncthreads();
     // ---- pass 2 and the back transform: quad pi, lane pj owns rows k = pj + 4 u
     if (pi < nimg) {
@@ -390,7 +440,7 @@ __global__ void __launch_bounds__(kTcTransThreads, 1) k_tc_trans(const SplitArgs
 #pragma unroll
         for (int u = 0; u < KU; ++u) {
           const int k = pj + 4 * u;
-          if (k < Kp1) ab = __ffma2_rn(cq[u], td[k * a.nd + dc], ab);
+          if (k < Kp1) ab = __ffma2_rn(cq[u], tdat(k, dc), ab);
         }
         ab.x += __shfl_xor_sync(qmask, ab.x, 1);
         ab.y += __shfl_xor_sync(qmask, ab.y, 1);
@@ -449,7 +499,7 @@ __global__ void __launch_bounds__(kTcTransThreads, 1) k_tc_trans(const SplitArgs
 #pragma unroll
           for (int u = 0; u < KU; ++u) {
             const int k = pj + 4 * u;
-            if (k < Kp1) Wd[u] = __ffma2_rn(sw, td[k * a.nd + dc], Wd[u]);
+            if (k < Kp1) Wd[u] = __ffma2_rn(sw, tdat(k, dc), Wd[u]);
           }
         }
       }

@@ -47,7 +47,7 @@ __device__ __forceinline__ double block_sum_d(double v, double* red) {
   return red[32];
 }
 
-// Shared memory of k_update: xn [M] double2, t64 [L] double2, t32 [L] float2, d32 [Kp1] float2,
+// Shared memory of the update: xn [M] double2, t64 [L] double2, t32 [L] float2, d32 [Kp1] float2,
 // sc [L] float, then xf [M] float4 (a_{t+1}, a_t in FP32) at a 16-byte boundary.
 __host__ __device__ inline int update_xf_offset(int M, int L, int Kp1) {
   return (16 * M + 28 * L + 8 * Kp1 + 15) & ~15;
@@ -77,7 +77,7 @@ __device__ __forceinline__ float block_sum_f(float v, float* red) {
 constexpr int kUpdateThreads = 512;
 
 // A device function, so that the batched persistent kernel runs the same update for each instance;
-// k_update launches it as one CTA of kUpdateThreads threads.
+// k_finalize runs it in the last of its CTAs (kUpdateThreads threads).
 __device__ __forceinline__ void update_body(const UpdateArgs& a) {
   extern __shared__ __align__(16) unsigned char usmem[];
   // the state, the totals and the control words may come from other CTAs of a persistent launch:

@@ -55,12 +55,14 @@ def sweep(request, monkeypatch):
 
 
 # (K, Q, N, L, Lw, l0, step): a one-chunk window, a wide one, the paper's example at a reduced L
-# (Lw = 2 L + 1, l0 = -L, step = BW / (2 L) with BW = 18), and a window off centre
+# (Lw = 2 L + 1, l0 = -L, step = BW / (2 L) with BW = 18), a window off centre, and one of more
+# than 512 rotations (the split sweep's transform in two passes of tensor-memory columns)
 SHAPES = [
     (12, 16, 1500, 90, 31, -15, 0.35),
     (8, 16, 900, 120, 201, -100, 0.4),
     (10, 8, 700, 60, 121, -60, 0.15),
     (6, 24, 1100, 72, 47, -9, 0.6),
+    (10, 16, 600, 360, 601, -300, 0.5),
 ]
 
 
@@ -75,12 +77,14 @@ def test_dense_em_step_matches_oracle(gpu_lib, sweep, K, Q, N, L, Lw, l0, step):
     _compare(gpu_lib, inst, x0, lr, Lw, l0, step, shifts=inst.s)
 
 
-@pytest.mark.parametrize("kind", ["warp", "cta"])
+@pytest.mark.parametrize("kind", ["warp", "cta", "tc"])
 def test_dense_paper_example_window_full_workload_shape(gpu_lib, kind, monkeypatch):
     """The paper's example of the denser window at the Synch-EM workload's shape: the range
     [-pi BW/L, pi BW/L] with BW = 36 at spacing pi BW/L^2 (Lw = 2 L + 1 = 721 rotations 0.05 grid units
     apart, |k| <= 32, Q = 24, L = 360).  Its unit tables do not fit in shared memory next to the image
-    rings, so the warp sweep and the batch sweep read them from global memory."""
+    rings, so the warp sweep and the batch sweep read them from global memory; the split sweep runs
+    its transform in two passes of tensor-memory columns and keeps the first distances of its table
+    in shared memory."""
     monkeypatch.setenv("MRA_SWEEP", kind)
     K, Q, L = 32, 24, 360
     inst = synth.make_instance(K, Q, 300, L, snr=1 / 50, decay=400.0, seed=8150, offgrid=True)

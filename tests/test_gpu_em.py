@@ -295,3 +295,16 @@ def test_em_step_wide_windows_config2_shape(gpu_lib, sweep, Lw, l0, snr):
     y64 = synth.c64_round(inst.y)
     for x0 in (O.align_mean(y64, inst.s, inst.L), synth.random_init(inst.K, inst.Q, c["decay"], seed=7)):
         compare(gpu_lib, inst, x0, np.log(np.full(Lw, 1 / Lw)), Lw, l0=l0, shifts=inst.s)
+
+
+@pytest.mark.parametrize("kind", ["tc", ""])
+def test_em_step_whole_circle_beyond_512_rotations(gpu_lib, kind, monkeypatch):
+    """Full search on a grid of L = 720 rotations (more than the 512 tensor-memory columns of one CTA:
+    the split sweep's transform takes two passes and computes the first again for the cut), from the
+    aligned mean and from a random start; "" lets the autotuner choose."""
+    if kind:
+        monkeypatch.setenv("MRA_SWEEP", kind)
+    inst = synth.make_instance(16, 16, 700, 720, 1 / 20, 100.0, seed=3400)
+    y64 = synth.c64_round(inst.y)
+    for x0 in (O.align_mean(y64, inst.s, inst.L), synth.random_init(inst.K, inst.Q, 100.0, seed=9)):
+        compare(gpu_lib, inst, x0, np.log(np.full(720, 1 / 720)), 720, l0=0, shifts=inst.s)
