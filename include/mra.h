@@ -172,14 +172,15 @@ MRA_API int mra_em_run_hl(const mra_dims* dims, const mra_em_params* prm, const 
  * Neither has a counterpart in the paper, which treats one problem at a time. */
 
 /* (No counterpart in the paper.)  Times every EM sweep that can take the problem
- * (the paired-warp sweep, two warps per image, and the lean warp sweep for grid windows of at
+ * (the lean warp sweep and the paired-warp sweep, two warps per image, for grid windows of at
  * most 32 mirror units that are not the whole circle; the split sweep with its tcgen05 window transform for windows of 65 to 1024 rotations
  * and K+1 <= 48 (the default on the whole circle); the warp-per-image sweep; the batch sweep at
  * 16, 12, 8 or 4 images per batch and
  * 2 or 3 ring stages; the
  * chunked two-read sweep at 128, 64, 32 or 16 images per chunk and 1 or 2 CTAs per
  * SM) for one sweep over y from the state (x, log_rho), and caches the fastest for
- * this device and shape (K, Q, L, Lw, l0, step, y_format).  Later EM calls on that
+ * this device and shape (a candidate later in this list replaces an earlier one only when it
+ * is at least 1% faster) (K, Q, L, Lw, l0, step, y_format).  Later EM calls on that
  * shape use the cached choice unless the MRA_SWEEP* environment variables fix one.
  * Synchronizes the stream.
  *   y_format   0: y complex64; 1: the BF16 hi/lo split of mra_y_split_bf16

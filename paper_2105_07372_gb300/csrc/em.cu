@@ -1992,8 +1992,9 @@ namespace {
 
 constexpr int kBatchedImagesPerCta = 64;
 
-// Sweep candidates the autotuner times, in the order of the default preference.
-const SweepSel kTuneCandidates[] = {{6, 0, 0},  {4, 0, 0},  {5, 0, 0},  {1, 0, 0},  {2, 16, 2}, {2, 12, 2}, {2, 8, 3},  {2, 8, 2}, {2, 4, 3},
+// Sweep candidates the autotuner times, in the order of the default preference (a later candidate
+// replaces the best so far only when it is at least 1% faster, so near-ties keep the earlier one).
+const SweepSel kTuneCandidates[] = {{4, 0, 0},  {6, 0, 0},  {5, 0, 0},  {1, 0, 0},  {2, 16, 2}, {2, 12, 2}, {2, 8, 3},  {2, 8, 2}, {2, 4, 3},
                                     {2, 4, 2},  {3, 64, 2}, {3, 32, 2}, {3, 16, 2}, {3, 128, 1},
                                     {3, 64, 1}, {3, 32, 1}};
 
@@ -2038,7 +2039,7 @@ int autotune_impl(const mra_dims* d, const mra_em_params* p, const float* y, int
     if (rc != MRA_OK) return rc;
     const float ms = time_sweep(c, s, 2);
     if (ms < 0.f) return MRA_ECUDA;
-    if (best_ms < 0.f || ms < best_ms) best_ms = ms, best = cand;
+    if (best_ms < 0.f || ms < 0.99f * best_ms) best_ms = ms, best = cand;
   }
   if (best_ms >= 0.f) tune_store(tune_key(d, p->Lw, p->l0, param_step(p), yfmt), best);
   if (out) *out = best;
