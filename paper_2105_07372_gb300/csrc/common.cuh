@@ -383,7 +383,7 @@ struct SplitArgs {
   int off_ring, off_x, off_xs, off_tf;
   int NP, ncols;                    // transform: window columns padded to 16, tensor-memory columns
   int k2_off_b, k2_off_ah, k2_off_al, k2_off_lr, k2_off_tf, k2_off_wt, k2_off_ll;
-  int k2_off_cs;                    // transform: the tile's c (then W) rows [128][Kp1] float2
+  int k2_off_cs;                    // transform: the tile's c (then W) rows [128][Kp1] float2, at the end the CTA's ll sums
   int k2_off_td;                    // transform: the distance-unit table's first k2_ndp distances, or 0
   int k2_ndp;                       // distances of the table in shared memory (the rest read from global)
   int k2_off_info;                  // transform: per-image peaks, distances, scales and bounds

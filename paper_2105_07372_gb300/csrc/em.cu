@@ -1065,18 +1065,17 @@ bool plan_split(int Kp1, int Q, int L, int Lw, int max_smem, SplitPlan* p) {
   o = (o + 7) & ~7;
   p->k2_off_wt = o; o += al16(Lw * 8);
   p->k2_off_ll = o; o += al16(kTcTransThreads * 8);
-  p->k2_off_cs = o; o += al16(kTcTile * Kp1 * 8);
+  p->k2_off_cs = o; o += al16(std::max(kTcTile * Kp1, kTcTransThreads) * 8);  // later the CTA's ll sums
   p->k2_off_info = o; o += al16(kTcTile * 4 * 14);  // [4][128] maxima, indices, distances; scales; bounds
   if (o + 1024 > max_smem) return false;
-  // the distance-unit table in shared memory: whole, or its first distances (multiples of 16; those
-  // near each image's peak, where pass 2 works) with the rest read from global memory
+  // the distance-unit table in shared memory, [d][KP + 1]: whole, or its first distances (those near
+  // each image's peak, where pass 2 works) with the rest read from global memory
   const int nd = Lw == L ? L / 2 + 1 : Lw;
-  int ndp = std::min(nd, std::max(0, (max_smem - 1024 - o) & ~15) / (Kp1 * 8));
-  if (ndp < nd) ndp = ndp / 16 * 16;
-  if (ndp >= 16) {
+  const int ndp = std::min(nd, std::max(0, (max_smem - 1024 - o) & ~15) / ((p->KP + 1) * 8));
+  if (ndp >= 8) {
     p->k2_off_td = o;
     p->k2_ndp = ndp;
-    o += al16(Kp1 * ndp * 8);
+    o += al16((p->KP + 1) * ndp * 8);
   } else {
     p->k2_off_td = 0;
     p->k2_ndp = 0;

@@ -165,16 +165,19 @@ __global__ void __launch_bounds__(kTcStreamThreads, 1) k_tc_corr(const SplitArgs
 // ---------------------------------------------------------------- transform (tensor cores)
 // 512 threads per tile of 128 images.  Pass 1's row of image i is tensor-memory lane i: warp w reads
 // the lanes of quarter w % 4 over the column block w / 4, the four blocks' maxima are combined in
-// shared memory.  Pass 2 and the back transform run on four lanes per image (a quad, rows k = j,
-// j + 4, ... per lane, sums over the quad by shuffles).
-// KP: K+1 rounded up to a multiple of 4 (KP / 4 rows per lane); the MMA's K is 2 KP rounded up to 16.
+// shared memory.  Pass 2 and the back transform run on a warp per image (lanes over distances for
+// the values, over rows for the back transform), the images of the tile handed out to the warps
+// from a counter.
+// KP: K+1 rounded up to a multiple of 4; the MMA's K is 2 KP rounded up to 16.
 template <int KP>
 __global__ void __launch_bounds__(kTcTransThreads, 1) k_tc_trans(const SplitArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   constexpr int KA = (2 * KP + 15) / 16 * 16;
   constexpr int SBO = (KA / 8) * 128;  // bytes between 8-row groups of an operand
-  constexpr int KU = KP / 4;           // rows per quad lane
   constexpr int NT = kTcTransThreads;
+  constexpr int TP = KP + 1;  // pitch of a distance's row in the shared table (odd: no bank conflicts)
+  constexpr unsigned FULL = 0xffffffffu;
+  __shared__ int s_next;  // the tile's next image for pass 2
   if (a.ctrl->done) return;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int Kp1 = a.Kp1, L = a.L, Lw = a.Lw, NP = a.NP, M = a.M;
@@ -189,13 +192,15 @@ __global__ void __launch_bounds__(kTcTransThreads, 1) k_tc_trans(const SplitArgs
   float* lrs = reinterpret_cast<float*>(smem + a.k2_off_lr);                            // [Lw]
   float2* tfs = reinterpret_cast<float2*>(smem + a.k2_off_tf);                         // [L]
   unsigned long long* wts = reinterpret_cast<unsigned long long*>(smem + a.k2_off_wt);  // [Lw]
-  double* llr = reinterpret_cast<double*>(smem + a.k2_off_ll);                         // [NT]
+  float2* swb = reinterpret_cast<float2*>(smem + a.k2_off_ll);  // [NT / 32][32] back-transform terms
   float2* cst = reinterpret_cast<float2*>(smem + a.k2_off_cs);                         // [128][Kp1] c, then W
   float* ibest = reinterpret_cast<float*>(smem + a.k2_off_info);  // [4][128] block maxima
   int* ibl = reinterpret_cast<int*>(ibest + 4 * kTcTile);          // [4][128] their window indices
   int* iD = ibl + 4 * kTcTile;                                     // [4][128] block distances
   float* iscale = reinterpret_cast<float*>(iD + 4 * kTcTile);      // [128] A row scale
   float* ibound = iscale + kTcTile;                                // [128] pass-1 rounding bound
+  double* lli = reinterpret_cast<double*>(ibest);                   // [128] log-likelihoods (pass 2)
+  // the distance-unit table's first k2_ndp distances, [d][TP] (rows k >= K+1 zero)
   float2* tds = a.k2_off_td ? reinterpret_cast<float2*>(smem + a.k2_off_td) : nullptr;
   {
     const uint4* bg = reinterpret_cast<const uint4*>(a.tcb);
@@ -204,9 +209,9 @@ __global__ void __launch_bounds__(kTcTransThreads, 1) k_tc_trans(const SplitArgs
     for (int i = tid; i < Lw; i += NT) lrs[i] = a.logrho32[i], wts[i] = 0ull;
     for (int i = tid; i < L; i += NT) tfs[i] = a.tf32[i];
     if (tds)  // the first k2_ndp distances of every row (the ones near each image's peak)
-      for (int i = tid; i < Kp1 * a.k2_ndp; i += NT) {
-        const int k = i / a.k2_ndp;
-        tds[i] = a.td[k * a.nd + (i - k * a.k2_ndp)];
+      for (int i = tid; i < TP * a.k2_ndp; i += NT) {
+        const int d = i / TP, k = i - d * TP;
+        tds[i] = k < Kp1 ? a.td[k * a.nd + d] : make_float2(0.f, 0.f);
       }
     if (tid == 0) {
       mbar_init(bar, 1);
@@ -214,7 +219,6 @@ __global__ void __launch_bounds__(kTcTransThreads, 1) k_tc_trans(const SplitArgs
     }
   }
   const int ndp = tds ? a.k2_ndp : 0;
-  auto tdat = [&](int k, int d) -> float2 { return d < ndp ? tds[k * ndp + d] : a.td[k * a.nd + d]; };
   if (warp == 0) {
     tc::tmem_alloc(tbase_s, (uint32_t)a.ncols);
     tc::tmem_relinquish();
@@ -227,9 +231,6 @@ __global__ void __launch_bounds__(kTcTransThreads, 1) k_tc_trans(const SplitArgs
   const uint32_t trow = tbase + ((uint32_t)(qtr * 32) << 16);  // this warp's lanes
   const uint32_t ah_addr = smem_addr(Ah), al_addr = smem_addr(Al), b_addr = smem_addr(Bs);
   const int nd1 = a.nd - 1;
-  // pass 2: quad per image
-  const int pi = tid >> 2, pj = tid & 3;
-  const unsigned qmask = 0xFu << (lane & ~3);
   double ll_acc = 0.0;
   uint32_t phase = 0;
   const int ntiles = (a.N + kTcTile - 1) / kTcTile;
@@ -360,6 +361,7 @@ __global__ void __launch_bounds__(kTcTransThreads, 1) k_tc_trans(const SplitArgs
       ibest[tid] = best;
       ibl[tid] = bl;
     }
+    if (tid == 0) s_next = 0;
     __syncthreads();
     // ---- the distance D beyond which every value is more than 40 (plus twice the bound) below the peak;
     // the last pass is still in tensor memory, earlier passes are computed again
@@ -403,49 +405,49 @@ __global__ void __launch_bounds__(kTcTransThreads, 1) k_tc_trans(const SplitArgs
     }
     if (failed) break;
     __syncthreads();
-    // ---- pass 2 and the back transform: quad pi, lane pj owns rows k = pj + 4 u
-    if (pi < nimg) {
-      const int img = img0 + pi;
-      const int p = ibl[pi];
-      const int D = max(max(iD[pi], iD[kTcTile + pi]), max(iD[2 * kTcTile + pi], iD[3 * kTcTile + pi]));
+    // ---- pass 2 and the back transform: a warp per image (images handed out from the tile's counter,
+    // so that an image with a broad posterior holds one warp, not the tile), lanes over the distances
+    // d = c0 + lane of chunks of 32 for the values and over the rows k = lane, lane + 32 for the back
+    // transform; the rotated c of the image replaces its c in cst
+    for (;;) {
+      int i = 0;
+      if (lane == 0) i = atomicAdd(&s_next, 1);
+      i = __shfl_sync(FULL, i, 0);
+      if (i >= nimg) break;
+      const int img = img0 + i;
+      const int p = ibl[i];
+      const int D = max(max(iD[i], iD[kTcTile + i]), max(iD[2 * kTcTile + i], iD[3 * kTcTile + i]));
       int op = 0;
       if (!dense) {
         op = a.l0m + p;
         if (op >= L) op -= L;
       }
-      float2 cq[KU];
+      float2* cqi = cst + i * Kp1;
       float Sp = 0.f;
-      {
-        int idx = tc_mod(pj * op, L, invL);
-        const int ist = tc_mod(4 * op, L, invL);
-#pragma unroll
-        for (int u = 0; u < KU; ++u) {
-          const int k = pj + 4 * u;
-          cq[u] = make_float2(0.f, 0.f);
-          if (k < Kp1) {
-            const float2 f = dense ? a.tw[k * a.twp + p] : tfs[idx];
-            cq[u] = cmul(cst[pi * Kp1 + k], f);
-            Sp += cq[u].x;
-          }
-          idx += ist;
-          if (idx >= L) idx -= L;
-        }
+      for (int k = lane; k < Kp1; k += 32) {
+        const float2 f = dense ? a.tw[k * a.twp + p] : tfs[tc_mod(k * op, L, invL)];
+        const float2 cq = cmul(cqi[k], f);
+        cqi[k] = cq;
+        Sp += cq.x;
       }
-      Sp += __shfl_xor_sync(qmask, Sp, 1);
-      Sp += __shfl_xor_sync(qmask, Sp, 2);
+      Sp = warp_sum(Sp);
+      __syncwarp();
       const float lrp = lrs[p];
+      // S(l* + d) - S(l*) and S(l* - d) - S(l*) at this lane's distance (-inf where absent)
       auto values = [&](int d, float& sp, float& sm, int& la, int& lb) {
-        float2 ab = make_float2(0.f, 0.f);
         const int dc = min(d, nd1);
-#pragma unroll
-        for (int u = 0; u < KU; ++u) {
-          const int k = pj + 4 * u;
-          if (k < Kp1) ab = __ffma2_rn(cq[u], tdat(k, dc), ab);
+        float2 ab = make_float2(0.f, 0.f);
+        if (dc < ndp) {
+          const float2* t = tds + dc * TP;
+#pragma unroll 4
+          for (int k = 0; k < KP; ++k)
+            if (k < Kp1) ab = __ffma2_rn(cqi[k], t[k], ab);
+        } else {
+          const float2* t = a.td + dc;
+#pragma unroll 4
+          for (int k = 0; k < KP; ++k)
+            if (k < Kp1) ab = __ffma2_rn(cqi[k], t[(size_t)k * a.nd], ab);
         }
-        ab.x += __shfl_xor_sync(qmask, ab.x, 1);
-        ab.y += __shfl_xor_sync(qmask, ab.y, 1);
-        ab.x += __shfl_xor_sync(qmask, ab.x, 2);
-        ab.y += __shfl_xor_sync(qmask, ab.y, 2);
         la = p + d;
         lb = p - d;
         bool vp, vm;
@@ -458,50 +460,72 @@ __global__ void __launch_bounds__(kTcTransThreads, 1) k_tc_trans(const SplitArgs
           vp = la < Lw;
           vm = d > 0 && lb >= 0;
         }
-        sp = vp ? fmaf(two_beta, ab.x - ab.y, lrs[min(la, Lw - 1)] - lrp) : -INFINITY;
-        sm = vm ? fmaf(two_beta, ab.x + ab.y, lrs[max(lb, 0)] - lrp) : -INFINITY;
+        vp = vp && d <= D;
+        vm = vm && d <= D;
+        sp = vp ? fmaf(two_beta, ab.x - ab.y, lrs[min(max(la, 0), Lw - 1)] - lrp) : -INFINITY;
+        sm = vm ? fmaf(two_beta, ab.x + ab.y, lrs[min(max(lb, 0), Lw - 1)] - lrp) : -INFINITY;
       };
       // values relative to the peak (the peak's own is exactly 0, none exceeds twice pass 1's bound):
       // the normaliser sums their exponentials directly
       float z = 0.f;
-      for (int d = 0; d <= D; ++d) {
+      for (int c0 = 0; c0 <= D; c0 += 32) {
         float sp, sm;
         int la, lb;
-        values(d, sp, sm, la, lb);
+        values(c0 + lane, sp, sm, la, lb);
         z += expf(sp) + expf(sm);
       }
-      if (pj == 0) ll_acc += (double)(lrp + two_beta * Sp) + (double)logf(z);
+      z = warp_sum(z);
+      if (lane == 0) lli[i] = (double)(lrp + two_beta * Sp) + (double)logf(z);
       const float inv = 1.f / z;
-      float* wo = (a.w_out && pj == 0) ? a.w_out + (size_t)img * Lw : nullptr;
-      if (wo)
-        for (int l = 0; l < Lw; ++l) wo[l] = 0.f;
-      float2 Wd[KU];
-#pragma unroll
-      for (int u = 0; u < KU; ++u) Wd[u] = make_float2(0.f, 0.f);
-      for (int d = 0; d <= D; ++d) {
+      float* wo = a.w_out ? a.w_out + (size_t)img * Lw : nullptr;
+      if (wo) {
+        for (int l = lane; l < Lw; l += 32) wo[l] = 0.f;
+        __syncwarp();
+      }
+      const int k0 = lane, k1 = lane + 32;
+      float2 W0 = make_float2(0.f, 0.f), W1 = make_float2(0.f, 0.f);
+      float2* sw = swb + warp * 32;
+      for (int c0 = 0; c0 <= D; c0 += 32) {
         float sp, sm;
         int la, lb;
+        const int d = c0 + lane;
         values(d, sp, sm, la, lb);
         const float wp = expf(sp) * inv, wm = expf(sm) * inv;
-        if (pj == 0) {
-          if (sp > -INFINITY) {
-            atomicAdd(&wts[la], (unsigned long long)__float2ull_rn(wp * 1099511627776.f));
-            if (wo) wo[la] = wp;
+        if (sp > -INFINITY) {
+          atomicAdd(&wts[la], (unsigned long long)__float2ull_rn(wp * 1099511627776.f));
+          if (wo) wo[la] = wp;
+        }
+        if (sm > -INFINITY) {
+          atomicAdd(&wts[lb], (unsigned long long)__float2ull_rn(wm * 1099511627776.f));
+          if (wo) wo[lb] = wm;
+        }
+        // back transform around the peak: W_k e^{-i k theta_l*} = 1 + sum_{d>=1} [(w_{+d} + w_{-d}) (cos t - 1)
+        //   + i (w_{-d} - w_{+d}) (-sin t)], the chunk's terms staged per warp
+        sw[lane] = d >= 1 ? make_float2(wp + wm, wm - wp) : make_float2(0.f, 0.f);
+        __syncwarp();
+        const int n = min(32, D + 1 - c0);
+        if (c0 + n <= ndp) {
+          for (int e = 0; e < n; ++e) {
+            const float2 s = sw[e];
+            const float2* t = tds + (c0 + e) * TP;
+            W0 = __ffma2_rn(s, t[min(k0, KP - 1)], W0);
+            if (KP > 32) W1 = __ffma2_rn(s, t[min(k1, KP - 1)], W1);
           }
-          if (sm > -INFINITY) {
-            atomicAdd(&wts[lb], (unsigned long long)__float2ull_rn(wm * 1099511627776.f));
-            if (wo) wo[lb] = wm;
+        } else {
+          for (int e = 0; e < n; ++e) {
+            const float2 s = sw[e];
+            const int dc = min(c0 + e, nd1);
+            if (dc < ndp) {
+              const float2* t = tds + dc * TP;
+              W0 = __ffma2_rn(s, t[min(k0, KP - 1)], W0);
+              if (KP > 32) W1 = __ffma2_rn(s, t[min(k1, KP - 1)], W1);
+            } else {
+              if (k0 < Kp1) W0 = __ffma2_rn(s, a.td[(size_t)k0 * a.nd + dc], W0);
+              if (KP > 32 && k1 < Kp1) W1 = __ffma2_rn(s, a.td[(size_t)k1 * a.nd + dc], W1);
+            }
           }
         }
-        if (d >= 1) {
-          const float2 sw = make_float2(wp + wm, wm - wp);
-          const int dc = min(d, nd1);
-#pragma unroll
-          for (int u = 0; u < KU; ++u) {
-            const int k = pj + 4 * u;
-            if (k < Kp1) Wd[u] = __ffma2_rn(sw, tdat(k, dc), Wd[u]);
-          }
-        }
+        __syncwarp();  // the next chunk rewrites the stage
       }
       // W_k = e^{+i k (theta_hat_j + theta_l*)} (1 + sum ...): rotated back by the peak and the shift
       int sj = 0;
@@ -511,22 +535,20 @@ __global__ void __launch_bounds__(kTcTransThreads, 1) k_tc_trans(const SplitArgs
       }
       int q = dense ? sj : sj + op;
       if (q >= L) q -= L;
-      int idx = tc_mod(pj * q, L, invL);
-      const int ist = tc_mod(4 * q, L, invL);
 #pragma unroll
-      for (int u = 0; u < KU; ++u) {
-        const int k = pj + 4 * u;
+      for (int h = 0; h < 2; ++h) {
+        const int k = h ? k1 : k0;
         if (k < Kp1) {
-          float2 w = make_float2(1.f + Wd[u].x, Wd[u].y);
+          const float2 Wd = h ? W1 : W0;
+          float2 w = make_float2(1.f + Wd.x, Wd.y);
           if (dense) w = cmul_conj_b(w, a.tw[k * a.twp + p]);
-          w = cmul_conj_b(w, tfs[idx]);
-          cst[pi * Kp1 + k] = w;  // this lane's own rows (read above)
+          w = cmul_conj_b(w, tfs[tc_mod(k * q, L, invL)]);
+          cqi[k] = w;  // this lane's own rows (every lane has read the rotated c above)
         }
-        idx += ist;
-        if (idx >= L) idx -= L;
       }
     }
     __syncthreads();
+    if (tid < nimg) ll_acc += lli[tid];  // a fixed image per thread: the order is the same every run
     for (int i = tid; i < nimg * Kp1; i += NT) a.wbuf[(size_t)img0 * Kp1 + i] = cst[i];
     __syncthreads();  // the next tile's copy rewrites the stage
   }
@@ -534,6 +556,7 @@ __global__ void __launch_bounds__(kTcTransThreads, 1) k_tc_trans(const SplitArgs
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tbase, (uint32_t)a.ncols);
+  double* llr = reinterpret_cast<double*>(cst);  // [NT]: the stage is free after the last tile
   llr[tid] = ll_acc;
   __syncthreads();
   const int G = a.G, cta = blockIdx.x;
