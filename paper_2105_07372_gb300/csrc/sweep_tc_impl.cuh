@@ -200,6 +200,8 @@ __global__ void __launch_bounds__(kTcTransThreads, 1) k_tc_trans(const SplitArgs
   float* iscale = reinterpret_cast<float*>(iD + 4 * kTcTile);      // [128] A row scale
   float* ibound = iscale + kTcTile;                                // [128] pass-1 rounding bound
   double* lli = reinterpret_cast<double*>(ibest);                   // [128] log-likelihoods (pass 2)
+  int* iDm = reinterpret_cast<int*>(ibest + 2 * kTcTile);           // [128] D of each image (pass 2)
+  int* iord = iDm + kTcTile;                                       // [128] images by decreasing D
   // the distance-unit table's first k2_ndp distances, [d][TP] (rows k >= K+1 zero)
   float2* tds = a.k2_off_td ? reinterpret_cast<float2*>(smem + a.k2_off_td) : nullptr;
   {
@@ -405,18 +407,33 @@ __global__ void __launch_bounds__(kTcTransThreads, 1) k_tc_trans(const SplitArgs
     }
     if (failed) break;
     __syncthreads();
+    // images in order of decreasing D (ties by index), so that the broadest posteriors start first and
+    // the rest fill in around them
+    if (tid < nimg) iDm[tid] = max(max(iD[tid], iD[kTcTile + tid]), max(iD[2 * kTcTile + tid], iD[3 * kTcTile + tid]));
+    __syncthreads();
+    if (tid < nimg) {
+      const int Di = iDm[tid];
+      int rank = 0;
+      for (int j = 0; j < nimg; ++j) {
+        const int Dj = iDm[j];
+        rank += (Dj > Di || (Dj == Di && j < tid)) ? 1 : 0;
+      }
+      iord[rank] = tid;
+    }
+    __syncthreads();
     // ---- pass 2 and the back transform: a warp per image (images handed out from the tile's counter,
     // so that an image with a broad posterior holds one warp, not the tile), lanes over the distances
     // d = c0 + lane of chunks of 32 for the values and over the rows k = lane, lane + 32 for the back
     // transform; the rotated c of the image replaces its c in cst
     for (;;) {
-      int i = 0;
-      if (lane == 0) i = atomicAdd(&s_next, 1);
-      i = __shfl_sync(FULL, i, 0);
-      if (i >= nimg) break;
+      int n_ = 0;
+      if (lane == 0) n_ = atomicAdd(&s_next, 1);
+      n_ = __shfl_sync(FULL, n_, 0);
+      if (n_ >= nimg) break;
+      const int i = iord[n_];
       const int img = img0 + i;
       const int p = ibl[i];
-      const int D = max(max(iD[i], iD[kTcTile + i]), max(iD[2 * kTcTile + i], iD[3 * kTcTile + i]));
+      const int D = iDm[i];
       int op = 0;
       if (!dense) {
         op = a.l0m + p;
@@ -435,7 +452,7 @@ __global__ void __launch_bounds__(kTcTransThreads, 1) k_tc_trans(const SplitArgs
       const float lrp = lrs[p];
       // S(l* + d) - S(l*) and S(l* - d) - S(l*) at this lane's distance (-inf where absent)
       auto values = [&](int d, float& sp, float& sm, int& la, int& lb) {
-        const int dc = min(d, nd1);
+        const int dc = d <= D ? min(d, nd1) : 0;  // lanes past D read the shared table (their values are unused)
         float2 ab = make_float2(0.f, 0.f);
         if (dc < ndp) {
           const float2* t = tds + dc * TP;
