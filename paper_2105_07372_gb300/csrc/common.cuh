@@ -224,7 +224,6 @@ struct SweepV2Args {
   int slot_bytes;  // bytes per ring slot
   int sp;          // per-warp row pitch (floats) of the s/w and W[l] buffers
   int off_ring, off_x, off_tu, off_tf, off_lr, off_units, off_s, off_wl;
-  int off_xs;      // lean sweep: (x.im, -x.re) pairs [M/2] float4
   int cbp;         // lean sweep: per-warp buffer pitch (float2) for c_k and the window's values
   float two_beta;
   int align_only;  // 1: weights are 1 at offset 0 (align and average)
@@ -256,7 +255,7 @@ SweepV2Launch sweep_v2_q2(int MR, int ipw, int lwc);
 SweepV2Launch sweep_v2_q3(int MR, int ipw, int lwc);
 SweepV2Launch sweep_v2_q4(int MR, int ipw, int lwc);
 // Lean warp sweep (sweep5_impl.cuh): grid windows of at most 32 mirror units (unit pitch nup
-// 20 or 40), the same arguments and tables as the warp sweep plus off_xs and cbp.
+// 20 or 40), the same arguments and tables as the warp sweep plus cbp.
 SweepV2Launch sweep_v5_q1(int MR, int nup);
 SweepV2Launch sweep_v5_q2(int MR, int nup);
 SweepV2Launch sweep_v5_q3(int MR, int nup);

@@ -926,10 +926,9 @@ bool plan_v2(int Kp1, int Q, int L, int Lw, int nup, int max_smem, V2Plan* p) {
 }
 
 // Shared-memory plan of the lean warp sweep (grid windows of at most 32 mirror units that
-// are not the whole circle): the warp sweep's ring and tables plus the swapped copy of x, and
-// one per-warp buffer serving c_k (pass 1) and the window's values (images off the fast path).
-bool plan_v5(int Kp1, int Q, int L, int Lw, int nu, int nup, bool dense, int max_smem, V2Plan* p, int* cbp_out,
-             int* off_xs_out) {
+// are not the whole circle): the warp sweep's ring and tables, and one per-warp buffer serving
+// c_k (pass 1) and the window's values (images off the fast path).
+bool plan_v5(int Kp1, int Q, int L, int Lw, int nu, int nup, bool dense, int max_smem, V2Plan* p, int* cbp_out) {
   if (dense || Lw >= L || nu > 32 || Q % 8 != 0 || Q / 8 > 4) return false;
   const int QV = Q / 8, MR = (Kp1 + 7) / 8;
   if (MR > 7) return false;
@@ -945,7 +944,6 @@ bool plan_v5(int Kp1, int Q, int L, int Lw, int nu, int nup, bool dense, int max
     int o = al16(2 * maxw * 8);
     p->off_ring = o; o += 2 * nw * slot;
     p->off_x = o; o += al16(M * 8);
-    const int off_xs = o; o += al16(M * 8);
     p->off_tu = o; o += al16(8 * MR * nup * 8);  // rows padded to 8 MR
     p->off_tf = o; o += al16(L * 8);
     p->off_lr = o; o += al16(Lw * 4);
@@ -960,7 +958,6 @@ bool plan_v5(int Kp1, int Q, int L, int Lw, int nu, int nup, bool dense, int max
       p->smem = o;
       p->lwc = 0;
       *cbp_out = cbp;
-      *off_xs_out = off_xs;
       return true;
     }
   }
@@ -1337,7 +1334,7 @@ struct EmCall {
   int update_smem;
   bool v2;  // warp-per-image sweep (rows of Q a multiple of 8) instead of the tile sweep
   bool v5;  // with v2: the lean warp sweep's kernel and plan
-  int v5_cbp, v5_off_xs;
+  int v5_cbp;
   bool v6;  // with v2 (whose tables it reads): the paired-warp sweep
   V6Plan v6p;
   SweepV6Args sa6;
@@ -1434,7 +1431,7 @@ int prepare(const mra_dims* d, int Lw, int l0, double step, const float* y, cons
     c->v5 = false;
     if (allow_v3 && (sel.kind == 4 || (sel.kind == 0 && !c->v3 && !c->v4))) {
       V2Plan p5;
-      if (plan_v5(Kp1, d->Q, d->L, Lw, nu, nup, dense, di.max_smem_optin, &p5, &c->v5_cbp, &c->v5_off_xs)) {
+      if (plan_v5(Kp1, d->Q, d->L, Lw, nu, nup, dense, di.max_smem_optin, &p5, &c->v5_cbp)) {
         c->v2p = p5;
         c->v2 = c->v5 = true;
         c->v3 = c->v4 = false;
@@ -1529,7 +1526,6 @@ int prepare(const mra_dims* d, int Lw, int l0, double step, const float* y, cons
   v.nwarps = c->v2p.nwarps; v.slot_bytes = c->v2p.slot_bytes; v.sp = c->v2p.sp;
   v.off_ring = c->v2p.off_ring; v.off_x = c->v2p.off_x; v.off_tu = c->v2p.off_tu; v.off_tf = c->v2p.off_tf;
   v.off_lr = c->v2p.off_lr; v.off_units = c->v2p.off_units; v.off_s = c->v2p.off_s; v.off_wl = c->v2p.off_wl;
-  v.off_xs = c->v5 ? c->v5_off_xs : 0;
   v.cbp = c->v5 ? c->v5_cbp : 0;
   v.two_beta = s.two_beta;
   v.align_only = 0;

@@ -5,8 +5,9 @@
 //
 //   correlation   quad layout as in the warp sweep (quad r owns rows k = r, r+8, ...; lane j of
 //                 a quad owns the float4 columns j, j+4, ...), with packed FP32 FMAs: the two
-//                 partial sums (y.re x.re, y.im x.im) and (y.re x.im, -y.im x.re) of a complex
-//                 pair accumulate in one f32x2 FMA each, against a pre-swapped copy of x
+//                 partial sums (y.re x.re, y.im x.im) and (y.re x.im, y.im x.re) of a complex
+//                 pair accumulate in one f32x2 FMA each (the second against x with its parts
+//                 swapped in registers; Im c is the difference of its two lanes)
 //   pass 1        each lane owns one mirror unit {+o, -o} and sums over every row, reading c_k
 //                 as a shared-memory broadcast; no cross-lane sums per unit.  The peak and the
 //                 40-below cut come from two redux.sync each (floats mapped to ordered ints)
@@ -70,7 +71,6 @@ __device__ __forceinline__ void sweep_v5_body(const SweepV2Args& a, const int ct
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);  // [NT/32][2]
   unsigned char* ring = smem + a.off_ring;            // [nwarps][2][slot]
   const float4* xs4 = reinterpret_cast<const float4*>(smem + a.off_x);   // x
-  const float4* xw4 = reinterpret_cast<const float4*>(smem + a.off_xs);  // (x.im, -x.re) pairs
   const float2* tus = reinterpret_cast<const float2*>(smem + a.off_tu);  // [KR][NUP], rows >= K+1 zero
   const float2* tfs = reinterpret_cast<const float2*>(smem + a.off_tf);  // [L]
   const float* lrs = reinterpret_cast<const float*>(smem + a.off_lr);    // [Lw]
@@ -84,12 +84,10 @@ __device__ __forceinline__ void sweep_v5_body(const SweepV2Args& a, const int ct
   // ---- shared tables
   {
     float4* x4w = reinterpret_cast<float4*>(smem + a.off_x);
-    float4* xw4w = reinterpret_cast<float4*>(smem + a.off_xs);
     const float4* xg = reinterpret_cast<const float4*>(a.x32);
     for (int i = tid; i < M / 2; i += NT) {
       const float4 v = __ldcg(xg + i);
       x4w[i] = v;
-      xw4w[i] = make_float4(v.y, -v.x, v.w, -v.z);
     }
     float2* tuw = reinterpret_cast<float2*>(smem + a.off_tu);
     for (int i = tid; i < KR * NUP; i += NT) tuw[i] = i < Kp1 * NUP ? a.tu[i] : make_float2(0.f, 0.f);
@@ -188,19 +186,19 @@ __device__ __forceinline__ void sweep_v5_body(const SweepV2Args& a, const int ct
 #pragma unroll
         for (int u = 0; u < QV; ++u) {
           const int pidx = k * row4 + j + 4 * u;
-          const float4 yv = y4[pidx], xv = xs4[pidx], xw = xw4[pidx];
+          const float4 yv = y4[pidx], xv = xs4[pidx];
           const float2 y01 = make_float2(yv.x, yv.y), y23 = make_float2(yv.z, yv.w);
           P = __ffma2_rn(y01, make_float2(xv.x, xv.y), P);
           P = __ffma2_rn(y23, make_float2(xv.z, xv.w), P);
-          Qv = __ffma2_rn(y01, make_float2(xw.x, xw.y), Qv);
-          Qv = __ffma2_rn(y23, make_float2(xw.z, xw.w), Qv);
+          Qv = __ffma2_rn(y01, make_float2(xv.y, xv.x), Qv);
+          Qv = __ffma2_rn(y23, make_float2(xv.w, xv.z), Qv);
           if (want_ysq) {
             sq = __ffma2_rn(y01, y01, sq);
             sq = __ffma2_rn(y23, y23, sq);
           }
         }
       }
-      float cr = P.x + P.y, ci = Qv.x + Qv.y;
+      float cr = P.x + P.y, ci = Qv.x - Qv.y;
       cr += __shfl_xor_sync(FULL, cr, 1);
       ci += __shfl_xor_sync(FULL, ci, 1);
       cr += __shfl_xor_sync(FULL, cr, 2);
