@@ -98,13 +98,15 @@ def test_em_step_full_search_and_signal_prior(gpu_lib, sweep):
                                         (12, 10, 500, 90, 13), (4, 8, 1, 16, 16), (6, 16, 301, 40, 9),
                                         (48, 32, 203, 72, 72), (63, 8, 150, 128, 20), (63, 64, 90, 40, 9),
                                         (127, 32, 60, 256, 15), (5, 8, 100, 30, 3), (10, 8, 700, 120, 55),
-                                        (20, 16, 400, 200, 63), (1, 8, 257, 20, 5), (16, 24, 333, 90, 30)])
+                                        (20, 16, 400, 200, 63), (1, 8, 257, 20, 5), (16, 24, 333, 90, 30),
+                                        (44, 16, 300, 90, 90)])
 def test_em_step_shapes_and_edges(gpu_lib, sweep, K, Q, N, L, Lw):
     """Odd Q (float2 path), K = 0, N = 1, Lw = L, Lw = 1, ragged tiles and batches, the
     largest rows (M = 1568) and the most rows (64) of the batch sweep, the largest
     stored size M = 4096 (wide rows and many rows: the tile sweep), windows of 2, 28
-    and 32 mirror units (the lean sweep's narrowest and its second unit pitch), and for the
-    paired-warp sweep a second warp without rows (K = 1) and exactly one row group (K = 16)."""
+    and 32 mirror units (the lean sweep's narrowest and its second unit pitch), for the
+    paired-warp sweep a second warp without rows (K = 1) and exactly one row group (K = 16), and
+    full search with K + 1 = 45 rows (the split sweep's back transform on rows beyond 32)."""
     inst = synth.make_instance(K, Q, N, L, sigma2=1 / (0.3 * (K + 1) * Q), decay=20.0, seed=K * 100 + N)
     x0 = synth.random_init(K, Q, 20.0, seed=3)
     compare(gpu_lib, inst, x0, np.log(np.full(Lw, 1 / Lw)), Lw, shifts=inst.s, update_rho=(Lw % 2 == 1))
