@@ -443,8 +443,6 @@ def main():
             sweep_times.extend(list(sweep_ms)[:n])
         return n
 
-    # kernels of ours per step: sync 4, prior hist 5, fit 1, align 4, em_run 2 + 2 T + 1 (sweep and finalize)
-    launches_per_step = 4 + 5 + 1 + 4 + 2 + 2 * T + 1
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         step(False)
@@ -456,6 +454,9 @@ def main():
     tuned = _effective_choice(mra.mra_em_autotune(
         d, mra.em_params(Lw, l0=l0, gamma=c["gamma"], log_rho_bar=log_prior, step=wstep), y, shift, x, log_rho, ws.em))
     torch.cuda.synchronize()
+    # kernels of ours per step: sync 4, prior hist 5, fit 1, align 4, em_run 2 + T x (the sweep's kernels:
+    # three for the split sweep, else one; and the finalize) + 1
+    launches_per_step = 4 + 5 + 1 + 4 + 2 + ((3 if tuned[0] == 5 else 1) + 1) * T + 1
 
     def barrier():
         if world > 1:
