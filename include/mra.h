@@ -406,9 +406,9 @@ MRA_API int mra_relerr(int32_t K, int32_t Q, const double* x_hat, const double* 
  *   - All calls share the one array and it keeps the previous call's contents;
  *     the call initialises everything it reads.  Calls that overlap on the GPU
  *     (for example on two streams) race on the array: serialise them.
- *   - The cached address belongs to the device's context at the first call;
- *     calls after cudaDeviceReset (or any other teardown of that context) in
- *     the same process are not supported.
+ *   - The array's address is looked up in the current context on every call,
+ *     so calls after cudaDeviceReset get the array of the new context (its
+ *     contents start over).
  *   - A bounded wait that runs out inside the step is recorded in the array's
  *     status word, which only mra_em_step_noalloc_status reads; the next call
  *     of this entry point resets it, so query it after each step whose outputs

@@ -2572,24 +2572,17 @@ MRA_API int mra_prior_hist(const mra_dims* d, const float* y, const int32_t* shi
 }  // extern "C"
 
 // ---------------------------------------------------------------- fixed-scratch variant of mra_em_step
-// Scratch for mra_em_step_noalloc: one array per device, loaded with the library and kept
-// until the process exits.  Host code must not use the symbol itself as a device address;
-// the address comes from cudaGetSymbolAddress once per device.
+// Scratch for mra_em_step_noalloc: one array per device, loaded with the library's module in
+// the current context.  Host code must not use the symbol itself as a device address; the
+// address comes from cudaGetSymbolAddress on every call (cheap once the module is loaded), so a
+// context that was destroyed and created again is never handed a stale address.
 constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 static int noalloc_scratch(void** out) {
-  static void* addr[64] = {};
-  static std::mutex mu;
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return MRA_ECUDA;
-  std::lock_guard<std::mutex> lk(mu);
-  if (!addr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return MRA_ECUDA;
-    addr[dev] = p;
-  }
-  *out = addr[dev];
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return MRA_ECUDA;
+  *out = p;
   return MRA_OK;
 }
 
