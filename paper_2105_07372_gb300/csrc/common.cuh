@@ -379,7 +379,7 @@ struct SplitArgs {
   const int* shift;
   int N, Kp1, M, L, Lw;
   int nwarps, slot_bytes;           // stream kernels: active warps per CTA, bytes per ring slot
-  int off_ring, off_x, off_xs, off_tf;
+  int off_ring, off_x, off_tf;
   int NP, ncols;                    // transform: window columns padded to 16, tensor-memory columns
   int k2_off_b, k2_off_ah, k2_off_al, k2_off_lr, k2_off_tf, k2_off_wt, k2_off_ll;
   int k2_off_cs;                    // transform: the tile's c (then W) rows [128][Kp1] float2, at the end the CTA's ll sums

@@ -1011,14 +1011,14 @@ bool plan_v6(int Kp1, int Q, int L, int Lw, int nu, bool dense, int max_smem, V6
   return false;
 }
 
-// Plan of the split sweep: the stream kernels' ring (two slots per warp), x and its swapped copy and
+// Plan of the split sweep: the stream kernels' ring (two slots per warp), x and
 // the grid twiddles; the transform kernel's B operand, two A tiles, tables and reduction scratch
 // (at least 116 KB, so that one transform CTA holds a streaming multiprocessor's tensor memory).
 struct SplitPlan {
   SplitStreamFns fns;
   SplitTransFn trans;
   int KP, KA, NP, ncols, smem1, smem2, nwarps, slot_bytes;
-  int off_ring, off_x, off_xs, off_tf;
+  int off_ring, off_x, off_tf;
   int k2_off_b, k2_off_ah, k2_off_al, k2_off_lr, k2_off_tf, k2_off_wt, k2_off_ll, k2_off_cs, k2_off_td;
   int k2_off_info;
   int k2_ndp;
@@ -1043,7 +1043,6 @@ bool plan_split(int Kp1, int Q, int L, int Lw, int max_smem, SplitPlan* p) {
     int o = al16(2 * maxw * 8);
     p->off_ring = o; o += 2 * nw * p->slot_bytes;
     p->off_x = o; o += al16(M * 8);
-    p->off_xs = o; o += al16(M * 8);
     p->off_tf = o; o += al16(L * 8);
     if (o + 1024 <= max_smem) {
       p->nwarps = nw;
@@ -1618,7 +1617,7 @@ int prepare(const mra_dims* d, int Lw, int l0, double step, const float* y, cons
   x5.shift = shift;
   x5.N = d->N; x5.Kp1 = Kp1; x5.M = M; x5.L = d->L; x5.Lw = Lw;
   x5.nwarps = q5.nwarps; x5.slot_bytes = q5.slot_bytes;
-  x5.off_ring = q5.off_ring; x5.off_x = q5.off_x; x5.off_xs = q5.off_xs; x5.off_tf = q5.off_tf;
+  x5.off_ring = q5.off_ring; x5.off_x = q5.off_x; x5.off_tf = q5.off_tf;
   x5.NP = q5.NP; x5.ncols = q5.ncols;
   x5.k2_off_b = q5.k2_off_b; x5.k2_off_ah = q5.k2_off_ah; x5.k2_off_al = q5.k2_off_al; x5.k2_off_lr = q5.k2_off_lr;
   x5.k2_off_tf = q5.k2_off_tf; x5.k2_off_wt = q5.k2_off_wt; x5.k2_off_ll = q5.k2_off_ll;

@@ -51,16 +51,13 @@ __global__ void __launch_bounds__(kTcStreamThreads, 1) k_tc_corr(const SplitArgs
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
   unsigned char* ring = smem + a.off_ring;
   const float4* xs4 = reinterpret_cast<const float4*>(smem + a.off_x);
-  const float4* xw4 = reinterpret_cast<const float4*>(smem + a.off_xs);
   const float2* tfs = reinterpret_cast<const float2*>(smem + a.off_tf);
   {
     float4* x4w = reinterpret_cast<float4*>(smem + a.off_x);
-    float4* xw4w = reinterpret_cast<float4*>(smem + a.off_xs);
     const float4* xg = reinterpret_cast<const float4*>(a.x32);
     for (int i = tid; i < M / 2; i += NT) {
       const float4 v = xg[i];
       x4w[i] = v;
-      xw4w[i] = make_float4(v.y, -v.x, v.w, -v.z);
     }
     float2* tfw = reinterpret_cast<float2*>(smem + a.off_tf);
     for (int i = tid; i < L; i += NT) tfw[i] = a.tf32[i];
@@ -119,19 +116,19 @@ __global__ void __launch_bounds__(kTcStreamThreads, 1) k_tc_corr(const SplitArgs
 #pragma unroll
         for (int u = 0; u < QV; ++u) {
           const int pidx = k * row4 + j + 4 * u;
-          const float4 yv = y4[pidx], xv = xs4[pidx], xw = xw4[pidx];
+          const float4 yv = y4[pidx], xv = xs4[pidx];
           const float2 y01 = make_float2(yv.x, yv.y), y23 = make_float2(yv.z, yv.w);
           P = __ffma2_rn(y01, make_float2(xv.x, xv.y), P);
           P = __ffma2_rn(y23, make_float2(xv.z, xv.w), P);
-          Qv = __ffma2_rn(y01, make_float2(xw.x, xw.y), Qv);
-          Qv = __ffma2_rn(y23, make_float2(xw.z, xw.w), Qv);
+          Qv = __ffma2_rn(y01, make_float2(xv.y, xv.x), Qv);  // (y.re x.im, y.im x.re): Im c is their difference
+          Qv = __ffma2_rn(y23, make_float2(xv.w, xv.z), Qv);
           if (want_ysq) {
             sq = __ffma2_rn(y01, y01, sq);
             sq = __ffma2_rn(y23, y23, sq);
           }
         }
       }
-      float cr = P.x + P.y, ci = Qv.x + Qv.y;
+      float cr = P.x + P.y, ci = Qv.x - Qv.y;
       cr += __shfl_xor_sync(FULL, cr, 1);
       ci += __shfl_xor_sync(FULL, ci, 1);
       cr += __shfl_xor_sync(FULL, cr, 2);
